@@ -1,0 +1,387 @@
+"""FP64 CPU oracle of the RBSOG + RBL force evaluation (arXiv 2512.24970).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference the CUDA library is
+checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import it.  It shares no
+code with the CUDA path; the C part (``rbsog_oracle.c``) is compiled with gcc
+by :func:`build`.
+
+Sections of the paper followed here (Sec. 2.1 split and spectral form,
+Sec. 2.2 RBL and RBSOG estimators, Sec. 2.3 Langevin dynamics) are cited on
+each function.  Parity of the sampled MD trajectory statistics is unpinned
+(the paper's observables need PPPM runs); everything else is pinned by the
+tests listed in the repository's design notes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rbsog_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+KE = 14.3996454784          # eV * Angstrom / e^2
+KB = 8.617333262e-5         # eV / K
+FCONV = 9648.53321          # (eV / Angstrom) / amu -> Angstrom / ps^2
+
+INTEGRATOR_NVE_VV = 0
+INTEGRATOR_LANGEVIN_BAOAB = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, no FP contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+class _Sys(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("n_species", ctypes.c_int32), ("M", ctypes.c_int32),
+        ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p), ("charge", ctypes.c_void_p),
+        ("bmh", ctypes.c_void_p), ("w", ctypes.c_void_p),
+        ("L", ctypes.c_double * 3), ("b", ctypes.c_double), ("s", ctypes.c_double),
+        ("r_core", ctypes.c_double), ("r_shell", ctypes.c_double),
+        ("P_R", ctypes.c_int32), ("P_F", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("step", ctypes.c_int64),
+    ]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_D = ctypes.c_double
+
+
+def _declare(L):
+    sp = ctypes.POINTER(_Sys)
+    L.orc_philox.argtypes = [_I64, _P, _P, _P]
+    L.orc_draw.argtypes = [_U64, _I64, _I64, _P, _U32, _U32, _P]
+    L.orc_sog_solve.argtypes = [_D, _I32, _D, _P, _P]
+    L.orc_sog_solve.restype = ctypes.c_int
+    L.orc_sog_eval.argtypes = [_I32, _D, _D, _P, _I64, _P, _P, _P]
+    L.orc_sog_fhat.argtypes = [sp, _I64, _P, _P]
+    L.orc_pair_terms.argtypes = [sp, _I32, _I32, _I64, _P, _P, _P]
+    L.orc_fixed_point.argtypes = [sp, _P]
+    L.orc_cell_grid.argtypes = [sp, _P]
+    L.orc_floyd.argtypes = [_U64, _I64, _U32, _I32, _I32, _P]
+    L.orc_floyd.restype = _I32
+    L.orc_lists.argtypes = [sp, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_lists.restype = ctypes.c_int
+    L.orc_near.argtypes = [sp, _P, _I64, _I32, _P, _P]
+    L.orc_near.restype = ctypes.c_int
+    L.orc_sampler_S.argtypes = [sp]
+    L.orc_sampler_S.restype = _D
+    L.orc_sampler_Z.argtypes = [sp, _P]
+    L.orc_kbatch.argtypes = [sp, _P, _P]
+    L.orc_kbatch.restype = _D
+    L.orc_rho.argtypes = [sp, _I32, _P, _P]
+    L.orc_far.argtypes = [sp, _I32, _P, _P, _P, _P, _I64, _P, _P]
+    L.orc_self_energy.argtypes = [sp]
+    L.orc_self_energy.restype = _D
+    L.orc_num_threads.restype = _I32
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al. 2011)
+
+def philox(ctr: np.ndarray, key) -> np.ndarray:
+    """Raw Philox4x32-10 blocks: ctr [n,4] uint32, key (k0, k1) -> [n,4] uint32."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty_like(ctr)
+    lib().orc_philox(ctr.shape[0], _ptr(ctr), _ptr(k), _ptr(out))
+    return out
+
+
+def draw(seed: int, step: int, index: np.ndarray, stream: int, block: int) -> np.ndarray:
+    """Method draws: ctr = (index, step_lo, step_hi, stream<<24 | block), key = seed."""
+    idx = np.ascontiguousarray(index, dtype=np.uint32).reshape(-1)
+    out = np.empty((idx.size, 4), dtype=np.uint32)
+    lib().orc_draw(seed, step, idx.size, _ptr(idx), stream, block, _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# SOG split (Sec. 2.1)
+
+def sog_solve(b: float = 1.3, M: int = 64, rc: float = 12.0):
+    """(s, w[0..M]) with w_0 set for N(r_c) = 0 and s for N'(r_c) = 0."""
+    s = np.zeros(1)
+    w = np.zeros(M + 1)
+    st = lib().orc_sog_solve(b, M, rc, _ptr(s), _ptr(w))
+    if st != 0:
+        raise RuntimeError("oracle SOG solve failed: %d" % st)
+    return float(s[0]), w
+
+
+def sog_eval(b, M, s, w, r):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    F = np.empty_like(r)
+    dF = np.empty_like(r)
+    lib().orc_sog_eval(M, b, s, _ptr(np.ascontiguousarray(w, dtype=np.float64)), r.size,
+                       _ptr(r), _ptr(F), _ptr(dF))
+    return F, dF
+
+
+# --------------------------------------------------------------------------
+
+class System:
+    """A BMH system with its RBSOG/RBL parameters, held as numpy arrays."""
+
+    def __init__(self, pos, species, charge, mass, bmh, box, *, b=1.3, M=64, s=None, w=None,
+                 r_core=6.0, r_shell=12.0, P_R=20, P_F=200, seed=1, step=0):
+        self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self.species = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
+        self.charge = np.ascontiguousarray(charge, dtype=np.float64)
+        self.mass = np.ascontiguousarray(mass, dtype=np.float64)
+        ns = self.charge.size
+        self.bmh = np.ascontiguousarray(bmh, dtype=np.float64).reshape(ns, ns, 5)
+        self.box = np.asarray(box, dtype=np.float64).reshape(3)
+        self.b, self.M = float(b), int(M)
+        if s is None or w is None:
+            s, w = sog_solve(self.b, self.M, float(r_shell))
+        self.s = float(s)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        self.r_core, self.r_shell = float(r_core), float(r_shell)
+        self.P_R, self.P_F = int(P_R), int(P_F)
+        self.seed, self.step = int(seed), int(step)
+
+    @property
+    def n(self):
+        return self.pos.shape[0]
+
+    @property
+    def volume(self):
+        return float(np.prod(self.box))
+
+    def q(self):
+        return self.charge[self.species]
+
+    def _c(self):
+        st = _Sys()
+        st.n = self.n
+        st.n_species = self.charge.size
+        st.M = self.M
+        st.pos = self.pos.ctypes.data
+        st.species = self.species.ctypes.data
+        st.charge = self.charge.ctypes.data
+        st.bmh = self.bmh.ctypes.data
+        st.w = self.w.ctypes.data
+        for a in range(3):
+            st.L[a] = self.box[a]
+        st.b, st.s = self.b, self.s
+        st.r_core, st.r_shell = self.r_core, self.r_shell
+        st.P_R, st.P_F = self.P_R, self.P_F
+        st.seed, st.step = self.seed, self.step
+        return st
+
+    # ---- geometry -------------------------------------------------------
+    def fixed_point(self):
+        u = np.empty((self.n, 3), dtype=np.uint32)
+        st = self._c()
+        lib().orc_fixed_point(ctypes.byref(st), _ptr(u))
+        return u
+
+    def cell_grid(self):
+        nc = np.zeros(3, dtype=np.int32)
+        st = self._c()
+        lib().orc_cell_grid(ctypes.byref(st), _ptr(nc))
+        return nc
+
+    def lists(self, sel=None, cap_core=256, cap_shell=1024, batch=True):
+        """Core and shell lists (canonical order) and the shell batch of ``sel``."""
+        sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+        k = sel.size
+        core = np.full((k, cap_core), -1, dtype=np.int32)
+        ncore = np.zeros(k, dtype=np.int32)
+        shell = np.full((k, cap_shell), -1, dtype=np.int32)
+        nshell = np.zeros(k, dtype=np.int32)
+        PR = max(self.P_R, 1)
+        bt = np.full((k, PR), -1, dtype=np.int32) if batch else None
+        nb = np.zeros(k, dtype=np.int32) if batch else None
+        wt = np.zeros(k, dtype=np.float64) if batch else None
+        st = self._c()
+        rc = lib().orc_lists(ctypes.byref(st), _ptr(sel), k, cap_core, cap_shell, _ptr(core),
+                             _ptr(ncore), _ptr(shell), _ptr(nshell), _ptr(bt), _ptr(nb), _ptr(wt))
+        if rc != 0:
+            raise RuntimeError("oracle list capacity exceeded")
+        out = dict(core=core, ncore=ncore, shell=shell, nshell=nshell)
+        if batch:
+            out.update(batch=bt, nbatch=nb, weight=wt)
+        return out
+
+    # ---- near field (Sec. 2.2) -------------------------------------------
+    def near(self, sel=None, all_shell=False, energy=False):
+        """Uncorrected near-field force F_core + F*_shell of ``sel`` (and 1/2 pair energy)."""
+        sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+        F = np.zeros((sel.size, 3))
+        E = np.zeros(sel.size) if energy else None
+        st = self._c()
+        rc = lib().orc_near(ctypes.byref(st), _ptr(sel), sel.size, int(bool(all_shell)), _ptr(F), _ptr(E))
+        if rc != 0:
+            raise RuntimeError("oracle near-field capacity exceeded")
+        return (F, E) if energy else F
+
+    def pair_terms(self, si, sj, r2):
+        r2 = np.ascontiguousarray(r2, dtype=np.float64).reshape(-1)
+        phi = np.empty_like(r2)
+        e = np.empty_like(r2)
+        st = self._c()
+        lib().orc_pair_terms(ctypes.byref(st), si, sj, r2.size, _ptr(r2), _ptr(phi), _ptr(e))
+        return phi, e
+
+    # ---- far field (Sec. 2.1, 2.2) -----------------------------------------
+    def fhat(self, k2):
+        k2 = np.ascontiguousarray(k2, dtype=np.float64).reshape(-1)
+        out = np.empty_like(k2)
+        st = self._c()
+        lib().orc_sog_fhat(ctypes.byref(st), k2.size, _ptr(k2), _ptr(out))
+        return out
+
+    def sampler_S(self):
+        st = self._c()
+        return float(lib().orc_sampler_S(ctypes.byref(st)))
+
+    def sampler_Z(self):
+        Z = np.zeros((self.M + 1, 3))
+        st = self._c()
+        lib().orc_sampler_Z(ctypes.byref(st), _ptr(Z))
+        return Z
+
+    def kbatch(self):
+        """(m [P_F,3] int32, c [P_F] with c_p = S/(P_F |k_p|^2), S)."""
+        m = np.zeros((self.P_F, 3), dtype=np.int32)
+        c = np.zeros(self.P_F)
+        st = self._c()
+        S = lib().orc_kbatch(ctypes.byref(st), _ptr(m), _ptr(c))
+        return m, c, float(S)
+
+    def kvec(self, m):
+        return 2.0 * np.pi * np.asarray(m, dtype=np.float64) / self.box
+
+    def enumerated_modes(self, m_max):
+        """All m != 0 with |m_d| <= m_max and weight c = Fhat(k) (Eq. (Long))."""
+        r = np.arange(-m_max, m_max + 1)
+        mm = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+        mm = mm[np.any(mm != 0, axis=1)].astype(np.int32)
+        k2 = (self.kvec(mm) ** 2).sum(1)
+        return np.ascontiguousarray(mm), self.fhat(k2)
+
+    def rho(self, m):
+        m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+        out = np.zeros((m.shape[0], 2))
+        st = self._c()
+        lib().orc_rho(ctypes.byref(st), m.shape[0], _ptr(m), _ptr(out))
+        return out
+
+    def far(self, m, c, rho=None, sel=None):
+        """Far-field force of ``sel`` and U_F* for modes m with weights c."""
+        m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        if rho is None:
+            rho = self.rho(m)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+        F = np.zeros((sel.size, 3))
+        U = np.zeros(1)
+        st = self._c()
+        lib().orc_far(ctypes.byref(st), m.shape[0], _ptr(m), _ptr(c), _ptr(rho), _ptr(sel), sel.size,
+                      _ptr(F), _ptr(U))
+        return F, float(U[0])
+
+    def self_energy(self):
+        st = self._c()
+        return float(lib().orc_self_energy(ctypes.byref(st)))
+
+    # ---- full force evaluation ----------------------------------------------
+    def forces(self, sel=None, energy=False, kmodes=None, all_shell=False):
+        """IRBSOG force F* = F_core + F*_shell - F^corr + F*_F (Sec. 2.2).
+
+        ``kmodes=(m, c)`` replaces the sampled k-batch (enumeration mode).
+        Returns a dict with total F (of ``sel``), near (uncorrected), far, Fcorr
+        and, if ``energy``, [U_N, U_F*, U_self, U_total].
+        """
+        allsel = np.arange(self.n, dtype=np.int64)
+        Fn_all, En = self.near(allsel, all_shell=all_shell, energy=True)
+        Fcorr = Fn_all.mean(axis=0)
+        if kmodes is None:
+            m, c, S = self.kbatch()
+        else:
+            m, c = kmodes
+            S = None
+        rho = self.rho(m)
+        sel_ = allsel if sel is None else np.asarray(sel, dtype=np.int64)
+        Ff, Uf = self.far(m, c, rho, sel_)
+        Fn = Fn_all[sel_]
+        out = dict(F=Fn - Fcorr + Ff, near=Fn, far=Ff, Fcorr=Fcorr, m=m, c=c, S=S, rho=rho)
+        if energy:
+            UN = float(En.sum())
+            Us = self.self_energy()
+            out["energy"] = np.array([UN, Uf, Us, UN + Uf - Us])
+        return out
+
+    # ---- integrators (Sec. 2.3) ----------------------------------------------
+    def gaussian_noise(self, step):
+        """Langevin noise xi[n,3]: Box-Muller on Philox stream 2, block 0."""
+        w = draw(self.seed, step, np.arange(self.n, dtype=np.uint32), 2, 0).astype(np.float64)
+        u = (w + 0.5) * 2.0 ** -32
+        r1 = np.sqrt(-2.0 * np.log(u[:, 0]))
+        r2 = np.sqrt(-2.0 * np.log(u[:, 2]))
+        return np.stack([r1 * np.cos(2.0 * np.pi * u[:, 1]), r1 * np.sin(2.0 * np.pi * u[:, 1]),
+                         r2 * np.cos(2.0 * np.pi * u[:, 3])], axis=1)
+
+    def run(self, vel, nsteps, dt, integrator=INTEGRATOR_LANGEVIN_BAOAB, T=1200.0, gamma=1.0,
+            F=None):
+        """Advance (pos, vel) by ``nsteps``; returns (vel, F).  Forces at step s use
+        RNG step index s; the Langevin O-step of the step s -> s+1 uses index s+1.
+        ``gamma`` is the collision rate gamma/m in 1/ps (same for all species)."""
+        vel = np.array(vel, dtype=np.float64).reshape(-1, 3)
+        minv = (FCONV / self.mass[self.species])[:, None]
+        if F is None:
+            F = self.forces()["F"]
+        c1 = np.exp(-gamma * dt)
+        sig = np.sqrt((1.0 - c1 * c1) * KB * T * FCONV / self.mass[self.species])[:, None]
+        for _ in range(nsteps):
+            nxt = self.step + 1
+            vel = vel + 0.5 * dt * F * minv
+            if integrator == INTEGRATOR_LANGEVIN_BAOAB:
+                self.pos = self.pos + 0.5 * dt * vel
+                vel = c1 * vel + sig * self.gaussian_noise(nxt)
+                self.pos = self.pos + 0.5 * dt * vel
+            else:
+                self.pos = self.pos + dt * vel
+            self.step = nxt
+            F = self.forces()["F"]
+            vel = vel + 0.5 * dt * F * minv
+        return vel, F

@@ -1,0 +1,258 @@
+"""Physics pins of the oracle: Madelung constant of rock salt, brute-force
+Ewald forces and energy, energy/force consistency, momentum invariants, the
+RBL whole-shell identity and the unbiasedness (1/sqrt(n) convergence) of the
+RBL and RBSOG estimators (Sec. 2.2, Theorem of Sec. 2.3)."""
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erfc
+
+from paper_2512_24970_gb300 import workloads as W
+
+KE = 14.3996454784
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+def coulomb_only(w):
+    bmh = w.bmh.copy()
+    bmh[..., 0] = 0.0   # A
+    bmh[..., 3] = 0.0   # C
+    bmh[..., 4] = 0.0   # D
+    return bmh
+
+
+def make(orc, w, bmh=None, **kw):
+    return orc.System(w.pos, w.species, w.charge, w.mass, w.bmh if bmh is None else bmh, w.box, **kw)
+
+
+def deterministic(S, m_max=14, sel=None, energy=True):
+    """Full r_shell-cutoff near field + all k with |m_d| <= m_max (Eq. (Long))."""
+    return S.forces(sel=sel, energy=energy, kmodes=S.enumerated_modes(m_max), all_shell=True)
+
+
+def test_madelung_rock_salt(orc):
+    """Perfect rock salt: U_coul = -N M k_e / (2 d), d = a/2, M = 1.747565;
+    every force vanishes by symmetry."""
+    g = _golden("madelung_rocksalt.txt")
+    w = W.rock_salt((4, 4, 4), jitter=0.0)
+    S = make(orc, w, coulomb_only(w))
+    out = deterministic(S)
+    U = out["energy"][3]
+    d = W.A_CELL / 2
+    ref = -w.n * g["M_rocksalt"] * KE / (2 * d)
+    assert abs(U - ref) <= 2e-6 * abs(ref), (U, ref)
+    # positions enter through 32-bit fixed point (quantum L/2^32 = 6e-9 A), so
+    # the symmetric zero is met to the force constant times that quantum
+    assert np.abs(out["F"]).max() < 1e-7
+
+
+def ewald(pos, q, box, alpha=0.32, rcut=12.0, mmax=14):
+    """Textbook Ewald sum (tinfoil) of point charges, minimum image real space."""
+    n = pos.shape[0]
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= box * np.round(d / box)
+    r = np.sqrt((d**2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    qq = q[:, None] * q[None, :]
+    mask = r < rcut
+    er = np.where(mask, erfc(alpha * r) / r, 0.0)
+    E_real = 0.5 * (qq * er).sum()
+    fr = np.where(mask, (erfc(alpha * r) / r**2 + 2 * alpha / np.sqrt(np.pi) * np.exp(-(alpha * r) ** 2) / r) / r, 0.0)
+    F_real = ((qq * fr)[:, :, None] * d).sum(1)
+    rng = np.arange(-mmax, mmax + 1)
+    mm = np.stack(np.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3)
+    mm = mm[np.any(mm != 0, 1)]
+    k = 2 * np.pi * mm / box
+    k2 = (k**2).sum(1)
+    V = np.prod(box)
+    a = 4 * np.pi / k2 * np.exp(-k2 / (4 * alpha**2))
+    E_rec = 0.0
+    F_rec = np.zeros_like(pos)
+    for c in range(0, k.shape[0], 2000):
+        kc = k[c:c + 2000]
+        ph = pos @ kc.T
+        rho = (q[:, None] * np.exp(1j * ph)).sum(0)
+        E_rec += (a[c:c + 2000] * np.abs(rho) ** 2).sum() / (2 * V)
+        im = np.imag(np.exp(-1j * ph) * rho[None, :])
+        F_rec += -(q[:, None] / V) * ((a[c:c + 2000] * im) @ kc)
+    E_self = -alpha / np.sqrt(np.pi) * (q**2).sum()
+    return KE * (E_real + E_rec + E_self), KE * (F_real + F_rec)
+
+
+def test_sog_matches_ewald(orc):
+    """Deterministic SOG Coulomb forces and energy vs brute-force Ewald, N=512
+    jittered NaCl: RMS relative force error and energy error <= 1e-5."""
+    w = W.rock_salt((4, 4, 4), seed=7)
+    S = make(orc, w, coulomb_only(w))
+    out = deterministic(S)
+    E, F = ewald(w.pos, w.charge[w.species], w.box)
+    err = np.sqrt(((out["F"] - F) ** 2).sum() / (F**2).sum())
+    assert err < 1e-5, err
+    assert abs(out["energy"][3] - E) < 1e-5 * abs(E)
+
+
+def test_force_is_minus_energy_gradient(orc):
+    """Central differences of the deterministic BMH + SOG energy reproduce the
+    force of Eq. (Fshort) + Eq. (Long) (catches sign and factor errors)."""
+    w = W.rock_salt((4, 4, 4), seed=8)
+    S = make(orc, w)
+    base = deterministic(S, m_max=14)
+    h = 2e-4
+    checked = 0
+    for i in range(0, w.n, 11):
+        # skip atoms with a neighbour within 2h of the unshifted BMH cutoff
+        d = w.pos - w.pos[i]
+        d -= w.box * np.round(d / w.box)
+        r = np.sqrt((d**2).sum(1))
+        if np.any(np.abs(r - S.r_shell) < 2e-3):
+            continue
+        for a in range(3):
+            Up = []
+            for sgn in (1, -1):
+                S.pos = w.pos.copy()
+                S.pos[i, a] += sgn * h
+                Up.append(deterministic(S, m_max=14, sel=[i])["energy"][3])
+            fd = -(Up[0] - Up[1]) / (2 * h)
+            assert abs(fd - base["F"][i, a]) < 2e-5 * max(1.0, abs(base["F"][i, a])), (i, a, fd, base["F"][i, a])
+        checked += 1
+        if checked == 4:
+            break
+    assert checked == 4
+    S.pos = w.pos.copy()
+
+
+def test_momentum_invariants(orc):
+    """sum_i F*_F,i = 0 for any k-batch; sum_i F*_N,i = 0 after F^corr."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    S = make(orc, w, P_F=100, P_R=20, seed=3)
+    out = S.forces()
+    scale = np.abs(out["F"]).max()
+    assert np.abs(out["far"].sum(0)).max() < 1e-11 * scale * w.n
+    assert np.abs((out["near"] - out["Fcorr"]).sum(0)).max() < 1e-11 * scale * w.n
+    assert np.abs(out["F"].sum(0)).max() < 1e-11 * scale * w.n
+
+
+def test_whole_shell_batch_is_full_cutoff_force(orc):
+    """P_R >= N_shell takes the whole shell with weight 1: the RBL near field
+    equals the deterministic r_shell-cutoff force."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    S = make(orc, w, P_R=4000, seed=2)
+    F1 = S.near()
+    F2 = S.near(all_shell=True)
+    np.testing.assert_array_equal(F1, F2)
+    L = S.lists(np.arange(0, w.n, 50), cap_shell=1024)
+    assert np.all(L["weight"] == 1.0)
+    np.testing.assert_array_equal(L["nbatch"], L["nshell"])
+
+
+def test_lists_against_float64_distances(orc):
+    """Core/shell membership agrees with FP64 minimum-image distances except
+    within FP32 rounding of the thresholds; lists are in canonical order."""
+    w = W.rock_salt((5, 5, 5), seed=4)
+    S = make(orc, w)
+    sel = np.arange(0, w.n, 7)
+    L = S.lists(sel)
+    u = S.fixed_point()
+    nc = S.cell_grid()
+    cell = (u.astype(np.uint64) * nc.astype(np.uint64)) >> np.uint64(32)
+    lin = cell[:, 0] + nc[0] * (cell[:, 1] + nc[1] * cell[:, 2])
+    for q, i in enumerate(sel):
+        d = w.pos - w.pos[i]
+        d -= w.box * np.round(d / w.box)
+        r = np.sqrt((d**2).sum(1))
+        r[i] = np.inf
+        core = set(L["core"][q, :L["ncore"][q]].tolist())
+        shell = set(L["shell"][q, :L["nshell"][q]].tolist())
+        tol = 1e-4
+        assert core == set(np.where(r < S.r_core - tol)[0]) | (core & set(np.where(np.abs(r - S.r_core) <= tol)[0]))
+        sure_shell = set(np.where((r > S.r_core + tol) & (r < S.r_shell - tol))[0])
+        assert sure_shell <= shell
+        assert shell <= set(np.where((r > S.r_core - tol) & (r < S.r_shell + tol))[0])
+        s_list = L["shell"][q, :L["nshell"][q]]
+        key = lin[s_list].astype(np.int64) * w.n + s_list
+        assert np.all(np.diff(key) > 0)
+        b = L["batch"][q, :L["nbatch"][q]]
+        assert set(b.tolist()) <= shell and len(set(b.tolist())) == len(b)
+
+
+def _zstats(samples, ref):
+    mean = samples.mean(0)
+    sd = samples.std(0, ddof=1) / np.sqrt(samples.shape[0])
+    return (mean - ref) / np.maximum(sd, 1e-300)
+
+
+def test_rbl_estimator_unbiased(orc):
+    """E[F_core + F*_shell] = full r_shell-cutoff force (Sec. 2.2); the error
+    of the n-sample mean decays as 1/sqrt(n)."""
+    w = W.rock_salt((4, 4, 4), seed=5)
+    S = make(orc, w, P_R=10)
+    sel = np.arange(0, w.n, 16)
+    ref = S.near(sel, all_shell=True)
+    draws = []
+    for step in range(400):
+        S.step = step
+        draws.append(S.near(sel))
+    X = np.array(draws)
+    z = _zstats(X, ref)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    e1 = np.sqrt(((X[:25].mean(0) - ref) ** 2).mean())
+    e2 = np.sqrt(((X.mean(0) - ref) ** 2).mean())
+    assert 1.5 < e1 / e2 < 7.0, (e1, e2)       # sqrt(16) = 4 expected
+
+
+def test_rbsog_estimator_unbiased(orc):
+    """E[F*_F] = F_F of Eq. (Long) (importance sampling of Eq. (Pk)); the error
+    of the n-sample mean decays as 1/sqrt(n) (Lemma of Sec. 2.3)."""
+    w = W.rock_salt((4, 4, 4), seed=6)
+    S = make(orc, w, P_F=50)
+    sel = np.arange(0, w.n, 16)
+    m, c = S.enumerated_modes(14)
+    ref, _ = S.far(m, c, sel=sel)
+    draws = []
+    for step in range(400):
+        S.step = step
+        mk, ck, _ = S.kbatch()
+        draws.append(S.far(mk, ck, sel=sel)[0])
+    X = np.array(draws)
+    z = _zstats(X, ref)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    e1 = np.sqrt(((X[:25].mean(0) - ref) ** 2).mean())
+    e2 = np.sqrt(((X.mean(0) - ref) ** 2).mean())
+    assert 1.5 < e1 / e2 < 7.0, (e1, e2)
+
+
+def test_nve_energy_conservation(orc):
+    """Velocity Verlet with the deterministic force conserves the total energy
+    to O(dt^2) over a short NVE run (1 fs steps)."""
+    w = W.rock_salt((4, 4, 4), seed=9)
+    S = make(orc, w)
+    kin = lambda v: 0.5 * (w.mass[w.species][:, None] * v**2).sum() / W.FCONV
+    v = W.maxwell_boltzmann(w, 1200.0)
+    km = S.enumerated_modes(10)
+
+    def etot(S, v):
+        return S.forces(energy=True, kmodes=km, all_shell=True)["energy"][3] + kin(v)
+
+    E0 = etot(S, v)
+    F = S.forces(kmodes=km, all_shell=True)["F"]
+    minv = (W.FCONV / w.mass[w.species])[:, None]
+    dt = 0.001
+    for _ in range(20):
+        v = v + 0.5 * dt * F * minv
+        S.pos = S.pos + dt * v
+        F = S.forces(kmodes=km, all_shell=True)["F"]
+        v = v + 0.5 * dt * F * minv
+    E1 = etot(S, v)
+    assert abs(E1 - E0) < 2e-4 * kin(v), (E0, E1, kin(v))

@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark: atom-steps/s of the RBSOG + RBL MD step (force evaluation of
+stages a-d + the BAOAB integrator of stage e) on molten NaCl, N = 64,000
+(20^3 rock-salt cells, L = 126 A, P_R = 20, P_F = 500, r_core = 6 A,
+r_shell = 12 A, Langevin 1200 K, dt = 1 fs), mixed precision.
+
+One JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead (the reference arm).
+
+Timing: W warm-up steps, then K steps, each preceded by an L2 flush (a
+512 MiB memset, outside the timed interval) and timed with CUDA events on the
+stream the library runs on; per-stage times come from the event nodes the
+library records inside its step graph.  Multi-GPU (torchrun): every rank runs
+an independent replica (weak scaling, no collective on the data path); the
+time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+SFU_LANES_PER_SM = 16      # MUFU lanes per SM per clock (sin, cos, ex2, rsq ...)
+ISSUE_PER_SM = 4           # warp instructions per SM per clock (4 schedulers)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="nacl_64k")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--P_F", type=int, default=None)
+    ap.add_argument("--P_R", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(w, cfg, P_F, P_R, budget_s=20.0, n_sample=None):
+    """Oracle (FP64 CPU) atom-steps/s on a bounded sample of the workload:
+    structure factor over a chunk of atoms for all P_F modes (scaled to N),
+    near + far field of n_sample atoms.  Returns (value, seconds, sample text)."""
+    import oracle
+    S = oracle.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=P_R, P_F=P_F, seed=cfg.seed)
+    N = w.n
+    t0 = time.perf_counter()
+    m, c, _ = S.kbatch()
+    chunk = min(N, 16000)
+    sub = oracle.System(w.pos[:chunk], w.species[:chunk], w.charge, w.mass, w.bmh, w.box, s=S.s, w=S.w,
+                        P_R=P_R, P_F=P_F, seed=cfg.seed)
+    t1 = time.perf_counter()
+    rho_sub = sub.rho(m)
+    t_rho = (time.perf_counter() - t1) * N / chunk
+    rho = S.rho(m) if chunk == N else rho_sub * (N / chunk)  # magnitude only matters for timing
+    if n_sample is None:
+        n_sample = 256
+    sel = np.linspace(0, N - 1, n_sample).astype(np.int64)
+    t2 = time.perf_counter()
+    S.near(sel)
+    S.far(m, c, rho, sel)
+    t_atoms = time.perf_counter() - t2
+    per_atom = t_atoms / n_sample
+    T = t_rho + N * per_atom
+    wall = time.perf_counter() - t0
+    sample = ("one force evaluation of %s: structure factor of %d of %d atoms x %d modes (scaled to N), "
+              "near + far field of %d atoms (scaled to N)" % (cfg.key, chunk, N, P_F, n_sample))
+    return N / T, wall, sample
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2512_24970_gb300 import workloads as W
+    w, cfg = W.make(args.config)
+    P_F = args.P_F or cfg.P_F
+    P_R = args.P_R or cfg.P_R
+    oracle.build()
+    nthreads = oracle.num_threads()
+    total = max(1, args.steps + args.warmup)
+    n_sample = int(np.clip(2000 // total, 16, 256))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, wall, sample = oracle_sample(w, cfg, P_F, P_R, n_sample=n_sample)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "atom-steps/s of RBSOG+RBL force step (FP64 CPU oracle)",
+        "value": value, "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * w.n / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.description, "P_F": P_F, "P_R": P_R},
+        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2512_24970_gb300 import build, rbsog, workloads as W
+    build.build()
+    w, cfg = W.make(args.config)
+    P_F = args.P_F or cfg.P_F
+    P_R = args.P_R or cfg.P_R
+    prec = rbsog.MIXED if args.precision == "mixed" else rbsog.FP64
+    prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=cfg.seed + 1000 * rank, precision=prec,
+                             integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
+                             T=cfg.T, dt=0.001, gamma=1.0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rbsog.Context(local, stream.cuda_stream)
+    ctx.set_workload(w, prm)
+    ctx.set_profiling(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    K, Wm = args.steps, args.warmup
+    with torch.cuda.stream(stream):
+        for _ in range(Wm):
+            flush.zero_()
+            ctx.step(1)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        clocks = Clocks(local)
+        clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        stage = np.zeros(rbsog.NSTAGE)
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx.step(1)
+            ev[k][1].record(stream)
+            stage += ctx.stage_times()          # waits for this step's last event
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        clk = clocks.stop()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    ctx.sync()
+    t_total = float(ms.sum())
+    if ws > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    stage_ms = stage / K
+    value = ws * w.n * K / (t_total / 1000.0)
+    # ---- roofline of the dominant kernel -------------------------------------
+    pk, pk_kind = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    names = rbsog.STAGES
+    dom = int(np.argmax(stage_ms))
+    N, P = w.n, P_F
+    if names[dom] in ("rho", "force"):
+        ops = 2.0 * N * P            # one MUFU sin + one MUFU cos per (atom, k)
+        achieved = ops / (stage_ms[dom] * 1e-3) / 1e9
+        peak = SFU_LANES_PER_SM * nsm * f_max / 1e9
+        roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": achieved, "peak": peak,
+                "unit": "Gop/s (SFU sin/cos lane-ops)", "frac": achieved / peak, "traffic": None,
+                "peak_source": "16 SFU lanes/SM/clk x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
+    else:
+        roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+    # ---- end to end through the public API (host buffers) --------------------
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        frc_h = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        pos_h[:] = w.pos
+        ctx.set_profiling(False)
+        ctx2 = ctx
+        Ke = args.e2e_steps
+        with torch.cuda.stream(stream):
+            for k in range(3):
+                ctx2.set_state(pos_h, None, k)
+                ctx2.compute_forces(frc_h)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(Ke):
+                ctx2.set_state(pos_h, None, k)     # H2D positions (pinned)
+                ctx2.compute_forces(frc_h)         # force evaluation, D2H forces (pinned)
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
+        e2e = {"value": w.n * Ke / te, "unit": "atom-steps/s", "h2d_bytes_per_step": 24 * w.n,
+               "d2h_bytes_per_step": 24 * w.n,
+               "what": "rbsog_set_state(host positions) + rbsog_compute_forces(host forces) per step"}
+    # ---- CPU baseline (oracle) ---------------------------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, wall, sample = oracle_sample(w, cfg, P_F, P_R, n_sample=512)
+        cpu = {"value": v, "unit": "atom-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": sample, "wall_s": wall}
+    if rank == 0:
+        line = {
+            "metric": "atom-steps/s of RBSOG+RBL force step at <=1e-5 RMS rel. force err, mixed vs FP64",
+            "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
+            "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
+                       "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
+            "roofline": roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
+            "gpu_launches": 8 * K, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * rbsog.h -- C ABI of the GB300 (sm_103a) RBSOG + RBL force evaluation and MD
+ * step for Born-Mayer-Huggins (BMH) ionic systems.
+ *
+ * Method: arXiv 2512.24970, Sec. 2 ("Method").  The Coulomb kernel is split by
+ * the sum-of-Gaussians u-series (Sec. 2.1, Eqs. (1r), (far), (short), C^1 cutoff
+ * at r_c = r_shell); the short-range residual plus the BMH repulsion and
+ * dispersion (Eq. (BMH), Eq. (Fshort)) are summed over the random batch list
+ * (Sec. 2.2: exact core r < r_core, P_R sampled shell neighbours weighted
+ * N_shell/P_R, momentum correction F^corr); the long-range part is the RBSOG
+ * estimator (Eq. (long-rangeforce)) over P_F k-vectors drawn from
+ * P(k) = k^2 Fhat(k)/S (Eq. (Pk)) with structure factors rho(k) (Sec. 2.1).
+ * The step integrates the underdamped Langevin equation of Sec. 2.3 (BAOAB)
+ * or NVE velocity Verlet.
+ *
+ * Units: metal -- Angstrom, eV, ps, amu, elementary charge.  Coulomb terms
+ * carry k_e = 14.3996454784 eV*Angstrom.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success or a negative RBSOG_E_* code; rbsog_last_error()
+ *     gives a one-line message.  No call traps or aborts.
+ *   - Pointer arguments are host or device memory as ptr_kind says
+ *     (RBSOG_PTR_HOST / RBSOG_PTR_DEVICE, device = the context's device).
+ *   - The caller owns every buffer it passes; the library copies inputs and
+ *     keeps no caller pointer after a call returns.
+ *   - Atom order at the ABI is the caller's order.  Per-atom arrays are AoS
+ *     [n][3] FP64 unless stated.
+ *   - Work runs on a library stream ordered after, and before, the stream
+ *     given to rbsog_create (events both ways); host-pointer outputs are
+ *     complete when the call returns, device-pointer outputs are ordered on
+ *     the caller's stream.
+ *   - Errors raised inside kernels (capacity overflow) are latched in a device
+ *     error word and reported by rbsog_sync() or the next synchronising call.
+ *   - Only the device given to rbsog_create is used; there is no CPU path.
+ */
+#ifndef RBSOG_H
+#define RBSOG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define RBSOG_OK 0
+#define RBSOG_E_INVAL (-1)          /* bad argument or state */
+#define RBSOG_E_NONNEUTRAL (-2)     /* |sum of charges| > 1e-10 (Sec. 2.1 assumes neutrality) */
+#define RBSOG_E_BOX_TOO_SMALL (-3)  /* min L_d < 2 r_shell (minimum image) */
+#define RBSOG_E_CAP_OVERFLOW (-4)   /* a fixed capacity (core list, per-cell shell count) overflowed */
+#define RBSOG_E_CUDA (-5)           /* CUDA runtime error */
+#define RBSOG_E_TIMEOUT (-6)        /* bounded device wait expired */
+#define RBSOG_E_NO_SOG_ROOT (-7)    /* no s with N'(r_c) = 0 in [r_c/6, r_c/2] */
+#define RBSOG_E_NO_SYSTEM (-8)      /* call needs rbsog_set_system first */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define RBSOG_FP64 0   /* analytic FP64 pair terms (M+1 Gaussians), FP64 sincospi and sums */
+#define RBSOG_MIXED 1  /* FP32 pair math (tabulated SOG residual), exact integer phases,
+                          FP32 MUFU trig, FP64 structure-factor / energy / position sums */
+
+#define RBSOG_NVE_VV 0          /* velocity Verlet */
+#define RBSOG_LANGEVIN_BAOAB 1  /* BAOAB splitting of the Langevin SDE of Sec. 2.3 */
+
+#define RBSOG_PTR_HOST 0
+#define RBSOG_PTR_DEVICE 1
+
+/* Capacities of the device path (exceeding one sets RBSOG_E_CAP_OVERFLOW). */
+#define RBSOG_MAX_SPECIES 8
+#define RBSOG_MAX_PR 64        /* shell batch size P_R */
+#define RBSOG_MAX_CORE 96      /* core neighbours per atom */
+#define RBSOG_MAX_CELL_SHELL 255 /* shell neighbours of one atom inside one cell */
+#define RBSOG_MAX_M 128        /* Gaussians m = 0..M */
+
+typedef struct rbsog_ctx rbsog_ctx; /* opaque, library-owned */
+
+/* Method parameters (Sec. 2.1-2.3).  r_shell is both the RBL shell radius and
+ * the SOG cutoff r_c; BMH terms are truncated (unshifted) at r_shell. */
+typedef struct {
+  double b;        /* SOG base b > 1 (Eq. (1-r)) */
+  int32_t M;       /* Gaussians m = 0..M of Eq. (far) */
+  double s;        /* SOG bandwidth; s <= 0 or w0 <= 0: solve (s, w0) for C^1 at r_shell */
+  double w0;       /* modified narrowest weight (value continuity at r_c) */
+  double r_core;   /* RBL core radius (Sec. 2.2) */
+  double r_shell;  /* RBL shell radius = SOG cutoff */
+  int32_t P_R;     /* shell batch size, 1..RBSOG_MAX_PR */
+  int32_t P_F;     /* Fourier batch size >= 1 */
+  uint64_t seed;   /* key of every Philox4x32-10 draw */
+  int32_t precision;   /* RBSOG_FP64 | RBSOG_MIXED */
+  int32_t integrator;  /* RBSOG_NVE_VV | RBSOG_LANGEVIN_BAOAB */
+  double dt;       /* time step [ps] */
+  double T;        /* Langevin temperature [K] */
+  double gamma;    /* Langevin collision rate gamma/m [1/ps], same for all species */
+} rbsog_params;
+
+/* Create a context on CUDA device `cuda_device`.  `cuda_stream` is the
+ * caller's cudaStream_t: if non-NULL the library's kernels and its captured
+ * step graph run on it directly; if NULL the library creates its own
+ * non-blocking stream and orders it after, and before, the legacy default
+ * stream with events.  Errors: RBSOG_E_INVAL, RBSOG_E_CUDA. */
+int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream);
+
+/* Destroy a context and free its device memory (NULL is ignored). */
+void rbsog_destroy(rbsog_ctx *ctx);
+
+/* Define the system (Sec. 2.1: N charges in a cuboid periodic box, neutral).
+ *   n        atoms, >= 2
+ *   pos      [n][3] FP64 positions (any image; wrapped internally)
+ *   species  [n] int32 in [0, n_species)
+ *   charge   [n_species] FP64 charges [e]; sum over atoms must vanish
+ *   mass     [n_species] FP64 masses [amu]
+ *   bmh      [n_species][n_species][5] FP64 = (A [eV], sigma [A], rho [A],
+ *            C [eV A^6], D [eV A^8]) of Eq. (BMH); must be symmetric
+ *   box      [3] FP64 box lengths, each >= 2 r_shell
+ *   params   method parameters (host pointer always)
+ * Resets velocities to zero and the step counter to 0; forces are evaluated
+ * on the first compute/step.  All arrays are copied.
+ * Errors: RBSOG_E_INVAL, RBSOG_E_NONNEUTRAL, RBSOG_E_BOX_TOO_SMALL,
+ * RBSOG_E_NO_SOG_ROOT, RBSOG_E_CUDA. */
+int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t *species,
+                     int32_t n_species, const double *charge, const double *mass,
+                     const double *bmh, const double box[3], const rbsog_params *params,
+                     int ptr_kind);
+
+/* Set velocities [n][3] FP64 [A/ps]. */
+int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind);
+
+/* One IRBSOG force evaluation at the current state and step counter s
+ * (Sec. 2.2: F* = F_core + F*_shell - F^corr + F*_F; shell batch and k-batch
+ * drawn with RNG step index s).  Outputs (each may be NULL):
+ *   forces [n][3] FP64 [eV/A]
+ *   energy [4] FP64 [eV] = (U_N, U_F*, U_F^self, U_N + U_F* - U_F^self), the
+ *          sampled estimators of Eqs. (short2), (UF): U_N = 1/2 sum_i
+ *          (sum_core e_ij + N_shell/P_R sum_B e_ij), U_F* = k_e S/(2 V P_F)
+ *          sum_p |rho_p|^2/|k_p|^2, U_self = k_e/2 sum_i q_i^2 sum_m w_m
+ *   virial reserved, must be NULL.
+ * Synchronous for host outputs.  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL,
+ * RBSOG_E_CAP_OVERFLOW, RBSOG_E_CUDA. */
+int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double *virial,
+                         int ptr_kind);
+
+/* Advance nsteps MD steps (asynchronous on the caller's stream).  Step
+ * s -> s+1: half kick, drift (BAOAB: half drift, Ornstein-Uhlenbeck with
+ * Philox noise of step index s+1, half drift), force evaluation with RNG step
+ * index s+1, half kick.  One step is captured once as a CUDA graph and
+ * replayed.  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_CUDA. */
+int rbsog_step(rbsog_ctx *ctx, int64_t nsteps);
+
+/* Read the state: pos/vel [n][3] FP64 (each may be NULL), step counter. */
+int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int ptr_kind);
+
+/* Overwrite the state (pos/vel may be NULL to keep them); forces are
+ * re-evaluated at the new state before the next step.  Because every draw
+ * depends only on (seed, step, index), save + restore + run(n) reproduces
+ * run(2n) bit for bit. */
+int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_t step,
+                    int ptr_kind);
+
+/* Wait for the context's work; return the latched device error, if any. */
+int rbsog_sync(rbsog_ctx *ctx);
+
+/* SOG parameters in use: s, w[0..M] (w[0] modified), S = sum_{k!=0} k^2 Fhat(k). */
+int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
+
+/* ---- parity hooks (test use) ---------------------------------------------- */
+
+/* Lists and shell batch of atoms sel[0..nsel) at the current state and step
+ * counter, computed by the device list kernel that shares the hot path's
+ * predicate and canonical order: core/shell rows of width cap_core/cap_shell
+ * hold caller atom indices in canonical order (ascending (cell index of j,
+ * j)), batch rows of width P_R the sampled shell neighbours in the same order,
+ * weight = N_shell/P_R (1 if the whole shell is taken).  Host pointers. */
+int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_core,
+                          int32_t cap_shell, int32_t *core, int32_t *ncore, int32_t *shell,
+                          int32_t *nshell, int32_t *batch, int32_t *nbatch, double *weight);
+
+/* k-batch of the last force evaluation: m [P][3] int32, c [P] FP64 with
+ * c_p = S/(P_F |k_p|^2) (or the weights set below).  Host pointers. */
+int rbsog_debug_get_kbatch(rbsog_ctx *ctx, int32_t *m, double *c);
+
+/* Replace the sampled k-batch by a fixed list of P modes m [P][3] with
+ * weights c [P] (c_p = Fhat(k_p) over all k gives Eq. (Long)); P = 0 restores
+ * sampling.  Host pointers. */
+int rbsog_debug_set_kbatch(rbsog_ctx *ctx, int32_t P, const int32_t *m, const double *c);
+
+/* Parts of the last force evaluation: uncorrected near field F_core +
+ * F*_shell [n][3], far field F*_F [n][3], F^corr [3], structure factors
+ * rho [P][2].  Host pointers, each may be NULL. */
+int rbsog_debug_get_parts(rbsog_ctx *ctx, double *near, double *far, double *fcorr,
+                          double *rho);
+
+/* Take the whole shell with weight 1 for every atom (flag != 0), i.e. the
+ * deterministic r_shell-cutoff near field; 0 restores the P_R batch. */
+int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Stages timed by the profiling events, in launch order. */
+#define RBSOG_NSTAGE 6  /* prepare+k-batch, bin (scan/scatter/cell sort), near field,
+                           structure factor, reduction, far force + kick */
+
+/* Record a CUDA event between consecutive stages of every force evaluation
+ * (also inside the captured step graph, as event nodes) when on != 0. */
+int rbsog_set_profiling(rbsog_ctx *ctx, int on);
+
+/* Durations [ms] of the RBSOG_NSTAGE stages of the most recent force
+ * evaluation (waits for it).  Requires profiling on.  Host pointer. */
+int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage);
+
+/* Message of the last error of this context (never NULL). */
+const char *rbsog_last_error(const rbsog_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBSOG_H */

@@ -1,0 +1,734 @@
+// C ABI of the library (include/rbsog.h): context and device memory, system
+// set-up, the force evaluation sequence, the CUDA-graph-captured MD step,
+// state I/O and the parity hooks.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rbsog_internal.cuh"
+#include "setup.h"
+
+using rb::View;
+
+struct rbsog_ctx {
+  int dev = 0;
+  int nsm = 0;
+  cudaStream_t user = nullptr;  // caller's stream (may be the legacy stream)
+  cudaStream_t st = nullptr;    // library stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::string err;
+  bool has_system = false;
+  bool forces_valid = false;
+  rbsog_params prm{};
+  int64_t n = 0;
+  int ns = 0;
+  std::vector<double> charge, mass, bmh;
+  rb::SogParams sog;
+  rb::Sampler samp;
+  double self_energy = 0.0;
+  View v{};                    // device view (evaluation)
+  std::vector<void *> allocs;  // system-lifetime device buffers
+  int Pmax = 0;
+  double *stage = nullptr;     // [n][3] FP64 staging
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+  bool own_stream = false;
+  bool profiling = false;
+  cudaEvent_t prof[RBSOG_NSTAGE + 1] = {};
+};
+
+namespace {
+
+int fail(rbsog_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ctx, RBSOG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(rbsog_ctx *ctx, T **p, size_t count) {
+  void *q = nullptr;
+  if (count == 0) count = 1;
+  CK(cudaMalloc(&q, sizeof(T) * count));
+  ctx->allocs.push_back(q);
+  *p = (T *)q;
+  return RBSOG_OK;
+}
+
+void free_system(rbsog_ctx *ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->graph_ok = false;
+  for (void *p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->has_system = false;
+  ctx->forces_valid = false;
+}
+
+// With a library-owned stream, order its work after the caller's (legacy)
+// stream and the caller's after ours; with a caller stream nothing to do.
+int enter(rbsog_ctx *ctx) {
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->own_stream) {
+    CK(cudaEventRecord(ctx->ev_in, ctx->user));
+    CK(cudaStreamWaitEvent(ctx->st, ctx->ev_in, 0));
+  }
+  return RBSOG_OK;
+}
+int leave(rbsog_ctx *ctx) {
+  if (ctx->own_stream) {
+    CK(cudaEventRecord(ctx->ev_out, ctx->st));
+    CK(cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0));
+  }
+  return RBSOG_OK;
+}
+
+int check_launch(rbsog_ctx *ctx) {
+  CK(cudaGetLastError());
+  return RBSOG_OK;
+}
+
+// One force evaluation; mode 0 = evaluate, 1 = VV step, 2 = BAOAB step.
+int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
+  cudaStream_t st = ctx->st;
+  const bool pr = ctx->profiling;
+  if (pr) CK(cudaEventRecord(ctx->prof[0], st));
+  rb::launch_prepare(v, st, mode, step_off);
+  if (pr) CK(cudaEventRecord(ctx->prof[1], st));
+  rb::launch_bin(v, st);
+  if (pr) CK(cudaEventRecord(ctx->prof[2], st));
+  rb::launch_near(v, st, step_off, energy);
+  if (pr) CK(cudaEventRecord(ctx->prof[3], st));
+  rb::launch_rho(v, st);
+  if (pr) CK(cudaEventRecord(ctx->prof[4], st));
+  rb::launch_reduce(v, st, step_off, energy);
+  if (pr) CK(cudaEventRecord(ctx->prof[5], st));
+  rb::launch_force(v, st, mode);
+  if (pr) CK(cudaEventRecord(ctx->prof[6], st));
+  return check_launch(ctx);
+}
+
+int read_err(rbsog_ctx *ctx) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->v.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (e) {
+    CK(cudaMemsetAsync(ctx->v.err, 0, sizeof(int), ctx->st));
+    std::string m = "device capacity overflow:";
+    if (e & rb::ERR_CORE_CAP) m += " core list > RBSOG_MAX_CORE";
+    if (e & rb::ERR_CELL_SHELL_CAP) m += " shell count in one cell > RBSOG_MAX_CELL_SHELL";
+    if (e & rb::ERR_PR_CAP) m += " P_R";
+    return fail(ctx, RBSOG_E_CAP_OVERFLOW, m);
+  }
+  return RBSOG_OK;
+}
+
+// Copy [n][3] FP64 from the caller into the SoA array dst.
+int import_aos(rbsog_ctx *ctx, const double *src, double *dst, int kind) {
+  const int64_t n = ctx->n;
+  if (kind == RBSOG_PTR_HOST) {
+    CK(cudaMemcpyAsync(ctx->stage, src, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->st));
+    rb::launch_aos_to_soa(ctx->stage, dst, n, ctx->st);
+  } else {
+    rb::launch_aos_to_soa(src, dst, n, ctx->st);
+  }
+  return check_launch(ctx);
+}
+
+// Copy an SoA FP64/FP32 array to the caller as [n][3] FP64.
+int export_aos(rbsog_ctx *ctx, const double *srcd, const float *srcf, double *dst, int kind) {
+  const int64_t n = ctx->n;
+  double *out = (kind == RBSOG_PTR_HOST) ? ctx->stage : dst;
+  if (srcd) rb::launch_soa_to_aos_d(srcd, out, n, ctx->st);
+  else rb::launch_soa_to_aos_f(srcf, out, n, ctx->st);
+  int rc = check_launch(ctx);
+  if (rc) return rc;
+  if (kind == RBSOG_PTR_HOST) {
+    CK(cudaMemcpyAsync(dst, ctx->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return RBSOG_OK;
+}
+
+// Host copy of a caller array (host or device pointer).
+template <typename T>
+int fetch(rbsog_ctx *ctx, const T *src, size_t count, int kind, std::vector<T> &out) {
+  out.resize(count);
+  if (count == 0) return RBSOG_OK;
+  if (kind == RBSOG_PTR_HOST) {
+    std::memcpy(out.data(), src, sizeof(T) * count);
+  } else {
+    CK(cudaMemcpy(out.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  }
+  return RBSOG_OK;
+}
+
+int ensure_kcap(rbsog_ctx *ctx, int P) {
+  View &v = ctx->v;
+  if (P <= ctx->Pmax) return RBSOG_OK;
+  int rc;
+  if ((rc = dalloc(ctx, &v.km, P)) || (rc = dalloc(ctx, &v.kc, P)) ||
+      (rc = dalloc(ctx, &v.rho, 2 * (size_t)P)) || (rc = dalloc(ctx, &v.uf, P)) ||
+      (rc = dalloc(ctx, &v.kff, P)) || (rc = dalloc(ctx, &v.kfB, P)) ||
+      (rc = dalloc(ctx, &v.kfd, 5 * (size_t)P)) ||
+      (rc = dalloc(ctx, &v.rho_part, 2 * (size_t)P * (size_t)v.ntile)))
+    return rc;
+  ctx->Pmax = P;
+  return RBSOG_OK;
+}
+
+void set_rho_tiling(rbsog_ctx *ctx, int P) {
+  View &v = ctx->v;
+  const int nky = (P + rb::RHO_BLOCK * rb::RHO_KPT - 1) / (rb::RHO_BLOCK * rb::RHO_KPT);
+  const int target = 4 * ctx->nsm;
+  int64_t nt = (target + nky - 1) / nky;
+  nt = std::min<int64_t>(nt, (ctx->n + 31) / 32);
+  nt = std::max<int64_t>(nt, 1);
+  v.tile_atoms = (int)((ctx->n + nt - 1) / nt);
+  v.ntile = (int)((ctx->n + v.tile_atoms - 1) / v.tile_atoms);
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
+  rbsog_ctx *ctx = nullptr;
+  if (!out) return RBSOG_E_INVAL;
+  *out = nullptr;
+  ctx = new rbsog_ctx();
+  ctx->dev = cuda_device;
+  ctx->user = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(cuda_device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, cuda_device);
+  if (ctx->user) {
+    ctx->st = ctx->user;
+  } else if (e == cudaSuccess) {
+    e = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+    ctx->own_stream = (e == cudaSuccess);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+  for (int k = 0; k <= RBSOG_NSTAGE && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
+  if (e != cudaSuccess) {
+    rbsog_destroy(ctx);
+    return RBSOG_E_CUDA;
+  }
+  *out = ctx;
+  return RBSOG_OK;
+}
+
+void rbsog_destroy(rbsog_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  free_system(ctx);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  for (int k = 0; k <= RBSOG_NSTAGE; k++)
+    if (ctx->prof[k]) cudaEventDestroy(ctx->prof[k]);
+  if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+const char *rbsog_last_error(const rbsog_ctx *ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t *species,
+                     int32_t n_species, const double *charge, const double *mass,
+                     const double *bmh, const double box[3], const rbsog_params *params,
+                     int ptr_kind) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!pos || !species || !charge || !mass || !bmh || !box || !params)
+    return fail(ctx, RBSOG_E_INVAL, "null argument");
+  if (ptr_kind != RBSOG_PTR_HOST && ptr_kind != RBSOG_PTR_DEVICE)
+    return fail(ctx, RBSOG_E_INVAL, "bad ptr_kind");
+  const rbsog_params P = *params;
+  if (n < 2 || n > (int64_t)0x7fffffff) return fail(ctx, RBSOG_E_INVAL, "n out of range");
+  if (n_species < 1 || n_species > RBSOG_MAX_SPECIES) return fail(ctx, RBSOG_E_INVAL, "n_species out of range");
+  if (!(P.b > 1.0) || P.M < 1 || P.M > RBSOG_MAX_M) return fail(ctx, RBSOG_E_INVAL, "SOG b/M out of range");
+  if (!(P.r_core > 0.0) || !(P.r_shell > P.r_core)) return fail(ctx, RBSOG_E_INVAL, "need 0 < r_core < r_shell");
+  if (P.P_R < 1 || P.P_R > RBSOG_MAX_PR) return fail(ctx, RBSOG_E_INVAL, "P_R out of range");
+  if (P.P_F < 1) return fail(ctx, RBSOG_E_INVAL, "P_F out of range");
+  if (P.precision != RBSOG_FP64 && P.precision != RBSOG_MIXED) return fail(ctx, RBSOG_E_INVAL, "bad precision");
+  if (P.integrator != RBSOG_NVE_VV && P.integrator != RBSOG_LANGEVIN_BAOAB) return fail(ctx, RBSOG_E_INVAL, "bad integrator");
+  std::vector<double> hb(3);
+  int rc;
+  if ((rc = fetch(ctx, box, 3, RBSOG_PTR_HOST, hb))) return rc;
+  for (int a = 0; a < 3; a++) {
+    if (!(hb[a] > 0.0)) return fail(ctx, RBSOG_E_INVAL, "box must be positive");
+    if (hb[a] < 2.0 * P.r_shell) return fail(ctx, RBSOG_E_BOX_TOO_SMALL, "box length < 2 r_shell");
+  }
+  std::vector<double> hpos, hq, hm, hbmh;
+  std::vector<int32_t> hsp;
+  if ((rc = fetch(ctx, pos, 3 * (size_t)n, ptr_kind, hpos)) || (rc = fetch(ctx, species, (size_t)n, ptr_kind, hsp)) ||
+      (rc = fetch(ctx, charge, (size_t)n_species, ptr_kind, hq)) || (rc = fetch(ctx, mass, (size_t)n_species, ptr_kind, hm)) ||
+      (rc = fetch(ctx, bmh, 5 * (size_t)n_species * n_species, ptr_kind, hbmh)))
+    return rc;
+  double qsum = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    if (hsp[i] < 0 || hsp[i] >= n_species) return fail(ctx, RBSOG_E_INVAL, "species out of range");
+    qsum += hq[hsp[i]];
+  }
+  if (std::fabs(qsum) > 1e-10) return fail(ctx, RBSOG_E_NONNEUTRAL, "system is not charge neutral");
+  for (int a = 0; a < n_species; a++) {
+    if (!(hm[a] > 0.0)) return fail(ctx, RBSOG_E_INVAL, "mass must be positive");
+    for (int b = 0; b < n_species; b++)
+      for (int k = 0; k < 5; k++)
+        if (hbmh[5 * (a * n_species + b) + k] != hbmh[5 * (b * n_species + a) + k])
+          return fail(ctx, RBSOG_E_INVAL, "BMH table not symmetric");
+    for (int b = 0; b < n_species; b++)
+      if (!(hbmh[5 * (a * n_species + b) + 2] > 0.0)) return fail(ctx, RBSOG_E_INVAL, "BMH rho must be positive");
+  }
+  // --- SOG parameters (Sec. 2.1) ------------------------------------------
+  rb::SogParams sog;
+  if (P.s <= 0.0 || P.w0 <= 0.0) {
+    if ((rc = rb::sog_solve(P.b, P.M, P.r_shell, sog)) != RBSOG_OK)
+      return fail(ctx, rc, "no C1 SOG bandwidth in [r_c/6, r_c/2]");
+  } else {
+    rb::sog_fill(P.b, P.M, P.s, P.w0, sog);
+  }
+  rb::Sampler samp;
+  rb::sampler_build(sog, hb.data(), samp);
+  std::vector<float> gt, ft;
+  rb::sog_tables(sog, P.r_shell * P.r_shell, rb::NT_TAB, gt, ft);
+
+  // --- (re)allocate ----------------------------------------------------------
+  if ((rc = enter(ctx))) return rc;
+  CK(cudaStreamSynchronize(ctx->st));
+  free_system(ctx);
+  ctx->prm = P;
+  ctx->n = n;
+  ctx->ns = n_species;
+  ctx->charge = hq;
+  ctx->mass = hm;
+  ctx->bmh = hbmh;
+  ctx->sog = sog;
+  ctx->samp = samp;
+  ctx->Pmax = 0;
+  View &v = ctx->v;
+  v = View{};
+  v.n = n;
+  v.ns = n_species;
+  v.M = P.M;
+  v.G = P.M + 1;
+  v.prec = P.precision;
+  v.whole_shell = 0;
+  v.P_R = P.P_R;
+  v.P_F = P.P_F;
+  v.P = P.P_F;
+  v.fixed_k = 0;
+  v.integ = P.integrator;
+  v.seed = P.seed;
+  v.V = hb[0] * hb[1] * hb[2];
+  for (int a = 0; a < 3; a++) {
+    v.L[a] = hb[a];
+    v.invL[a] = 1.0 / hb[a];
+    v.hp[a] = (float)(hb[a] * 0x1p-23);
+    v.hf[a] = (float)(hb[a] * 0x1p-32);
+    v.hd[a] = hb[a] * 0x1p-32;
+    v.kunit[a] = 2.0 * M_PI / hb[a];
+    v.nc[a] = rb::cell_count(hb[a], P.r_shell);
+  }
+  v.rc2f = (float)(P.r_core * P.r_core);
+  v.rs2f = (float)(P.r_shell * P.r_shell);
+  v.ncell = v.nc[0] * v.nc[1] * v.nc[2];
+  v.small = (v.nc[0] < rb::STENCIL || v.nc[1] < rb::STENCIL || v.nc[2] < rb::STENCIL) ? 1 : 0;
+  v.tscale = (float)(rb::NT_TAB / (P.r_shell * P.r_shell));
+  v.S = samp.S;
+  v.dt = P.dt;
+  v.c1 = std::exp(-P.gamma * P.dt);
+  for (int a = 0; a < n_species; a++) {
+    v.qs[a] = hq[a];
+    v.kick[a] = 0.5 * P.dt * rb::FCONV / hm[a];
+    v.sig_ou[a] = std::sqrt(std::max(0.0, (1.0 - v.c1 * v.c1) * rb::KBOLTZ * P.T * rb::FCONV / hm[a]));
+  }
+  v.nblk_atoms = (int)((n + 255) / 256);
+  v.nblk_kq = (P.P_F + 255) / 256;
+  v.nblk_near = (int)((n + rb::NEAR_BLOCK - 1) / rb::NEAR_BLOCK);
+  set_rho_tiling(ctx, P.P_F);
+  // self term U_F^self = k_e/2 sum_i q_i^2 F(0)
+  double F0 = 0.0, q2 = 0.0;
+  for (int m = 0; m <= P.M; m++) F0 += sog.w[m];
+  for (int64_t i = 0; i < n; i++) q2 += hq[hsp[i]] * hq[hsp[i]];
+  ctx->self_energy = 0.5 * rb::KE * q2 * F0;
+
+  const size_t N = (size_t)n;
+  int *spc_d = nullptr;
+  rb::PairF *pf = nullptr;
+  rb::PairD *pd = nullptr;
+  double *wa = nullptr, *w = nullptr, *h2 = nullptr;
+  float4 *gtab = nullptr, *ftab = nullptr;
+  unsigned long long *cmix = nullptr, *cdf = nullptr;
+  int *off0 = nullptr, *off2 = nullptr, *nmax = nullptr;
+  if ((rc = dalloc(ctx, &v.x, 3 * N)) || (rc = dalloc(ctx, &v.v, 3 * N)) ||
+      (rc = dalloc(ctx, &v.Ff, 3 * N)) || (rc = dalloc(ctx, &v.FNf, 3 * N)) || (rc = dalloc(ctx, &v.FFf, 3 * N)) ||
+      (rc = dalloc(ctx, &v.Fd, 3 * N)) || (rc = dalloc(ctx, &v.FNd, 3 * N)) || (rc = dalloc(ctx, &v.FFd, 3 * N)) ||
+      (rc = dalloc(ctx, &spc_d, N)) || (rc = dalloc(ctx, &v.ua, N)) || (rc = dalloc(ctx, &v.cellid, N)) ||
+      (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
+      (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, N)) ||
+      (rc = dalloc(ctx, &v.perm, N)) || (rc = dalloc(ctx, &v.slot_of, N)) || (rc = dalloc(ctx, &v.sv, N)) ||
+      (rc = dalloc(ctx, &v.su, N)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
+      (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
+      (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
+      (rc = dalloc(ctx, &wa, (size_t)v.G)) || (rc = dalloc(ctx, &w, (size_t)v.G)) || (rc = dalloc(ctx, &h2, (size_t)v.G)) ||
+      (rc = dalloc(ctx, &gtab, rb::NT_TAB)) || (rc = dalloc(ctx, &ftab, rb::NT_TAB)) ||
+      (rc = dalloc(ctx, &cmix, samp.cmix.size())) || (rc = dalloc(ctx, &cdf, samp.cdf.size())) ||
+      (rc = dalloc(ctx, &off0, samp.off0.size())) || (rc = dalloc(ctx, &off2, samp.off2.size())) ||
+      (rc = dalloc(ctx, &nmax, samp.nmax.size())) || (rc = dalloc(ctx, &ctx->stage, 3 * N)) ||
+      (rc = ensure_kcap(ctx, P.P_F))) {
+    free_system(ctx);
+    return rc;
+  }
+  v.spc = spc_d;
+  v.pf = pf;
+  v.pd = pd;
+  v.sog_wa = wa;
+  v.sog_w = w;
+  v.sog_h = h2;
+  v.gtab = gtab;
+  v.ftab = ftab;
+  v.cmix = cmix;
+  v.cdf = cdf;
+  v.cdf_off0 = off0;
+  v.cdf_off2 = off2;
+  v.cdf_nmax = nmax;
+  // pair records
+  std::vector<rb::PairF> hpf((size_t)n_species * n_species);
+  std::vector<rb::PairD> hpd((size_t)n_species * n_species);
+  const double LOG2E = 1.4426950408889634;
+  for (int a = 0; a < n_species; a++)
+    for (int b = 0; b < n_species; b++) {
+      const double *t = &hbmh[5 * (a * n_species + b)];
+      const double A = t[0], sig = t[1], rho = t[2], C = t[3], D = t[4];
+      const double kqq = rb::KE * hq[a] * hq[b];
+      rb::PairF f{};
+      f.kqq = (float)kqq; f.Ar = (float)(A / rho); f.lr = (float)(LOG2E / rho); f.sig = (float)sig;
+      f.C6 = (float)(6.0 * C); f.D8 = (float)(8.0 * D); f.A = (float)A; f.C = (float)C; f.D = (float)D;
+      hpf[a * n_species + b] = f;
+      hpd[a * n_species + b] = rb::PairD{kqq, A, sig, rho, C, D};
+    }
+  std::vector<double> hwa(v.G), hw(v.G), hh2(v.G);
+  for (int m = 0; m < v.G; m++) {
+    hwa[m] = sog.w[m] / sog.a[m];
+    hw[m] = sog.w[m];
+    hh2[m] = 1.0 / (2.0 * sog.a[m]);
+  }
+  // positions [n][3] -> SoA
+  std::vector<double> soa(3 * N);
+  for (size_t i = 0; i < N; i++)
+    for (int a = 0; a < 3; a++) soa[a * N + i] = hpos[3 * i + a];
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->st);
+  };
+  CK(up(v.x, soa.data(), sizeof(double) * 3 * N));
+  CK(cudaMemsetAsync(v.v, 0, sizeof(double) * 3 * N, ctx->st));
+  CK(cudaMemsetAsync(v.Ff, 0, sizeof(float) * 3 * N, ctx->st));
+  CK(cudaMemsetAsync(v.Fd, 0, sizeof(double) * 3 * N, ctx->st));
+  CK(up(spc_d, hsp.data(), sizeof(int) * N));
+  CK(up(pf, hpf.data(), sizeof(rb::PairF) * hpf.size()));
+  CK(up(pd, hpd.data(), sizeof(rb::PairD) * hpd.size()));
+  CK(up(wa, hwa.data(), sizeof(double) * v.G));
+  CK(up(w, hw.data(), sizeof(double) * v.G));
+  CK(up(h2, hh2.data(), sizeof(double) * v.G));
+  CK(up(gtab, gt.data(), sizeof(float) * gt.size()));
+  CK(up(ftab, ft.data(), sizeof(float) * ft.size()));
+  CK(up(cmix, samp.cmix.data(), sizeof(unsigned long long) * samp.cmix.size()));
+  CK(up(cdf, samp.cdf.data(), sizeof(unsigned long long) * samp.cdf.size()));
+  CK(up(off0, samp.off0.data(), sizeof(int) * samp.off0.size()));
+  CK(up(off2, samp.off2.data(), sizeof(int) * samp.off2.size()));
+  CK(up(nmax, samp.nmax.data(), sizeof(int) * samp.nmax.size()));
+  CK(cudaMemsetAsync(v.err, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(v.step, 0, sizeof(long long), ctx->st));
+  CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 8, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
+  ctx->has_system = true;
+  ctx->forces_valid = false;
+  return leave(ctx);
+}
+
+int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!vel) return fail(ctx, RBSOG_E_INVAL, "null velocities");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if ((rc = import_aos(ctx, vel, ctx->v.v, ptr_kind))) return rc;
+  if (ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));
+  return leave(ctx);
+}
+
+int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double *virial,
+                         int ptr_kind) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (virial) return fail(ctx, RBSOG_E_INVAL, "virial output is not provided");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if ((rc = run_force(ctx, ctx->v, 0, 0, energy != nullptr))) return rc;
+  ctx->forces_valid = true;
+  if (forces) {
+    if (ctx->v.prec == RBSOG_FP64) rc = export_aos(ctx, ctx->v.Fd, nullptr, forces, ptr_kind);
+    else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind);
+    if (rc) return rc;
+  }
+  if (energy) {
+    double red[8];
+    CK(cudaMemcpyAsync(red, ctx->v.red, sizeof(red), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const double e[4] = {red[3], red[4], ctx->self_energy, red[3] + red[4] - ctx->self_energy};
+    if (ptr_kind == RBSOG_PTR_HOST) std::memcpy(energy, e, sizeof(e));
+    else CK(cudaMemcpyAsync(energy, e, sizeof(e), cudaMemcpyHostToDevice, ctx->st));
+  }
+  if (ptr_kind == RBSOG_PTR_HOST || energy) {
+    if ((rc = read_err(ctx))) return rc;
+  }
+  return leave(ctx);
+}
+
+int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (nsteps < 0) return fail(ctx, RBSOG_E_INVAL, "negative step count");
+  if (!(ctx->prm.dt > 0.0)) return fail(ctx, RBSOG_E_INVAL, "dt must be positive");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if (!ctx->forces_valid) {
+    if ((rc = run_force(ctx, ctx->v, 0, 0, false))) return rc;
+    ctx->forces_valid = true;
+  }
+  if (!ctx->graph_ok) {
+    View vs = ctx->v;
+    vs.FFf = nullptr;  // the step writes no debug parts
+    vs.FFd = nullptr;
+    const int mode = ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 2;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    rc = run_force(ctx, vs, mode, 1, false);
+    cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->graph_ok = true;
+  }
+  for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+  return leave(ctx);
+}
+
+int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int ptr_kind) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if (pos && (rc = export_aos(ctx, ctx->v.x, nullptr, pos, ptr_kind))) return rc;
+  if (vel && (rc = export_aos(ctx, ctx->v.v, nullptr, vel, ptr_kind))) return rc;
+  if (step) {
+    long long s = 0;
+    CK(cudaMemcpyAsync(&s, ctx->v.step, sizeof(s), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *step = (int64_t)s;
+  }
+  return leave(ctx);
+}
+
+int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_t step,
+                    int ptr_kind) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (step < 0) return fail(ctx, RBSOG_E_INVAL, "negative step");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if (pos && (rc = import_aos(ctx, pos, ctx->v.x, ptr_kind))) return rc;
+  if (pos && ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));
+  if (vel && (rc = import_aos(ctx, vel, ctx->v.v, ptr_kind))) return rc;
+  long long s = step;
+  CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->forces_valid = false;
+  return leave(ctx);
+}
+
+int rbsog_sync(rbsog_ctx *ctx) {
+  if (!ctx) return RBSOG_E_INVAL;
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (!ctx->has_system) return RBSOG_OK;
+  return read_err(ctx);
+}
+
+int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (s) *s = ctx->sog.s;
+  if (w) std::memcpy(w, ctx->sog.w.data(), sizeof(double) * ctx->sog.w.size());
+  if (S) *S = ctx->samp.S;
+  return RBSOG_OK;
+}
+
+int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_core,
+                          int32_t cap_shell, int32_t *core, int32_t *ncore, int32_t *shell,
+                          int32_t *nshell, int32_t *batch, int32_t *nbatch, double *weight) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!sel || nsel <= 0 || cap_core < 1 || cap_shell < 1 || !core || !ncore || !shell || !nshell)
+    return fail(ctx, RBSOG_E_INVAL, "bad list arguments");
+  for (int64_t q = 0; q < nsel; q++)
+    if (sel[q] < 0 || sel[q] >= ctx->n) return fail(ctx, RBSOG_E_INVAL, "selected atom out of range");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  View &v = ctx->v;
+  rb::launch_prepare(v, ctx->st, 0, 0);
+  rb::launch_bin(v, ctx->st);
+  const size_t k = (size_t)nsel;
+  long long *dsel;
+  int *dcore, *dnc, *dshell, *dns, *dbatch = nullptr, *dnb = nullptr;
+  double *dw = nullptr;
+  CK(cudaMalloc(&dsel, sizeof(long long) * k));
+  CK(cudaMalloc(&dcore, sizeof(int) * k * cap_core));
+  CK(cudaMalloc(&dnc, sizeof(int) * k));
+  CK(cudaMalloc(&dshell, sizeof(int) * k * cap_shell));
+  CK(cudaMalloc(&dns, sizeof(int) * k));
+  if (batch) {
+    CK(cudaMalloc(&dbatch, sizeof(int) * k * v.P_R));
+    CK(cudaMalloc(&dnb, sizeof(int) * k));
+    CK(cudaMalloc(&dw, sizeof(double) * k));
+  }
+  std::vector<long long> hs(sel, sel + k);
+  CK(cudaMemcpyAsync(dsel, hs.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, ctx->st));
+  rb::launch_lists(v, ctx->st, 0, dsel, (int)nsel, cap_core, cap_shell, dcore, dnc, dshell, dns, dbatch,
+                   dnb, dw);
+  if ((rc = check_launch(ctx))) return rc;
+  CK(cudaMemcpyAsync(core, dcore, sizeof(int) * k * cap_core, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ncore, dnc, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(shell, dshell, sizeof(int) * k * cap_shell, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(nshell, dns, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+  if (batch) {
+    CK(cudaMemcpyAsync(batch, dbatch, sizeof(int) * k * v.P_R, cudaMemcpyDeviceToHost, ctx->st));
+    if (nbatch) CK(cudaMemcpyAsync(nbatch, dnb, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+    if (weight) CK(cudaMemcpyAsync(weight, dw, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  cudaFree(dsel); cudaFree(dcore); cudaFree(dnc); cudaFree(dshell); cudaFree(dns);
+  if (batch) { cudaFree(dbatch); cudaFree(dnb); cudaFree(dw); }
+  return leave(ctx);
+}
+
+int rbsog_debug_get_kbatch(rbsog_ctx *ctx, int32_t *m, double *c) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  const int P = ctx->v.P;
+  if (m) {
+    std::vector<int4> hm(P);
+    CK(cudaMemcpyAsync(hm.data(), ctx->v.km, sizeof(int4) * P, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int k = 0; k < P; k++) { m[3 * k] = hm[k].x; m[3 * k + 1] = hm[k].y; m[3 * k + 2] = hm[k].z; }
+  }
+  if (c) {
+    CK(cudaMemcpyAsync(c, ctx->v.kc, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return leave(ctx);
+}
+
+int rbsog_debug_set_kbatch(rbsog_ctx *ctx, int32_t P, const int32_t *m, const double *c) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (P < 0 || (P > 0 && (!m || !c))) return fail(ctx, RBSOG_E_INVAL, "bad k list");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  CK(cudaStreamSynchronize(ctx->st));
+  View &v = ctx->v;
+  if (P == 0) {
+    v.fixed_k = 0;
+    v.P = v.P_F;
+  } else {
+    set_rho_tiling(ctx, P);
+    if (P > ctx->Pmax || true) {
+      ctx->Pmax = 0;  // re-size per-k buffers for the new tiling
+      if ((rc = ensure_kcap(ctx, std::max(P, v.P_F)))) return rc;
+    }
+    std::vector<int4> hm(P);
+    for (int k = 0; k < P; k++) hm[k] = make_int4(m[3 * k], m[3 * k + 1], m[3 * k + 2], 0);
+    CK(cudaMemcpyAsync(v.km, hm.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(v.kc, c, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    v.fixed_k = 1;
+    v.P = P;
+  }
+  if (P == 0) {
+    set_rho_tiling(ctx, v.P_F);
+    ctx->Pmax = 0;
+    if ((rc = ensure_kcap(ctx, v.P_F))) return rc;
+  }
+  ctx->graph_ok = false;
+  ctx->forces_valid = false;
+  return leave(ctx);
+}
+
+int rbsog_debug_get_parts(rbsog_ctx *ctx, double *near, double *far, double *fcorr,
+                          double *rho) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  const View &v = ctx->v;
+  const bool d = v.prec == RBSOG_FP64;
+  if (near && (rc = export_aos(ctx, d ? v.FNd : nullptr, d ? nullptr : v.FNf, near, RBSOG_PTR_HOST))) return rc;
+  if (far && (rc = export_aos(ctx, d ? v.FFd : nullptr, d ? nullptr : v.FFf, far, RBSOG_PTR_HOST))) return rc;
+  if (fcorr) {
+    CK(cudaMemcpyAsync(fcorr, v.red, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (rho) {
+    CK(cudaMemcpyAsync(rho, v.rho, sizeof(double) * 2 * v.P, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return leave(ctx);
+}
+
+int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  ctx->v.whole_shell = flag ? 1 : 0;
+  ctx->graph_ok = false;
+  ctx->forces_valid = false;
+  return RBSOG_OK;
+}
+
+int rbsog_set_profiling(rbsog_ctx *ctx, int on) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (ctx->profiling != (on != 0)) {
+    ctx->profiling = on != 0;
+    ctx->graph_ok = false;
+  }
+  return RBSOG_OK;
+}
+
+int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage) {
+  if (!ctx || !ms || nstage < 1) return RBSOG_E_INVAL;
+  if (!ctx->profiling) return fail(ctx, RBSOG_E_INVAL, "profiling is off");
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaEventSynchronize(ctx->prof[RBSOG_NSTAGE]));
+  for (int k = 0; k < nstage && k < RBSOG_NSTAGE; k++)
+    CK(cudaEventElapsedTime(ms + k, ctx->prof[k], ctx->prof[k + 1]));
+  return RBSOG_OK;
+}
+
+}  // extern "C"

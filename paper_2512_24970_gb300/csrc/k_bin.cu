@@ -1,0 +1,217 @@
+// Stage (a) and the integrator's first half, plus the k-batch draw of stage (d):
+//   k_prepare   per atom: [half kick, drift / BAOAB B-A-O-A (Sec. 2.3)], 32-bit
+//               fixed-point coordinates, cell index and cell histogram; extra
+//               blocks draw the P_F k-vectors from P(k) (Eq. (Pk)).
+//   k_scan      exclusive scan of the cell histogram (one block).
+//   k_scatter   counting-sort scatter (slot claimed by atomicAdd).
+//   k_cellsort  per cell: restore ascending caller order inside the cell (the
+//               canonical order of the list), write the sorted SoA arrays.
+#include "rbsog_internal.cuh"
+
+namespace rb {
+
+// ---------------------------------------------------------------------------
+// k-batch: exact i.i.d. draw from the mixture form of P(k) = k^2 Fhat(k)/S.
+// U0 picks the (Gaussian g, axis d) component, U1 picks m_d from the
+// k^2-weighted 1-D CDF, U2/U3 pick the other two axes (ascending axis order)
+// from the plain 1-D CDFs; c_p = S / (P_F |k_p|^2).
+__device__ void ksample(const View &p, int q, long long s) {
+  if (q >= p.P_F || p.fixed_k) return;
+  const uint4 w0 = draw(p.seed, s, (uint32_t)q, 1u, 0u);
+  const uint4 w1 = draw(p.seed, s, (uint32_t)q, 1u, 1u);
+  const unsigned long long U0 = ((unsigned long long)w0.y << 32) | w0.x;
+  const unsigned long long U1 = ((unsigned long long)w0.w << 32) | w0.z;
+  const unsigned long long U2 = ((unsigned long long)w1.y << 32) | w1.x;
+  const unsigned long long U3 = ((unsigned long long)w1.w << 32) | w1.z;
+  const int c = cdf_pick(p.cmix, 3 * p.G, U0);
+  const int d = c % 3;
+  const int g = c / 3;
+  int m[3];
+  {
+    const int nm = p.cdf_nmax[c];
+    m[d] = cdf_pick(p.cdf + p.cdf_off2[c], 2 * nm + 1, U1) - nm;
+  }
+  unsigned long long Uo[2] = {U2, U3};
+  int o = 0;
+  for (int e = 0; e < 3; e++) {
+    if (e == d) continue;
+    const int ce = 3 * g + e;
+    const int nm = p.cdf_nmax[ce];
+    m[e] = cdf_pick(p.cdf + p.cdf_off0[ce], 2 * nm + 1, Uo[o++]) - nm;
+  }
+  double k2 = 0.0;
+  for (int e = 0; e < 3; e++) {
+    const double k = 2.0 * 3.141592653589793 * (double)m[e] / p.L[e];
+    k2 += k * k;
+  }
+  p.km[q] = make_int4(m[0], m[1], m[2], 0);
+  p.kc[q] = p.S / ((double)p.P_F * k2);
+}
+
+// Gaussian triple of the O-step: Box-Muller on Philox stream 2, block 0.
+__device__ __forceinline__ void noise3(const View &p, long long s, uint32_t i, double g[3]) {
+  const uint4 w = draw(p.seed, s, i, 2u, 0u);
+  const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+  const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+  const double u2 = ((double)w.z + 0.5) * 2.3283064365386963e-10;
+  const double u3 = ((double)w.w + 0.5) * 2.3283064365386963e-10;
+  const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+  double s0, c0, s1, c1;
+  sincospi(2.0 * u1, &s0, &c0);
+  sincospi(2.0 * u3, &s1, &c1);
+  g[0] = r0 * c0;
+  g[1] = r0 * s0;
+  g[2] = r1 * c1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
+  const long long s = *p.step + step_off;
+  if ((int)blockIdx.x >= p.nblk_atoms) {
+    ksample(p, ((int)blockIdx.x - p.nblk_atoms) * blockDim.x + threadIdx.x, s);
+    return;
+  }
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int64_t n = p.n;
+  const int sp = p.spc[i];
+  double x[3] = {p.x[i], p.x[n + i], p.x[2 * n + i]};
+  if (MODE != 0) {
+    double v[3] = {p.v[i], p.v[n + i], p.v[2 * n + i]};
+    double F[3];
+    if (p.prec == RBSOG_FP64) {
+      F[0] = p.Fd[i]; F[1] = p.Fd[n + i]; F[2] = p.Fd[2 * n + i];
+    } else {
+      F[0] = p.Ff[i]; F[1] = p.Ff[n + i]; F[2] = p.Ff[2 * n + i];
+    }
+    const double kick = p.kick[sp];
+    for (int a = 0; a < 3; a++) v[a] += kick * F[a];
+    if (MODE == 1) {
+      for (int a = 0; a < 3; a++) x[a] += p.dt * v[a];
+    } else {
+      double g[3];
+      noise3(p, s, (uint32_t)i, g);
+      const double h = 0.5 * p.dt, so = p.sig_ou[sp];
+      for (int a = 0; a < 3; a++) {
+        x[a] += h * v[a];
+        v[a] = p.c1 * v[a] + so * g[a];
+        x[a] += h * v[a];
+      }
+    }
+    for (int a = 0; a < 3; a++) {
+      p.x[a * n + i] = x[a];
+      p.v[a * n + i] = v[a];
+    }
+  }
+  uint32_t u[3];
+  for (int a = 0; a < 3; a++) u[a] = fixed_point(x[a], p.invL[a]);
+  const int cell = cell_of(u[0], p.nc[0]) + p.nc[0] * (cell_of(u[1], p.nc[1]) + p.nc[1] * cell_of(u[2], p.nc[2]));
+  p.ua[i] = make_uint4(u[0], u[1], u[2], (uint32_t)sp);
+  p.cellid[i] = cell;
+  atomicAdd(p.cell_count + cell, 1);
+}
+
+// Exclusive scan of cell_count into cell_start[0..ncell] (and cell_cursor).
+__global__ void __launch_bounds__(1024) k_scan(View p) {
+  __shared__ int wsum[32];
+  const int nt = blockDim.x, t = threadIdx.x;
+  const int per = (p.ncell + nt - 1) / nt;
+  const int b = t * per, e = min(b + per, p.ncell);
+  int local = 0;
+  for (int c = b; c < e; c++) local += p.cell_count[c];
+  // block exclusive scan of `local`
+  int incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) wsum[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    int w = (t < (nt >> 5)) ? wsum[t] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (t >= o) w += y;
+    }
+    wsum[t] = w;
+  }
+  __syncthreads();
+  int run = incl - local + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
+  for (int c = b; c < e; c++) {
+    p.cell_start[c] = run;
+    p.cell_cursor[c] = run;
+    run += p.cell_count[c];
+  }
+  if (t == nt - 1) p.cell_start[p.ncell] = (int)p.n;
+}
+
+__global__ void __launch_bounds__(256) k_scatter(View p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int slot = atomicAdd(p.cell_cursor + p.cellid[i], 1);
+  p.perm_tmp[slot] = (int)i;
+}
+
+// One thread per cell: insertion sort of the cell's caller ids (ascending),
+// then the sorted arrays.  Cells hold ~8 atoms at r_shell/2 cells.
+__global__ void __launch_bounds__(256) k_cellsort(View p) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.ncell) return;
+  const int b = p.cell_start[c], e = p.cell_start[c + 1];
+  for (int a = b + 1; a < e; a++) {
+    const int v = p.perm_tmp[a];
+    int k = a - 1;
+    while (k >= b && p.perm_tmp[k] > v) {
+      p.perm_tmp[k + 1] = p.perm_tmp[k];
+      k--;
+    }
+    p.perm_tmp[k + 1] = v;
+  }
+  for (int slot = b; slot < e; slot++) {
+    const int id = p.perm_tmp[slot];
+    const uint4 u = p.ua[id];
+    p.perm[slot] = id;
+    p.slot_of[id] = slot;
+    p.sv[slot] = make_float4((float)(u.x >> 9), (float)(u.y >> 9), (float)(u.z >> 9), __int_as_float((int)u.w));
+    p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)id);
+  }
+}
+
+void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
+  cudaMemsetAsync(v.cell_count, 0, sizeof(int) * (size_t)v.ncell, st);
+  const int blocks = v.nblk_atoms + v.nblk_kq;
+  if (mode == 0) k_prepare<0><<<blocks, 256, 0, st>>>(v, step_off);
+  else if (mode == 1) k_prepare<1><<<blocks, 256, 0, st>>>(v, step_off);
+  else k_prepare<2><<<blocks, 256, 0, st>>>(v, step_off);
+}
+
+void launch_bin(const View &v, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(v);
+  k_scatter<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
+  k_cellsort<<<(v.ncell + 255) / 256, 256, 0, st>>>(v);
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversions between the ABI's [n][3] FP64 and the internal [3][n].
+__global__ void k_aos_to_soa(const double *aos, double *soa, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < 3; a++) soa[a * n + i] = aos[3 * i + a];
+}
+template <typename T>
+__global__ void k_soa_to_aos(const T *soa, double *aos, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < 3; a++) aos[3 * i + a] = (double)soa[a * n + i];
+}
+void launch_aos_to_soa(const double *aos, double *soa, int64_t n, cudaStream_t st) {
+  k_aos_to_soa<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(aos, soa, n);
+}
+void launch_soa_to_aos_d(const double *soa, double *aos, int64_t n, cudaStream_t st) {
+  k_soa_to_aos<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(soa, aos, n);
+}
+void launch_soa_to_aos_f(const float *soa, double *aos, int64_t n, cudaStream_t st) {
+  k_soa_to_aos<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(soa, aos, n);
+}
+
+}  // namespace rb

@@ -1,0 +1,264 @@
+// Stage (d) far field and stage (e) second half (Sec. 2.2, Eq. (long-rangeforce)):
+//   k_rho     structure-factor partials rho(k_p) = sum_j q_j e^{i k_p . r_j} over
+//             an atom tile, phase k . r = 2 pi (m . u mod 2^32) / 2^32 reduced
+//             exactly in uint32; FP32 MUFU sincos with FP32 accumulation over
+//             at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
+//   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
+//             force coefficients c_p Im rho_p, c_p Re rho_p, and F^corr.
+//   k_force   F_i = F_N,i - F^corr - (k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p),
+//             fused with the closing half kick of the MD step.
+#include "rbsog_internal.cuh"
+
+namespace rb {
+
+constexpr double TWO_PI = 6.283185307179586;
+constexpr float ANG23 = 7.490115661286456e-07f;  // 2 pi / 2^23
+
+// Mixed phase: int32(theta + 2^8) >> 9 in [-2^22, 2^22) -> radians in [-pi, pi).
+__device__ __forceinline__ void sincos_phase_f(uint32_t th, float &s, float &c) {
+  const int xs = ((int)(th + 256u)) >> 9;
+  __sincosf(i2f_small(xs) * ANG23, &s, &c);
+}
+__device__ __forceinline__ void sincos_phase_d(uint32_t th, double &s, double &c) {
+  sincospi((double)(int)th * 4.656612873077393e-10, &s, &c);  // * 2^-31
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
+  constexpr bool MIX = sizeof(R) == 4;
+  __shared__ uint4 sa[256];
+  __shared__ R sq[256];
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x;
+  const int64_t a0 = (int64_t)tile * p.tile_atoms;
+  const int64_t a1 = min(a0 + (int64_t)p.tile_atoms, p.n);
+  uint32_t mx[RHO_KPT], my[RHO_KPT], mz[RHO_KPT];
+  int kk[RHO_KPT];
+#pragma unroll
+  for (int t = 0; t < RHO_KPT; t++) {
+    kk[t] = blockIdx.y * (RHO_BLOCK * RHO_KPT) + t * RHO_BLOCK + tid;
+    const int4 m = kk[t] < p.P ? p.km[kk[t]] : make_int4(0, 0, 0, 0);
+    mx[t] = (uint32_t)m.x; my[t] = (uint32_t)m.y; mz[t] = (uint32_t)m.z;
+  }
+  double re[RHO_KPT], im[RHO_KPT];
+#pragma unroll
+  for (int t = 0; t < RHO_KPT; t++) re[t] = im[t] = 0.0;
+  for (int64_t base = a0; base < a1; base += 256) {
+    const int cnt = (int)min((int64_t)256, a1 - base);
+    __syncthreads();
+    if (tid < cnt) {
+      const uint4 u = p.ua[base + tid];
+      sa[tid] = u;
+      sq[tid] = (R)p.qs[u.w];
+    }
+    __syncthreads();
+    if (MIX) {
+      float fr[RHO_KPT], fi[RHO_KPT];
+#pragma unroll
+      for (int t = 0; t < RHO_KPT; t++) fr[t] = fi[t] = 0.0f;
+#pragma unroll 4
+      for (int a = 0; a < cnt; a++) {
+        const uint4 u = sa[a];
+        const float q = (float)sq[a];
+#pragma unroll
+        for (int t = 0; t < RHO_KPT; t++) {
+          const uint32_t th = mx[t] * u.x + my[t] * u.y + mz[t] * u.z;
+          float s, c;
+          sincos_phase_f(th, s, c);
+          fr[t] = __fmaf_rn(q, c, fr[t]);
+          fi[t] = __fmaf_rn(q, s, fi[t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < RHO_KPT; t++) {
+        re[t] += (double)fr[t];
+        im[t] += (double)fi[t];
+      }
+    } else {
+      for (int a = 0; a < cnt; a++) {
+        const uint4 u = sa[a];
+        const double q = (double)sq[a];
+#pragma unroll
+        for (int t = 0; t < RHO_KPT; t++) {
+          const uint32_t th = mx[t] * u.x + my[t] * u.y + mz[t] * u.z;
+          double s, c;
+          sincos_phase_d(th, s, c);
+          re[t] += q * c;
+          im[t] += q * s;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RHO_KPT; t++) {
+    if (kk[t] < p.P) {
+      double *d = p.rho_part + 2 * ((int64_t)kk[t] * p.ntile + tile);
+      d[0] = re[t];
+      d[1] = im[t];
+    }
+  }
+}
+
+// One warp per k: fixed-order sum over tiles (lane-strided, then a shuffle
+// tree), per-k force coefficients.  Block 0 / warp 0 also forms F^corr.
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce(View p, int step_off) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * 8 + w;
+  if (k < p.P) {
+    double sr = 0.0, si = 0.0;
+    for (int t = lane; t < p.ntile; t += 32) {
+      const double *d = p.rho_part + 2 * ((int64_t)k * p.ntile + t);
+      sr += d[0];
+      si += d[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_down_sync(0xffffffffu, sr, o);
+      si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      p.rho[2 * k] = sr;
+      p.rho[2 * k + 1] = si;
+      const int4 m = p.km[k];
+      const double c = p.kc[k];
+      const double kx = TWO_PI * (double)m.x / p.L[0];
+      const double ky = TWO_PI * (double)m.y / p.L[1];
+      const double kz = TWO_PI * (double)m.z / p.L[2];
+      const double A = c * si, B = c * sr;
+      if (sizeof(R) == 4) {
+        p.kff[k] = make_float4((float)kx, (float)ky, (float)kz, (float)A);
+        p.kfB[k] = (float)B;
+      } else {
+        double *o = p.kfd + 5 * (int64_t)k;
+        o[0] = kx; o[1] = ky; o[2] = kz; o[3] = A; o[4] = B;
+      }
+      p.uf[k] = c * (sr * sr + si * si);
+    }
+  }
+  if (blockIdx.x == 0 && w == 0) {
+    double f[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = lane; b < p.nblk_near; b += 32)
+      for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
+    for (int a = 0; a < 4; a++)
+      for (int o = 16; o > 0; o >>= 1) f[a] += __shfl_down_sync(0xffffffffu, f[a], o);
+    if (lane == 0) {
+      for (int a = 0; a < 3; a++) p.red[a] = f[a] / (double)p.n;
+      p.red[3] = f[3];
+      if (step_off) *p.step += step_off;
+    }
+  }
+}
+
+// Energies: U_F* = k_e/(2V) sum_p c_p |rho_p|^2 (fixed order); U_self is host-side.
+__global__ void k_energy(View p) {
+  if (threadIdx.x != 0) return;
+  double u = 0.0;
+  for (int k = 0; k < p.P; k++) u += p.uf[k];
+  p.red[4] = KE / (2.0 * p.V) * u;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
+  constexpr bool MIX = sizeof(R) == 4;
+  __shared__ int4 sm[FORCE_KCHUNK];
+  __shared__ float4 skf[MIX ? FORCE_KCHUNK : 1];
+  __shared__ float skB[MIX ? FORCE_KCHUNK : 1];
+  __shared__ double skd[MIX ? 1 : FORCE_KCHUNK * 5];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * FORCE_BLOCK + tid;
+  const bool act = i < p.n;
+  const uint4 u = act ? p.ua[i] : make_uint4(0, 0, 0, 0);
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int k0 = 0; k0 < p.P; k0 += FORCE_KCHUNK) {
+    const int cnt = min(FORCE_KCHUNK, p.P - k0);
+    __syncthreads();
+    for (int k = tid; k < cnt; k += FORCE_BLOCK) {
+      sm[k] = p.km[k0 + k];
+      if (MIX) {
+        skf[k] = p.kff[k0 + k];
+        skB[k] = p.kfB[k0 + k];
+      } else {
+        for (int a = 0; a < 5; a++) skd[5 * k + a] = p.kfd[5 * (int64_t)(k0 + k) + a];
+      }
+    }
+    __syncthreads();
+    if (MIX) {
+      float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll 4
+      for (int k = 0; k < cnt; k++) {
+        const int4 m = sm[k];
+        const uint32_t th = (uint32_t)m.x * u.x + (uint32_t)m.y * u.y + (uint32_t)m.z * u.z;
+        float s, c;
+        sincos_phase_f(th, s, c);
+        const float4 kf = skf[k];
+        const float sv = __fmaf_rn(c, kf.w, -s * skB[k]);
+        fx = __fmaf_rn(sv, kf.x, fx);
+        fy = __fmaf_rn(sv, kf.y, fy);
+        fz = __fmaf_rn(sv, kf.z, fz);
+      }
+      ax += fx; ay += fy; az += fz;
+    } else {
+      for (int k = 0; k < cnt; k++) {
+        const int4 m = sm[k];
+        const uint32_t th = (uint32_t)m.x * u.x + (uint32_t)m.y * u.y + (uint32_t)m.z * u.z;
+        double s, c;
+        sincos_phase_d(th, s, c);
+        const double *kd = skd + 5 * k;
+        const double sv = c * kd[3] - s * kd[4];
+        ax += sv * kd[0];
+        ay += sv * kd[1];
+        az += sv * kd[2];
+      }
+    }
+  }
+  if (!act) return;
+  const int64_t n = p.n;
+  const int sp = (int)u.w;
+  const double pre = -KE * p.qs[sp] / p.V;
+  const double far[3] = {pre * ax, pre * ay, pre * az};
+  double F[3];
+  for (int a = 0; a < 3; a++) {
+    const double fn = MIX ? (double)p.FNf[a * n + i] : p.FNd[a * n + i];
+    F[a] = fn - p.red[a] + far[a];
+  }
+  if (MIX) {
+    for (int a = 0; a < 3; a++) p.Ff[a * n + i] = (float)F[a];
+    if (p.FFf) for (int a = 0; a < 3; a++) p.FFf[a * n + i] = (float)far[a];
+  } else {
+    for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
+    if (p.FFd) for (int a = 0; a < 3; a++) p.FFd[a * n + i] = far[a];
+  }
+  if (MODE != 0) {
+    const double kick = p.kick[sp];
+    for (int a = 0; a < 3; a++) {
+      const double Fa = MIX ? (double)(float)F[a] : F[a];
+      p.v[a * n + i] += kick * Fa;
+    }
+  }
+}
+
+void launch_rho(const View &v, cudaStream_t st) {
+  const dim3 g(v.ntile, (v.P + RHO_BLOCK * RHO_KPT - 1) / (RHO_BLOCK * RHO_KPT));
+  if (v.prec == RBSOG_MIXED) k_rho<float><<<g, RHO_BLOCK, 0, st>>>(v);
+  else k_rho<double><<<g, RHO_BLOCK, 0, st>>>(v);
+}
+
+void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
+  const int g = max(1, (v.P + 7) / 8);
+  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, step_off);
+  else k_reduce<double><<<g, 256, 0, st>>>(v, step_off);
+  if (energy) k_energy<<<1, 32, 0, st>>>(v);
+}
+
+void launch_force(const View &v, cudaStream_t st, int mode) {
+  const int g = (int)((v.n + FORCE_BLOCK - 1) / FORCE_BLOCK);
+  if (v.prec == RBSOG_MIXED) {
+    if (mode) k_force<float, 1><<<g, FORCE_BLOCK, 0, st>>>(v);
+    else k_force<float, 0><<<g, FORCE_BLOCK, 0, st>>>(v);
+  } else {
+    if (mode) k_force<double, 1><<<g, FORCE_BLOCK, 0, st>>>(v);
+    else k_force<double, 0><<<g, FORCE_BLOCK, 0, st>>>(v);
+  }
+}
+
+}  // namespace rb

@@ -1,0 +1,189 @@
+// Internal definitions of the GB300 RBSOG + RBL library: the device view of a
+// context (all device pointers and per-system scalars passed by value to every
+// kernel), device helpers (Philox4x32-10, fixed-point phases, the FP32 list
+// predicate), pair-parameter records and the kernel launchers of each
+// translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rbsog.h"
+
+namespace rb {
+
+constexpr double KE = 14.3996454784;     // eV * Angstrom / e^2
+constexpr double FCONV = 9648.53321;     // (eV/A)/amu -> A/ps^2
+constexpr double KBOLTZ = 8.617333262e-5;  // eV/K
+
+constexpr int NT_TAB = 512;        // intervals of the FP32 SOG tables on [0, r_shell^2]
+constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
+constexpr int RHO_BLOCK = 256;     // threads per block of the structure-factor kernel
+constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernel
+constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernel
+constexpr int FORCE_KCHUNK = 512;  // k-vectors staged in shared memory per chunk
+constexpr int STENCIL = 5;         // cells per axis in the neighbour stencil (cell >= r_shell/2)
+
+// device error bits (latched with atomicOr)
+constexpr int ERR_CORE_CAP = 1;
+constexpr int ERR_CELL_SHELL_CAP = 2;
+constexpr int ERR_PR_CAP = 4;
+
+// Pair record, mixed precision: force phi(r) r_ij with
+//   phi = kqq (1/r^3 - G(r^2)) + Ar/r * 2^((sig - r) lr) - (C6 + D8/r^2)/r^8
+// and pair energy kqq (1/r - F(r^2)) + A 2^((sig - r) lr) - (C + D/r^2)/r^6.
+struct PairF {
+  float kqq, Ar, lr, sig;
+  float C6, D8, A, C;
+  float D, pad0, pad1, pad2;
+};
+// Pair record, FP64: the Eq. (BMH) parameters and k_e q_i q_j.
+struct PairD {
+  double kqq, A, sig, rho, C, D;
+};
+
+// Everything a kernel needs, by value.
+struct View {
+  int64_t n;
+  int ns, M, prec, whole_shell;
+  int P_R, P_F, P;        // P = modes in use (P_F, or the fixed list length)
+  int fixed_k;
+  int integ;
+  uint64_t seed;
+  double L[3], invL[3], V;
+  float hp[3];            // fl32(L * 2^-23): predicate scale (23-bit coordinates)
+  float hf[3];            // fl32(L * 2^-32): mixed force scale of the low bits
+  double hd[3];           // L * 2^-32
+  double kunit[3];        // 2 pi / L
+  float rc2f, rs2f;
+  int nc[3], ncell, small;
+  float tscale;           // NT_TAB / r_shell^2
+  double S;
+  double dt, c1;
+  double qs[RBSOG_MAX_SPECIES];
+  double kick[RBSOG_MAX_SPECIES];    // 0.5 dt FCONV / m
+  double sig_ou[RBSOG_MAX_SPECIES];  // sqrt((1 - c1^2) kT FCONV / m)
+  int G;                  // M + 1
+  int ntile, tile_atoms, nblk_atoms, nblk_kq, nblk_near;
+  // per-atom state, caller order ([3][n] SoA)
+  double *x, *v;
+  float *Ff, *FNf, *FFf;
+  double *Fd, *FNd, *FFd;
+  const int *spc;         // [n] species
+  uint4 *ua;              // [n] (u_x, u_y, u_z, species)
+  int *cellid;            // [n]
+  // binning
+  int *cell_count, *cell_start, *cell_cursor;
+  int *perm_tmp, *perm, *slot_of;
+  float4 *sv;             // [n] sorted (v_x, v_y, v_z as exact floats, species bits)
+  uint4 *su;              // [n] sorted (u_x, u_y, u_z, caller id)
+  double *near_part;      // [nblk_near][4]: sum F_N (x,y,z), sum pair energy
+  // far field
+  int4 *km;               // [Pmax] lattice vectors m
+  double *kc;             // [Pmax] weights c_p
+  double *rho_part;       // [P][ntile][2]
+  double *rho;            // [P][2]
+  double *uf;             // [P] c_p |rho_p|^2
+  float4 *kff;            // [Pmax] mixed (k_x, k_y, k_z, c_p Im rho_p)
+  float *kfB;             // [Pmax] mixed c_p Re rho_p
+  double *kfd;            // [Pmax][5] FP64 (k_x, k_y, k_z, c Im rho, c Re rho)
+  double *red;            // [8]: F^corr (3), U_N, U_F*, spare
+  int *err;
+  long long *step;
+  // tables
+  const PairF *pf;        // [ns*ns]
+  const PairD *pd;        // [ns*ns]
+  const double *sog_wa;   // [M+1] w_m / a_m
+  const double *sog_w;    // [M+1] w_m
+  const double *sog_h;    // [M+1] 1 / (2 a_m)
+  const float4 *gtab;     // [NT_TAB] cubic of G(x) = sum w_m/a_m e^{-x/(2 a_m)}
+  const float4 *ftab;     // [NT_TAB] cubic of F(x) = sum w_m e^{-x/(2 a_m)}
+  const unsigned long long *cmix;  // [3G]
+  const unsigned long long *cdf;   // flat 1-D CDFs
+  const int *cdf_off0, *cdf_off2, *cdf_nmax;  // [3G]
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32 multiplies
+// (0xD2511F53, 0xCD9E8D57) with the key bumped by the Weyl constants.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Draw of the method: counter (index, step_lo, step_hi, stream << 24 | block),
+// key = seed.  Streams: 0 shell batch, 1 k-batch, 2 Langevin noise.
+__device__ __forceinline__ uint4 draw(uint64_t seed, long long step, uint32_t index,
+                                      uint32_t stream, uint32_t block) {
+  const unsigned long long st = (unsigned long long)step;
+  return philox(make_uint4(index, (uint32_t)st, (uint32_t)(st >> 32), (stream << 24) | block),
+                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Exact int -> float for |x| < 2^22 with one integer add and one float add.
+__device__ __forceinline__ float i2f_small(int x) {
+  return __int_as_float(x + 0x4B400000) - 12582912.0f;
+}
+
+// 32-bit fixed-point fractional coordinate floor(frac(x / L) 2^32).
+__device__ __forceinline__ uint32_t fixed_point(double x, double invL) {
+  const double t = __dmul_rn(x, invL);
+  const double y = floor(__dmul_rn(t, 4294967296.0));
+  return (uint32_t)(unsigned long long)(long long)y;
+}
+
+// cell index of a fixed-point coordinate on an axis with nc cells
+__device__ __forceinline__ int cell_of(uint32_t u, int nc) {
+  return (int)(((unsigned long long)u * (unsigned long long)nc) >> 32);
+}
+
+// FP32 list predicate: r^2 from exact 23-bit differences (as floats) d_a.
+__device__ __forceinline__ float pred_r2(float dx, float dy, float dz, const float hp[3]) {
+  const float ax = __fmul_rn(dx, hp[0]);
+  const float ay = __fmul_rn(dy, hp[1]);
+  const float az = __fmul_rn(dz, hp[2]);
+  float r2 = __fmul_rn(ax, ax);
+  r2 = __fmaf_rn(ay, ay, r2);
+  r2 = __fmaf_rn(az, az, r2);
+  return r2;
+}
+
+// 23-bit minimum-image difference v_j - v_i (sign-extended), exact.
+__device__ __forceinline__ int wrap23(uint32_t uj, uint32_t ui) {
+  return ((int)(((uj >> 9) - (ui >> 9)) << 9)) >> 9;
+}
+
+// 64-bit CDF pick: #{i < len-1 : C[i] <= U} by binary search.
+__device__ __forceinline__ int cdf_pick(const unsigned long long *C, int len, unsigned long long U) {
+  int lo = 0, hi = len - 1;  // answer in [0, len-1]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (C[mid] <= U) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (one translation unit each).
+// MODE: 0 = evaluate only, 1 = velocity Verlet step, 2 = BAOAB step.
+void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off);
+void launch_bin(const View &v, cudaStream_t st);
+void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
+void launch_rho(const View &v, cudaStream_t st);
+void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy);
+void launch_force(const View &v, cudaStream_t st, int mode);
+void launch_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
+                  int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
+                  int *batch, int *nbatch, double *weight);
+void launch_aos_to_soa(const double *aos, double *soa, int64_t n, cudaStream_t st);
+void launch_soa_to_aos_d(const double *soa, double *aos, int64_t n, cudaStream_t st);
+void launch_soa_to_aos_f(const float *soa, double *aos, int64_t n, cudaStream_t st);
+
+}  // namespace rb

@@ -1,0 +1,304 @@
+"""ctypes binding of ``librbsog.so`` (the C ABI declared in ``include/rbsog.h``).
+
+Argument marshalling only: every stage of the force evaluation and MD step
+runs in the library's CUDA kernels.  Host arrays are numpy (``ptr_kind`` =
+HOST); device arrays are torch CUDA tensors (``ptr_kind`` = DEVICE), used for
+device memory and streams only.  If the library has not been built, loading
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64 = 0
+MIXED = 1
+NVE_VV = 0
+LANGEVIN_BAOAB = 1
+PTR_HOST = 0
+PTR_DEVICE = 1
+
+MAX_PR = 64
+
+ERRORS = {
+    -1: "RBSOG_E_INVAL", -2: "RBSOG_E_NONNEUTRAL", -3: "RBSOG_E_BOX_TOO_SMALL",
+    -4: "RBSOG_E_CAP_OVERFLOW", -5: "RBSOG_E_CUDA", -6: "RBSOG_E_TIMEOUT",
+    -7: "RBSOG_E_NO_SOG_ROOT", -8: "RBSOG_E_NO_SYSTEM",
+}
+
+EXPORTS = [
+    "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
+    "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
+    "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_set_profiling",
+    "rbsog_get_stage_times", "rbsog_last_error",
+]
+NSTAGE = 6
+STAGES = ["prepare", "bin", "near", "rho", "reduce", "force"]
+
+
+class RbsogError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("b", ctypes.c_double), ("M", ctypes.c_int32), ("s", ctypes.c_double), ("w0", ctypes.c_double),
+        ("r_core", ctypes.c_double), ("r_shell", ctypes.c_double),
+        ("P_R", ctypes.c_int32), ("P_F", ctypes.c_int32), ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
+        ("dt", ctypes.c_double), ("T", ctypes.c_double), ("gamma", ctypes.c_double),
+    ]
+
+
+@dataclasses.dataclass
+class MethodParams:
+    b: float = 1.3
+    M: int = 64
+    s: float = 0.0          # <= 0: solve with w0 for C^1 at r_shell
+    w0: float = 0.0
+    r_core: float = 6.0
+    r_shell: float = 12.0
+    P_R: int = 20
+    P_F: int = 500
+    seed: int = 1
+    precision: int = MIXED
+    integrator: int = LANGEVIN_BAOAB
+    dt: float = 0.001
+    T: float = 1200.0
+    gamma: float = 1.0
+
+    def c(self):
+        p = Params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load librbsog.so (built by ``paper_2512_24970_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("librbsog.so is not built (%s): run paper_2512_24970_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    I32, I64 = ctypes.c_int32, ctypes.c_int64
+    L.rbsog_create.argtypes = [ctypes.POINTER(P), I, P]
+    L.rbsog_destroy.argtypes = [P]
+    L.rbsog_destroy.restype = None
+    L.rbsog_set_system.argtypes = [P, I64, P, P, I32, P, P, P, P, ctypes.POINTER(Params), I]
+    L.rbsog_set_velocities.argtypes = [P, P, I]
+    L.rbsog_compute_forces.argtypes = [P, P, P, P, I]
+    L.rbsog_step.argtypes = [P, I64]
+    L.rbsog_get_state.argtypes = [P, P, P, P, I]
+    L.rbsog_set_state.argtypes = [P, P, P, I64, I]
+    L.rbsog_sync.argtypes = [P]
+    L.rbsog_get_sog.argtypes = [P, P, P, P]
+    L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
+    L.rbsog_debug_get_kbatch.argtypes = [P, P, P]
+    L.rbsog_debug_set_kbatch.argtypes = [P, I32, P, P]
+    L.rbsog_debug_get_parts.argtypes = [P, P, P, P, P]
+    L.rbsog_debug_set_whole_shell.argtypes = [P, I]
+    L.rbsog_set_profiling.argtypes = [P, I]
+    L.rbsog_get_stage_times.argtypes = [P, P, I32]
+    L.rbsog_last_error.argtypes = [P]
+    L.rbsog_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _ptr_kind(a):
+    """(pointer, kind) of a numpy array (HOST) or a torch CUDA tensor (DEVICE)."""
+    if a is None:
+        return None, PTR_HOST
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data), PTR_HOST
+    # torch tensor
+    if a.is_cuda:
+        return ctypes.c_void_p(a.data_ptr()), PTR_DEVICE
+    return ctypes.c_void_p(a.data_ptr()), PTR_HOST
+
+
+class Context:
+    """One simulation context on one GPU (a thin owner of ``rbsog_ctx*``)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        """``stream``: a cudaStream_t handle (e.g. ``torch.cuda.Stream().cuda_stream``)
+        the library runs on; None/0 = a library-owned stream ordered with the
+        legacy default stream."""
+        self._L = load()
+        if stream is None:
+            stream = 0
+        h = ctypes.c_void_p()
+        rc = self._L.rbsog_create(ctypes.byref(h), device, ctypes.c_void_p(stream))
+        if rc != 0:
+            raise RbsogError(rc, "rbsog_create failed")
+        self.h = h
+        self.n = 0
+        self.params = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.rbsog_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise RbsogError(rc, self._L.rbsog_last_error(self.h).decode())
+
+    # ------------------------------------------------------------------
+    def set_system(self, pos, species, charge, mass, bmh, box, params: MethodParams):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        charge = np.ascontiguousarray(charge, dtype=np.float64)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        bmh = np.ascontiguousarray(bmh, dtype=np.float64)
+        box = np.ascontiguousarray(box, dtype=np.float64)
+        p = params.c()
+        self._ck(self._L.rbsog_set_system(self.h, pos.shape[0], _np_ptr(pos), _np_ptr(species), charge.size,
+                                          _np_ptr(charge), _np_ptr(mass), _np_ptr(bmh), _np_ptr(box),
+                                          ctypes.byref(p), PTR_HOST))
+        self.n = pos.shape[0]
+        self.params = params
+        return self
+
+    def set_workload(self, w, params: MethodParams):
+        self.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, params)
+        if w.vel is not None:
+            self.set_velocities(w.vel)
+        return self
+
+    def set_velocities(self, vel):
+        if isinstance(vel, np.ndarray):
+            vel = np.ascontiguousarray(vel, dtype=np.float64)
+        ptr, kind = _ptr_kind(vel)
+        self._ck(self._L.rbsog_set_velocities(self.h, ptr, kind))
+
+    def compute_forces(self, forces=None, energy=False):
+        """Forces [n,3] FP64 (numpy unless ``forces`` is a CUDA tensor to fill)
+        and, if ``energy``, the energy 4-vector."""
+        out = np.zeros((self.n, 3)) if forces is None else forces
+        ptr, kind = _ptr_kind(out)
+        e = np.zeros(4) if energy else None
+        self._ck(self._L.rbsog_compute_forces(self.h, ptr, _np_ptr(e) if energy and kind == PTR_HOST else None,
+                                              None, kind))
+        if energy and kind == PTR_DEVICE:
+            raise ValueError("energy output with device forces: call again with host arrays")
+        return (out, e) if energy else out
+
+    def step(self, nsteps: int):
+        self._ck(self._L.rbsog_step(self.h, int(nsteps)))
+
+    def get_state(self, pos=None, vel=None):
+        pos = np.zeros((self.n, 3)) if pos is None else pos
+        vel = np.zeros((self.n, 3)) if vel is None else vel
+        pp, kind = _ptr_kind(pos)
+        vp, _ = _ptr_kind(vel)
+        st = ctypes.c_int64()
+        self._ck(self._L.rbsog_get_state(self.h, pp, vp, ctypes.byref(st), kind))
+        return pos, vel, st.value
+
+    def set_state(self, pos=None, vel=None, step=0):
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
+        if isinstance(vel, np.ndarray):
+            vel = np.ascontiguousarray(vel, dtype=np.float64)
+        pp, kind = _ptr_kind(pos)
+        vp, kind2 = _ptr_kind(vel)
+        if pos is None:
+            kind = kind2
+        self._ck(self._L.rbsog_set_state(self.h, pp, vp, int(step), kind))
+
+    def sync(self):
+        self._ck(self._L.rbsog_sync(self.h))
+
+    def sog(self):
+        M = self.params.M
+        s = ctypes.c_double()
+        S = ctypes.c_double()
+        w = np.zeros(M + 1)
+        self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
+        return s.value, w, S.value
+
+    # ---- parity hooks -----------------------------------------------------
+    def debug_lists(self, sel, cap_core=128, cap_shell=512, batch=True):
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        k = sel.size
+        core = np.full((k, cap_core), -1, dtype=np.int32)
+        ncore = np.zeros(k, dtype=np.int32)
+        shell = np.full((k, cap_shell), -1, dtype=np.int32)
+        nshell = np.zeros(k, dtype=np.int32)
+        PR = self.params.P_R
+        bt = np.full((k, PR), -1, dtype=np.int32) if batch else None
+        nb = np.zeros(k, dtype=np.int32) if batch else None
+        wt = np.zeros(k) if batch else None
+        self._ck(self._L.rbsog_debug_get_lists(self.h, _np_ptr(sel), k, cap_core, cap_shell, _np_ptr(core),
+                                               _np_ptr(ncore), _np_ptr(shell), _np_ptr(nshell), _np_ptr(bt),
+                                               _np_ptr(nb), _np_ptr(wt)))
+        out = dict(core=core, ncore=ncore, shell=shell, nshell=nshell)
+        if batch:
+            out.update(batch=bt, nbatch=nb, weight=wt)
+        return out
+
+    def debug_kbatch(self, P=None):
+        P = self.params.P_F if P is None else P
+        m = np.zeros((P, 3), dtype=np.int32)
+        c = np.zeros(P)
+        self._ck(self._L.rbsog_debug_get_kbatch(self.h, _np_ptr(m), _np_ptr(c)))
+        return m, c
+
+    def debug_set_kbatch(self, m=None, c=None):
+        if m is None:
+            self._ck(self._L.rbsog_debug_set_kbatch(self.h, 0, None, None))
+            return
+        m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self._ck(self._L.rbsog_debug_set_kbatch(self.h, m.shape[0], _np_ptr(m), _np_ptr(c)))
+
+    def debug_parts(self, P=None):
+        P = self.params.P_F if P is None else P
+        near = np.zeros((self.n, 3))
+        far = np.zeros((self.n, 3))
+        fc = np.zeros(3)
+        rho = np.zeros((P, 2))
+        self._ck(self._L.rbsog_debug_get_parts(self.h, _np_ptr(near), _np_ptr(far), _np_ptr(fc), _np_ptr(rho)))
+        return dict(near=near, far=far, Fcorr=fc, rho=rho)
+
+    def set_profiling(self, on: bool):
+        self._ck(self._L.rbsog_set_profiling(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        ms = np.zeros(NSTAGE, dtype=np.float32)
+        self._ck(self._L.rbsog_get_stage_times(self.h, _np_ptr(ms), NSTAGE))
+        return ms
+
+    def debug_whole_shell(self, flag: bool):
+        self._ck(self._L.rbsog_debug_set_whole_shell(self.h, 1 if flag else 0))

@@ -188,6 +188,11 @@ int rbsog_debug_set_kbatch(rbsog_ctx *ctx, int32_t P, const int32_t *m, const do
 int rbsog_debug_get_parts(rbsog_ctx *ctx, double *near, double *far, double *fcorr,
                           double *rho);
 
+/* FP32 phase factors of the mixed-precision far field: s[i], c[i] = sin, cos
+ * of 2 pi th[i] / 2^32 evaluated by the device routine the structure-factor
+ * and far-force kernels use.  Host pointers; needs a context for its device. */
+int rbsog_debug_sincos(rbsog_ctx *ctx, int64_t n, const uint32_t *th, float *s, float *c);
+
 /* Take the whole shell with weight 1 for every atom (flag != 0), i.e. the
  * deterministic r_shell-cutoff near field; 0 restores the P_R batch. */
 int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag);

@@ -102,19 +102,23 @@ int check_launch(rbsog_ctx *ctx) {
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
   cudaStream_t st = ctx->st;
   const bool pr = ctx->profiling;
-  if (pr) CK(cudaEventRecord(ctx->prof[0], st));
+  // inside stream capture the stage events must become event-record nodes
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (pr) CK(cudaStreamIsCapturing(st, &cap));
+  const unsigned evflag = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[0], st, evflag));
   rb::launch_prepare(v, st, mode, step_off);
-  if (pr) CK(cudaEventRecord(ctx->prof[1], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[1], st, evflag));
   rb::launch_bin(v, st);
-  if (pr) CK(cudaEventRecord(ctx->prof[2], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[2], st, evflag));
   rb::launch_near(v, st, step_off, energy);
-  if (pr) CK(cudaEventRecord(ctx->prof[3], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[3], st, evflag));
   rb::launch_rho(v, st);
-  if (pr) CK(cudaEventRecord(ctx->prof[4], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st, evflag));
   rb::launch_reduce(v, st, step_off, energy);
-  if (pr) CK(cudaEventRecord(ctx->prof[5], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[5], st, evflag));
   rb::launch_force(v, st, mode);
-  if (pr) CK(cudaEventRecord(ctx->prof[6], st));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[6], st, evflag));
   return check_launch(ctx);
 }
 
@@ -609,6 +613,9 @@ int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int3
     CK(cudaMalloc(&dnb, sizeof(int) * k));
     CK(cudaMalloc(&dw, sizeof(double) * k));
   }
+  CK(cudaMemsetAsync(dcore, 0xFF, sizeof(int) * k * cap_core, ctx->st));   // pad rows with -1
+  CK(cudaMemsetAsync(dshell, 0xFF, sizeof(int) * k * cap_shell, ctx->st));
+  if (batch) CK(cudaMemsetAsync(dbatch, 0xFF, sizeof(int) * k * v.P_R, ctx->st));
   std::vector<long long> hs(sel, sel + k);
   CK(cudaMemcpyAsync(dsel, hs.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, ctx->st));
   rb::launch_lists(v, ctx->st, 0, dsel, (int)nsel, cap_core, cap_shell, dcore, dnc, dshell, dns, dbatch,
@@ -709,6 +716,24 @@ int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag) {
   ctx->v.whole_shell = flag ? 1 : 0;
   ctx->graph_ok = false;
   ctx->forces_valid = false;
+  return RBSOG_OK;
+}
+
+int rbsog_debug_sincos(rbsog_ctx *ctx, int64_t n, const uint32_t *th, float *s, float *c) {
+  if (!ctx || n < 1 || !th || !s || !c) return fail(ctx, RBSOG_E_INVAL, "bad sincos arguments");
+  CK(cudaSetDevice(ctx->dev));
+  uint32_t *dt = nullptr;
+  float *ds = nullptr, *dc = nullptr;
+  CK(cudaMalloc(&dt, sizeof(uint32_t) * n));
+  CK(cudaMalloc(&ds, sizeof(float) * n));
+  CK(cudaMalloc(&dc, sizeof(float) * n));
+  CK(cudaMemcpyAsync(dt, th, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  rb::launch_sincos(n, dt, ds, dc, ctx->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s, ds, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(c, dc, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  cudaFree(dt); cudaFree(ds); cudaFree(dc);
   return RBSOG_OK;
 }
 

@@ -1,8 +1,8 @@
 // Stage (d) far field and stage (e) second half (Sec. 2.2, Eq. (long-rangeforce)):
 //   k_rho     structure-factor partials rho(k_p) = sum_j q_j e^{i k_p . r_j} over
 //             an atom tile, phase k . r = 2 pi (m . u mod 2^32) / 2^32 reduced
-//             exactly in uint32; FP32 MUFU sincos with FP32 accumulation over
-//             at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
+//             exactly in uint32; FP32 polynomial sincos with FP32 accumulation
+//             over at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
 //   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
 //             force coefficients c_p Im rho_p, c_p Re rho_p, and F^corr.
 //   k_force   F_i = F_N,i - F^corr - (k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p),
@@ -12,12 +12,17 @@
 namespace rb {
 
 constexpr double TWO_PI = 6.283185307179586;
-constexpr float ANG23 = 7.490115661286456e-07f;  // 2 pi / 2^23
+constexpr float ANG23 = (float)(TWO_PI / 8388608.0);  // 2 pi / 2^23
 
-// Mixed phase: int32(theta + 2^8) >> 9 in [-2^22, 2^22) -> radians in [-pi, pi).
+// Mixed phase e^{i 2 pi th / 2^32}: FP32 polynomial with exact quarter-turn
+// reduction (RB_MUFU_TRIG selects the hardware approximation for experiments).
 __device__ __forceinline__ void sincos_phase_f(uint32_t th, float &s, float &c) {
+#ifdef RB_MUFU_TRIG
   const int xs = ((int)(th + 256u)) >> 9;
   __sincosf(i2f_small(xs) * ANG23, &s, &c);
+#else
+  sincos_turn(th, s, c);
+#endif
 }
 __device__ __forceinline__ void sincos_phase_d(uint32_t th, double &s, double &c) {
   sincospi((double)(int)th * 4.656612873077393e-10, &s, &c);  // * 2^-31
@@ -235,6 +240,18 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
       p.v[a * n + i] += kick * Fa;
     }
   }
+}
+
+__global__ void k_sincos(int64_t n, const uint32_t *th, float *s, float *c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a, b;
+  sincos_phase_f(th[i], a, b);
+  s[i] = a;
+  c[i] = b;
+}
+void launch_sincos(int64_t n, const uint32_t *th, float *s, float *c, cudaStream_t st) {
+  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, th, s, c);
 }
 
 void launch_rho(const View &v, cudaStream_t st) {

@@ -35,7 +35,7 @@ EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
-    "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_set_profiling",
+    "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error",
 ]
 NSTAGE = 6
@@ -117,6 +117,7 @@ def load():
     L.rbsog_debug_set_kbatch.argtypes = [P, I32, P, P]
     L.rbsog_debug_get_parts.argtypes = [P, P, P, P, P]
     L.rbsog_debug_set_whole_shell.argtypes = [P, I]
+    L.rbsog_debug_sincos.argtypes = [P, I64, P, P, P]
     L.rbsog_set_profiling.argtypes = [P, I]
     L.rbsog_get_stage_times.argtypes = [P, P, I32]
     L.rbsog_last_error.argtypes = [P]
@@ -299,6 +300,13 @@ class Context:
         ms = np.zeros(NSTAGE, dtype=np.float32)
         self._ck(self._L.rbsog_get_stage_times(self.h, _np_ptr(ms), NSTAGE))
         return ms
+
+    def debug_sincos(self, th):
+        th = np.ascontiguousarray(th, dtype=np.uint32)
+        s = np.zeros(th.size, dtype=np.float32)
+        c = np.zeros(th.size, dtype=np.float32)
+        self._ck(self._L.rbsog_debug_sincos(self.h, th.size, _np_ptr(th), _np_ptr(s), _np_ptr(c)))
+        return s, c
 
     def debug_whole_shell(self, flag: bool):
         self._ck(self._L.rbsog_debug_set_whole_shell(self.h, 1 if flag else 0))

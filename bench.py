@@ -245,7 +245,7 @@ def run_ours(args):
     nsm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    dom = int(np.argmax(stage_ms))
+    dom = int(np.argmax(stage_ms[:-1]))
     N, P = w.n, P_F
     if names[dom] in ("rho", "force"):
         ops = 2.0 * N * P            # one MUFU sin + one MUFU cos per (atom, k)

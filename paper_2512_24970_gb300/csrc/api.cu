@@ -38,7 +38,9 @@ struct rbsog_ctx {
   bool graph_ok = false;
   bool own_stream = false;
   bool profiling = false;
-  cudaEvent_t prof[RBSOG_NSTAGE + 1] = {};
+  cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t prof[9] = {};  // stage boundaries, see rbsog_get_stage_times
 };
 
 namespace {
@@ -99,26 +101,35 @@ int check_launch(rbsog_ctx *ctx) {
 }
 
 // One force evaluation; mode 0 = evaluate, 1 = VV step, 2 = BAOAB step.
+// The structure-factor kernel needs only the prepared coordinates and the
+// k-batch, so it runs on a side stream concurrently with binning and the
+// near field (two branches of the captured step graph).
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
-  cudaStream_t st = ctx->st;
+  cudaStream_t st = ctx->st, st2 = ctx->st2;
   const bool pr = ctx->profiling;
   // inside stream capture the stage events must become event-record nodes
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (pr) CK(cudaStreamIsCapturing(st, &cap));
+  CK(cudaStreamIsCapturing(st, &cap));
   const unsigned evflag = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[0], st, evflag));
   rb::launch_prepare(v, st, mode, step_off);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[1], st, evflag));
+  CK(cudaEventRecord(ctx->ev_fork, st));
+  CK(cudaStreamWaitEvent(st2, ctx->ev_fork, 0));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[3], st2, evflag));
+  rb::launch_rho(v, st2);
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st2, evflag));
+  CK(cudaEventRecord(ctx->ev_join, st2));
   rb::launch_bin(v, st);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[2], st, evflag));
   rb::launch_near(v, st, step_off, energy);
-  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[3], st, evflag));
-  rb::launch_rho(v, st);
-  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st, evflag));
-  rb::launch_reduce(v, st, step_off, energy);
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[7], st, evflag));
+  CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[5], st, evflag));
-  rb::launch_force(v, st, mode);
+  rb::launch_reduce(v, st, step_off, energy);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[6], st, evflag));
+  rb::launch_force(v, st, mode);
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[8], st, evflag));
   return check_launch(ctx);
 }
 
@@ -224,7 +235,10 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
-  for (int k = 0; k <= RBSOG_NSTAGE && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
+  for (int k = 0; k < 9 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     rbsog_destroy(ctx);
     return RBSOG_E_CUDA;
@@ -237,11 +251,15 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->dev);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  if (ctx->st2) cudaStreamSynchronize(ctx->st2);
   free_system(ctx);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
-  for (int k = 0; k <= RBSOG_NSTAGE; k++)
+  for (int k = 0; k < 9; k++)
     if (ctx->prof[k]) cudaEventDestroy(ctx->prof[k]);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
 }
@@ -261,7 +279,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   if (ptr_kind != RBSOG_PTR_HOST && ptr_kind != RBSOG_PTR_DEVICE)
     return fail(ctx, RBSOG_E_INVAL, "bad ptr_kind");
   const rbsog_params P = *params;
-  if (n < 2 || n > (int64_t)0x7fffffff) return fail(ctx, RBSOG_E_INVAL, "n out of range");
+  if (n < 2 || n > (int64_t)rb::SU_ID_MASK) return fail(ctx, RBSOG_E_INVAL, "n out of range (2 .. 2^28 - 1)");
   if (n_species < 1 || n_species > RBSOG_MAX_SPECIES) return fail(ctx, RBSOG_E_INVAL, "n_species out of range");
   if (!(P.b > 1.0) || P.M < 1 || P.M > RBSOG_MAX_M) return fail(ctx, RBSOG_E_INVAL, "SOG b/M out of range");
   if (!(P.r_core > 0.0) || !(P.r_shell > P.r_core)) return fail(ctx, RBSOG_E_INVAL, "need 0 < r_core < r_shell");
@@ -362,7 +380,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   }
   v.nblk_atoms = (int)((n + 255) / 256);
   v.nblk_kq = (P.P_F + 255) / 256;
-  v.nblk_near = (int)((n + rb::NEAR_BLOCK - 1) / rb::NEAR_BLOCK);
+  // chunks <= n / NEAR_CHUNK + rows; one warp per chunk
+  v.nblk_near = (int)(((n + rb::NEAR_CHUNK - 1) / rb::NEAR_CHUNK + (int64_t)v.nc[1] * v.nc[2] + rb::NEAR_WARPS - 1) / rb::NEAR_WARPS);
   set_rho_tiling(ctx, P.P_F);
   // self term U_F^self = k_e/2 sum_i q_i^2 F(0)
   double F0 = 0.0, q2 = 0.0;
@@ -384,7 +403,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &spc_d, N)) || (rc = dalloc(ctx, &v.ua, N)) || (rc = dalloc(ctx, &v.cellid, N)) ||
       (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
       (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, N)) ||
-      (rc = dalloc(ctx, &v.perm, N)) || (rc = dalloc(ctx, &v.slot_of, N)) || (rc = dalloc(ctx, &v.sv, N)) ||
+      (rc = dalloc(ctx, &v.perm, N)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
+      (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) || (rc = dalloc(ctx, &v.sv, N)) ||
       (rc = dalloc(ctx, &v.su, N)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
       (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
@@ -750,9 +770,11 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage) {
   if (!ctx || !ms || nstage < 1) return RBSOG_E_INVAL;
   if (!ctx->profiling) return fail(ctx, RBSOG_E_INVAL, "profiling is off");
   CK(cudaSetDevice(ctx->dev));
-  CK(cudaEventSynchronize(ctx->prof[RBSOG_NSTAGE]));
-  for (int k = 0; k < nstage && k < RBSOG_NSTAGE; k++)
-    CK(cudaEventElapsedTime(ms + k, ctx->prof[k], ctx->prof[k + 1]));
+  CK(cudaEventSynchronize(ctx->prof[8]));
+  // (start, end) event of each stage: prepare, bin, near, rho, reduce, force, total
+  static const int b[7] = {0, 1, 2, 3, 5, 6, 0};
+  static const int e[7] = {1, 2, 7, 4, 6, 8, 8};
+  for (int k = 0; k < nstage && k < 7; k++) CK(cudaEventElapsedTime(ms + k, ctx->prof[b[k]], ctx->prof[e[k]]));
   return RBSOG_OK;
 }
 

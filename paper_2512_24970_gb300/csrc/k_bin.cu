@@ -64,6 +64,23 @@ __device__ __forceinline__ void noise3(const View &p, long long s, uint32_t i, d
   g[2] = r1 * c1;
 }
 
+// Mixed precision: the same Box-Muller transform in FP32 (FP64 transcendental
+// throughput is low on this part; the noise needs no more than FP32).
+__device__ __forceinline__ void noise3f(const View &p, long long s, uint32_t i, double g[3]) {
+  const uint4 w = draw(p.seed, s, i, 2u, 0u);
+  const float u0 = ((float)(w.x >> 8) + 0.5f) * 5.9604645e-08f;  // 24-bit uniforms in (0, 1)
+  const float u1 = ((float)(w.y >> 8) + 0.5f) * 5.9604645e-08f;
+  const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604645e-08f;
+  const float u3 = ((float)(w.w >> 8) + 0.5f) * 5.9604645e-08f;
+  const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+  float s0, c0, s1, c1;
+  sincospif(2.0f * u1, &s0, &c0);
+  sincospif(2.0f * u3, &s1, &c1);
+  g[0] = r0 * c0;
+  g[1] = r0 * s0;
+  g[2] = r1 * c1;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   const long long s = *p.step + step_off;
@@ -90,7 +107,8 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
       for (int a = 0; a < 3; a++) x[a] += p.dt * v[a];
     } else {
       double g[3];
-      noise3(p, s, (uint32_t)i, g);
+      if (p.prec == RBSOG_FP64) noise3(p, s, (uint32_t)i, g);
+      else noise3f(p, s, (uint32_t)i, g);
       const double h = 0.5 * p.dt, so = p.sig_ou[sp];
       for (int a = 0; a < 3; a++) {
         x[a] += h * v[a];
@@ -143,6 +161,42 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
     run += p.cell_count[c];
   }
   if (t == nt - 1) p.cell_start[p.ncell] = (int)p.n;
+  // Chunks of the near-field kernel: the atoms of every row of cells (fixed
+  // y and z) are cut into runs of NEAR_CHUNK consecutive sorted atoms;
+  // row_chunk[r] is the first chunk of row r (exclusive scan).
+  __syncthreads();
+  const int nrow = p.nc[1] * p.nc[2];
+  const int rper = (nrow + nt - 1) / nt;
+  const int rb = t * rper, re = min(rb + rper, nrow);
+  int lc = 0;
+  for (int r = rb; r < re; r++) {
+    const int na = p.cell_start[(r + 1) * p.nc[0]] - p.cell_start[r * p.nc[0]];
+    lc += (na + NEAR_CHUNK - 1) / NEAR_CHUNK;
+  }
+  int inc = lc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if ((t & 31) >= o) inc += y;
+  }
+  __syncthreads();
+  if ((t & 31) == 31) wsum[t >> 5] = inc;
+  __syncthreads();
+  if (t < 32) {
+    int w = (t < (nt >> 5)) ? wsum[t] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (t >= o) w += y;
+    }
+    wsum[t] = w;
+  }
+  __syncthreads();
+  int rr = inc - lc + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
+  for (int r = rb; r < re; r++) {
+    p.row_chunk[r] = rr;
+    const int na = p.cell_start[(r + 1) * p.nc[0]] - p.cell_start[r * p.nc[0]];
+    rr += (na + NEAR_CHUNK - 1) / NEAR_CHUNK;
+  }
+  if (t == nt - 1) p.row_chunk[nrow] = rr;
 }
 
 __global__ void __launch_bounds__(256) k_scatter(View p) {
@@ -173,7 +227,7 @@ __global__ void __launch_bounds__(256) k_cellsort(View p) {
     p.perm[slot] = id;
     p.slot_of[id] = slot;
     p.sv[slot] = make_float4((float)(u.x >> 9), (float)(u.y >> 9), (float)(u.z >> 9), __int_as_float((int)u.w));
-    p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)id);
+    p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)id | (u.w << SU_SP_SHIFT));
   }
 }
 

@@ -12,12 +12,12 @@
 namespace rb {
 
 constexpr double TWO_PI = 6.283185307179586;
-constexpr float ANG23 = (float)(TWO_PI / 8388608.0);  // 2 pi / 2^23
 
 // Mixed phase e^{i 2 pi th / 2^32}: FP32 polynomial with exact quarter-turn
 // reduction (RB_MUFU_TRIG selects the hardware approximation for experiments).
 __device__ __forceinline__ void sincos_phase_f(uint32_t th, float &s, float &c) {
 #ifdef RB_MUFU_TRIG
+  constexpr float ANG23 = (float)(TWO_PI / 8388608.0);  // 2 pi / 2^23
   const int xs = ((int)(th + 256u)) >> 9;
   __sincosf(i2f_small(xs) * ANG23, &s, &c);
 #else

@@ -79,8 +79,11 @@ __device__ __forceinline__ void pair_mixed(const View &p, const PairF &q, const 
     d[a] = __fmaf_rn(i2f_small(dl >> 9), p.hp[a], __fmul_rn(i2f_small(dl & 511), p.hf[a]));
   }
   const float x = __fmaf_rn(d[2], d[2], __fmaf_rn(d[1], d[1], d[0] * d[0]));
-  const float r = sqrtf(x);
-  const float rinv = 1.0f / r;
+  // 1/r from the hardware reciprocal square root refined by one Newton step
+  // (relative error ~1 ulp), r = x / r
+  float rinv = rsqrtf(x);
+  rinv = rinv * __fmaf_rn(-0.5f * x * rinv, rinv, 1.5f);
+  const float r = x * rinv;
   const float rinv2 = rinv * rinv;
   const float t = x * p.tscale;
   const int it = min((int)t, NT_TAB - 1);
@@ -153,15 +156,88 @@ __device__ __forceinline__ void floyd(const View &p, long long s, uint32_t id, i
 }
 
 // ---------------------------------------------------------------------------
+// Conservative cell culling: gap (23-bit units) between v_i and the image of
+// cell c of an axis with cell width cw = 2^23 / n, widened by 4 units so that
+// rounding of the cell bounds can only keep a cell, never drop one.
+__device__ __forceinline__ float cell_gap(float vi, int c, float shift, float cw) {
+  const float lo = __fmaf_rn((float)c, cw, shift) - 4.0f;
+  const float hi = __fmaf_rn((float)(c + 1), cw, shift) + 4.0f;
+  return fmaxf(0.0f, fmaxf(lo - vi, vi - hi));
+}
+
+template <typename R>
+struct Acc {
+  R x = 0, y = 0, z = 0, e = 0;
+};
+
+// Pair force of atom i with the sorted candidate uj (species in its top bits).
+template <typename R, bool ENERGY>
+__device__ __forceinline__ void add_pair(const View &p, const PairF *spf, const PairD *spd,
+                                         const float4 *sg, const double *swa, const double *sw,
+                                         const double *sh2, int spi, uint4 ui, uint4 uj, Acc<R> &a) {
+  const int spj = (int)(uj.w >> SU_SP_SHIFT);
+  if (sizeof(R) == 4) {
+    float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    pair_mixed<ENERGY>(p, spf[spi * p.ns + spj], sg, ui, uj, a0, a1, a2, a3);
+    a.x += a0; a.y += a1; a.z += a2; a.e += a3;
+  } else {
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    pair_fp64<ENERGY>(p, spd[spi * p.ns + spj], swa, sw, sh2, ui, uj, a0, a1, a2, a3);
+    a.x += a0; a.y += a1; a.z += a2; a.e += a3;
+  }
+}
+
+// One warp per chunk of NEAR_CHUNK = 8 consecutive sorted atoms of one row of
+// cells (fixed y, z); TPA = 4 threads per atom.  Pass 1 has two forms:
+//  - lockstep (the union of the chunk's x-stencils is at most WMAX cells and
+//    narrower than the box): the warp first caches the candidate ranges of
+//    the 25 rows x W union cells in shared memory; thread g of every atom
+//    walks stencil rows g, g + 4, ... and, in each, the union cells in
+//    ascending index order, so all 8 atoms test the same candidates in the
+//    same order (uniform loops, broadcast loads, four loads in flight); each
+//    atom files a candidate under its own stencil position;
+//  - per atom (otherwise): the atom's own 125 cells dealt round-robin, with
+//    conservative culling of cells beyond r_shell.
+// Both fill the same per-atom state in shared memory: per-cell shell counts
+// (canonical order) and per-thread core lists coded (stencil cell << 8 |
+// offset in cell).  Floyd's set is a bitmask over canonical positions; the
+// sorted samples are mapped to (cell, rank) by one sweep of the counts.
+constexpr int TPA = 4;
+constexpr int APW = NEAR_CHUNK;              // atoms per warp
+constexpr int APB = NEAR_WARPS * NEAR_CHUNK; // atoms per block
+constexpr int CORE_T = 40;                   // core neighbours per thread
+constexpr int SHELL_BITS = 1024;             // canonical shell positions held by the bitmask
+constexpr int WMAX = 8;                      // union x-cells of a lockstep chunk
+static_assert(TPA * NEAR_CHUNK == 32 && NEAR_WARPS * 32 == NEAR_BLOCK, "near-field block layout");
+
+// stencil position (0..4, ascending cell order) of cell x on an axis of n >= 5
+// cells as seen from cell ci, or -1 when x is not among ci's five neighbours
+__device__ __forceinline__ int stencil_pos(int x, const Axis &ax) {
+  int o = x - ax.ci;
+  if (o > ax.n / 2) o -= ax.n;
+  if (o < -(ax.n / 2)) o += ax.n;
+  if (o < -2 || o > 2) return -1;
+  int k = o + 2 - ax.rot;
+  return k < 0 ? k + STENCIL : k;
+}
+
+constexpr float FAR_AWAY = 1e30f;  // padding of a batch of candidates: fails every predicate
+
 template <typename R, bool SMALL, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
-  __shared__ unsigned char cnt[125][NEAR_BLOCK];
-  __shared__ float4 sg[NT_TAB];
-  __shared__ PairF spf[RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
-  __shared__ PairD spd[RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
-  __shared__ double swa[RBSOG_MAX_M + 1], sw[RBSOG_MAX_M + 1], sh2[RBSOG_MAX_M + 1];
-  __shared__ double red[4][NEAR_BLOCK / 32];
   constexpr bool MIX = sizeof(R) == 4;
+  __shared__ unsigned char cnt[125][APB];
+  __shared__ unsigned char scell[APB][RBSOG_MAX_PR];
+  __shared__ unsigned char srank[APB][RBSOG_MAX_PR];
+  __shared__ unsigned short stsel[APB][RBSOG_MAX_PR];
+  __shared__ uint32_t bmask[APB][SHELL_BITS / 32];
+  __shared__ unsigned short score[NEAR_BLOCK][CORE_T];
+  __shared__ int2 crange[NEAR_WARPS][STENCIL * STENCIL][WMAX];
+  __shared__ float4 sg[MIX ? NT_TAB : 1];
+  __shared__ PairF spf[MIX ? RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
+  __shared__ PairD spd[MIX ? 1 : RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
+  __shared__ double swa[MIX ? 1 : RBSOG_MAX_M + 1], sw[MIX ? 1 : RBSOG_MAX_M + 1], sh2[MIX ? 1 : RBSOG_MAX_M + 1];
+  __shared__ double red[4][NEAR_WARPS];
   const int tid = threadIdx.x;
   const int nsp2 = p.ns * p.ns;
   for (int k = tid; k < nsp2; k += NEAR_BLOCK) {
@@ -178,158 +254,308 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   }
   __syncthreads();
   const long long s = *p.step + step_off;
-  const int slot = blockIdx.x * NEAR_BLOCK + tid;
-  R fcx = 0, fcy = 0, fcz = 0, ec = 0;   // core
-  R fsx = 0, fsy = 0, fsz = 0, es = 0;   // shell batch (unweighted)
-  R wgt = 1;
-  if (slot < p.n) {
-    const float4 me = p.sv[slot];
-    const uint4 ui = p.su[slot];
-    const int spi = __float_as_int(me.w);
+  const int warp = tid >> 5, lane = tid & 31;
+  const int a = warp * APW + lane / TPA;      // atom row of the shared arrays
+  const int g = lane % TPA;
+  const int nrow = p.nc[1] * p.nc[2];
+  const int chunk = blockIdx.x * NEAR_WARPS + warp;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  if (chunk < p.row_chunk[nrow]) {
+    // ---- the chunk's row of cells and atoms ------------------------------
+    int lo = 0, hi = nrow - 1;  // last row with row_chunk[row] <= chunk
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.row_chunk[mid] <= chunk) lo = mid; else hi = mid - 1;
+    }
+    const int row = lo;
+    const int rbeg = p.cell_start[row * p.nc[0]], rend = p.cell_start[(row + 1) * p.nc[0]];
+    const int base = rbeg + (chunk - p.row_chunk[row]) * APW;
+    const int cend = min(base + APW, rend);
+    const int slot = base + lane / TPA;
+    const bool active = slot < cend;
+    const float4 me = active ? p.sv[slot] : make_float4(0, 0, 0, 0);
+    const uint4 ui = active ? p.su[slot] : p.su[base];
+    const int spi = (int)(ui.w >> SU_SP_SHIFT);
+    const int cyr = row % p.nc[1], czr = row / p.nc[1];
     const Axis ax = make_axis(cell_of(ui.x, p.nc[0]), p.nc[0]);
-    const Axis ay = make_axis(cell_of(ui.y, p.nc[1]), p.nc[1]);
-    const Axis az = make_axis(cell_of(ui.z, p.nc[2]), p.nc[2]);
+    const Axis ay = make_axis(cyr, p.nc[1]), az = make_axis(czr, p.nc[2]);
     const int nkx = axis_count(ax, SMALL), nky = axis_count(ay, SMALL), nkz = axis_count(az, SMALL);
-    int core[RBSOG_MAX_CORE];
-    int ncore = 0;
-    int nshell = 0;
+    const int cx_lo = cell_of(p.su[base].x, p.nc[0]), cx_hi = cell_of(p.su[cend - 1].x, p.nc[0]);
+    const int W = cx_hi - cx_lo + STENCIL;     // union x-cells of the chunk
+    const bool lock = !SMALL && W <= WMAX && W <= p.nc[0];
+    const int xs = cx_lo - 2;                  // first union cell (may be < 0)
+    Acc<R> fc, fs;
+    R wgt = 1;
+    int my_total = 0, ncore = 0;
     bool over = false;
-    // ---- pass 1 -------------------------------------------------------
-    for (int kz = 0; kz < STENCIL; kz++) {
-      float shz;
-      const int cz = axis_cell(az, kz, SMALL, shz);
-      for (int ky = 0; ky < STENCIL; ky++) {
-        float shy;
-        const int cy = axis_cell(ay, ky, SMALL, shy);
-        const int rowbase = p.nc[0] * (cy + p.nc[1] * cz);
+    if (lock) {
+      // ---- candidate ranges of the union cells, cached per warp --------------
+      for (int it = lane; it < STENCIL * STENCIL * W; it += 32) {
+        const int r = it / W, ux = it - r * W;
+        const int kz = r / STENCIL, ky = r - kz * STENCIL;
+        float sh;
+        const int cz = axis_cell(az, kz, false, sh);
+        const int cy = axis_cell(ay, ky, false, sh);
+        int x = xs + ux;
+        x = x < 0 ? x + p.nc[0] : (x >= p.nc[0] ? x - p.nc[0] : x);
+        const int cell = x + p.nc[0] * (cy + p.nc[1] * cz);
+        crange[warp][r][ux] = make_int2(p.cell_start[cell], p.cell_start[cell + 1]);
+      }
+      __syncwarp();
+      // ---- pass 1, lockstep form ---------------------------------------------
+      const int rot = xs < 0 ? -xs : (cx_hi + 2 >= p.nc[0] ? W - (cx_hi + 2 - p.nc[0] + 1) : 0);
+      for (int r = g; r < STENCIL * STENCIL; r += TPA) {
+        const int kz = r / STENCIL, ky = r - kz * STENCIL;
+        float shz, shy;
+        axis_cell(az, kz, false, shz);
+        axis_cell(ay, ky, false, shy);
         const float iy = me.y - shy, iz = me.z - shz;
-        for (int kx = 0; kx < STENCIL; kx++) {
-          const int cidx = (kz * STENCIL + ky) * STENCIL + kx;
-          if (kz >= nkz || ky >= nky || kx >= nkx) {
-            cnt[cidx][tid] = 0;
-            continue;
-          }
-          float shx;
-          const int cx = axis_cell(ax, kx, SMALL, shx);
-          const int cell = rowbase + cx;
-          const int b = p.cell_start[cell], e = p.cell_start[cell + 1];
+        for (int k = 0; k < W; k++) {
+          int ux = k + rot;
+          ux = ux >= W ? ux - W : ux;           // union index, ascending cell order
+          const int u = xs + ux;
+          int x = u;
+          float shx = 0.0f;
+          if (u < 0) { x = u + p.nc[0]; shx = -8388608.0f; }
+          else if (u >= p.nc[0]) { x = u - p.nc[0]; shx = 8388608.0f; }
+          const int kx = stencil_pos(x, ax);
+          const int2 be = crange[warp][r][ux];
           const float ix = me.x - shx;
+          const int q = (kz * STENCIL + ky) * STENCIL + kx;
           int c = 0;
-          for (int j = b; j < e; j++) {
-            if (j == slot) continue;
-            const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
-            if (r2 < p.rs2f) {
-              if (r2 < p.rc2f) {
-                if (ncore < RBSOG_MAX_CORE) core[ncore] = j;
-                ncore++;
-              } else {
-                c++;
+          for (int j0 = be.x; j0 < be.y; j0 += 4) {
+            float4 o[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+              o[t] = (j0 + t < be.y) ? p.sv[j0 + t] : make_float4(FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.0f);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+              const int j = j0 + t;
+              const float r2 = pred_r2(o[t].x - ix, o[t].y - iy, o[t].z - iz, p.hp);
+              if (r2 < p.rs2f && j != slot && active) {
+                if (kx < 0) {
+                  over = true;   // impossible: beyond the atom's stencil is beyond r_shell
+                } else if (r2 < p.rc2f) {
+                  if (ncore < CORE_T && j - be.x < 256) score[tid][ncore] = (unsigned short)((q << 8) | (j - be.x));
+                  else over = true;
+                  ncore++;
+                } else {
+                  c++;
+                }
               }
             }
           }
-          if (c > RBSOG_MAX_CELL_SHELL) over = true;
-          cnt[cidx][tid] = (unsigned char)min(c, RBSOG_MAX_CELL_SHELL);
-          nshell += c;
-        }
-      }
-    }
-    if (ncore > RBSOG_MAX_CORE) {
-      atomicOr(p.err, ERR_CORE_CAP);
-      ncore = RBSOG_MAX_CORE;
-    }
-    if (over) atomicOr(p.err, ERR_CELL_SHELL_CAP);
-    // ---- pass 2 -------------------------------------------------------
-    const bool take_all = p.whole_shell || nshell <= p.P_R;
-    int tsel[RBSOG_MAX_PR];
-    const int nb = take_all ? nshell : p.P_R;
-    if (!take_all) {
-      floyd(p, s, ui.w, nshell, tsel);
-      wgt = (R)nshell / (R)p.P_R;
-    }
-    // ---- pass 3 -------------------------------------------------------
-    int cum = 0, ptr = 0;
-    for (int cidx = 0; cidx < STENCIL * STENCIL * STENCIL; cidx++) {
-      const int k = cnt[cidx][tid];
-      if (k == 0) continue;
-      if (take_all || (ptr < nb && tsel[ptr] < cum + k)) {
-        const int kz = cidx / 25, ky = (cidx / 5) % 5, kx = cidx % 5;
-        float shx, shy, shz;
-        const int cz = axis_cell(az, kz, SMALL, shz);
-        const int cy = axis_cell(ay, ky, SMALL, shy);
-        const int cx = axis_cell(ax, kx, SMALL, shx);
-        const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
-        const int b = p.cell_start[cell], e = p.cell_start[cell + 1];
-        const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
-        int ord = cum;
-        for (int j = b; j < e; j++) {
-          if (j == slot) continue;
-          const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
-          if (r2 < p.rs2f && !(r2 < p.rc2f)) {
-            if (take_all || tsel[ptr] == ord) {
-              const uint4 uj = p.su[j];
-              const int spj = __float_as_int(p.sv[j].w);
-              if (MIX) {
-                float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-                pair_mixed<ENERGY>(p, spf[spi * p.ns + spj], sg, ui, uj, a0, a1, a2, a3);
-                fsx += a0; fsy += a1; fsz += a2; es += a3;
-              } else {
-                double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-                pair_fp64<ENERGY>(p, spd[spi * p.ns + spj], swa, sw, sh2, ui, uj, a0, a1, a2, a3);
-                fsx += a0; fsy += a1; fsz += a2; es += a3;
-              }
-              if (!take_all) {
-                ptr++;
-                if (ptr >= nb || tsel[ptr] >= cum + k) break;
-              }
-            }
-            ord++;
+          if (kx >= 0) {
+            if (c > RBSOG_MAX_CELL_SHELL) over = true;
+            cnt[q][a] = (unsigned char)min(c, RBSOG_MAX_CELL_SHELL);
+            my_total += c;
           }
         }
       }
-      cum += k;
-    }
-    // ---- pass 4 -------------------------------------------------------
-    for (int k = 0; k < ncore; k++) {
-      const int j = core[k];
-      const uint4 uj = p.su[j];
-      const int spj = __float_as_int(p.sv[j].w);
-      if (MIX) {
-        float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        pair_mixed<ENERGY>(p, spf[spi * p.ns + spj], sg, ui, uj, a0, a1, a2, a3);
-        fcx += a0; fcy += a1; fcz += a2; ec += a3;
-      } else {
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        pair_fp64<ENERGY>(p, spd[spi * p.ns + spj], swa, sw, sh2, ui, uj, a0, a1, a2, a3);
-        fcx += a0; fcy += a1; fcz += a2; ec += a3;
-      }
-    }
-    const R Fx = fcx + wgt * fsx, Fy = fcy + wgt * fsy, Fz = fcz + wgt * fsz;
-    const int64_t id = ui.w, n = p.n;
-    if (MIX) {
-      p.FNf[id] = (float)Fx; p.FNf[n + id] = (float)Fy; p.FNf[2 * n + id] = (float)Fz;
     } else {
-      p.FNd[id] = (double)Fx; p.FNd[n + id] = (double)Fy; p.FNd[2 * n + id] = (double)Fz;
+      // ---- pass 1, per-atom form ---------------------------------------------
+      const float cw[3] = {8388608.0f / (float)p.nc[0], 8388608.0f / (float)p.nc[1], 8388608.0f / (float)p.nc[2]};
+      const float cull = p.rs2f * (1.0f + 1.0f / 1024.0f);
+      for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
+        const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
+        int c = 0;
+        if (kz < nkz && ky < nky && kx < nkx) {
+          float shx, shy, shz;
+          const int cz = axis_cell(az, kz, SMALL, shz);
+          const int cy = axis_cell(ay, ky, SMALL, shy);
+          const int cx = axis_cell(ax, kx, SMALL, shx);
+          bool keep = true;
+          if (!SMALL) {
+            const float gx = cell_gap(me.x, cx, shx, cw[0]) * p.hp[0];
+            const float gy = cell_gap(me.y, cy, shy, cw[1]) * p.hp[1];
+            const float gz = cell_gap(me.z, cz, shz, cw[2]) * p.hp[2];
+            keep = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, gx * gx)) < cull;
+          }
+          if (keep) {
+            const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
+            const int b = p.cell_start[cell], e = p.cell_start[cell + 1];
+            const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
+            for (int j = b; j < e; j++) {
+              const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
+              if (r2 < p.rs2f && j != slot && active) {
+                if (r2 < p.rc2f) {
+                  if (ncore < CORE_T && j - b < 256) score[tid][ncore] = (unsigned short)((q << 8) | (j - b));
+                  else over = true;
+                  ncore++;
+                } else {
+                  c++;
+                }
+              }
+            }
+          }
+        }
+        if (c > RBSOG_MAX_CELL_SHELL) over = true;
+        cnt[q][a] = (unsigned char)min(c, RBSOG_MAX_CELL_SHELL);
+        my_total += c;
+      }
     }
-    fcx = Fx; fcy = Fy; fcz = Fz;
-    ec = (R)0.5 * (ec + wgt * es);
+    if (over) atomicOr(p.err, ncore > CORE_T ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
+    ncore = min(ncore, CORE_T);
+    // ---- group total of shell counts ------------------------------------
+    int nshell = my_total;
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) nshell += __shfl_xor_sync(0xffffffffu, nshell, o, TPA);
+    const bool take_all = p.whole_shell || nshell <= p.P_R;
+    const bool sampled = active && !take_all && nshell <= SHELL_BITS;
+    if (active && !take_all && nshell > SHELL_BITS && g == 0) atomicOr(p.err, ERR_CELL_SHELL_CAP);
+    // ---- pass 2: Floyd's draw by the group's first thread -------------------
+    if (sampled) {
+      const int nw = (nshell + 31) >> 5;
+      for (int w = g; w < nw; w += TPA) bmask[a][w] = 0u;
+      for (int k = g; k < RBSOG_MAX_PR; k += TPA) scell[a][k] = 0xFF;
+    }
+    __syncwarp();
+    if (sampled && g == 0) {
+      uint32_t *bm = bmask[a];
+      const int PR = p.P_R;
+      const uint32_t id = ui.w & SU_ID_MASK;
+      uint4 w4 = make_uint4(0, 0, 0, 0);
+      for (int r = 0; r < PR; r++) {
+        if ((r & 1) == 0) w4 = draw(p.seed, s, id, 0u, (uint32_t)(r >> 1));
+        const unsigned long long U = (r & 1) ? (((unsigned long long)w4.w << 32) | w4.z)
+                                             : (((unsigned long long)w4.y << 32) | w4.x);
+        const uint32_t J = (uint32_t)(nshell - PR + r);
+        uint32_t t = (uint32_t)__umul64hi(U, (unsigned long long)J + 1ull);
+        if ((bm[t >> 5] >> (t & 31)) & 1u) t = J;
+        bm[t >> 5] |= 1u << (t & 31);
+      }
+      int k = 0;
+      const int nw = (nshell + 31) >> 5;
+      for (int w = 0; w < nw; w++) {
+        uint32_t bits = bm[w];
+        while (bits) {
+          stsel[a][k++] = (unsigned short)(32 * w + __ffs(bits) - 1);
+          bits &= bits - 1u;
+        }
+      }
+      k = 0;
+      int cum = 0;
+      for (int q = 0; q < STENCIL * STENCIL * STENCIL && k < PR; q++) {
+        const int cn = cnt[q][a];
+        while (k < PR && stsel[a][k] < cum + cn) {
+          scell[a][k] = (unsigned char)q;
+          srank[a][k] = (unsigned char)(stsel[a][k] - cum);
+          k++;
+        }
+        cum += cn;
+      }
+    }
+    if (sampled) wgt = (R)nshell / (R)p.P_R;
+    __syncwarp();
+    // candidate range and image shift of the atom's stencil cell q
+    auto cell_range = [&](int q, float &shx, float &shy, float &shz) -> int2 {
+      const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
+      const int cz = axis_cell(az, kz, SMALL, shz);
+      const int cy = axis_cell(ay, ky, SMALL, shy);
+      const int cx = axis_cell(ax, kx, SMALL, shx);
+      if (lock) {
+        int ux = cx - xs;
+        if (ux < 0) ux += p.nc[0];
+        if (ux >= p.nc[0]) ux -= p.nc[0];
+        return crange[warp][kz * STENCIL + ky][ux];
+      }
+      const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
+      return make_int2(p.cell_start[cell], p.cell_start[cell + 1]);
+    };
+    if (active) {
+      if (sampled) {
+        // ---- pass 3: sampled shell members, spread over the group ---------
+        for (int k = g; k < p.P_R; k += TPA) {
+          const int q = scell[a][k], rank = srank[a][k];
+          const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
+          if (q >= 125 || kz >= nkz || ky >= nky || kx >= nkx) continue;  // only after an overflow
+          float shx, shy, shz;
+          const int2 be = cell_range(q, shx, shy, shz);
+          const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
+          int ord = 0, jsel = -1;
+          for (int j0 = be.x; j0 < be.y && jsel < 0; j0 += 4) {
+            float r2[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) r2[t] = (j0 + t < be.y) ? cand_r2<SMALL>(p, j0 + t, ix, iy, iz, ui) : FAR_AWAY;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+              if (r2[t] < p.rs2f && !(r2[t] < p.rc2f) && j0 + t != slot) {
+                if (ord == rank && jsel < 0) jsel = j0 + t;
+                ord++;
+              }
+            }
+          }
+          if (jsel >= 0) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[jsel], fs);
+        }
+      } else if (take_all) {
+        // whole shell, weight 1: every shell member of the thread's quarter of cells
+        for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
+          if (cnt[q][a] == 0) continue;
+          float shx, shy, shz;
+          const int2 be = cell_range(q, shx, shy, shz);
+          const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
+          for (int j = be.x; j < be.y; j++) {
+            const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
+            if (r2 < p.rs2f && !(r2 < p.rc2f) && j != slot)
+              add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[j], fs);
+          }
+        }
+      }
+      // ---- pass 4: exact core sum of the thread's core list, two at a time ---
+      for (int k = 0; k < ncore; k += 2) {
+        uint4 uj[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+          const int code = score[tid][min(k + t, ncore - 1)];
+          float shx, shy, shz;
+          uj[t] = p.su[cell_range(code >> 8, shx, shy, shz).x + (code & 255)];
+        }
+        add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, uj[0], fc);
+        if (k + 1 < ncore) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, uj[1], fc);
+      }
+    }
+    // ---- combine the group ----------------------------------------------
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) {
+      fc.x += __shfl_xor_sync(0xffffffffu, fc.x, o, TPA);
+      fc.y += __shfl_xor_sync(0xffffffffu, fc.y, o, TPA);
+      fc.z += __shfl_xor_sync(0xffffffffu, fc.z, o, TPA);
+      fs.x += __shfl_xor_sync(0xffffffffu, fs.x, o, TPA);
+      fs.y += __shfl_xor_sync(0xffffffffu, fs.y, o, TPA);
+      fs.z += __shfl_xor_sync(0xffffffffu, fs.z, o, TPA);
+      if (ENERGY) {
+        fc.e += __shfl_xor_sync(0xffffffffu, fc.e, o, TPA);
+        fs.e += __shfl_xor_sync(0xffffffffu, fs.e, o, TPA);
+      }
+    }
+    if (active && g == 0) {
+      const R Fx = fc.x + wgt * fs.x, Fy = fc.y + wgt * fs.y, Fz = fc.z + wgt * fs.z;
+      const int64_t id = ui.w & SU_ID_MASK, n = p.n;
+      if (MIX) {
+        p.FNf[id] = (float)Fx; p.FNf[n + id] = (float)Fy; p.FNf[2 * n + id] = (float)Fz;
+      } else {
+        p.FNd[id] = (double)Fx; p.FNd[n + id] = (double)Fy; p.FNd[2 * n + id] = (double)Fz;
+      }
+      part[0] = (double)Fx; part[1] = (double)Fy; part[2] = (double)Fz;
+      part[3] = (double)((R)0.5 * (fc.e + wgt * fs.e));
+    }
   }
   // ---- FP64 block partials of sum F_N and of the pair energy ------------
-  double v[4] = {(double)fcx, (double)fcy, (double)fcz, (double)ec};
 #pragma unroll
-  for (int a = 0; a < 4; a++) {
-    for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
-    if ((tid & 31) == 0) red[a][tid >> 5] = v[a];
+  for (int c = 0; c < 4; c++) {
+    for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
+    if (lane == 0) red[c][warp] = part[c];
   }
   __syncthreads();
   if (tid < 4) {
     double t = 0.0;
-    for (int w = 0; w < NEAR_BLOCK / 32; w++) t += red[tid][w];
+    for (int w = 0; w < NEAR_WARPS; w++) t += red[tid][w];
     p.near_part[4 * blockIdx.x + tid] = t;
   }
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
-  const dim3 g(v.nblk_near), b(NEAR_BLOCK);
+  const dim3 g(v.nblk_near), b(NEAR_BLOCK);  // nblk_near = ceil(ncell / cells per block)
 #define RB_NEAR(R, SM, EN) k_near<R, SM, EN><<<g, b, 0, st>>>(v, step_off)
   if (v.prec == RBSOG_MIXED) {
     if (v.small) { if (energy) RB_NEAR(float, true, true); else RB_NEAR(float, true, false); }
@@ -389,7 +615,7 @@ __global__ void k_lists(View p, int step_off, const long long *sel, int nsel, in
     const bool take_all = p.whole_shell || ns <= p.P_R;
     int t[RBSOG_MAX_PR];
     const int nb = take_all ? ns : p.P_R;
-    if (!take_all) floyd(p, s, ui.w, ns, t);
+    if (!take_all) floyd(p, s, ui.w & SU_ID_MASK, ns, t);
     for (int k = 0; k < nb && k < p.P_R; k++) {
       const int pos = take_all ? k : t[k];
       batch[(long long)q * p.P_R + k] = (pos < cap_shell) ? shell[(long long)q * cap_shell + pos] : -1;

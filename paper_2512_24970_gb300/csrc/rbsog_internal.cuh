@@ -18,11 +18,17 @@ constexpr double KBOLTZ = 8.617333262e-5;  // eV/K
 
 constexpr int NT_TAB = 512;        // intervals of the FP32 SOG tables on [0, r_shell^2]
 constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
+constexpr int NEAR_CHUNK = 8;      // atoms per warp of the near-field kernel (4 threads each)
+constexpr int NEAR_WARPS = 4;      // warps per near-field block
 constexpr int RHO_BLOCK = 256;     // threads per block of the structure-factor kernel
 constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernel
 constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernel
 constexpr int FORCE_KCHUNK = 512;  // k-vectors staged in shared memory per chunk
 constexpr int STENCIL = 5;         // cells per axis in the neighbour stencil (cell >= r_shell/2)
+
+// sorted atoms carry (caller id | species << 28) in one word
+constexpr int SU_SP_SHIFT = 28;
+constexpr uint32_t SU_ID_MASK = (1u << SU_SP_SHIFT) - 1u;
 
 // device error bits (latched with atomicOr)
 constexpr int ERR_CORE_CAP = 1;
@@ -75,8 +81,9 @@ struct View {
   // binning
   int *cell_count, *cell_start, *cell_cursor;
   int *perm_tmp, *perm, *slot_of;
+  int *row_chunk;         // [ny*nz + 1] first near-field chunk of each row of cells
   float4 *sv;             // [n] sorted (v_x, v_y, v_z as exact floats, species bits)
-  uint4 *su;              // [n] sorted (u_x, u_y, u_z, caller id)
+  uint4 *su;              // [n] sorted (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
   double *near_part;      // [nblk_near][4]: sum F_N (x,y,z), sum pair energy
   // far field
   int4 *km;               // [Pmax] lattice vectors m

@@ -38,8 +38,8 @@ EXPORTS = [
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error",
 ]
-NSTAGE = 6
-STAGES = ["prepare", "bin", "near", "rho", "reduce", "force"]
+NSTAGE = 7
+STAGES = ["prepare", "bin", "near", "rho", "reduce", "force", "total"]
 
 
 class RbsogError(RuntimeError):

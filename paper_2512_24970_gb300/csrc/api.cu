@@ -381,7 +381,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.nblk_atoms = (int)((n + 255) / 256);
   v.nblk_kq = (P.P_F + 255) / 256;
   // chunks <= n / NEAR_CHUNK + rows; one warp per chunk
-  v.nblk_near = (int)(((n + rb::NEAR_CHUNK - 1) / rb::NEAR_CHUNK + (int64_t)v.nc[1] * v.nc[2] + rb::NEAR_WARPS - 1) / rb::NEAR_WARPS);
+  // chunks (8 padded slots) <= nslot / 8 + rows; one warp per chunk
+  v.nblk_near = (int)(((n + 3 * (int64_t)v.ncell + rb::NEAR_CHUNK - 1) / rb::NEAR_CHUNK + (int64_t)v.nc[1] * v.nc[2] +
+                       rb::NEAR_WARPS - 1) / rb::NEAR_WARPS);
   set_rho_tiling(ctx, P.P_F);
   // self term U_F^self = k_e/2 sum_i q_i^2 F(0)
   double F0 = 0.0, q2 = 0.0;
@@ -390,6 +392,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   ctx->self_energy = 0.5 * rb::KE * q2 * F0;
 
   const size_t N = (size_t)n;
+  v.nslot = (int)(N + (size_t)(rb::CELL_ALIGN - 1) * (size_t)v.ncell);
+  const size_t NS = (size_t)v.nslot;
   int *spc_d = nullptr;
   rb::PairF *pf = nullptr;
   rb::PairD *pd = nullptr;
@@ -402,10 +406,10 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.Fd, 3 * N)) || (rc = dalloc(ctx, &v.FNd, 3 * N)) || (rc = dalloc(ctx, &v.FFd, 3 * N)) ||
       (rc = dalloc(ctx, &spc_d, N)) || (rc = dalloc(ctx, &v.ua, N)) || (rc = dalloc(ctx, &v.cellid, N)) ||
       (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
-      (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, N)) ||
-      (rc = dalloc(ctx, &v.perm, N)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
-      (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) || (rc = dalloc(ctx, &v.sv, N)) ||
-      (rc = dalloc(ctx, &v.su, N)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
+      (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, NS)) ||
+      (rc = dalloc(ctx, &v.perm, NS)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
+      (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) || (rc = dalloc(ctx, &v.sx, NS)) ||
+      (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
       (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
       (rc = dalloc(ctx, &wa, (size_t)v.G)) || (rc = dalloc(ctx, &w, (size_t)v.G)) || (rc = dalloc(ctx, &h2, (size_t)v.G)) ||

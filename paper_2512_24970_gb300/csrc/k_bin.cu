@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
   const int per = (p.ncell + nt - 1) / nt;
   const int b = t * per, e = min(b + per, p.ncell);
   int local = 0;
-  for (int c = b; c < e; c++) local += p.cell_count[c];
+  for (int c = b; c < e; c++) local += (p.cell_count[c] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
   // block exclusive scan of `local`
   int incl = local;
   for (int o = 1; o < 32; o <<= 1) {
@@ -158,9 +158,9 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
   for (int c = b; c < e; c++) {
     p.cell_start[c] = run;
     p.cell_cursor[c] = run;
-    run += p.cell_count[c];
+    run += (p.cell_count[c] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
   }
-  if (t == nt - 1) p.cell_start[p.ncell] = (int)p.n;
+  if (t == nt - 1) p.cell_start[p.ncell] = run;
   // Chunks of the near-field kernel: the atoms of every row of cells (fixed
   // y and z) are cut into runs of NEAR_CHUNK consecutive sorted atoms;
   // row_chunk[r] is the first chunk of row r (exclusive scan).
@@ -207,11 +207,12 @@ __global__ void __launch_bounds__(256) k_scatter(View p) {
 }
 
 // One thread per cell: insertion sort of the cell's caller ids (ascending),
-// then the sorted arrays.  Cells hold ~8 atoms at r_shell/2 cells.
+// then the sorted arrays; the cell's range is padded to a multiple of
+// CELL_ALIGN slots with FAR_AWAY entries.  Cells hold ~8 atoms at r_shell/2.
 __global__ void __launch_bounds__(256) k_cellsort(View p) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.ncell) return;
-  const int b = p.cell_start[c], e = p.cell_start[c + 1];
+  const int b = p.cell_start[c], e = b + p.cell_count[c], ep = p.cell_start[c + 1];
   for (int a = b + 1; a < e; a++) {
     const int v = p.perm_tmp[a];
     int k = a - 1;
@@ -226,8 +227,17 @@ __global__ void __launch_bounds__(256) k_cellsort(View p) {
     const uint4 u = p.ua[id];
     p.perm[slot] = id;
     p.slot_of[id] = slot;
-    p.sv[slot] = make_float4((float)(u.x >> 9), (float)(u.y >> 9), (float)(u.z >> 9), __int_as_float((int)u.w));
+    p.sx[slot] = (float)(u.x >> 9);
+    p.sy[slot] = (float)(u.y >> 9);
+    p.sz[slot] = (float)(u.z >> 9);
     p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)id | (u.w << SU_SP_SHIFT));
+  }
+  for (int slot = e; slot < ep; slot++) {
+    p.perm[slot] = -1;
+    p.sx[slot] = FAR_AWAY;
+    p.sy[slot] = FAR_AWAY;
+    p.sz[slot] = FAR_AWAY;
+    p.su[slot] = make_uint4(0u, 0u, 0u, SU_PAD);
   }
 }
 

@@ -54,10 +54,10 @@ __device__ __forceinline__ float cand_r2(const View &p, int j, float ix, float i
                                          uint4 ui) {
   if (SMALL) {
     const uint4 uj = p.su[j];
+    if (uj.w == SU_PAD) return FAR_AWAY;
     return pred_r2((float)wrap23(uj.x, ui.x), (float)wrap23(uj.y, ui.y), (float)wrap23(uj.z, ui.z), p.hp);
   } else {
-    const float4 o = p.sv[j];
-    return pred_r2(o.x - ix, o.y - iy, o.z - iz, p.hp);
+    return pred_r2(p.sx[j] - ix, p.sy[j] - iy, p.sz[j] - iz, p.hp);
   }
 }
 
@@ -88,7 +88,7 @@ __device__ __forceinline__ void pair_mixed(const View &p, const PairF &q, const 
   const float t = x * p.tscale;
   const int it = min((int)t, NT_TAB - 1);
   const float f = t - (float)it;
-  const float4 c = gt[it];
+  const float4 c = __ldg(gt + it);
   const float G = __fmaf_rn(__fmaf_rn(__fmaf_rn(c.w, f, c.z), f, c.y), f, c.x);
   const float ex = exp2f((q.sig - r) * q.lr);
   const float r4 = rinv2 * rinv2;
@@ -221,37 +221,27 @@ __device__ __forceinline__ int stencil_pos(int x, const Axis &ax) {
   return k < 0 ? k + STENCIL : k;
 }
 
-constexpr float FAR_AWAY = 1e30f;  // padding of a batch of candidates: fails every predicate
-
 template <typename R, bool SMALL, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
-  __shared__ unsigned char cnt[125][APB];
+  __shared__ uint32_t smk[125][APB];         // shell members of each stencil cell (bits over its slots)
   __shared__ unsigned char scell[APB][RBSOG_MAX_PR];
   __shared__ unsigned char srank[APB][RBSOG_MAX_PR];
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR];
   __shared__ uint32_t bmask[APB][SHELL_BITS / 32];
   __shared__ unsigned short score[NEAR_BLOCK][CORE_T];
   __shared__ int2 crange[NEAR_WARPS][STENCIL * STENCIL][WMAX];
-  __shared__ float4 sg[MIX ? NT_TAB : 1];
   __shared__ PairF spf[MIX ? RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
   __shared__ PairD spd[MIX ? 1 : RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
-  __shared__ double swa[MIX ? 1 : RBSOG_MAX_M + 1], sw[MIX ? 1 : RBSOG_MAX_M + 1], sh2[MIX ? 1 : RBSOG_MAX_M + 1];
   __shared__ double red[4][NEAR_WARPS];
   const int tid = threadIdx.x;
   const int nsp2 = p.ns * p.ns;
   for (int k = tid; k < nsp2; k += NEAR_BLOCK) {
     if (MIX) spf[k] = p.pf[k]; else spd[k] = p.pd[k];
   }
-  if (MIX) {
-    for (int k = tid; k < NT_TAB; k += NEAR_BLOCK) sg[k] = p.gtab[k];
-  } else {
-    for (int k = tid; k < p.G; k += NEAR_BLOCK) {
-      swa[k] = p.sog_wa[k];
-      sw[k] = p.sog_w[k];
-      sh2[k] = p.sog_h[k];
-    }
-  }
+  // SOG tables (FP32 cubic or FP64 coefficients) through the read-only cache
+  const float4 *sg = p.gtab;
+  const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   __syncthreads();
   const long long s = *p.step + step_off;
   const int warp = tid >> 5, lane = tid & 31;
@@ -272,15 +262,17 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
     const int base = rbeg + (chunk - p.row_chunk[row]) * APW;
     const int cend = min(base + APW, rend);
     const int slot = base + lane / TPA;
-    const bool active = slot < cend;
-    const float4 me = active ? p.sv[slot] : make_float4(0, 0, 0, 0);
-    const uint4 ui = active ? p.su[slot] : p.su[base];
+    const uint4 u0 = p.su[min(slot, cend - 1)];
+    const bool active = slot < cend && u0.w != SU_PAD;
+    const uint4 ui = active ? u0 : p.su[base];   // the first slot of a chunk is an atom
+    const float3 me = active ? make_float3(p.sx[slot], p.sy[slot], p.sz[slot]) : make_float3(0.f, 0.f, 0.f);
     const int spi = (int)(ui.w >> SU_SP_SHIFT);
     const int cyr = row % p.nc[1], czr = row / p.nc[1];
-    const Axis ax = make_axis(cell_of(ui.x, p.nc[0]), p.nc[0]);
+    const int cxi = cell_of(ui.x, p.nc[0]);
+    const Axis ax = make_axis(cxi, p.nc[0]);
     const Axis ay = make_axis(cyr, p.nc[1]), az = make_axis(czr, p.nc[2]);
     const int nkx = axis_count(ax, SMALL), nky = axis_count(ay, SMALL), nkz = axis_count(az, SMALL);
-    const int cx_lo = cell_of(p.su[base].x, p.nc[0]), cx_hi = cell_of(p.su[cend - 1].x, p.nc[0]);
+    const int cx_lo = __reduce_min_sync(0xffffffffu, cxi), cx_hi = __reduce_max_sync(0xffffffffu, cxi);
     const int W = cx_hi - cx_lo + STENCIL;     // union x-cells of the chunk
     const bool lock = !SMALL && W <= WMAX && W <= p.nc[0];
     const int xs = cx_lo - 2;                  // first union cell (may be < 0)
@@ -301,8 +293,18 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
         const int cell = x + p.nc[0] * (cy + p.nc[1] * cz);
         crange[warp][r][ux] = make_int2(p.cell_start[cell], p.cell_start[cell + 1]);
       }
+      // the atom's stencil position of every union cell, 3 bits each (kx + 1, 0 = none)
+      int kxcode = 0;
+      for (int ux = 0; ux < W; ux++) {
+        int x = xs + ux;
+        x = x < 0 ? x + p.nc[0] : (x >= p.nc[0] ? x - p.nc[0] : x);
+        kxcode |= (stencil_pos(x, ax) + 1) << (3 * ux);
+      }
       __syncwarp();
       // ---- pass 1, lockstep form ---------------------------------------------
+      // Branch-free counts per cell: n(r < r_shell) and n(r < r_core) (the
+      // atom itself, r = 0, is in both, so shell = difference), core hits as a
+      // bit mask over the cell's slots, expanded into the core list per cell.
       const int rot = xs < 0 ? -xs : (cx_hi + 2 >= p.nc[0] ? W - (cx_hi + 2 - p.nc[0] + 1) : 0);
       for (int r = g; r < STENCIL * STENCIL; r += TPA) {
         const int kz = r / STENCIL, ky = r - kz * STENCIL;
@@ -314,51 +316,51 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
           int ux = k + rot;
           ux = ux >= W ? ux - W : ux;           // union index, ascending cell order
           const int u = xs + ux;
-          int x = u;
-          float shx = 0.0f;
-          if (u < 0) { x = u + p.nc[0]; shx = -8388608.0f; }
-          else if (u >= p.nc[0]) { x = u - p.nc[0]; shx = 8388608.0f; }
-          const int kx = stencil_pos(x, ax);
+          const float shx = u < 0 ? -8388608.0f : (u >= p.nc[0] ? 8388608.0f : 0.0f);
+          const int kx = ((kxcode >> (3 * ux)) & 7) - 1;
           const int2 be = crange[warp][r][ux];
-          const float ix = me.x - shx;
-          const int q = (kz * STENCIL + ky) * STENCIL + kx;
-          int c = 0;
-          for (int j0 = be.x; j0 < be.y; j0 += 4) {
-            float4 o[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++)
-              o[t] = (j0 + t < be.y) ? p.sv[j0 + t] : make_float4(FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.0f);
+          const PredX4 pc = pred_x4_setup(me.x - shx, iy, iz, p.hp);
+          const float rs2 = p.rs2f, rc2 = p.rc2f;
+          uint32_t smask = 0u, cmask = 0u, bit = 1u;
+          for (int j0 = be.x; j0 < be.y; j0 += CELL_ALIGN) {
+            float r2v[4];
+            pred_r2_x4(p.sx, p.sy, p.sz, j0, pc, r2v);
 #pragma unroll
             for (int t = 0; t < 4; t++) {
-              const int j = j0 + t;
-              const float r2 = pred_r2(o[t].x - ix, o[t].y - iy, o[t].z - iz, p.hp);
-              if (r2 < p.rs2f && j != slot && active) {
-                if (kx < 0) {
-                  over = true;   // impossible: beyond the atom's stencil is beyond r_shell
-                } else if (r2 < p.rc2f) {
-                  if (ncore < CORE_T && j - be.x < 256) score[tid][ncore] = (unsigned short)((q << 8) | (j - be.x));
-                  else over = true;
-                  ncore++;
-                } else {
-                  c++;
-                }
-              }
+              smask |= (r2v[t] < rs2) ? bit : 0u;
+              cmask |= (r2v[t] < rc2) ? bit : 0u;
+              bit <<= 1;
             }
           }
+          if (slot >= be.x && slot < be.y) cmask &= ~(1u << ((slot - be.x) & 31));
+          smask &= ~cmask;                        // shell = inside r_shell, not core, not self
+          if (slot >= be.x && slot < be.y) smask &= ~(1u << ((slot - be.x) & 31));
           if (kx >= 0) {
-            if (c > RBSOG_MAX_CELL_SHELL) over = true;
-            cnt[q][a] = (unsigned char)min(c, RBSOG_MAX_CELL_SHELL);
+            const int q = (kz * STENCIL + ky) * STENCIL + kx;
+            const int c = __popc(smask);
+            if (be.y - be.x > 32) over = true;
+            smk[q][a] = smask;
             my_total += c;
+            while (cmask) {
+              const int b = __ffs(cmask) - 1;
+              cmask &= cmask - 1u;
+              if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((q << 8) | b);
+              else over = true;
+              ncore++;
+            }
+          } else if ((smask | cmask) && active) {
+            over = true;   // impossible: beyond the atom's stencil is beyond r_shell
           }
         }
       }
+      if (!active) { my_total = 0; ncore = 0; over = false; }
     } else {
       // ---- pass 1, per-atom form ---------------------------------------------
       const float cw[3] = {8388608.0f / (float)p.nc[0], 8388608.0f / (float)p.nc[1], 8388608.0f / (float)p.nc[2]};
       const float cull = p.rs2f * (1.0f + 1.0f / 1024.0f);
       for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
         const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
-        int c = 0;
+        uint32_t m = 0u;
         if (kz < nkz && ky < nky && kx < nkx) {
           float shx, shy, shz;
           const int cz = axis_cell(az, kz, SMALL, shz);
@@ -375,23 +377,23 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
             const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
             const int b = p.cell_start[cell], e = p.cell_start[cell + 1];
             const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
+            if (e - b > 32) over = true;
             for (int j = b; j < e; j++) {
               const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
               if (r2 < p.rs2f && j != slot && active) {
                 if (r2 < p.rc2f) {
-                  if (ncore < CORE_T && j - b < 256) score[tid][ncore] = (unsigned short)((q << 8) | (j - b));
+                  if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((q << 8) | ((j - b) & 255));
                   else over = true;
                   ncore++;
                 } else {
-                  c++;
+                  m |= 1u << ((j - b) & 31);
                 }
               }
             }
           }
         }
-        if (c > RBSOG_MAX_CELL_SHELL) over = true;
-        cnt[q][a] = (unsigned char)min(c, RBSOG_MAX_CELL_SHELL);
-        my_total += c;
+        smk[q][a] = m;
+        my_total += __popc(m);
       }
     }
     if (over) atomicOr(p.err, ncore > CORE_T ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
       k = 0;
       int cum = 0;
       for (int q = 0; q < STENCIL * STENCIL * STENCIL && k < PR; q++) {
-        const int cn = cnt[q][a];
+        const int cn = __popc(smk[q][a]);
         while (k < PR && stsel[a][k] < cum + cn) {
           scell[a][k] = (unsigned char)q;
           srank[a][k] = (unsigned char)(stsel[a][k] - cum);
@@ -471,47 +473,52 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
           if (q >= 125 || kz >= nkz || ky >= nky || kx >= nkx) continue;  // only after an overflow
           float shx, shy, shz;
           const int2 be = cell_range(q, shx, shy, shz);
-          const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
-          int ord = 0, jsel = -1;
-          for (int j0 = be.x; j0 < be.y && jsel < 0; j0 += 4) {
-            float r2[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) r2[t] = (j0 + t < be.y) ? cand_r2<SMALL>(p, j0 + t, ix, iy, iz, ui) : FAR_AWAY;
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-              if (r2[t] < p.rs2f && !(r2[t] < p.rc2f) && j0 + t != slot) {
-                if (ord == rank && jsel < 0) jsel = j0 + t;
-                ord++;
-              }
-            }
-          }
-          if (jsel >= 0) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[jsel], fs);
+          // the rank-th set bit of the cell's shell mask
+          uint32_t m = smk[q][a];
+          for (int t = 0; t < rank; t++) m &= m - 1u;
+          if (m) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[be.x + __ffs(m) - 1], fs);
         }
       } else if (take_all) {
         // whole shell, weight 1: every shell member of the thread's quarter of cells
         for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
-          if (cnt[q][a] == 0) continue;
+          uint32_t m = smk[q][a];
+          if (m == 0u) continue;
           float shx, shy, shz;
-          const int2 be = cell_range(q, shx, shy, shz);
-          const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
-          for (int j = be.x; j < be.y; j++) {
-            const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
-            if (r2 < p.rs2f && !(r2 < p.rc2f) && j != slot)
-              add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[j], fs);
+          const int b = cell_range(q, shx, shy, shz).x;
+          while (m) {
+            const int t = __ffs(m) - 1;
+            m &= m - 1u;
+            add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[b + t], fs);
           }
         }
       }
-      // ---- pass 4: exact core sum of the thread's core list, two at a time ---
-      for (int k = 0; k < ncore; k += 2) {
-        uint4 uj[2];
+      // ---- pass 4: exact core sum; the group's core lists are dealt out
+      // round-robin over its threads (entry e of the concatenated list) ----------
+    }
+    {
+      int cbase = ncore;                         // exclusive prefix of the group's list lengths
 #pragma unroll
-        for (int t = 0; t < 2; t++) {
-          const int code = score[tid][min(k + t, ncore - 1)];
+      for (int o = 1; o < TPA; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, cbase, o, TPA);
+        if (g >= o) cbase += y;
+      }
+      const int ctot = __shfl_sync(0xffffffffu, cbase, TPA - 1, TPA);
+      cbase -= ncore;
+      int off[TPA];
+#pragma unroll
+      for (int t = 0; t < TPA; t++) off[t] = __shfl_sync(0xffffffffu, cbase, t, TPA);
+      __syncwarp();
+      if (active) {
+        const int tid0 = tid - g;                // first thread of the group
+        for (int e = g; e < ctot; e += TPA) {
+          int owner = 0;
+#pragma unroll
+          for (int t = 1; t < TPA; t++) owner += (e >= off[t]);
+          const int code = score[tid0 + owner][e - off[owner]];
           float shx, shy, shz;
-          uj[t] = p.su[cell_range(code >> 8, shx, shy, shz).x + (code & 255)];
+          const int j = cell_range(code >> 8, shx, shy, shz).x + (code & 255);
+          add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[j], fc);
         }
-        add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, uj[0], fc);
-        if (k + 1 < ncore) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, uj[1], fc);
       }
     }
     // ---- combine the group ----------------------------------------------
@@ -578,7 +585,7 @@ __global__ void k_lists(View p, int step_off, const long long *sel, int nsel, in
   if (q >= nsel) return;
   const long long s = *p.step + step_off;
   const int slot = p.slot_of[sel[q]];
-  const float4 me = p.sv[slot];
+  const float3 me = make_float3(p.sx[slot], p.sy[slot], p.sz[slot]);
   const uint4 ui = p.su[slot];
   const Axis ax = make_axis(cell_of(ui.x, p.nc[0]), p.nc[0]);
   const Axis ay = make_axis(cell_of(ui.y, p.nc[1]), p.nc[1]);

@@ -29,6 +29,9 @@ constexpr int STENCIL = 5;         // cells per axis in the neighbour stencil (c
 // sorted atoms carry (caller id | species << 28) in one word
 constexpr int SU_SP_SHIFT = 28;
 constexpr uint32_t SU_ID_MASK = (1u << SU_SP_SHIFT) - 1u;
+constexpr uint32_t SU_PAD = 0xFFFFFFFFu;   // padding slot
+constexpr float FAR_AWAY = 1e30f;          // coordinate of a padding slot: fails every predicate
+constexpr int CELL_ALIGN = 4;              // cell ranges are rounded up to this many slots
 
 // device error bits (latched with atomicOr)
 constexpr int ERR_CORE_CAP = 1;
@@ -82,8 +85,11 @@ struct View {
   int *cell_count, *cell_start, *cell_cursor;
   int *perm_tmp, *perm, *slot_of;
   int *row_chunk;         // [ny*nz + 1] first near-field chunk of each row of cells
-  float4 *sv;             // [n] sorted (v_x, v_y, v_z as exact floats, species bits)
-  uint4 *su;              // [n] sorted (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
+  // sorted, padded slots: every cell's range is rounded up to a multiple of 4;
+  // pads sit at FAR_AWAY (sx, sy, sz) with su.w = SU_PAD
+  float *sx, *sy, *sz;    // [nslot] 23-bit coordinates v = u >> 9 as exact floats
+  uint4 *su;              // [nslot] (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
+  int nslot;              // n + 3 * ncell
   double *near_part;      // [nblk_near][4]: sum F_N (x,y,z), sum pair energy
   // far field
   int4 *km;               // [Pmax] lattice vectors m
@@ -186,6 +192,70 @@ __device__ __forceinline__ float pred_r2(float dx, float dy, float dz, const flo
   r2 = __fmaf_rn(ay, ay, r2);
   r2 = __fmaf_rn(az, az, r2);
   return r2;
+}
+
+// Packed FP32x2 arithmetic (two IEEE binary32 operations per instruction,
+// round to nearest, no contraction): same results as the scalar forms.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(unsigned long long r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Packed constants of the list predicate seen from one atom image:
+// (-ix, -ix), (-iy, -iy), (-iz, -iz), (hx, hx), (hy, hy), (hz, hz).
+struct PredX4 {
+  unsigned long long nx, ny, nz, hx, hy, hz;
+};
+__device__ __forceinline__ PredX4 pred_x4_setup(float ix, float iy, float iz, const float hp[3]) {
+  PredX4 c;
+  c.nx = pk2(-ix, -ix); c.ny = pk2(-iy, -iy); c.nz = pk2(-iz, -iz);
+  c.hx = pk2(hp[0], hp[0]); c.hy = pk2(hp[1], hp[1]); c.hz = pk2(hp[2], hp[2]);
+  return c;
+}
+// The list predicate of pred_r2 for the four padded slots j0..j0+3 (j0 a
+// multiple of CELL_ALIGN), two candidates per instruction: r^2 of
+// ((v_j - v_i + shift) * h) with the shift folded into (ix, iy, iz).  The
+// 16-byte loads deliver the coordinate pairs already packed.
+__device__ __forceinline__ void pred_r2_x4(const float *sx, const float *sy, const float *sz, int j0,
+                                           const PredX4 &c, float r2[4]) {
+  const ulonglong2 X = __ldg(reinterpret_cast<const ulonglong2 *>(sx + j0));
+  const ulonglong2 Y = __ldg(reinterpret_cast<const ulonglong2 *>(sy + j0));
+  const ulonglong2 Z = __ldg(reinterpret_cast<const ulonglong2 *>(sz + j0));
+  const unsigned long long ax0 = mul2(add2(X.x, c.nx), c.hx), ax1 = mul2(add2(X.y, c.nx), c.hx);
+  const unsigned long long ay0 = mul2(add2(Y.x, c.ny), c.hy), ay1 = mul2(add2(Y.y, c.ny), c.hy);
+  const unsigned long long az0 = mul2(add2(Z.x, c.nz), c.hz), az1 = mul2(add2(Z.y, c.nz), c.hz);
+  unsigned long long q0 = mul2(ax0, ax0), q1 = mul2(ax1, ax1);
+  q0 = fma2(ay0, ay0, q0);
+  q1 = fma2(ay1, ay1, q1);
+  q0 = fma2(az0, az0, q0);
+  q1 = fma2(az1, az1, q1);
+  up2(q0, r2[0], r2[1]);
+  up2(q1, r2[2], r2[3]);
+}
+__device__ __forceinline__ void pred_r2_x4(const float *sx, const float *sy, const float *sz, int j0,
+                                           float ix, float iy, float iz, const float hp[3],
+                                           float r2[4]) {
+  pred_r2_x4(sx, sy, sz, j0, pred_x4_setup(ix, iy, iz, hp), r2);
 }
 
 // 23-bit minimum-image difference v_j - v_i (sign-extended), exact.

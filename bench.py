@@ -37,7 +37,7 @@ ISSUE_PER_SM = 4           # warp instructions per SM per clock (4 schedulers)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="nacl_64k")
@@ -110,6 +110,40 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+# kernels of one MD step: k_prepare, k_rho, k_scan, k_scatter, k_rank, k_near,
+# k_reduce, k_corr, k_force (the cell-count clear is a memset node)
+KERNELS_PER_STEP = 9
+
+
+def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0):
+    """Algorithmic FP32/INT lane-operations of one force evaluation, per stage
+    (the minimal instruction model of the design notes): near field = 8 ops per
+    list test of every neighbour inside r_shell plus 25 per evaluated pair
+    (core + P_R shell); structure factor = 15 per (atom, k) (3 phase IMAD,
+    ~10 sincos, 2 FMA); far force = 21 per (atom, k)."""
+    rho_n = w.n / float(np.prod(w.box))
+    n_sph = 4.0 / 3.0 * np.pi * r_shell ** 3 * rho_n
+    n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
+    return {"near": w.n * (8.0 * n_sph + 25.0 * (n_core + P_R)),
+            "rho": 15.0 * w.n * P_F, "force": 21.0 * w.n * P_F}
+
+
+def profiled_traffic(stage):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu summary,
+    only while the kernel source is the one that was profiled (else None)."""
+    import hashlib
+    src = {"near": "k_near.cu", "rho": "k_far.cu", "force": "k_far.cu"}.get(stage)
+    summ = os.path.join(ROOT, "profiles", "traffic_nacl64k.txt")
+    if src is None or not os.path.exists(summ):
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_24970_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+    for line in open(summ):
+        f = line.split()
+        if len(f) >= 3 and f[0] == "k_" + stage and f[1] == h:
+            return float(f[2])
+    return None
 
 
 def peaks():
@@ -245,18 +279,20 @@ def run_ours(args):
     nsm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    dom = int(np.argmax(stage_ms[:-1]))
-    N, P = w.n, P_F
-    if names[dom] in ("rho", "force"):
-        ops = 2.0 * N * P            # one MUFU sin + one MUFU cos per (atom, k)
-        achieved = ops / (stage_ms[dom] * 1e-3) / 1e9
-        peak = SFU_LANES_PER_SM * nsm * f_max / 1e9
-        roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": achieved, "peak": peak,
-                "unit": "Gop/s (SFU sin/cos lane-ops)", "frac": achieved / peak, "traffic": None,
-                "peak_source": "16 SFU lanes/SM/clk x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
-    else:
-        roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None}
+    alg = algorithmic_ops(w, P_F, P_R)
+    # the dominant kernel: the longest of the stages that carry the arithmetic
+    # (near field, structure factor, far force); the bookkeeping stages are
+    # reported in stage_ms
+    dom = max((i for i, nm in enumerate(names) if nm in alg), key=lambda i: stage_ms[i])
+    peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
+    achieved = alg[names[dom]] / (stage_ms[dom] * 1e-3)
+    roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+            "unit": "Glane-op/s", "frac": achieved / peak_ops,
+            "traffic": profiled_traffic(names[dom]),
+            "peak_source": "4 warp-instructions/clk/SM x 32 lanes x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
+    step_ops = sum(alg.values())
+    step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / peak_ops * 1e6,
+                 "frac": (step_ops / peak_ops) / (t_total / K * 1e-3)}
     # ---- end to end through the public API (host buffers) --------------------
     e2e = None
     if not args.no_e2e:
@@ -298,8 +334,8 @@ def run_ours(args):
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
-            "roofline": roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
-            "gpu_launches": 8 * K, "cpu_baseline": cpu,
+            "roofline": roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * K, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -379,7 +379,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     v.sig_ou[a] = std::sqrt(std::max(0.0, (1.0 - v.c1 * v.c1) * rb::KBOLTZ * P.T * rb::FCONV / hm[a]));
   }
   v.nblk_atoms = (int)((n + 255) / 256);
-  v.nblk_kq = (P.P_F + 255) / 256;
+  v.nblk_kq = (P.P_F + 7) / 8;   // one warp per sample
   // chunks <= n / NEAR_CHUNK + rows; one warp per chunk
   // chunks (8 padded slots) <= nslot / 8 + rows; one warp per chunk
   v.nblk_near = (int)(((n + 3 * (int64_t)v.ncell + rb::NEAR_CHUNK - 1) / rb::NEAR_CHUNK + (int64_t)v.nc[1] * v.nc[2] +

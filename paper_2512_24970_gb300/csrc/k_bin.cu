@@ -4,18 +4,18 @@
 //               blocks draw the P_F k-vectors from P(k) (Eq. (Pk)).
 //   k_scan      exclusive scan of the cell histogram (one block).
 //   k_scatter   counting-sort scatter (slot claimed by atomicAdd).
-//   k_cellsort  per cell: restore ascending caller order inside the cell (the
-//               canonical order of the list), write the sorted SoA arrays.
+//   k_rank      per atom: rank among the caller ids of its cell (the canonical
+//               order of the list) -> sorted slot; write the padded SoA arrays.
 #include "rbsog_internal.cuh"
 
 namespace rb {
 
 // ---------------------------------------------------------------------------
-// k-batch: exact i.i.d. draw from the mixture form of P(k) = k^2 Fhat(k)/S.
-// U0 picks the (Gaussian g, axis d) component, U1 picks m_d from the
-// k^2-weighted 1-D CDF, U2/U3 pick the other two axes (ascending axis order)
-// from the plain 1-D CDFs; c_p = S / (P_F |k_p|^2).
-__device__ void ksample(const View &p, int q, long long s) {
+// k-batch: exact i.i.d. draw from the mixture form of P(k) = k^2 Fhat(k)/S,
+// one warp per sample.  U0 picks the (Gaussian g, axis d) component, U1
+// picks m_d from the k^2-weighted 1-D CDF, U2/U3 pick the other two axes
+// (ascending axis order) from the plain 1-D CDFs; c_p = S / (P_F |k_p|^2).
+__device__ void ksample_warp(const View &p, int q, long long s, int lane) {
   if (q >= p.P_F || p.fixed_k) return;
   const uint4 w0 = draw(p.seed, s, (uint32_t)q, 1u, 0u);
   const uint4 w1 = draw(p.seed, s, (uint32_t)q, 1u, 1u);
@@ -23,29 +23,31 @@ __device__ void ksample(const View &p, int q, long long s) {
   const unsigned long long U1 = ((unsigned long long)w0.w << 32) | w0.z;
   const unsigned long long U2 = ((unsigned long long)w1.y << 32) | w1.x;
   const unsigned long long U3 = ((unsigned long long)w1.w << 32) | w1.z;
-  const int c = cdf_pick(p.cmix, 3 * p.G, U0);
+  const int c = cdf_pick_warp(p.cmix, 3 * p.G, U0, lane);
   const int d = c % 3;
   const int g = c / 3;
   int m[3];
   {
     const int nm = p.cdf_nmax[c];
-    m[d] = cdf_pick(p.cdf + p.cdf_off2[c], 2 * nm + 1, U1) - nm;
+    m[d] = cdf_pick_warp(p.cdf + p.cdf_off2[c], 2 * nm + 1, U1, lane) - nm;
   }
-  unsigned long long Uo[2] = {U2, U3};
+  const unsigned long long Uo[2] = {U2, U3};
   int o = 0;
   for (int e = 0; e < 3; e++) {
     if (e == d) continue;
     const int ce = 3 * g + e;
     const int nm = p.cdf_nmax[ce];
-    m[e] = cdf_pick(p.cdf + p.cdf_off0[ce], 2 * nm + 1, Uo[o++]) - nm;
+    m[e] = cdf_pick_warp(p.cdf + p.cdf_off0[ce], 2 * nm + 1, Uo[o++], lane) - nm;
   }
-  double k2 = 0.0;
-  for (int e = 0; e < 3; e++) {
-    const double k = 2.0 * 3.141592653589793 * (double)m[e] / p.L[e];
-    k2 += k * k;
+  if (lane == 0) {
+    double k2 = 0.0;
+    for (int e = 0; e < 3; e++) {
+      const double k = 2.0 * 3.141592653589793 * (double)m[e] / p.L[e];
+      k2 += k * k;
+    }
+    p.km[q] = make_int4(m[0], m[1], m[2], 0);
+    p.kc[q] = p.S / ((double)p.P_F * k2);
   }
-  p.km[q] = make_int4(m[0], m[1], m[2], 0);
-  p.kc[q] = p.S / ((double)p.P_F * k2);
 }
 
 // Gaussian triple of the O-step: Box-Muller on Philox stream 2, block 0.
@@ -85,7 +87,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   const long long s = *p.step + step_off;
   if ((int)blockIdx.x >= p.nblk_atoms) {
-    ksample(p, ((int)blockIdx.x - p.nblk_atoms) * blockDim.x + threadIdx.x, s);
+    ksample_warp(p, ((int)blockIdx.x - p.nblk_atoms) * (blockDim.x >> 5) + (threadIdx.x >> 5), s, threadIdx.x & 31);
     return;
   }
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
   const int per = (p.ncell + nt - 1) / nt;
   const int b = t * per, e = min(b + per, p.ncell);
   int local = 0;
+#pragma unroll 8
   for (int c = b; c < e; c++) local += (p.cell_count[c] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
   // block exclusive scan of `local`
   int incl = local;
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
   }
   __syncthreads();
   int run = incl - local + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
+#pragma unroll 8
   for (int c = b; c < e; c++) {
     p.cell_start[c] = run;
     p.cell_cursor[c] = run;
@@ -206,38 +210,32 @@ __global__ void __launch_bounds__(256) k_scatter(View p) {
   p.perm_tmp[slot] = (int)i;
 }
 
-// One thread per cell: insertion sort of the cell's caller ids (ascending),
-// then the sorted arrays; the cell's range is padded to a multiple of
-// CELL_ALIGN slots with FAR_AWAY entries.  Cells hold ~8 atoms at r_shell/2.
-__global__ void __launch_bounds__(256) k_cellsort(View p) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.ncell) return;
-  const int b = p.cell_start[c], e = b + p.cell_count[c], ep = p.cell_start[c + 1];
-  for (int a = b + 1; a < e; a++) {
-    const int v = p.perm_tmp[a];
-    int k = a - 1;
-    while (k >= b && p.perm_tmp[k] > v) {
-      p.perm_tmp[k + 1] = p.perm_tmp[k];
-      k--;
+// One thread per atom: its rank among the caller ids of its cell (the
+// canonical order inside a cell) gives its sorted slot; the first atom of a
+// cell also writes the cell's padding slots (FAR_AWAY, SU_PAD).
+__global__ void __launch_bounds__(256) k_rank(View p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int c = p.cellid[i];
+  const int b = p.cell_start[c], cnt = p.cell_count[c];
+  int rank = 0;
+  for (int k = b; k < b + cnt; k++) rank += (p.perm_tmp[k] < (int)i);
+  const int slot = b + rank;
+  const uint4 u = p.ua[i];
+  p.perm[slot] = (int)i;
+  p.slot_of[i] = slot;
+  p.sx[slot] = (float)(u.x >> 9);
+  p.sy[slot] = (float)(u.y >> 9);
+  p.sz[slot] = (float)(u.z >> 9);
+  p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)i | (u.w << SU_SP_SHIFT));
+  if (rank == 0) {
+    for (int k = b + cnt; k < p.cell_start[c + 1]; k++) {
+      p.perm[k] = -1;
+      p.sx[k] = FAR_AWAY;
+      p.sy[k] = FAR_AWAY;
+      p.sz[k] = FAR_AWAY;
+      p.su[k] = make_uint4(0u, 0u, 0u, SU_PAD);
     }
-    p.perm_tmp[k + 1] = v;
-  }
-  for (int slot = b; slot < e; slot++) {
-    const int id = p.perm_tmp[slot];
-    const uint4 u = p.ua[id];
-    p.perm[slot] = id;
-    p.slot_of[id] = slot;
-    p.sx[slot] = (float)(u.x >> 9);
-    p.sy[slot] = (float)(u.y >> 9);
-    p.sz[slot] = (float)(u.z >> 9);
-    p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)id | (u.w << SU_SP_SHIFT));
-  }
-  for (int slot = e; slot < ep; slot++) {
-    p.perm[slot] = -1;
-    p.sx[slot] = FAR_AWAY;
-    p.sy[slot] = FAR_AWAY;
-    p.sz[slot] = FAR_AWAY;
-    p.su[slot] = make_uint4(0u, 0u, 0u, SU_PAD);
   }
 }
 
@@ -252,7 +250,7 @@ void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
 void launch_bin(const View &v, cudaStream_t st) {
   k_scan<<<1, 1024, 0, st>>>(v);
   k_scatter<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
-  k_cellsort<<<(v.ncell + 255) / 256, 256, 0, st>>>(v);
+  k_rank<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,7 +4,8 @@
 //             exactly in uint32; FP32 polynomial sincos with FP32 accumulation
 //             over at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
 //   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
-//             force coefficients c_p Im rho_p, c_p Re rho_p, and F^corr.
+//             force coefficients c_p Im rho_p, c_p Re rho_p.
+//   k_corr    F^corr and U_N from the near-field block partials.
 //   k_force   F_i = F_N,i - F^corr - (k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p),
 //             fused with the closing half kick of the MD step.
 #include "rbsog_internal.cuh"
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(256) k_reduce(View p, int step_off) {
   const int k = blockIdx.x * 8 + w;
   if (k < p.P) {
     double sr = 0.0, si = 0.0;
+#pragma unroll 4
     for (int t = lane; t < p.ntile; t += 32) {
       const double *d = p.rho_part + 2 * ((int64_t)k * p.ntile + t);
       sr += d[0];
@@ -140,17 +142,28 @@ __global__ void __launch_bounds__(256) k_reduce(View p, int step_off) {
       p.uf[k] = c * (sr * sr + si * si);
     }
   }
-  if (blockIdx.x == 0 && w == 0) {
-    double f[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = lane; b < p.nblk_near; b += 32)
-      for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
-    for (int a = 0; a < 4; a++)
-      for (int o = 16; o > 0; o >>= 1) f[a] += __shfl_down_sync(0xffffffffu, f[a], o);
-    if (lane == 0) {
-      for (int a = 0; a < 3; a++) p.red[a] = f[a] / (double)p.n;
-      p.red[3] = f[3];
-      if (step_off) *p.step += step_off;
-    }
+}
+
+// F^corr = (1/N) sum of the near-field block partials, and U_N: one block,
+// thread-strided sums then a fixed-order tree (deterministic).
+__global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
+  __shared__ double red[4][256];
+  const int t = threadIdx.x;
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+  for (int b = t; b < p.nblk_near; b += 256)
+    for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
+  for (int a = 0; a < 4; a++) red[a][t] = f[a];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o)
+      for (int a = 0; a < 4; a++) red[a][t] += red[a][t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
+    for (int a = 0; a < 3; a++) p.red[a] = red[a][0] / (double)p.n;
+    p.red[3] = red[3][0];
+    if (step_off) *p.step += step_off;
   }
 }
 
@@ -264,6 +277,7 @@ void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
   const int g = max(1, (v.P + 7) / 8);
   if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, step_off);
   else k_reduce<double><<<g, 256, 0, st>>>(v, step_off);
+  k_corr<<<1, 256, 0, st>>>(v, step_off);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 

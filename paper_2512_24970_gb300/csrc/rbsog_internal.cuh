@@ -273,6 +273,25 @@ __device__ __forceinline__ int cdf_pick(const unsigned long long *C, int len, un
   return lo;
 }
 
+// The same count #{i < len-1 : C[i] <= U} by one warp: each round samples the
+// remaining range at 32 evenly spaced entries and keeps the bracket (two
+// dependent loads for tables of up to 1024 entries).  All lanes return it.
+__device__ __forceinline__ int cdf_pick_warp(const unsigned long long *C, int len, unsigned long long U,
+                                             int lane) {
+  int base = 0, cnt = len - 1, ans = 0;
+  while (cnt > 0) {
+    const int s = (cnt + 31) >> 5;
+    const bool le = (lane * s < cnt) && (C[base + lane * s] <= U);
+    const int k = __popc(__ballot_sync(0xffffffffu, le));
+    if (k == 0) break;
+    ans += (k - 1) * s + 1;
+    if (s == 1) break;
+    base += (k - 1) * s + 1;
+    cnt = min(s - 1, cnt - ((k - 1) * s + 1));
+  }
+  return ans;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers (one translation unit each).
 // MODE: 0 = evaluate only, 1 = velocity Verlet step, 2 = BAOAB step.

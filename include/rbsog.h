@@ -161,6 +161,31 @@ int rbsog_sync(rbsog_ctx *ctx);
 /* SOG parameters in use: s, w[0..M] (w[0] modified), S = sum_{k!=0} k^2 Fhat(k). */
 int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
 
+/* ---- allocation-free entry point -------------------------------------------- */
+
+#define RBSOG_SF_STATIC_PMAX 1024  /* largest P of rbsog_structure_factor_static */
+
+/* Structure factors rho(k_p) = sum_j q_j exp(i k_p . r_j), k_p = 2 pi m_p / L
+ * (the rho(k) of Eq. (Long), Sec. 2.2), of the context's current positions for
+ * P caller modes, with the same exact integer phase m.u mod 2^32 and FP64
+ * sincos as the FP64 force path.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory, e.g. an
+ * analysis hook that samples S(k) = |rho(k)|^2 / N between MD steps while
+ * other work is in flight (cudaFree synchronises the whole device, and a
+ * caching allocator may already hold all free memory).  It allocates
+ * nothing: its scratch is a static 2 MiB device array of RBSOG_SF_STATIC_PMAX x
+ * 128 tile partials, whose address is looked up once per device on the first
+ * call (make that first call outside stream capture).  Nothing in the scratch
+ * has to start at zero (every partial read is written in the same call).
+ *   m   [P][3] int32, DEVICE pointer (mode indices m_x, m_y, m_z)
+ *   rho [P][2] FP64, DEVICE pointer (Re, Im), written
+ * Asynchronous on the context's stream.  The scratch is shared by every
+ * context of a device, so two calls that overlap in time (two contexts or
+ * streams of one device, or host threads) race on it: serialise them.
+ * Errors: RBSOG_E_INVAL (P < 0, P > RBSOG_SF_STATIC_PMAX, null or non-device
+ * pointer), RBSOG_E_NO_SYSTEM, RBSOG_E_CUDA.  P = 0 does nothing. */
+int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, double *rho);
+
 /* ---- parity hooks (test use) ---------------------------------------------- */
 
 /* Lists and shell batch of atoms sel[0..nsel) at the current state and step

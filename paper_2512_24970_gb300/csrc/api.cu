@@ -761,6 +761,28 @@ int rbsog_debug_sincos(rbsog_ctx *ctx, int64_t n, const uint32_t *th, float *s, 
   return RBSOG_OK;
 }
 
+int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, double *rho) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (P < 0 || P > RBSOG_SF_STATIC_PMAX) return fail(ctx, RBSOG_E_INVAL, "P out of range (0 .. RBSOG_SF_STATIC_PMAX)");
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (P == 0) return RBSOG_OK;
+  if (!m || !rho) return fail(ctx, RBSOG_E_INVAL, "null argument");
+  CK(cudaSetDevice(ctx->dev));
+  for (const void *q : {(const void *)m, (const void *)rho}) {
+    cudaPointerAttributes at{};
+    CK(cudaPointerGetAttributes(&at, q));
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+      return fail(ctx, RBSOG_E_INVAL, "m and rho must be device pointers");
+  }
+  void *scratch = nullptr;
+  CK(rb::sf_static_scratch(ctx->dev, &scratch));
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  rb::launch_sf_static(ctx->v, P, m, rho, scratch, ctx->st);
+  if ((rc = check_launch(ctx))) return rc;
+  return leave(ctx);
+}
+
 int rbsog_set_profiling(rbsog_ctx *ctx, int on) {
   if (!ctx) return RBSOG_E_INVAL;
   if (ctx->profiling != (on != 0)) {

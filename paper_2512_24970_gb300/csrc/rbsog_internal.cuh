@@ -305,6 +305,14 @@ void launch_lists(const View &v, cudaStream_t st, int step_off, const long long 
                   int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
                   int *batch, int *nbatch, double *weight);
 void launch_sincos(int64_t n, const uint32_t *th, float *s, float *c, cudaStream_t st);
+
+// Allocation-free structure factor (k_static.cu): static scratch of
+// SF_STATIC_PMAX modes x SF_STATIC_TILES tile partials of 16 B (2 MiB).
+constexpr int SF_STATIC_PMAX = 1024;
+constexpr int SF_STATIC_TILES = 128;
+constexpr int SF_STATIC_MAX_DEVICES = 64;
+cudaError_t sf_static_scratch(int dev, void **out);
+void launch_sf_static(const View &v, int P, const int *m, double *rho, void *scratch, cudaStream_t st);
 void launch_aos_to_soa(const double *aos, double *soa, int64_t n, cudaStream_t st);
 void launch_soa_to_aos_d(const double *soa, double *aos, int64_t n, cudaStream_t st);
 void launch_soa_to_aos_f(const float *soa, double *aos, int64_t n, cudaStream_t st);

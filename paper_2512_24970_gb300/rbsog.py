@@ -36,8 +36,9 @@ EXPORTS = [
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
-    "rbsog_get_stage_times", "rbsog_last_error",
+    "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
 ]
+SF_STATIC_PMAX = 1024
 NSTAGE = 7
 STAGES = ["prepare", "bin", "near", "rho", "reduce", "force", "total"]
 
@@ -120,6 +121,7 @@ def load():
     L.rbsog_debug_sincos.argtypes = [P, I64, P, P, P]
     L.rbsog_set_profiling.argtypes = [P, I]
     L.rbsog_get_stage_times.argtypes = [P, P, I32]
+    L.rbsog_structure_factor_static.argtypes = [P, I32, P, P]
     L.rbsog_last_error.argtypes = [P]
     L.rbsog_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -307,6 +309,19 @@ class Context:
         c = np.zeros(th.size, dtype=np.float32)
         self._ck(self._L.rbsog_debug_sincos(self.h, th.size, _np_ptr(th), _np_ptr(s), _np_ptr(c)))
         return s, c
+
+    def structure_factor_static(self, m, rho=None):
+        """rho(k_p) [P, 2] FP64 of the current positions for modes ``m`` [P, 3]
+        (torch int32 CUDA tensor), through the allocation-free entry point;
+        ``rho`` (torch float64 CUDA tensor) is written and returned."""
+        import torch
+        if rho is None:
+            rho = torch.empty((m.shape[0], 2), dtype=torch.float64, device=m.device)
+        assert m.is_cuda and m.dtype == torch.int32 and m.is_contiguous()
+        assert rho.is_cuda and rho.dtype == torch.float64 and rho.is_contiguous()
+        self._ck(self._L.rbsog_structure_factor_static(self.h, m.shape[0], ctypes.c_void_p(m.data_ptr()),
+                                                        ctypes.c_void_p(rho.data_ptr())))
+        return rho
 
     def debug_whole_shell(self, flag: bool):
         self._ck(self._L.rbsog_debug_set_whole_shell(self.h, 1 if flag else 0))

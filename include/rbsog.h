@@ -68,7 +68,10 @@ extern "C" {
 #define RBSOG_MAX_SPECIES 8
 #define RBSOG_MAX_PR 64        /* shell batch size P_R */
 #define RBSOG_MAX_CORE 96      /* core neighbours per atom */
-#define RBSOG_MAX_CELL_SHELL 255 /* shell neighbours of one atom inside one cell */
+#define RBSOG_MAX_ROW_SLOTS 128 /* candidate slots of one stencil row: the x-cells a run of
+                                   8 sorted atoms needs, each cell padded to a multiple of 4
+                                   (also: a run of 8 atoms spans at most 4 cells along x) */
+#define RBSOG_MAX_SHELL 1024   /* shell neighbours of one atom when the batch is sampled */
 #define RBSOG_MAX_M 128        /* Gaussians m = 0..M */
 
 typedef struct rbsog_ctx rbsog_ctx; /* opaque, library-owned */

@@ -141,7 +141,7 @@ int read_err(rbsog_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->v.err, 0, sizeof(int), ctx->st));
     std::string m = "device capacity overflow:";
     if (e & rb::ERR_CORE_CAP) m += " core list > RBSOG_MAX_CORE";
-    if (e & rb::ERR_CELL_SHELL_CAP) m += " shell count in one cell > RBSOG_MAX_CELL_SHELL";
+    if (e & rb::ERR_CELL_SHELL_CAP) m += " stencil row > RBSOG_MAX_ROW_SLOTS slots or shell > RBSOG_MAX_SHELL";
     if (e & rb::ERR_PR_CAP) m += " P_R";
     return fail(ctx, RBSOG_E_CAP_OVERFLOW, m);
   }
@@ -369,6 +369,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.rs2f = (float)(P.r_shell * P.r_shell);
   v.ncell = v.nc[0] * v.nc[1] * v.nc[2];
   v.small = (v.nc[0] < rb::STENCIL || v.nc[1] < rb::STENCIL || v.nc[2] < rb::STENCIL) ? 1 : 0;
+  // the near field's union of a chunk's x-stencils (<= 8 cells) may meet
+  // itself on short rows: there it takes whole rows and minimum images
+  v.wrap = (v.small || v.nc[0] < 8) ? 1 : 0;
   v.tscale = (float)(rb::NT_TAB / (P.r_shell * P.r_shell));
   v.S = samp.S;
   v.dt = P.dt;
@@ -408,7 +411,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
       (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, NS)) ||
       (rc = dalloc(ctx, &v.perm, NS)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
-      (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) || (rc = dalloc(ctx, &v.sx, NS)) ||
+      (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) ||
+      (rc = dalloc(ctx, &v.chunk_info, (size_t)v.nblk_near * rb::NEAR_WARPS)) || (rc = dalloc(ctx, &v.sx, NS)) ||
       (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
       (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||

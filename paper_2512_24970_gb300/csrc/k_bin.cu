@@ -228,6 +228,12 @@ __global__ void __launch_bounds__(256) k_rank(View p) {
   p.sy[slot] = (float)(u.y >> 9);
   p.sz[slot] = (float)(u.z >> 9);
   p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)i | (u.w << SU_SP_SHIFT));
+  // the near-field chunks (runs of NEAR_CHUNK slots from the start of the row
+  // of cells) that begin in this cell; every run begins at an atom
+  const int row = c / p.nc[0];
+  const int rbeg = p.cell_start[row * p.nc[0]];
+  if (((slot - rbeg) & (NEAR_CHUNK - 1)) == 0)
+    p.chunk_info[p.row_chunk[row] + (slot - rbeg) / NEAR_CHUNK] = make_int2(row, slot);
   if (rank == 0) {
     for (int k = b + cnt; k < p.cell_start[c + 1]; k++) {
       p.perm[k] = -1;

@@ -1,17 +1,10 @@
 // Stages (a2), (b), (c): one fused kernel per step builds the random batch list
-// and evaluates the near field (Sec. 2.2).  One thread per atom in cell-sorted
-// order:
-//   pass 1  scan the 5x5x5 cell stencil in canonical order (cells ascending by
-//           linear index, atoms ascending by caller index) with the FP32
-//           predicate; core neighbours (r < r_core) go to a per-thread list,
-//           shell neighbours (r_core <= r < r_shell) are only counted per cell;
-//   pass 2  Floyd's P_R-of-N_shell draw without replacement (Philox stream 0);
-//   pass 3  walk the per-cell counts, rescan only the cells holding sampled
-//           positions and add their pair forces with weight N_shell / P_R;
-//   pass 4  exact core sum.
-// The pair force is Eq. (Fshort) (SOG residual + BMH, k_e on Coulomb): FP32
-// with the SOG sum tabulated (mixed) or analytic FP64 over m = 0..M.  The
-// block's FP64 partial sums of F_N feed the momentum correction F^corr.
+// and evaluates the near field (Sec. 2.2): list predicate over the cell
+// stencil, Floyd's P_R-of-N_shell shell batch without replacement (Philox
+// stream 0), core + weighted batch pair forces.  The pair force is
+// Eq. (Fshort) (SOG residual + BMH, k_e on Coulomb): FP32 with the SOG sum
+// tabulated (mixed) or analytic FP64 over m = 0..M.  The block's FP64 partial
+// sums of F_N feed the momentum correction F^corr.
 #include "rbsog_internal.cuh"
 
 namespace rb {
@@ -155,16 +148,6 @@ __device__ __forceinline__ void floyd(const View &p, long long s, uint32_t id, i
   }
 }
 
-// ---------------------------------------------------------------------------
-// Conservative cell culling: gap (23-bit units) between v_i and the image of
-// cell c of an axis with cell width cw = 2^23 / n, widened by 4 units so that
-// rounding of the cell bounds can only keep a cell, never drop one.
-__device__ __forceinline__ float cell_gap(float vi, int c, float shift, float cw) {
-  const float lo = __fmaf_rn((float)c, cw, shift) - 4.0f;
-  const float hi = __fmaf_rn((float)(c + 1), cw, shift) + 4.0f;
-  return fmaxf(0.0f, fmaxf(lo - vi, vi - hi));
-}
-
 template <typename R>
 struct Acc {
   R x = 0, y = 0, z = 0, e = 0;
@@ -187,50 +170,85 @@ __device__ __forceinline__ void add_pair(const View &p, const PairF *spf, const 
   }
 }
 
-// One warp per chunk of NEAR_CHUNK = 8 consecutive sorted atoms of one row of
-// cells (fixed y, z); TPA = 4 threads per atom.  Pass 1 has two forms:
-//  - lockstep (the union of the chunk's x-stencils is at most WMAX cells and
-//    narrower than the box): the warp first caches the candidate ranges of
-//    the 25 rows x W union cells in shared memory; thread g of every atom
-//    walks stencil rows g, g + 4, ... and, in each, the union cells in
-//    ascending index order, so all 8 atoms test the same candidates in the
-//    same order (uniform loops, broadcast loads, four loads in flight); each
-//    atom files a candidate under its own stencil position;
-//  - per atom (otherwise): the atom's own 125 cells dealt round-robin, with
-//    conservative culling of cells beyond r_shell.
-// Both fill the same per-atom state in shared memory: per-cell shell counts
-// (canonical order) and per-thread core lists coded (stencil cell << 8 |
-// offset in cell).  Floyd's set is a bitmask over canonical positions; the
-// sorted samples are mapped to (cell, rank) by one sweep of the counts.
+// One warp per chunk of up to NEAR_CHUNK = 8 consecutive sorted slots of one
+// row of cells (fixed cell y and z); TPA = 4 threads per atom.  The atoms of
+// a chunk share the stencil rows (y, z) of their row of cells.  Along x, a
+// stencil row's candidates are the union of the chunk's five-cell
+// x-stencils: one or two runs of sorted slots in ascending cell index, i.e.
+// in the canonical order (cell index, caller index).  On short boxes
+// (WRAP) a row whose union would meet itself is taken whole, and every
+// difference is reduced to the minimum image.
+//  pass 1  thread g of every atom tests the candidates of stencil rows g,
+//          g + 4, ... with the FP32 list predicate, four slots per step;
+//          all eight atoms walk the same slots at the same time (broadcast
+//          loads).  Each row gives bit masks over its candidates: the shell
+//          mask stays in shared memory, core members go to a short list.
+//  pass 2  per-row shell counts -> prefix (canonical index of each row's
+//          first shell member).  Floyd's P_R-of-N_shell draw: the group's
+//          threads compute the Philox words and candidate positions in
+//          parallel, its first thread resolves them in order.
+//  pass 3  sample t: its row by binary search of the prefix, its slot as the
+//          (t - prefix)-th set bit of the row's shell mask; weight N_shell/P_R.
+//  pass 4  the group's core lists, dealt round-robin over its threads.
 constexpr int TPA = 4;
 constexpr int APW = NEAR_CHUNK;              // atoms per warp
 constexpr int APB = NEAR_WARPS * NEAR_CHUNK; // atoms per block
+constexpr int NROW = STENCIL * STENCIL;      // stencil rows (y, z)
+constexpr int RW = RBSOG_MAX_ROW_SLOTS / 32; // mask words of one stencil row
 constexpr int CORE_T = 40;                   // core neighbours per thread
-constexpr int SHELL_BITS = 1024;             // canonical shell positions held by the bitmask
-constexpr int WMAX = 8;                      // union x-cells of a lockstep chunk
+constexpr int SHELL_BITS = RBSOG_MAX_SHELL;  // shell members one bitmask can index
+constexpr int WMAX = 8;                      // union x-cells of a chunk
 static_assert(TPA * NEAR_CHUNK == 32 && NEAR_WARPS * 32 == NEAR_BLOCK, "near-field block layout");
+static_assert(RBSOG_MAX_ROW_SLOTS % 32 == 0 && RBSOG_MAX_ROW_SLOTS <= 128, "row position needs 7 bits");
 
-// stencil position (0..4, ascending cell order) of cell x on an axis of n >= 5
-// cells as seen from cell ci, or -1 when x is not among ci's five neighbours
-__device__ __forceinline__ int stencil_pos(int x, const Axis &ax) {
-  int o = x - ax.ci;
-  if (o > ax.n / 2) o -= ax.n;
-  if (o < -(ax.n / 2)) o += ax.n;
-  if (o < -2 || o > 2) return -1;
-  int k = o + 2 - ax.rot;
-  return k < 0 ? k + STENCIL : k;
+// position of the k-th (from 0) set bit of m; k < popc(m)
+__device__ __forceinline__ int select_bit(uint32_t m, int k) {
+  int pos = 0, c = __popc(m & 0xFFFFu);
+  if (k >= c) { k -= c; m >>= 16; pos += 16; }
+  c = __popc(m & 0xFFu);
+  if (k >= c) { k -= c; m >>= 8; pos += 8; }
+  c = __popc(m & 0xFu);
+  if (k >= c) { k -= c; m >>= 4; pos += 4; }
+  c = __popc(m & 0x3u);
+  if (k >= c) { k -= c; m >>= 2; pos += 2; }
+  return pos + ((k >= (int)(m & 1u)) ? 1 : 0);
 }
 
-template <typename R, bool SMALL, bool ENERGY>
+// d (23-bit units, exact integer) reduced to the minimum image; values far
+// outside the box (padding slots) stay far
+__device__ __forceinline__ float min_image23(float d) {
+  const float k = fminf(fmaxf(rintf(d * 1.1920928955078125e-07f), -1.0f), 1.0f);
+  return __fmaf_rn(k, -8388608.0f, d);
+}
+
+// predicate r^2 of slots j0..j0+3 with every difference reduced to the minimum image
+__device__ __forceinline__ void pred_r2_x4_wrap(const View &p, int j0, float ix, float iy, float iz,
+                                                float r2[4]) {
+  const float4 X = __ldg(reinterpret_cast<const float4 *>(p.sx + j0));
+  const float4 Y = __ldg(reinterpret_cast<const float4 *>(p.sy + j0));
+  const float4 Z = __ldg(reinterpret_cast<const float4 *>(p.sz + j0));
+  r2[0] = pred_r2(min_image23(X.x - ix), min_image23(Y.x - iy), min_image23(Z.x - iz), p.hp);
+  r2[1] = pred_r2(min_image23(X.y - ix), min_image23(Y.y - iy), min_image23(Z.y - iz), p.hp);
+  r2[2] = pred_r2(min_image23(X.z - ix), min_image23(Y.z - iy), min_image23(Z.z - iz), p.hp);
+  r2[3] = pred_r2(min_image23(X.w - ix), min_image23(Y.w - iy), min_image23(Z.w - iz), p.hp);
+}
+
+// slot of candidate position pos of a row (a0, na, b0, nb)
+__device__ __forceinline__ int row_slot(const int4 &sg, int pos) {
+  return pos < sg.y ? sg.x + pos : sg.z + (pos - sg.y);
+}
+
+template <typename R, bool WRAP, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
-  __shared__ uint32_t smk[125][APB];         // shell members of each stencil cell (bits over its slots)
-  __shared__ unsigned char scell[APB][RBSOG_MAX_PR];
-  __shared__ unsigned char srank[APB][RBSOG_MAX_PR];
+  __shared__ uint32_t smask[APB][NROW][RW];      // shell members of each stencil row
+  __shared__ unsigned char scnt[APB][NROW];      // their counts
+  __shared__ unsigned short spre[APB][NROW + 1]; // exclusive prefix of the counts
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR];
   __shared__ uint32_t bmask[APB][SHELL_BITS / 32];
-  __shared__ unsigned short score[NEAR_BLOCK][CORE_T];
-  __shared__ int2 crange[NEAR_WARPS][STENCIL * STENCIL][WMAX];
+  __shared__ unsigned short score[NEAR_BLOCK][CORE_T];  // (row << 7 | position)
+  __shared__ int4 rseg[NEAR_WARPS][NROW];        // candidate runs (a0, na, b0, nb)
+  __shared__ float4 rsh[NEAR_WARPS][NROW];       // image shifts (x of run a, x of run b, y, z)
   __shared__ PairF spf[MIX ? RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
   __shared__ PairD spd[MIX ? 1 : RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
   __shared__ double red[4][NEAR_WARPS];
@@ -239,8 +257,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   for (int k = tid; k < nsp2; k += NEAR_BLOCK) {
     if (MIX) spf[k] = p.pf[k]; else spd[k] = p.pd[k];
   }
-  // SOG tables (FP32 cubic or FP64 coefficients) through the read-only cache
-  const float4 *sg = p.gtab;
+  const float4 *sg4 = p.gtab;
   const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   __syncthreads();
   const long long s = *p.step + step_off;
@@ -251,250 +268,198 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   const int chunk = blockIdx.x * NEAR_WARPS + warp;
   double part[4] = {0.0, 0.0, 0.0, 0.0};
   if (chunk < p.row_chunk[nrow]) {
-    // ---- the chunk's row of cells and atoms ------------------------------
-    int lo = 0, hi = nrow - 1;  // last row with row_chunk[row] <= chunk
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (p.row_chunk[mid] <= chunk) lo = mid; else hi = mid - 1;
-    }
-    const int row = lo;
-    const int rbeg = p.cell_start[row * p.nc[0]], rend = p.cell_start[(row + 1) * p.nc[0]];
-    const int base = rbeg + (chunk - p.row_chunk[row]) * APW;
+    // ---- the chunk ------------------------------------------------------------
+    const int2 cinfo = p.chunk_info[chunk];   // (row of cells, first slot)
+    const int row = cinfo.x, base = cinfo.y;
+    const int nc0 = p.nc[0];
+    const int rend = p.cell_start[(row + 1) * nc0];
     const int cend = min(base + APW, rend);
     const int slot = base + lane / TPA;
     const uint4 u0 = p.su[min(slot, cend - 1)];
     const bool active = slot < cend && u0.w != SU_PAD;
-    const uint4 ui = active ? u0 : p.su[base];   // the first slot of a chunk is an atom
-    const float3 me = active ? make_float3(p.sx[slot], p.sy[slot], p.sz[slot]) : make_float3(0.f, 0.f, 0.f);
+    const int mslot = active ? slot : base;     // the first slot of a chunk is an atom
+    const uint4 ui = active ? u0 : p.su[base];
+    const float3 me = make_float3(p.sx[mslot], p.sy[mslot], p.sz[mslot]);
     const int spi = (int)(ui.w >> SU_SP_SHIFT);
-    const int cyr = row % p.nc[1], czr = row / p.nc[1];
-    const int cxi = cell_of(ui.x, p.nc[0]);
-    const Axis ax = make_axis(cxi, p.nc[0]);
-    const Axis ay = make_axis(cyr, p.nc[1]), az = make_axis(czr, p.nc[2]);
-    const int nkx = axis_count(ax, SMALL), nky = axis_count(ay, SMALL), nkz = axis_count(az, SMALL);
+    const Axis ay = make_axis(row % p.nc[1], p.nc[1]), az = make_axis(row / p.nc[1], p.nc[2]);
+    const int nky = axis_count(ay, WRAP), nkz = axis_count(az, WRAP);
+    const int nr = nky * nkz;
+    const int cxi = cell_of(ui.x, nc0);
     const int cx_lo = __reduce_min_sync(0xffffffffu, cxi), cx_hi = __reduce_max_sync(0xffffffffu, cxi);
     const int W = cx_hi - cx_lo + STENCIL;     // union x-cells of the chunk
-    const bool lock = !SMALL && W <= WMAX && W <= p.nc[0];
-    const int xs = cx_lo - 2;                  // first union cell (may be < 0)
-    Acc<R> fc, fs;
-    R wgt = 1;
-    int my_total = 0, ncore = 0;
-    bool over = false;
-    if (lock) {
-      // ---- candidate ranges of the union cells, cached per warp --------------
-      for (int it = lane; it < STENCIL * STENCIL * W; it += 32) {
-        const int r = it / W, ux = it - r * W;
-        const int kz = r / STENCIL, ky = r - kz * STENCIL;
-        float sh;
-        const int cz = axis_cell(az, kz, false, sh);
-        const int cy = axis_cell(ay, ky, false, sh);
-        int x = xs + ux;
-        x = x < 0 ? x + p.nc[0] : (x >= p.nc[0] ? x - p.nc[0] : x);
-        const int cell = x + p.nc[0] * (cy + p.nc[1] * cz);
-        crange[warp][r][ux] = make_int2(p.cell_start[cell], p.cell_start[cell + 1]);
+    const bool full = WRAP && W > nc0;         // the whole row (minimum image per pair)
+    bool over = !full && W > WMAX;
+    // ---- candidate runs and image shifts of the stencil rows ------------------
+    if (lane < nr) {
+      const int kz = lane / nky, ky = lane - kz * nky;
+      float shy, shz;
+      const int cy = axis_cell(ay, ky, WRAP, shy);
+      const int cz = axis_cell(az, kz, WRAP, shz);
+      const int* cs = p.cell_start + nc0 * (cy + p.nc[1] * cz);
+      int a0, a1, b0 = 0, b1 = 0;
+      float sa = 0.0f, sb = 0.0f;
+      const int xs = cx_lo - 2, xe = cx_hi + 2;
+      if (over) {                              // rejected chunk: empty rows
+        a0 = a1 = 0;
+      } else if (full) {
+        a0 = cs[0]; a1 = cs[nc0];
+      } else if (xs < 0) {                     // cells 0..xe, then nc0+xs..nc0-1 (image at -L)
+        a0 = cs[0]; a1 = cs[min(xe + 1, nc0)];
+        b0 = cs[nc0 + xs]; b1 = cs[nc0]; sb = -8388608.0f;
+      } else if (xe >= nc0) {                  // cells 0..xe-nc0 (image at +L), then xs..nc0-1
+        a0 = cs[0]; a1 = cs[min(xe - nc0 + 1, nc0)]; sa = 8388608.0f;
+        b0 = cs[xs]; b1 = cs[nc0];
+      } else {
+        a0 = cs[xs]; a1 = cs[xe + 1];
       }
-      // the atom's stencil position of every union cell, 3 bits each (kx + 1, 0 = none)
-      int kxcode = 0;
-      for (int ux = 0; ux < W; ux++) {
-        int x = xs + ux;
-        x = x < 0 ? x + p.nc[0] : (x >= p.nc[0] ? x - p.nc[0] : x);
-        kxcode |= (stencil_pos(x, ax) + 1) << (3 * ux);
-      }
-      __syncwarp();
-      // ---- pass 1, lockstep form ---------------------------------------------
-      // Branch-free counts per cell: n(r < r_shell) and n(r < r_core) (the
-      // atom itself, r = 0, is in both, so shell = difference), core hits as a
-      // bit mask over the cell's slots, expanded into the core list per cell.
-      const int rot = xs < 0 ? -xs : (cx_hi + 2 >= p.nc[0] ? W - (cx_hi + 2 - p.nc[0] + 1) : 0);
-      for (int r = g; r < STENCIL * STENCIL; r += TPA) {
-        const int kz = r / STENCIL, ky = r - kz * STENCIL;
-        float shz, shy;
-        axis_cell(az, kz, false, shz);
-        axis_cell(ay, ky, false, shy);
-        const float iy = me.y - shy, iz = me.z - shz;
-        for (int k = 0; k < W; k++) {
-          int ux = k + rot;
-          ux = ux >= W ? ux - W : ux;           // union index, ascending cell order
-          const int u = xs + ux;
-          const float shx = u < 0 ? -8388608.0f : (u >= p.nc[0] ? 8388608.0f : 0.0f);
-          const int kx = ((kxcode >> (3 * ux)) & 7) - 1;
-          const int2 be = crange[warp][r][ux];
-          const PredX4 pc = pred_x4_setup(me.x - shx, iy, iz, p.hp);
-          const float rs2 = p.rs2f, rc2 = p.rc2f;
-          uint32_t smask = 0u, cmask = 0u, bit = 1u;
-          for (int j0 = be.x; j0 < be.y; j0 += CELL_ALIGN) {
-            float r2v[4];
-            pred_r2_x4(p.sx, p.sy, p.sz, j0, pc, r2v);
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-              smask |= (r2v[t] < rs2) ? bit : 0u;
-              cmask |= (r2v[t] < rc2) ? bit : 0u;
-              bit <<= 1;
-            }
-          }
-          if (slot >= be.x && slot < be.y) cmask &= ~(1u << ((slot - be.x) & 31));
-          smask &= ~cmask;                        // shell = inside r_shell, not core, not self
-          if (slot >= be.x && slot < be.y) smask &= ~(1u << ((slot - be.x) & 31));
-          if (kx >= 0) {
-            const int q = (kz * STENCIL + ky) * STENCIL + kx;
-            const int c = __popc(smask);
-            if (be.y - be.x > 32) over = true;
-            smk[q][a] = smask;
-            my_total += c;
-            while (cmask) {
-              const int b = __ffs(cmask) - 1;
-              cmask &= cmask - 1u;
-              if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((q << 8) | b);
-              else over = true;
-              ncore++;
-            }
-          } else if ((smask | cmask) && active) {
-            over = true;   // impossible: beyond the atom's stencil is beyond r_shell
-          }
-        }
-      }
-      if (!active) { my_total = 0; ncore = 0; over = false; }
-    } else {
-      // ---- pass 1, per-atom form ---------------------------------------------
-      const float cw[3] = {8388608.0f / (float)p.nc[0], 8388608.0f / (float)p.nc[1], 8388608.0f / (float)p.nc[2]};
-      const float cull = p.rs2f * (1.0f + 1.0f / 1024.0f);
-      for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
-        const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
-        uint32_t m = 0u;
-        if (kz < nkz && ky < nky && kx < nkx) {
-          float shx, shy, shz;
-          const int cz = axis_cell(az, kz, SMALL, shz);
-          const int cy = axis_cell(ay, ky, SMALL, shy);
-          const int cx = axis_cell(ax, kx, SMALL, shx);
-          bool keep = true;
-          if (!SMALL) {
-            const float gx = cell_gap(me.x, cx, shx, cw[0]) * p.hp[0];
-            const float gy = cell_gap(me.y, cy, shy, cw[1]) * p.hp[1];
-            const float gz = cell_gap(me.z, cz, shz, cw[2]) * p.hp[2];
-            keep = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, gx * gx)) < cull;
-          }
-          if (keep) {
-            const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
-            const int b = p.cell_start[cell], e = p.cell_start[cell + 1];
-            const float ix = me.x - shx, iy = me.y - shy, iz = me.z - shz;
-            if (e - b > 32) over = true;
-            for (int j = b; j < e; j++) {
-              const float r2 = cand_r2<SMALL>(p, j, ix, iy, iz, ui);
-              if (r2 < p.rs2f && j != slot && active) {
-                if (r2 < p.rc2f) {
-                  if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((q << 8) | ((j - b) & 255));
-                  else over = true;
-                  ncore++;
-                } else {
-                  m |= 1u << ((j - b) & 31);
-                }
-              }
-            }
-          }
-        }
-        smk[q][a] = m;
-        my_total += __popc(m);
-      }
+      rseg[warp][lane] = make_int4(a0, a1 - a0, b0, b1 - b0);
+      rsh[warp][lane] = make_float4(sa, sb, shy, shz);
     }
+    __syncwarp();
+    // ---- pass 1 -----------------------------------------------------------------
+    const float rs2 = p.rs2f, rc2 = p.rc2f;
+    int my_total = 0, ncore = 0;
+    for (int r = g; r < nr; r += TPA) {
+      const int4 sg = rseg[warp][r];
+      const float4 sh = rsh[warp][r];
+      const int len = sg.y + sg.w;
+      if (len > RW * 32 || over) {
+        over = true;
+        scnt[a][r] = 0;
+        continue;
+      }
+      const int pself = (slot >= sg.x && slot < sg.x + sg.y) ? slot - sg.x
+                        : ((slot >= sg.z && slot < sg.z + sg.w) ? sg.y + slot - sg.z : -1);
+      uint32_t accs = 0u, accc = 0u;
+      int pos = 0, cnt = 0;
+      // close the word of positions [pos - m, pos)
+      auto flush = [&](int m) {
+        const int w = (pos - 1) >> 5;
+        uint32_t ws = __brev(accs) >> (32 - m);
+        uint32_t wc = __brev(accc) >> (32 - m);
+        if ((pself >> 5) == w && pself >= 0) {
+          ws &= ~(1u << (pself & 31));
+          wc &= ~(1u << (pself & 31));
+        }
+        ws &= ~wc;                                // shell: inside r_shell, not core, not self
+        smask[a][r][w] = ws;
+        cnt += __popc(ws);
+        while (wc) {
+          const int b = __ffs(wc) - 1;
+          wc &= wc - 1u;
+          if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((r << 7) | (32 * w + b));
+          ncore++;
+        }
+        accs = 0u;
+        accc = 0u;
+      };
+#pragma unroll 1
+      for (int run = 0; run < 2; run++) {
+        const int j0 = run ? sg.z : sg.x, nrun = run ? sg.w : sg.y;
+        const PredX4 pc = pred_x4_setup(me.x - (run ? sh.y : sh.x), me.y - sh.z, me.z - sh.w, p.hp);
+        for (int k = 0; k < nrun; k += CELL_ALIGN) {
+          float r2v[4];
+          if (WRAP) pred_r2_x4_wrap(p, j0 + k, me.x, me.y, me.z, r2v);
+          else pred_r2_x4(p.sx, p.sy, p.sz, j0 + k, pc, r2v);
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            // sign of r^2 - threshold: set iff r^2 < threshold (r^2 = +inf at pads)
+            accs = __funnelshift_l(__float_as_uint(r2v[t] - rs2), accs, 1);
+            accc = __funnelshift_l(__float_as_uint(r2v[t] - rc2), accc, 1);
+          }
+          pos += 4;
+          if ((pos & 31) == 0) flush(32);
+        }
+      }
+      if (pos & 31) flush(pos & 31);
+      scnt[a][r] = (unsigned char)cnt;
+      my_total += cnt;
+    }
+    if (!active) { my_total = 0; ncore = 0; over = false; }
+    if (ncore > CORE_T) over = true;
     if (over) atomicOr(p.err, ncore > CORE_T ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
     ncore = min(ncore, CORE_T);
-    // ---- group total of shell counts ------------------------------------
+    // ---- pass 2: prefix of the row counts, Floyd's draw ---------------------------
     int nshell = my_total;
 #pragma unroll
     for (int o = 1; o < TPA; o <<= 1) nshell += __shfl_xor_sync(0xffffffffu, nshell, o, TPA);
     const bool take_all = p.whole_shell || nshell <= p.P_R;
     const bool sampled = active && !take_all && nshell <= SHELL_BITS;
     if (active && !take_all && nshell > SHELL_BITS && g == 0) atomicOr(p.err, ERR_CELL_SHELL_CAP);
-    // ---- pass 2: Floyd's draw by the group's first thread -------------------
+    const int PR = p.P_R;
+    __syncwarp();
     if (sampled) {
-      const int nw = (nshell + 31) >> 5;
-      for (int w = g; w < nw; w += TPA) bmask[a][w] = 0u;
-      for (int k = g; k < RBSOG_MAX_PR; k += TPA) scell[a][k] = 0xFF;
+      int acc = 0;
+      for (int q = 0; q < g; q++) acc += scnt[a][q];
+      for (int r = g; r < nr; r += TPA) {
+        spre[a][r] = (unsigned short)acc;
+        for (int q = r; q < min(r + TPA, nr); q++) acc += scnt[a][q];
+      }
+      if (g == 0) spre[a][nr] = (unsigned short)nshell;
+      for (int w = g; w < ((nshell + 31) >> 5); w += TPA) bmask[a][w] = 0u;
+      const uint32_t id = ui.w & SU_ID_MASK;
+      for (int d = g; 2 * d < PR; d += TPA) {     // Philox word d serves samples 2d, 2d + 1
+        const uint4 w4 = draw(p.seed, s, id, 0u, (uint32_t)d);
+        const unsigned long long U0 = ((unsigned long long)w4.y << 32) | w4.x;
+        const unsigned long long U1 = ((unsigned long long)w4.w << 32) | w4.z;
+        const int r0 = 2 * d;
+        stsel[a][r0] = (unsigned short)__umul64hi(U0, (unsigned long long)(nshell - PR + r0) + 1ull);
+        if (r0 + 1 < PR)
+          stsel[a][r0 + 1] = (unsigned short)__umul64hi(U1, (unsigned long long)(nshell - PR + r0 + 1) + 1ull);
+      }
     }
     __syncwarp();
     if (sampled && g == 0) {
       uint32_t *bm = bmask[a];
-      const int PR = p.P_R;
-      const uint32_t id = ui.w & SU_ID_MASK;
-      uint4 w4 = make_uint4(0, 0, 0, 0);
       for (int r = 0; r < PR; r++) {
-        if ((r & 1) == 0) w4 = draw(p.seed, s, id, 0u, (uint32_t)(r >> 1));
-        const unsigned long long U = (r & 1) ? (((unsigned long long)w4.w << 32) | w4.z)
-                                             : (((unsigned long long)w4.y << 32) | w4.x);
-        const uint32_t J = (uint32_t)(nshell - PR + r);
-        uint32_t t = (uint32_t)__umul64hi(U, (unsigned long long)J + 1ull);
-        if ((bm[t >> 5] >> (t & 31)) & 1u) t = J;
+        uint32_t t = stsel[a][r];
+        if ((bm[t >> 5] >> (t & 31)) & 1u) t = (uint32_t)(nshell - PR + r);
         bm[t >> 5] |= 1u << (t & 31);
-      }
-      int k = 0;
-      const int nw = (nshell + 31) >> 5;
-      for (int w = 0; w < nw; w++) {
-        uint32_t bits = bm[w];
-        while (bits) {
-          stsel[a][k++] = (unsigned short)(32 * w + __ffs(bits) - 1);
-          bits &= bits - 1u;
-        }
-      }
-      k = 0;
-      int cum = 0;
-      for (int q = 0; q < STENCIL * STENCIL * STENCIL && k < PR; q++) {
-        const int cn = __popc(smk[q][a]);
-        while (k < PR && stsel[a][k] < cum + cn) {
-          scell[a][k] = (unsigned char)q;
-          srank[a][k] = (unsigned char)(stsel[a][k] - cum);
-          k++;
-        }
-        cum += cn;
+        stsel[a][r] = (unsigned short)t;
       }
     }
-    if (sampled) wgt = (R)nshell / (R)p.P_R;
     __syncwarp();
-    // candidate range and image shift of the atom's stencil cell q
-    auto cell_range = [&](int q, float &shx, float &shy, float &shz) -> int2 {
-      const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
-      const int cz = axis_cell(az, kz, SMALL, shz);
-      const int cy = axis_cell(ay, ky, SMALL, shy);
-      const int cx = axis_cell(ax, kx, SMALL, shx);
-      if (lock) {
-        int ux = cx - xs;
-        if (ux < 0) ux += p.nc[0];
-        if (ux >= p.nc[0]) ux -= p.nc[0];
-        return crange[warp][kz * STENCIL + ky][ux];
-      }
-      const int cell = cx + p.nc[0] * (cy + p.nc[1] * cz);
-      return make_int2(p.cell_start[cell], p.cell_start[cell + 1]);
-    };
+    Acc<R> fc, fs;
+    R wgt = 1;
+    if (sampled) wgt = (R)nshell / (R)PR;
     if (active) {
       if (sampled) {
-        // ---- pass 3: sampled shell members, spread over the group ---------
-        for (int k = g; k < p.P_R; k += TPA) {
-          const int q = scell[a][k], rank = srank[a][k];
-          const int kz = q / 25, ky = (q / 5) % 5, kx = q % 5;
-          if (q >= 125 || kz >= nkz || ky >= nky || kx >= nkx) continue;  // only after an overflow
-          float shx, shy, shz;
-          const int2 be = cell_range(q, shx, shy, shz);
-          // the rank-th set bit of the cell's shell mask
-          uint32_t m = smk[q][a];
-          for (int t = 0; t < rank; t++) m &= m - 1u;
-          if (m) add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[be.x + __ffs(m) - 1], fs);
+        // ---- pass 3: the sampled shell members ----------------------------------
+        for (int k = g; k < PR; k += TPA) {
+          const int t = stsel[a][k];
+          int lo = 0, hi = nr - 1;                // last row with prefix <= t
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (spre[a][mid] <= t) lo = mid; else hi = mid - 1;
+          }
+          int rank = t - spre[a][lo];
+          int pos = 0;
+          for (int w = 0; w < RW; w++) {
+            const uint32_t m = smask[a][lo][w];
+            const int c = __popc(m);
+            if (rank < c) { pos = 32 * w + select_bit(m, rank); break; }
+            rank -= c;
+          }
+          add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[row_slot(rseg[warp][lo], pos)], fs);
         }
       } else if (take_all) {
-        // whole shell, weight 1: every shell member of the thread's quarter of cells
-        for (int q = g; q < STENCIL * STENCIL * STENCIL; q += TPA) {
-          uint32_t m = smk[q][a];
-          if (m == 0u) continue;
-          float shx, shy, shz;
-          const int b = cell_range(q, shx, shy, shz).x;
-          while (m) {
-            const int t = __ffs(m) - 1;
-            m &= m - 1u;
-            add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[b + t], fs);
+        // whole shell, weight 1: every shell member of the thread's rows
+        for (int r = g; r < nr; r += TPA) {
+          const int4 sg = rseg[warp][r];
+          const int nw = (sg.y + sg.w + 31) >> 5;
+          if (sg.y + sg.w > RW * 32) continue;   // only after an overflow
+          for (int w = 0; w < nw; w++) {
+            uint32_t m = smask[a][r][w];
+            while (m) {
+              const int b = __ffs(m) - 1;
+              m &= m - 1u;
+              add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[row_slot(sg, 32 * w + b)], fs);
+            }
           }
         }
       }
-      // ---- pass 4: exact core sum; the group's core lists are dealt out
-      // round-robin over its threads (entry e of the concatenated list) ----------
     }
+    // ---- pass 4: exact core sum over the group's concatenated core lists ---------
     {
       int cbase = ncore;                         // exclusive prefix of the group's list lengths
 #pragma unroll
@@ -515,9 +480,8 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
 #pragma unroll
           for (int t = 1; t < TPA; t++) owner += (e >= off[t]);
           const int code = score[tid0 + owner][e - off[owner]];
-          float shx, shy, shz;
-          const int j = cell_range(code >> 8, shx, shy, shz).x + (code & 255);
-          add_pair<R, ENERGY>(p, spf, spd, sg, swa, sw, sh2, spi, ui, p.su[j], fc);
+          const int j = row_slot(rseg[warp][code >> 7], code & 127);
+          add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[j], fc);
         }
       }
     }
@@ -562,13 +526,13 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
-  const dim3 g(v.nblk_near), b(NEAR_BLOCK);  // nblk_near = ceil(ncell / cells per block)
-#define RB_NEAR(R, SM, EN) k_near<R, SM, EN><<<g, b, 0, st>>>(v, step_off)
+  const dim3 g(v.nblk_near), b(NEAR_BLOCK);  // one warp per chunk
+#define RB_NEAR(R, WR, EN) k_near<R, WR, EN><<<g, b, 0, st>>>(v, step_off)
   if (v.prec == RBSOG_MIXED) {
-    if (v.small) { if (energy) RB_NEAR(float, true, true); else RB_NEAR(float, true, false); }
+    if (v.wrap) { if (energy) RB_NEAR(float, true, true); else RB_NEAR(float, true, false); }
     else { if (energy) RB_NEAR(float, false, true); else RB_NEAR(float, false, false); }
   } else {
-    if (v.small) { if (energy) RB_NEAR(double, true, true); else RB_NEAR(double, true, false); }
+    if (v.wrap) { if (energy) RB_NEAR(double, true, true); else RB_NEAR(double, true, false); }
     else { if (energy) RB_NEAR(double, false, true); else RB_NEAR(double, false, false); }
   }
 #undef RB_NEAR

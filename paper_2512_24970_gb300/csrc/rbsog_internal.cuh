@@ -66,6 +66,7 @@ struct View {
   double kunit[3];        // 2 pi / L
   float rc2f, rs2f;
   int nc[3], ncell, small;
+  int wrap;               // near field reduces differences to the minimum image (short box)
   float tscale;           // NT_TAB / r_shell^2
   double S;
   double dt, c1;
@@ -85,6 +86,7 @@ struct View {
   int *cell_count, *cell_start, *cell_cursor;
   int *perm_tmp, *perm, *slot_of;
   int *row_chunk;         // [ny*nz + 1] first near-field chunk of each row of cells
+  int2 *chunk_info;       // [chunks] (row of cells, first slot) of each near-field chunk
   // sorted, padded slots: every cell's range is rounded up to a multiple of 4;
   // pads sit at FAR_AWAY (sx, sy, sz) with su.w = SU_PAD
   float *sx, *sy, *sz;    // [nslot] 23-bit coordinates v = u >> 9 as exact floats

@@ -280,10 +280,11 @@ static float pred_r2(const uint32_t *ui, const uint32_t *uj, const float h[3]) {
   return r2;
 }
 
-typedef struct { int64_t key; int32_t j; } cand_t;
+typedef struct { int64_t key; uint32_t ux; int32_t j; } cand_t;
 static int cand_cmp(const void *a, const void *b) {
   const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
   if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->ux != y->ux) return x->ux < y->ux ? -1 : 1;
   return x->j < y->j ? -1 : (x->j > y->j);
 }
 
@@ -308,7 +309,8 @@ static void geo_free(orc_geo *G) { free(G->u); free(G->cell); }
 
 /* Core set {j != i : r^2 < fl32(r_core^2)} and shell set
  * {j != i : fl32(r_core^2) <= r^2 < fl32(r_shell^2)} of atom i, both in
- * canonical order: ascending (cell linear index of j, j).  Brute force.   */
+ * canonical order: ascending (cell linear index of j, fixed-point x
+ * coordinate u_x of j, j).  Brute force.                                  */
 static int atom_lists(const orc_sys *S, const orc_geo *G, int64_t i, cand_t *core,
                       int32_t *ncore, int cap_core, cand_t *shell, int32_t *nshell,
                       int cap_shell) {
@@ -318,11 +320,11 @@ static int atom_lists(const orc_sys *S, const orc_geo *G, int64_t i, cand_t *cor
     if (j == i) continue;
     float r2 = pred_r2(ui, G->u + 3 * j, G->h);
     if (r2 < G->rc2) {
-      if (nc < cap_core) { core[nc].key = G->cell[j]; core[nc].j = (int32_t)j; }
+      if (nc < cap_core) { core[nc].key = G->cell[j]; core[nc].ux = G->u[3 * j]; core[nc].j = (int32_t)j; }
       else over = 1;
       nc++;
     } else if (r2 < G->rs2) {
-      if (ns < cap_shell) { shell[ns].key = G->cell[j]; shell[ns].j = (int32_t)j; }
+      if (ns < cap_shell) { shell[ns].key = G->cell[j]; shell[ns].ux = G->u[3 * j]; shell[ns].j = (int32_t)j; }
       else over = 1;
       ns++;
     }

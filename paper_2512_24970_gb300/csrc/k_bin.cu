@@ -2,10 +2,11 @@
 //   k_prepare   per atom: [half kick, drift / BAOAB B-A-O-A (Sec. 2.3)], 32-bit
 //               fixed-point coordinates, cell index and cell histogram; extra
 //               blocks draw the P_F k-vectors from P(k) (Eq. (Pk)).
-//   k_scan      exclusive scan of the cell histogram (one block).
+//   k_scan      cell ranges (rows of cells padded to a multiple of 4 slots),
+//               padding slots and the near-field chunk table offsets (one block).
 //   k_scatter   counting-sort scatter (slot claimed by atomicAdd).
-//   k_rank      per atom: rank among the caller ids of its cell (the canonical
-//               order of the list) -> sorted slot; write the padded SoA arrays.
+//   k_rank      per atom: rank in its cell by (u_x, caller id), the canonical
+//               order of the list -> sorted slot; write the SoA arrays.
 #include "rbsog_internal.cuh"
 
 namespace rb {
@@ -131,21 +132,15 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   atomicAdd(p.cell_count + cell, 1);
 }
 
-// Exclusive scan of cell_count into cell_start[0..ncell] (and cell_cursor).
-__global__ void __launch_bounds__(1024) k_scan(View p) {
-  __shared__ int wsum[32];
-  const int nt = blockDim.x, t = threadIdx.x;
-  const int per = (p.ncell + nt - 1) / nt;
-  const int b = t * per, e = min(b + per, p.ncell);
-  int local = 0;
-#pragma unroll 8
-  for (int c = b; c < e; c++) local += (p.cell_count[c] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
-  // block exclusive scan of `local`
-  int incl = local;
+// Block-wide exclusive scan of one value per thread (1024 threads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  int incl = v;
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, incl, o);
     if ((t & 31) >= o) incl += y;
   }
+  __syncthreads();
   if ((t & 31) == 31) wsum[t >> 5] = incl;
   __syncthreads();
   if (t < 32) {
@@ -157,50 +152,54 @@ __global__ void __launch_bounds__(1024) k_scan(View p) {
     wsum[t] = w;
   }
   __syncthreads();
-  int run = incl - local + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
-#pragma unroll 8
-  for (int c = b; c < e; c++) {
-    p.cell_start[c] = run;
-    p.cell_cursor[c] = run;
-    run += (p.cell_count[c] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
-  }
-  if (t == nt - 1) p.cell_start[p.ncell] = run;
-  // Chunks of the near-field kernel: the atoms of every row of cells (fixed
-  // y and z) are cut into runs of NEAR_CHUNK consecutive sorted atoms;
-  // row_chunk[r] is the first chunk of row r (exclusive scan).
-  __syncthreads();
-  const int nrow = p.nc[1] * p.nc[2];
-  const int rper = (nrow + nt - 1) / nt;
-  const int rb = t * rper, re = min(rb + rper, nrow);
-  int lc = 0;
+  return incl - v + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
+}
+
+// Cell ranges: the cells of a row of cells (fixed y, z) are contiguous and
+// unpadded; every row is padded to a multiple of CELL_ALIGN slots (padding
+// slots at FAR_AWAY, su.w = SU_PAD, written here).  cell_start[0..ncell],
+// cell_cursor, and the near-field chunks: each row's slots cut into runs of
+// NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.
+__global__ void __launch_bounds__(1024) k_scan(View p) {
+  __shared__ int wsum[32];
+  const int nt = blockDim.x, t = threadIdx.x;
+  const int nc0 = p.nc[0], nrow = p.nc[1] * p.nc[2];
+  const int per = (nrow + nt - 1) / nt;
+  const int rb = min(t * per, nrow), re = min(rb + per, nrow);
+  int local = 0, lchunk = 0;
   for (int r = rb; r < re; r++) {
-    const int na = p.cell_start[(r + 1) * p.nc[0]] - p.cell_start[r * p.nc[0]];
-    lc += (na + NEAR_CHUNK - 1) / NEAR_CHUNK;
+    int tot = 0;
+#pragma unroll 4
+    for (int c = 0; c < nc0; c++) tot += p.cell_count[r * nc0 + c];
+    const int padded = (tot + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
+    local += padded;
+    lchunk += (padded + NEAR_CHUNK - 1) / NEAR_CHUNK;
   }
-  int inc = lc;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if ((t & 31) >= o) inc += y;
-  }
-  __syncthreads();
-  if ((t & 31) == 31) wsum[t >> 5] = inc;
-  __syncthreads();
-  if (t < 32) {
-    int w = (t < (nt >> 5)) ? wsum[t] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (t >= o) w += y;
+  int run = block_exclusive_scan(local, wsum);
+  int crun = block_exclusive_scan(lchunk, wsum);
+  for (int r = rb; r < re; r++) {
+    const int r0 = run;
+    for (int c = 0; c < nc0; c++) {
+      p.cell_start[r * nc0 + c] = run;
+      p.cell_cursor[r * nc0 + c] = run;
+      run += p.cell_count[r * nc0 + c];
     }
-    wsum[t] = w;
+    const int padded = (run - r0 + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
+    for (int k = run; k < r0 + padded; k++) {
+      p.perm[k] = -1;
+      p.sx[k] = FAR_AWAY;
+      p.sy[k] = FAR_AWAY;
+      p.sz[k] = FAR_AWAY;
+      p.su[k] = make_uint4(0u, 0u, 0u, SU_PAD);
+    }
+    run = r0 + padded;
+    p.row_chunk[r] = crun;
+    crun += padded / NEAR_CHUNK + ((padded % NEAR_CHUNK) ? 1 : 0);
   }
-  __syncthreads();
-  int rr = inc - lc + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
-  for (int r = rb; r < re; r++) {
-    p.row_chunk[r] = rr;
-    const int na = p.cell_start[(r + 1) * p.nc[0]] - p.cell_start[r * p.nc[0]];
-    rr += (na + NEAR_CHUNK - 1) / NEAR_CHUNK;
+  if (t == nt - 1) {
+    p.cell_start[p.ncell] = run;
+    p.row_chunk[nrow] = crun;
   }
-  if (t == nt - 1) p.row_chunk[nrow] = rr;
 }
 
 __global__ void __launch_bounds__(256) k_scatter(View p) {
@@ -210,18 +209,22 @@ __global__ void __launch_bounds__(256) k_scatter(View p) {
   p.perm_tmp[slot] = (int)i;
 }
 
-// One thread per atom: its rank among the caller ids of its cell (the
-// canonical order inside a cell) gives its sorted slot; the first atom of a
-// cell also writes the cell's padding slots (FAR_AWAY, SU_PAD).
+// One thread per atom: its rank in its cell under the canonical order
+// (fixed-point x coordinate, caller id), so every row of cells is sorted by x;
+// writes the sorted SoA arrays and the near-field chunk table.
 __global__ void __launch_bounds__(256) k_rank(View p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
   const int c = p.cellid[i];
   const int b = p.cell_start[c], cnt = p.cell_count[c];
-  int rank = 0;
-  for (int k = b; k < b + cnt; k++) rank += (p.perm_tmp[k] < (int)i);
-  const int slot = b + rank;
   const uint4 u = p.ua[i];
+  int rank = 0;
+  for (int k = b; k < b + cnt; k++) {
+    const int j = p.perm_tmp[k];
+    const uint32_t xj = p.ua[j].x;
+    rank += (xj < u.x || (xj == u.x && j < (int)i)) ? 1 : 0;
+  }
+  const int slot = b + rank;
   p.perm[slot] = (int)i;
   p.slot_of[i] = slot;
   p.sx[slot] = (float)(u.x >> 9);
@@ -229,20 +232,12 @@ __global__ void __launch_bounds__(256) k_rank(View p) {
   p.sz[slot] = (float)(u.z >> 9);
   p.su[slot] = make_uint4(u.x, u.y, u.z, (uint32_t)i | (u.w << SU_SP_SHIFT));
   // the near-field chunks (runs of NEAR_CHUNK slots from the start of the row
-  // of cells) that begin in this cell; every run begins at an atom
+  // of cells) that begin at this slot; padding only ends a row, so every run
+  // begins at an atom
   const int row = c / p.nc[0];
   const int rbeg = p.cell_start[row * p.nc[0]];
   if (((slot - rbeg) & (NEAR_CHUNK - 1)) == 0)
     p.chunk_info[p.row_chunk[row] + (slot - rbeg) / NEAR_CHUNK] = make_int2(row, slot);
-  if (rank == 0) {
-    for (int k = b + cnt; k < p.cell_start[c + 1]; k++) {
-      p.perm[k] = -1;
-      p.sx[k] = FAR_AWAY;
-      p.sy[k] = FAR_AWAY;
-      p.sz[k] = FAR_AWAY;
-      p.su[k] = make_uint4(0u, 0u, 0u, SU_PAD);
-    }
-  }
 }
 
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {

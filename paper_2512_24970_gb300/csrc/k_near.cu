@@ -238,6 +238,34 @@ __device__ __forceinline__ int row_slot(const int4 &sg, int pos) {
   return pos < sg.y ? sg.x + pos : sg.z + (pos - sg.y);
 }
 
+// First slot of row-of-cells rb whose sorted x coordinate is >= v (upper:
+// > v); the search is confined to the cells around v's cell.
+__device__ __forceinline__ int sx_bound(const View &p, int rb, float v, bool upper) {
+  const int nc0 = p.nc[0];
+  const int c = min(max((int)(v * ((float)nc0 * 1.1920928955078125e-07f)), 0), nc0 - 1);
+  int lo = p.cell_start[rb + max(c - 1, 0)], hi = p.cell_start[rb + min(c + 2, nc0)];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float x = __ldg(p.sx + mid);
+    if (upper ? (x <= v) : (x < v)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// pred_r2_x4 with the results left packed: q0 = (r2[0], r2[1]), q1 = (r2[2], r2[3])
+__device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *sy, const float *sz, int j0,
+                                                  const PredX4 &c, unsigned long long &q0,
+                                                  unsigned long long &q1) {
+  const ulonglong2 X = __ldg(reinterpret_cast<const ulonglong2 *>(sx + j0));
+  const ulonglong2 Y = __ldg(reinterpret_cast<const ulonglong2 *>(sy + j0));
+  const ulonglong2 Z = __ldg(reinterpret_cast<const ulonglong2 *>(sz + j0));
+  const unsigned long long ax0 = mul2(add2(X.x, c.nx), c.hx), ax1 = mul2(add2(X.y, c.nx), c.hx);
+  const unsigned long long ay0 = mul2(add2(Y.x, c.ny), c.hy), ay1 = mul2(add2(Y.y, c.ny), c.hy);
+  const unsigned long long az0 = mul2(add2(Z.x, c.nz), c.hz), az1 = mul2(add2(Z.y, c.nz), c.hz);
+  q0 = fma2(az0, az0, fma2(ay0, ay0, mul2(ax0, ax0)));
+  q1 = fma2(az1, az1, fma2(ay1, ay1, mul2(ax1, ax1)));
+}
+
 template <typename R, bool WRAP, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
@@ -290,89 +318,167 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
     const bool full = WRAP && W > nc0;         // the whole row (minimum image per pair)
     bool over = !full && W > WMAX;
     // ---- candidate runs and image shifts of the stencil rows ------------------
+    // Rows of cells are sorted by x.  Without WRAP, lane r culls stencil row r
+    // to the union, over the chunk's atoms, of the x-intervals that can hold a
+    // neighbour (|dx| <= sqrt(r_s^2 - gap_y^2 - gap_z^2) with the gaps to the
+    // row's y and z slabs, all widened), inside the union of their five-cell
+    // x-stencils; the interval becomes one or two runs of slots by binary
+    // search.  Runs are widened to whole groups of CELL_ALIGN slots: a slot
+    // outside every atom's interval fails the predicate, and a slot in both
+    // runs of a row passes for at most one of its two images (L >= 2 r_shell).
+    float qx[APW], qy[APW], qz[APW];
+#pragma unroll
+    for (int q = 0; q < APW; q++) {
+      qx[q] = __shfl_sync(0xffffffffu, me.x, TPA * q);
+      qy[q] = __shfl_sync(0xffffffffu, me.y, TPA * q);
+      qz[q] = __shfl_sync(0xffffffffu, me.z, TPA * q);
+    }
+    const uint32_t qact = __ballot_sync(0xffffffffu, active);   // bit TPA*q: atom q
     if (lane < nr) {
       const int kz = lane / nky, ky = lane - kz * nky;
       float shy, shz;
       const int cy = axis_cell(ay, ky, WRAP, shy);
       const int cz = axis_cell(az, kz, WRAP, shz);
-      const int* cs = p.cell_start + nc0 * (cy + p.nc[1] * cz);
-      int a0, a1, b0 = 0, b1 = 0;
+      const int rb = nc0 * (cy + p.nc[1] * cz);
+      const int rs0 = p.cell_start[rb], rs1 = p.cell_start[rb + nc0];   // the row (padded end)
+      int a0 = 0, a1 = 0, b0 = 0, b1 = 0;
       float sa = 0.0f, sb = 0.0f;
       const int xs = cx_lo - 2, xe = cx_hi + 2;
       if (over) {                              // rejected chunk: empty rows
-        a0 = a1 = 0;
-      } else if (full) {
-        a0 = cs[0]; a1 = cs[nc0];
-      } else if (xs < 0) {                     // cells 0..xe, then nc0+xs..nc0-1 (image at -L)
-        a0 = cs[0]; a1 = cs[min(xe + 1, nc0)];
-        b0 = cs[nc0 + xs]; b1 = cs[nc0]; sb = -8388608.0f;
-      } else if (xe >= nc0) {                  // cells 0..xe-nc0 (image at +L), then xs..nc0-1
-        a0 = cs[0]; a1 = cs[min(xe - nc0 + 1, nc0)]; sa = 8388608.0f;
-        b0 = cs[xs]; b1 = cs[nc0];
+      } else if (WRAP) {
+        if (full) {
+          a0 = rs0; a1 = rs1;
+        } else if (xs < 0) {                   // cells 0..xe, then nc0+xs..nc0-1
+          a0 = rs0; a1 = p.cell_start[rb + xe + 1];
+          b0 = p.cell_start[rb + nc0 + xs]; b1 = rs1;
+        } else if (xe >= nc0) {                // cells 0..xe-nc0, then xs..nc0-1
+          a0 = rs0; a1 = p.cell_start[rb + xe - nc0 + 1];
+          b0 = p.cell_start[rb + xs]; b1 = rs1;
+        } else {
+          a0 = p.cell_start[rb + xs]; a1 = p.cell_start[rb + xe + 1];
+        }
       } else {
-        a0 = cs[xs]; a1 = cs[xe + 1];
+        const float cwx = 8388608.0f / (float)nc0;
+        const float cwy = 8388608.0f / (float)p.nc[1], cwz = 8388608.0f / (float)p.nc[2];
+        const float ylo = __fmaf_rn((float)cy, cwy, shy) - 4.0f, yhi = __fmaf_rn((float)(cy + 1), cwy, shy) + 4.0f;
+        const float zlo = __fmaf_rn((float)cz, cwz, shz) - 4.0f, zhi = __fmaf_rn((float)(cz + 1), cwz, shz) + 4.0f;
+        const float cull2 = p.rs2f * 1.0005f;
+        const float unit = 1.0001f / p.hp[0];   // 23-bit units per Angstrom along x, widened
+        float xlo = 3.0e7f, xhi = -3.0e7f;
+#pragma unroll
+        for (int q = 0; q < APW; q++) {
+          if (!((qact >> (TPA * q)) & 1u)) continue;
+          const float gy = fmaxf(0.0f, fmaxf(ylo - qy[q], qy[q] - yhi)) * p.hp[1];
+          const float gz = fmaxf(0.0f, fmaxf(zlo - qz[q], qz[q] - zhi)) * p.hp[2];
+          const float R2 = cull2 - gy * gy - gz * gz;
+          if (R2 > 0.0f) {
+            const float R = __fmaf_rn(sqrtf(R2), unit, 8.0f);
+            xlo = fminf(xlo, qx[q] - R);
+            xhi = fmaxf(xhi, qx[q] + R);
+          }
+        }
+        xlo = fmaxf(xlo, (float)xs * cwx - 8.0f);
+        xhi = fminf(xhi, (float)(xe + 1) * cwx + 8.0f);
+        if (xlo <= xhi) {
+          if (xlo < 0.0f) {                    // [0, xhi], then [xlo + 2^23, 2^23) at image -L
+            a0 = rs0; a1 = sx_bound(p, rb, xhi, true);
+            b0 = sx_bound(p, rb, xlo + 8388608.0f, false); b1 = rs1; sb = -8388608.0f;
+          } else if (xhi >= 8388608.0f) {      // [0, xhi - 2^23] at image +L, then [xlo, 2^23)
+            a0 = rs0; a1 = sx_bound(p, rb, xhi - 8388608.0f, true); sa = 8388608.0f;
+            b0 = sx_bound(p, rb, xlo, false); b1 = rs1;
+          } else {
+            a0 = sx_bound(p, rb, xlo, false); a1 = sx_bound(p, rb, xhi, true);
+          }
+        }
+      }
+      a0 &= ~(CELL_ALIGN - 1);
+      a1 = max(a0, min((a1 + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1), rs1));
+      b0 &= ~(CELL_ALIGN - 1);
+      b1 = max(b0, min((b1 + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1), rs1));
+      if (WRAP && b1 > b0 && a1 >= b0) {      // touching runs of one image order merge
+        a1 = b1;
+        b0 = b1 = 0;
       }
       rseg[warp][lane] = make_int4(a0, a1 - a0, b0, b1 - b0);
       rsh[warp][lane] = make_float4(sa, sb, shy, shz);
     }
     __syncwarp();
-    // ---- pass 1 -----------------------------------------------------------------
-    const float rs2 = p.rs2f, rc2 = p.rc2f;
+    // ---- pass 1: the four threads of an atom split each row's groups of four
+    // slots (group q to thread q mod 4) and OR their bits into whole words ----
+    const unsigned long long RS2 = pk2(-p.rs2f, -p.rs2f), RC2 = pk2(-p.rc2f, -p.rc2f);
     int my_total = 0, ncore = 0;
-    for (int r = g; r < nr; r += TPA) {
+    for (int r = 0; r < nr; r++) {
       const int4 sg = rseg[warp][r];
       const float4 sh = rsh[warp][r];
       const int len = sg.y + sg.w;
       if (len > RW * 32 || over) {
         over = true;
-        scnt[a][r] = 0;
+        if (g == 0) scnt[a][r] = 0;
         continue;
       }
       const int pself = (slot >= sg.x && slot < sg.x + sg.y) ? slot - sg.x
                         : ((slot >= sg.z && slot < sg.z + sg.w) ? sg.y + slot - sg.z : -1);
-      uint32_t accs = 0u, accc = 0u;
-      int pos = 0, cnt = 0;
-      // close the word of positions [pos - m, pos)
-      auto flush = [&](int m) {
-        const int w = (pos - 1) >> 5;
-        uint32_t ws = __brev(accs) >> (32 - m);
-        uint32_t wc = __brev(accc) >> (32 - m);
-        if ((pself >> 5) == w && pself >= 0) {
-          ws &= ~(1u << (pself & 31));
-          wc &= ~(1u << (pself & 31));
-        }
-        ws &= ~wc;                                // shell: inside r_shell, not core, not self
-        smask[a][r][w] = ws;
-        cnt += __popc(ws);
-        while (wc) {
-          const int b = __ffs(wc) - 1;
-          wc &= wc - 1u;
-          if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((r << 7) | (32 * w + b));
-          ncore++;
-        }
-        accs = 0u;
-        accc = 0u;
-      };
-#pragma unroll 1
-      for (int run = 0; run < 2; run++) {
-        const int j0 = run ? sg.z : sg.x, nrun = run ? sg.w : sg.y;
-        const PredX4 pc = pred_x4_setup(me.x - (run ? sh.y : sh.x), me.y - sh.z, me.z - sh.w, p.hp);
-        for (int k = 0; k < nrun; k += CELL_ALIGN) {
-          float r2v[4];
-          if (WRAP) pred_r2_x4_wrap(p, j0 + k, me.x, me.y, me.z, r2v);
-          else pred_r2_x4(p.sx, p.sy, p.sz, j0 + k, pc, r2v);
+      PredX4 pc = pred_x4_setup(me.x - sh.x, me.y - sh.z, me.z - sh.w, p.hp);
+      const unsigned long long nxa = pc.nx;
+      const unsigned long long nxb = pk2(sh.y - me.x, sh.y - me.x);
+      int cnt = 0;
+      for (int w = 0; 32 * w < len; w++) {
+        uint32_t ms = 0u, mc = 0u;
 #pragma unroll
-          for (int t = 0; t < 4; t++) {
+        for (int h = 0; h < 2; h++) {
+          const int pos = 4 * (8 * w + g + TPA * h);
+          if (pos < len) {
+            const bool inb = pos >= sg.y;
+            const int j0 = inb ? sg.z + (pos - sg.y) : sg.x + pos;
+            unsigned long long q0, q1;
+            if (WRAP) {
+              float r2v[4];
+              pred_r2_x4_wrap(p, j0, me.x, me.y, me.z, r2v);
+              q0 = pk2(r2v[0], r2v[1]);
+              q1 = pk2(r2v[2], r2v[3]);
+            } else {
+              pc.nx = inb ? nxb : nxa;
+              pred_r2_x4_packed(p.sx, p.sy, p.sz, j0, pc, q0, q1);
+            }
             // sign of r^2 - threshold: set iff r^2 < threshold (r^2 = +inf at pads)
-            accs = __funnelshift_l(__float_as_uint(r2v[t] - rs2), accs, 1);
-            accc = __funnelshift_l(__float_as_uint(r2v[t] - rc2), accc, 1);
+            float s0, s1, s2, s3, c0, c1, c2, c3;
+            up2(add2(q0, RS2), s0, s1);
+            up2(add2(q1, RS2), s2, s3);
+            up2(add2(q0, RC2), c0, c1);
+            up2(add2(q1, RC2), c2, c3);
+            uint32_t ns = __float_as_uint(s3) >> 31, nc = __float_as_uint(c3) >> 31;
+            ns = __funnelshift_l(__float_as_uint(s2), ns, 1);
+            nc = __funnelshift_l(__float_as_uint(c2), nc, 1);
+            ns = __funnelshift_l(__float_as_uint(s1), ns, 1);
+            nc = __funnelshift_l(__float_as_uint(c1), nc, 1);
+            ns = __funnelshift_l(__float_as_uint(s0), ns, 1);
+            nc = __funnelshift_l(__float_as_uint(c0), nc, 1);
+            ms |= ns << (pos & 31);
+            mc |= nc << (pos & 31);
           }
-          pos += 4;
-          if ((pos & 31) == 0) flush(32);
+        }
+#pragma unroll
+        for (int o = 1; o < TPA; o <<= 1) {
+          ms |= __shfl_xor_sync(0xffffffffu, ms, o, TPA);
+          mc |= __shfl_xor_sync(0xffffffffu, mc, o, TPA);
+        }
+        if (pself >= 0 && (pself >> 5) == w) {
+          ms &= ~(1u << (pself & 31));
+          mc &= ~(1u << (pself & 31));
+        }
+        ms &= ~mc;                                // shell: inside r_shell, not core, not self
+        cnt += __popc(ms);
+        if (g == (w & (TPA - 1))) {               // one thread files the word
+          smask[a][r][w] = ms;
+          while (mc) {
+            const int b = __ffs(mc) - 1;
+            mc &= mc - 1u;
+            if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((r << 7) | (32 * w + b));
+            ncore++;
+          }
         }
       }
-      if (pos & 31) flush(pos & 31);
-      scnt[a][r] = (unsigned char)cnt;
+      if (g == 0) scnt[a][r] = (unsigned char)cnt;
       my_total += cnt;
     }
     if (!active) { my_total = 0; ncore = 0; over = false; }
@@ -380,9 +486,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
     if (over) atomicOr(p.err, ncore > CORE_T ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
     ncore = min(ncore, CORE_T);
     // ---- pass 2: prefix of the row counts, Floyd's draw ---------------------------
-    int nshell = my_total;
-#pragma unroll
-    for (int o = 1; o < TPA; o <<= 1) nshell += __shfl_xor_sync(0xffffffffu, nshell, o, TPA);
+    const int nshell = my_total;                 // every thread of the group counted all words
     const bool take_all = p.whole_shell || nshell <= p.P_R;
     const bool sampled = active && !take_all && nshell <= SHELL_BITS;
     if (active && !take_all && nshell > SHELL_BITS && g == 0) atomicOr(p.err, ERR_CELL_SHELL_CAP);

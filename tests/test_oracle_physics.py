@@ -181,8 +181,8 @@ def test_lists_against_float64_distances(orc):
         assert sure_shell <= shell
         assert shell <= set(np.where((r > S.r_core - tol) & (r < S.r_shell + tol))[0])
         s_list = L["shell"][q, :L["nshell"][q]]
-        key = lin[s_list].astype(np.int64) * w.n + s_list
-        assert np.all(np.diff(key) > 0)
+        key = np.lexsort((s_list, u[s_list, 0], lin[s_list]))     # (cell, u_x, j) ascending
+        np.testing.assert_array_equal(key, np.arange(len(s_list)))
         b = L["batch"][q, :L["nbatch"][q]]
         assert set(b.tolist()) <= shell and len(set(b.tolist())) == len(b)
 

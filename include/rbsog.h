@@ -67,7 +67,7 @@ extern "C" {
 /* Capacities of the device path (exceeding one sets RBSOG_E_CAP_OVERFLOW). */
 #define RBSOG_MAX_SPECIES 8
 #define RBSOG_MAX_PR 64        /* shell batch size P_R */
-#define RBSOG_MAX_CORE 96      /* core neighbours per atom */
+#define RBSOG_MAX_CORE 64      /* core neighbours per atom */
 #define RBSOG_MAX_ROW_SLOTS 128 /* candidate slots of one stencil row: the x-cells a run of
                                    8 sorted atoms needs, each cell padded to a multiple of 4
                                    (also: a run of 8 atoms spans at most 4 cells along x) */

@@ -413,7 +413,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.perm, NS)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
       (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) ||
       (rc = dalloc(ctx, &v.chunk_info, (size_t)v.nblk_near * rb::NEAR_WARPS)) || (rc = dalloc(ctx, &v.sx, NS)) ||
-      (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near)) ||
+      (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near * rb::NEAR_WARPS)) ||
+      (rc = dalloc(ctx, &v.corr_part, 4 * 64)) || (rc = dalloc(ctx, &v.corr_ticket, 1)) ||
       (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
       (rc = dalloc(ctx, &wa, (size_t)v.G)) || (rc = dalloc(ctx, &w, (size_t)v.G)) || (rc = dalloc(ctx, &h2, (size_t)v.G)) ||
@@ -486,6 +487,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaMemsetAsync(v.err, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(v.step, 0, sizeof(long long), ctx->st));
   CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 8, ctx->st));
+  CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
   CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
   ctx->has_system = true;
   ctx->forces_valid = false;

@@ -144,14 +144,20 @@ __global__ void __launch_bounds__(256) k_reduce(View p, int step_off) {
   }
 }
 
-// F^corr = (1/N) sum of the near-field block partials, and U_N: one block,
-// thread-strided sums then a fixed-order tree (deterministic).
+// F^corr = (1/N) sum of the near-field warp partials, and U_N.  Block b sums
+// the fixed slice b of the partials (thread-strided, then a fixed tree); the
+// last block to finish adds the CORR_BLOCKS block sums in index order, so the
+// result does not depend on which block finishes when.
+constexpr int CORR_BLOCKS = 64;
 __global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
   __shared__ double red[4][256];
+  __shared__ bool last;
   const int t = threadIdx.x;
+  const int np = p.nblk_near * NEAR_WARPS;
+  const int per = (np + CORR_BLOCKS - 1) / CORR_BLOCKS;
+  const int b0 = blockIdx.x * per, b1 = min(b0 + per, np);
   double f[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-  for (int b = t; b < p.nblk_near; b += 256)
+  for (int b = b0 + t; b < b1; b += 256)
     for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
   for (int a = 0; a < 4; a++) red[a][t] = f[a];
   __syncthreads();
@@ -160,9 +166,21 @@ __global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
       for (int a = 0; a < 4; a++) red[a][t] += red[a][t + o];
     __syncthreads();
   }
+  if (t < 4) p.corr_part[4 * blockIdx.x + t] = red[t][0];
+  __threadfence();
+  __syncthreads();
+  if (t == 0) last = (atomicAdd(p.corr_ticket, 1u) == CORR_BLOCKS - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (t < 4) {
+    double v = 0.0;
+    for (int k = 0; k < CORR_BLOCKS; k++) v += ((volatile double *)p.corr_part)[4 * k + t];
+    if (t < 3) p.red[t] = v / (double)p.n;
+    else p.red[3] = v;
+  }
   if (t == 0) {
-    for (int a = 0; a < 3; a++) p.red[a] = red[a][0] / (double)p.n;
-    p.red[3] = red[3][0];
+    *p.corr_ticket = 0u;                          // ready for the next evaluation
     if (step_off) *p.step += step_off;
   }
 }
@@ -277,7 +295,7 @@ void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
   const int g = max(1, (v.P + 7) / 8);
   if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, step_off);
   else k_reduce<double><<<g, 256, 0, st>>>(v, step_off);
-  k_corr<<<1, 256, 0, st>>>(v, step_off);
+  k_corr<<<CORR_BLOCKS, 256, 0, st>>>(v, step_off);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 

@@ -194,8 +194,7 @@ constexpr int TPA = 4;
 constexpr int APW = NEAR_CHUNK;              // atoms per warp
 constexpr int APB = NEAR_WARPS * NEAR_CHUNK; // atoms per block
 constexpr int NROW = STENCIL * STENCIL;      // stencil rows (y, z)
-constexpr int RW = RBSOG_MAX_ROW_SLOTS / 32; // mask words of one stencil row
-constexpr int CORE_T = 40;                   // core neighbours per thread
+constexpr int GBYTES = 384;                  // candidate groups one atom's chunk may test
 constexpr int SHELL_BITS = RBSOG_MAX_SHELL;  // shell members one bitmask can index
 constexpr int WMAX = 8;                      // union x-cells of a chunk
 static_assert(TPA * NEAR_CHUNK == 32 && NEAR_WARPS * 32 == NEAR_BLOCK, "near-field block layout");
@@ -269,17 +268,19 @@ __device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *
 template <typename R, bool WRAP, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
-  __shared__ uint32_t smask[APB][NROW][RW];      // shell members of each stencil row
-  __shared__ unsigned char scnt[APB][NROW];      // their counts
+  // per-atom rows padded by one word so that the eight atoms of a warp hit distinct banks
+  __shared__ __align__(16) unsigned char gres[APB][GBYTES + 4]; // per group of 4 candidates: r < r_shell (bits 0-3), r < r_core (4-7)
+  __shared__ unsigned char scnt[APB][NROW];      // shell members of each stencil row
   __shared__ unsigned short spre[APB][NROW + 1]; // exclusive prefix of the counts
-  __shared__ unsigned short stsel[APB][RBSOG_MAX_PR];
-  __shared__ uint32_t bmask[APB][SHELL_BITS / 32];
-  __shared__ unsigned short score[NEAR_BLOCK][CORE_T];  // (row << 7 | position)
+  __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
+  __shared__ uint32_t bmask[APB][SHELL_BITS / 32 + 1];
+  __shared__ unsigned short score[APB][RBSOG_MAX_CORE + 2];  // core list (row << 7 | position)
   __shared__ int4 rseg[NEAR_WARPS][NROW];        // candidate runs (a0, na, b0, nb)
   __shared__ float4 rsh[NEAR_WARPS][NROW];       // image shifts (x of run a, x of run b, y, z)
+  __shared__ int rgo[NEAR_WARPS][NROW + 1];      // first group of each row (flattened)
+  __shared__ int rbo[NEAR_WARPS][NROW];          // first byte of each row in gres
   __shared__ PairF spf[MIX ? RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
   __shared__ PairD spd[MIX ? 1 : RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
-  __shared__ double red[4][NEAR_WARPS];
   const int tid = threadIdx.x;
   const int nsp2 = p.ns * p.ns;
   for (int k = tid; k < nsp2; k += NEAR_BLOCK) {
@@ -402,91 +403,129 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
       rseg[warp][lane] = make_int4(a0, a1 - a0, b0, b1 - b0);
       rsh[warp][lane] = make_float4(sa, sb, shy, shz);
     }
-    __syncwarp();
-    // ---- pass 1: the four threads of an atom split each row's groups of four
-    // slots (group q to thread q mod 4) and OR their bits into whole words ----
-    const unsigned long long RS2 = pk2(-p.rs2f, -p.rs2f), RC2 = pk2(-p.rc2f, -p.rc2f);
-    int my_total = 0, ncore = 0;
-    for (int r = 0; r < nr; r++) {
-      const int4 sg = rseg[warp][r];
-      const float4 sh = rsh[warp][r];
-      const int len = sg.y + sg.w;
-      if (len > RW * 32 || over) {
-        over = true;
-        if (g == 0) scnt[a][r] = 0;
-        continue;
-      }
-      const int pself = (slot >= sg.x && slot < sg.x + sg.y) ? slot - sg.x
-                        : ((slot >= sg.z && slot < sg.z + sg.w) ? sg.y + slot - sg.z : -1);
-      PredX4 pc = pred_x4_setup(me.x - sh.x, me.y - sh.z, me.z - sh.w, p.hp);
-      const unsigned long long nxa = pc.nx;
-      const unsigned long long nxb = pk2(sh.y - me.x, sh.y - me.x);
-      int cnt = 0;
-      for (int w = 0; 32 * w < len; w++) {
-        uint32_t ms = 0u, mc = 0u;
+    // ---- flattened groups of four candidates: row r holds groups
+    // [rgo[r], rgo[r+1]) and bytes [rbo[r], rbo[r] + groups) of gres ----------
+    {
+      const int len = lane < nr ? rseg[warp][lane].y + rseg[warp][lane].w : 0;
+      if (len > RBSOG_MAX_ROW_SLOTS) over = true;
+      const int ng = len / CELL_ALIGN, nbyte = (ng + 3) & ~3;
+      int ig = ng, ib = nbyte;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const int pos = 4 * (8 * w + g + TPA * h);
-          if (pos < len) {
-            const bool inb = pos >= sg.y;
-            const int j0 = inb ? sg.z + (pos - sg.y) : sg.x + pos;
-            unsigned long long q0, q1;
-            if (WRAP) {
-              float r2v[4];
-              pred_r2_x4_wrap(p, j0, me.x, me.y, me.z, r2v);
-              q0 = pk2(r2v[0], r2v[1]);
-              q1 = pk2(r2v[2], r2v[3]);
-            } else {
-              pc.nx = inb ? nxb : nxa;
-              pred_r2_x4_packed(p.sx, p.sy, p.sz, j0, pc, q0, q1);
-            }
-            // sign of r^2 - threshold: set iff r^2 < threshold (r^2 = +inf at pads)
-            float s0, s1, s2, s3, c0, c1, c2, c3;
-            up2(add2(q0, RS2), s0, s1);
-            up2(add2(q1, RS2), s2, s3);
-            up2(add2(q0, RC2), c0, c1);
-            up2(add2(q1, RC2), c2, c3);
-            uint32_t ns = __float_as_uint(s3) >> 31, nc = __float_as_uint(c3) >> 31;
-            ns = __funnelshift_l(__float_as_uint(s2), ns, 1);
-            nc = __funnelshift_l(__float_as_uint(c2), nc, 1);
-            ns = __funnelshift_l(__float_as_uint(s1), ns, 1);
-            nc = __funnelshift_l(__float_as_uint(c1), nc, 1);
-            ns = __funnelshift_l(__float_as_uint(s0), ns, 1);
-            nc = __funnelshift_l(__float_as_uint(c0), nc, 1);
-            ms |= ns << (pos & 31);
-            mc |= nc << (pos & 31);
-          }
-        }
-#pragma unroll
-        for (int o = 1; o < TPA; o <<= 1) {
-          ms |= __shfl_xor_sync(0xffffffffu, ms, o, TPA);
-          mc |= __shfl_xor_sync(0xffffffffu, mc, o, TPA);
-        }
-        if (pself >= 0 && (pself >> 5) == w) {
-          ms &= ~(1u << (pself & 31));
-          mc &= ~(1u << (pself & 31));
-        }
-        ms &= ~mc;                                // shell: inside r_shell, not core, not self
-        cnt += __popc(ms);
-        if (g == (w & (TPA - 1))) {               // one thread files the word
-          smask[a][r][w] = ms;
-          while (mc) {
-            const int b = __ffs(mc) - 1;
-            mc &= mc - 1u;
-            if (ncore < CORE_T) score[tid][ncore] = (unsigned short)((r << 7) | (32 * w + b));
-            ncore++;
-          }
-        }
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y1 = __shfl_up_sync(0xffffffffu, ig, o), y2 = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ig += y1; ib += y2; }
       }
-      if (g == 0) scnt[a][r] = (unsigned char)cnt;
-      my_total += cnt;
+      if (lane < nr) {
+        rgo[warp][lane] = ig - ng;
+        rbo[warp][lane] = ib - nbyte;
+      }
+      if (lane == 31) rgo[warp][nr] = ig;
+      if (__shfl_sync(0xffffffffu, ib, 31) > GBYTES) over = true;
     }
-    if (!active) { my_total = 0; ncore = 0; over = false; }
-    if (ncore > CORE_T) over = true;
-    if (over) atomicOr(p.err, ncore > CORE_T ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
-    ncore = min(ncore, CORE_T);
+    over = __any_sync(0xffffffffu, over);
+    __syncwarp();
+    // ---- pass 1: the chunk's groups dealt round-robin over an atom's four
+    // threads (all eight atoms test the same group at the same time) ---------
+    const unsigned long long RS2 = pk2(-p.rs2f, -p.rs2f), RC2 = pk2(-p.rc2f, -p.rc2f);
+    if (!over) {
+      const int G = rgo[warp][nr];
+      int r = -1, rg0 = 0, rg1 = 0, bo = 0;
+      int4 sg = make_int4(0, 0, 0, 0);
+      PredX4 pc = pred_x4_setup(me.x, me.y, me.z, p.hp);
+      unsigned long long nxa = 0ull, nxb = 0ull;
+      for (int gi = g; gi < G; gi += TPA) {
+        if (gi >= rg1) {                          // next row holding group gi
+          do { r++; rg1 = rgo[warp][r + 1]; } while (gi >= rg1);
+          rg0 = rgo[warp][r];
+          bo = rbo[warp][r];
+          sg = rseg[warp][r];
+          const float4 sh = rsh[warp][r];
+          pc = pred_x4_setup(me.x - sh.x, me.y - sh.z, me.z - sh.w, p.hp);
+          nxa = pc.nx;
+          nxb = pk2(sh.y - me.x, sh.y - me.x);
+        }
+        const int pos = CELL_ALIGN * (gi - rg0);
+        const bool inb = pos >= sg.y;
+        const int j0 = inb ? sg.z + (pos - sg.y) : sg.x + pos;
+        unsigned long long q0, q1;
+        if (WRAP) {
+          float r2v[4];
+          pred_r2_x4_wrap(p, j0, me.x, me.y, me.z, r2v);
+          q0 = pk2(r2v[0], r2v[1]);
+          q1 = pk2(r2v[2], r2v[3]);
+        } else {
+          pc.nx = inb ? nxb : nxa;
+          pred_r2_x4_packed(p.sx, p.sy, p.sz, j0, pc, q0, q1);
+        }
+        // sign of r^2 - threshold: set iff r^2 < threshold (r^2 = +inf at pads)
+        float s0, s1, s2, s3, c0, c1, c2, c3;
+        up2(add2(q0, RS2), s0, s1);
+        up2(add2(q1, RS2), s2, s3);
+        up2(add2(q0, RC2), c0, c1);
+        up2(add2(q1, RC2), c2, c3);
+        uint32_t bits = __float_as_uint(c3) >> 31;
+        bits = __funnelshift_l(__float_as_uint(c2), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(c1), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(c0), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(s3), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(s2), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(s1), bits, 1);
+        bits = __funnelshift_l(__float_as_uint(s0), bits, 1);
+        const unsigned d = (unsigned)(slot - j0);
+        if (d < 4u) bits &= ~(0x11u << d);        // not the atom itself
+        gres[a][bo + (pos >> 2)] = (unsigned char)bits;
+      }
+    }
+    __syncwarp();
+    // ---- shell counts of the rows r = g, g + 4, ...; the atom's core list -----
+    int my_total = 0, mycore = 0;
+    if (!over) {
+      for (int r = g; r < nr; r += TPA) {
+        const int ng = rgo[warp][r + 1] - rgo[warp][r];
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(&gres[a][rbo[warp][r]]);
+        int cnt = 0;
+        for (int w = 0; 4 * w < ng; w++) {
+          uint32_t x = wp[w];
+          if (ng - 4 * w < 4) x &= (1u << (8 * (ng - 4 * w))) - 1u;   // groups past the row
+          const uint32_t cm = (x >> 4) & 0x0F0F0F0Fu;
+          cnt += __popc(x & 0x0F0F0F0Fu & ~cm);
+          mycore += __popc(cm);
+        }
+        scnt[a][r] = (unsigned char)min(cnt, 255);
+        my_total += cnt;
+      }
+    }
+    if (!active) { my_total = 0; mycore = 0; over = false; }
+    int cbase = mycore;                          // this thread's offset in the atom's core list
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, cbase, o, TPA);
+      if (g >= o) cbase += y;
+    }
+    const int ncore = __shfl_sync(0xffffffffu, cbase, TPA - 1, TPA);
+    cbase -= mycore;
+    if (active && !over && ncore <= RBSOG_MAX_CORE) {
+      for (int r = g; r < nr; r += TPA) {
+        const int ng = rgo[warp][r + 1] - rgo[warp][r];
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(&gres[a][rbo[warp][r]]);
+        for (int w = 0; 4 * w < ng; w++) {
+          uint32_t x = wp[w];
+          if (ng - 4 * w < 4) x &= (1u << (8 * (ng - 4 * w))) - 1u;
+          uint32_t cm = (x >> 4) & 0x0F0F0F0Fu;
+          while (cm) {
+            const int b = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            score[a][cbase++] = (unsigned short)((r << 7) | (16 * w + 4 * (b >> 3) + (b & 3)));
+          }
+        }
+      }
+    }
+    if (active && ncore > RBSOG_MAX_CORE) over = true;
+    if (over) atomicOr(p.err, (active && ncore > RBSOG_MAX_CORE) ? ERR_CORE_CAP : ERR_CELL_SHELL_CAP);
     // ---- pass 2: prefix of the row counts, Floyd's draw ---------------------------
-    const int nshell = my_total;                 // every thread of the group counted all words
+    int nshell = my_total;
+#pragma unroll
+    for (int o = 1; o < TPA; o <<= 1) nshell += __shfl_xor_sync(0xffffffffu, nshell, o, TPA);
     const bool take_all = p.whole_shell || nshell <= p.P_R;
     const bool sampled = active && !take_all && nshell <= SHELL_BITS;
     if (active && !take_all && nshell > SHELL_BITS && g == 0) atomicOr(p.err, ERR_CELL_SHELL_CAP);
@@ -526,67 +565,86 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
     Acc<R> fc, fs;
     R wgt = 1;
     if (sampled) wgt = (R)nshell / (R)PR;
+    // shell member position of row r -> slot; the shell bits of gres word x
+    auto shell_bits = [&](int r, int w, int ng) -> uint32_t {
+      uint32_t x = reinterpret_cast<const uint32_t *>(&gres[a][rbo[warp][r]])[w];
+      if (ng - 4 * w < 4) x &= (1u << (8 * (ng - 4 * w))) - 1u;
+      return x & 0x0F0F0F0Fu & ~((x >> 4) & 0x0F0F0F0Fu);
+    };
     if (active) {
       if (sampled) {
-        // ---- pass 3: the sampled shell members ----------------------------------
-        for (int k = g; k < PR; k += TPA) {
-          const int t = stsel[a][k];
-          int lo = 0, hi = nr - 1;                // last row with prefix <= t
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (spre[a][mid] <= t) lo = mid; else hi = mid - 1;
+        // ---- pass 3: the sampled shell members, four at a time per thread ------
+        for (int k0 = g; k0 < PR; k0 += 4 * TPA) {
+          int js[4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            const int k = k0 + TPA * i;
+            js[i] = -1;
+            if (k < PR) {
+              const int t = stsel[a][k];
+              int lo = 0, hi = nr - 1;            // last row with prefix <= t
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (spre[a][mid] <= t) lo = mid; else hi = mid - 1;
+              }
+              int rank = t - spre[a][lo];
+              const int ng = rgo[warp][lo + 1] - rgo[warp][lo];
+              for (int w = 0; 4 * w < ng; w++) {
+                const uint32_t m = shell_bits(lo, w, ng);
+                const int c = __popc(m);
+                if (rank < c) {
+                  const int b = select_bit(m, rank);
+                  js[i] = row_slot(rseg[warp][lo], 16 * w + 4 * (b >> 3) + (b & 3));
+                  break;
+                }
+                rank -= c;
+              }
+            }
           }
-          int rank = t - spre[a][lo];
-          int pos = 0;
-          for (int w = 0; w < RW; w++) {
-            const uint32_t m = smask[a][lo][w];
-            const int c = __popc(m);
-            if (rank < c) { pos = 32 * w + select_bit(m, rank); break; }
-            rank -= c;
-          }
-          add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[row_slot(rseg[warp][lo], pos)], fs);
+          uint4 uj[4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
+#pragma unroll
+          for (int i = 0; i < 4; i++)
+            if (js[i] >= 0) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fs);
         }
       } else if (take_all) {
         // whole shell, weight 1: every shell member of the thread's rows
         for (int r = g; r < nr; r += TPA) {
+          const int ng = rgo[warp][r + 1] - rgo[warp][r];
           const int4 sg = rseg[warp][r];
-          const int nw = (sg.y + sg.w + 31) >> 5;
-          if (sg.y + sg.w > RW * 32) continue;   // only after an overflow
-          for (int w = 0; w < nw; w++) {
-            uint32_t m = smask[a][r][w];
+          for (int w = 0; 4 * w < ng; w++) {
+            uint32_t m = shell_bits(r, w, ng);
             while (m) {
               const int b = __ffs(m) - 1;
               m &= m - 1u;
-              add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[row_slot(sg, 32 * w + b)], fs);
+              add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui,
+                                  p.su[row_slot(sg, 16 * w + 4 * (b >> 3) + (b & 3))], fs);
             }
           }
         }
       }
     }
-    // ---- pass 4: exact core sum over the group's concatenated core lists ---------
-    {
-      int cbase = ncore;                         // exclusive prefix of the group's list lengths
+    // ---- pass 4: exact core sum, the atom's core list dealt over its threads ----
+    __syncwarp();
+    if (active && ncore <= RBSOG_MAX_CORE) {
+      for (int e0 = g; e0 < ncore; e0 += 4 * TPA) {
+        int js[4];
 #pragma unroll
-      for (int o = 1; o < TPA; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, cbase, o, TPA);
-        if (g >= o) cbase += y;
-      }
-      const int ctot = __shfl_sync(0xffffffffu, cbase, TPA - 1, TPA);
-      cbase -= ncore;
-      int off[TPA];
-#pragma unroll
-      for (int t = 0; t < TPA; t++) off[t] = __shfl_sync(0xffffffffu, cbase, t, TPA);
-      __syncwarp();
-      if (active) {
-        const int tid0 = tid - g;                // first thread of the group
-        for (int e = g; e < ctot; e += TPA) {
-          int owner = 0;
-#pragma unroll
-          for (int t = 1; t < TPA; t++) owner += (e >= off[t]);
-          const int code = score[tid0 + owner][e - off[owner]];
-          const int j = row_slot(rseg[warp][code >> 7], code & 127);
-          add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, p.su[j], fc);
+        for (int i = 0; i < 4; i++) {
+          const int e = e0 + TPA * i;
+          js[i] = -1;
+          if (e < ncore) {
+            const int code = score[a][e];
+            js[i] = row_slot(rseg[warp][code >> 7], code & 127);
+          }
         }
+        uint4 uj[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (js[i] >= 0) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fc);
       }
     }
     // ---- combine the group ----------------------------------------------
@@ -615,17 +673,21 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
       part[3] = (double)((R)0.5 * (fc.e + wgt * fs.e));
     }
   }
-  // ---- FP64 block partials of sum F_N and of the pair energy ------------
+  // ---- partials of sum F_N and of the pair energy, one per warp (FP32 sums of
+  // the warp's eight atoms in mixed precision, FP64 otherwise) ----------------
 #pragma unroll
   for (int c = 0; c < 4; c++) {
-    for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
-    if (lane == 0) red[c][warp] = part[c];
+    if (MIX) {
+      float f = (float)part[c];
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+      part[c] = (double)f;
+    } else {
+      for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
+    }
   }
-  __syncthreads();
-  if (tid < 4) {
-    double t = 0.0;
-    for (int w = 0; w < NEAR_WARPS; w++) t += red[tid][w];
-    p.near_part[4 * blockIdx.x + tid] = t;
+  if (lane == 0) {
+    double *d = p.near_part + 4 * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
+    d[0] = part[0]; d[1] = part[1]; d[2] = part[2]; d[3] = part[3];
   }
 }
 

@@ -92,7 +92,9 @@ struct View {
   float *sx, *sy, *sz;    // [nslot] 23-bit coordinates v = u >> 9 as exact floats
   uint4 *su;              // [nslot] (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
   int nslot;              // n + 3 * ncell
-  double *near_part;      // [nblk_near][4]: sum F_N (x,y,z), sum pair energy
+  double *near_part;      // [nblk_near * NEAR_WARPS][4]: sum F_N (x,y,z), sum pair energy per warp
+  double *corr_part;      // [64][4] block sums of near_part
+  unsigned *corr_ticket;  // blocks of the F^corr reduction done (reset by the last)
   // far field
   int4 *km;               // [Pmax] lattice vectors m
   double *kc;             // [Pmax] weights c_p

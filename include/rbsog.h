@@ -230,8 +230,9 @@ int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag);
 /* Stages timed by the profiling events.  The structure factor runs on a side
  * stream concurrently with binning and the near field, so stage times do not
  * add up to the total, which is reported last. */
-#define RBSOG_NSTAGE 7  /* prepare+k-batch, bin (scan/scatter/cell sort), near field,
-                           structure factor, reduction, far force + kick, total */
+#define RBSOG_NSTAGE 7  /* integrator + fixed point + histograms, bin (row scan, cell
+                           prefix, scatter, rank), near field, k-batch + structure factor
+                           (side stream), reductions, far force + kick, total */
 
 /* Record a CUDA event between consecutive stages of every force evaluation
  * (also inside the captured step graph, as event nodes) when on != 0. */

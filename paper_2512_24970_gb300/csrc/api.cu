@@ -39,7 +39,7 @@ struct rbsog_ctx {
   bool own_stream = false;
   bool profiling = false;
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[9] = {};  // stage boundaries, see rbsog_get_stage_times
 };
 
@@ -101,9 +101,10 @@ int check_launch(rbsog_ctx *ctx) {
 }
 
 // One force evaluation; mode 0 = evaluate, 1 = VV step, 2 = BAOAB step.
-// The structure-factor kernel needs only the prepared coordinates and the
-// k-batch, so it runs on a side stream concurrently with binning and the
-// near field (two branches of the captured step graph).
+// The k-batch draw needs only the step counter and the structure-factor
+// kernel only the prepared coordinates and the k-batch, so both run on a
+// side stream, concurrently with the integrator/binning and with the near
+// field (two branches of the captured step graph).
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
   cudaStream_t st = ctx->st, st2 = ctx->st2;
   const bool pr = ctx->profiling;
@@ -112,11 +113,14 @@ int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy
   CK(cudaStreamIsCapturing(st, &cap));
   const unsigned evflag = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[0], st, evflag));
+  CK(cudaEventRecord(ctx->ev_fork0, st));
+  CK(cudaStreamWaitEvent(st2, ctx->ev_fork0, 0));
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[3], st2, evflag));
+  rb::launch_ksample(v, st2, step_off);
   rb::launch_prepare(v, st, mode, step_off);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[1], st, evflag));
   CK(cudaEventRecord(ctx->ev_fork, st));
   CK(cudaStreamWaitEvent(st2, ctx->ev_fork, 0));
-  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[3], st2, evflag));
   rb::launch_rho(v, st2);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st2, evflag));
   CK(cudaEventRecord(ctx->ev_join, st2));
@@ -239,6 +243,7 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork0, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     rbsog_destroy(ctx);
     return RBSOG_E_CUDA;
@@ -259,6 +264,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
     if (ctx->prof[k]) cudaEventDestroy(ctx->prof[k]);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_fork0) cudaEventDestroy(ctx->ev_fork0);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
@@ -408,7 +414,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.Ff, 3 * N)) || (rc = dalloc(ctx, &v.FNf, 3 * N)) || (rc = dalloc(ctx, &v.FFf, 3 * N)) ||
       (rc = dalloc(ctx, &v.Fd, 3 * N)) || (rc = dalloc(ctx, &v.FNd, 3 * N)) || (rc = dalloc(ctx, &v.FFd, 3 * N)) ||
       (rc = dalloc(ctx, &spc_d, N)) || (rc = dalloc(ctx, &v.ua, N)) || (rc = dalloc(ctx, &v.cellid, N)) ||
-      (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
+      (rc = dalloc(ctx, &v.cell_count, (size_t)v.ncell + (size_t)v.nc[1] * v.nc[2])) ||
+      (rc = dalloc(ctx, &v.row_start, (size_t)v.nc[1] * v.nc[2])) || (rc = dalloc(ctx, &v.key_tmp, NS)) || (rc = dalloc(ctx, &v.cell_start, (size_t)v.ncell + 1)) ||
       (rc = dalloc(ctx, &v.cell_cursor, (size_t)v.ncell)) || (rc = dalloc(ctx, &v.perm_tmp, NS)) ||
       (rc = dalloc(ctx, &v.perm, NS)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
       (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) ||
@@ -426,6 +433,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     free_system(ctx);
     return rc;
   }
+  v.row_count = v.cell_count + v.ncell;
   v.spc = spc_d;
   v.pf = pf;
   v.pd = pd;

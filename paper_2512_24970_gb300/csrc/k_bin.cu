@@ -1,9 +1,10 @@
 // Stage (a) and the integrator's first half, plus the k-batch draw of stage (d):
 //   k_prepare   per atom: [half kick, drift / BAOAB B-A-O-A (Sec. 2.3)], 32-bit
-//               fixed-point coordinates, cell index and cell histogram; extra
-//               blocks draw the P_F k-vectors from P(k) (Eq. (Pk)).
-//   k_scan      cell ranges (rows of cells padded to a multiple of 4 slots),
-//               padding slots and the near-field chunk table offsets (one block).
+//               fixed-point coordinates, cell index, cell and row histograms.
+//   k_ksample   the P_F k-vectors from P(k) (Eq. (Pk)), one warp per sample.
+//   k_rowscan   row ranges (rows of cells padded to a multiple of 4 slots),
+//               padding slots, near-field chunk offsets (one block).
+//   k_cellstart cell ranges inside each row (one warp per row).
 //   k_scatter   counting-sort scatter (slot claimed by atomicAdd).
 //   k_rank      per atom: rank in its cell by (u_x, caller id), the canonical
 //               order of the list -> sorted slot; write the SoA arrays.
@@ -87,10 +88,6 @@ __device__ __forceinline__ void noise3f(const View &p, long long s, uint32_t i, 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   const long long s = *p.step + step_off;
-  if ((int)blockIdx.x >= p.nblk_atoms) {
-    ksample_warp(p, ((int)blockIdx.x - p.nblk_atoms) * (blockDim.x >> 5) + (threadIdx.x >> 5), s, threadIdx.x & 31);
-    return;
-  }
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
   const int64_t n = p.n;
@@ -129,7 +126,13 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   const int cell = cell_of(u[0], p.nc[0]) + p.nc[0] * (cell_of(u[1], p.nc[1]) + p.nc[1] * cell_of(u[2], p.nc[2]));
   p.ua[i] = make_uint4(u[0], u[1], u[2], (uint32_t)sp);
   p.cellid[i] = cell;
-  atomicAdd(p.cell_count + cell, 1);
+  // histograms; lanes of one warp that share a cell (or row) add once
+  const unsigned act = __activemask();
+  const unsigned pc = __match_any_sync(act, cell);
+  if ((threadIdx.x & 31) == __ffs(pc) - 1) atomicAdd(p.cell_count + cell, __popc(pc));
+  const int row = cell / p.nc[0];
+  const unsigned pr = __match_any_sync(act, row);
+  if ((threadIdx.x & 31) == __ffs(pr) - 1) atomicAdd(p.row_count + row, __popc(pr));
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
@@ -155,50 +158,69 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
   return incl - v + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
 }
 
-// Cell ranges: the cells of a row of cells (fixed y, z) are contiguous and
-// unpadded; every row is padded to a multiple of CELL_ALIGN slots (padding
-// slots at FAR_AWAY, su.w = SU_PAD, written here).  cell_start[0..ncell],
-// cell_cursor, and the near-field chunks: each row's slots cut into runs of
-// NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.
-__global__ void __launch_bounds__(1024) k_scan(View p) {
+// Row ranges: every row of cells (fixed y, z) is padded to a multiple of
+// CELL_ALIGN slots (padding slots at FAR_AWAY, su.w = SU_PAD, written here);
+// row_start[r] (exclusive scan of the padded row totals, cell_start[ncell] =
+// all slots) and the near-field chunks: each row's slots cut into runs of
+// NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.  One block;
+// the row totals come from the binning's atomic counts.
+__global__ void __launch_bounds__(1024) k_rowscan(View p) {
   __shared__ int wsum[32];
   const int nt = blockDim.x, t = threadIdx.x;
-  const int nc0 = p.nc[0], nrow = p.nc[1] * p.nc[2];
+  const int nrow = p.nc[1] * p.nc[2];
   const int per = (nrow + nt - 1) / nt;
   const int rb = min(t * per, nrow), re = min(rb + per, nrow);
   int local = 0, lchunk = 0;
   for (int r = rb; r < re; r++) {
-    int tot = 0;
-#pragma unroll 4
-    for (int c = 0; c < nc0; c++) tot += p.cell_count[r * nc0 + c];
-    const int padded = (tot + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
+    const int padded = (p.row_count[r] + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
     local += padded;
     lchunk += (padded + NEAR_CHUNK - 1) / NEAR_CHUNK;
   }
   int run = block_exclusive_scan(local, wsum);
   int crun = block_exclusive_scan(lchunk, wsum);
   for (int r = rb; r < re; r++) {
-    const int r0 = run;
-    for (int c = 0; c < nc0; c++) {
-      p.cell_start[r * nc0 + c] = run;
-      p.cell_cursor[r * nc0 + c] = run;
-      run += p.cell_count[r * nc0 + c];
-    }
-    const int padded = (run - r0 + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
-    for (int k = run; k < r0 + padded; k++) {
+    const int tot = p.row_count[r];
+    const int padded = (tot + CELL_ALIGN - 1) & ~(CELL_ALIGN - 1);
+    p.row_start[r] = run;
+    for (int k = run + tot; k < run + padded; k++) {
       p.perm[k] = -1;
       p.sx[k] = FAR_AWAY;
       p.sy[k] = FAR_AWAY;
       p.sz[k] = FAR_AWAY;
       p.su[k] = make_uint4(0u, 0u, 0u, SU_PAD);
     }
-    run = r0 + padded;
+    run += padded;
     p.row_chunk[r] = crun;
-    crun += padded / NEAR_CHUNK + ((padded % NEAR_CHUNK) ? 1 : 0);
+    crun += (padded + NEAR_CHUNK - 1) / NEAR_CHUNK;
   }
   if (t == nt - 1) {
     p.cell_start[p.ncell] = run;
     p.row_chunk[nrow] = crun;
+  }
+}
+
+// Cell ranges inside each row: one warp per row, an inclusive warp scan of
+// the cell counts (32 cells per round) on top of the row's start.
+__global__ void __launch_bounds__(256) k_cellstart(View p) {
+  const int nrow = p.nc[1] * p.nc[2], nc0 = p.nc[0];
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nrow) return;
+  int base = p.row_start[r];
+  for (int c0 = 0; c0 < nc0; c0 += 32) {
+    const int c = c0 + lane;
+    const int cnt = c < nc0 ? p.cell_count[r * nc0 + c] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (c < nc0) {
+      p.cell_start[r * nc0 + c] = base + incl - cnt;
+      p.cell_cursor[r * nc0 + c] = base + incl - cnt;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
@@ -207,6 +229,7 @@ __global__ void __launch_bounds__(256) k_scatter(View p) {
   if (i >= p.n) return;
   const int slot = atomicAdd(p.cell_cursor + p.cellid[i], 1);
   p.perm_tmp[slot] = (int)i;
+  p.key_tmp[slot] = p.ua[i].x;
 }
 
 // One thread per atom: its rank in its cell under the canonical order
@@ -221,7 +244,7 @@ __global__ void __launch_bounds__(256) k_rank(View p) {
   int rank = 0;
   for (int k = b; k < b + cnt; k++) {
     const int j = p.perm_tmp[k];
-    const uint32_t xj = p.ua[j].x;
+    const uint32_t xj = p.key_tmp[k];
     rank += (xj < u.x || (xj == u.x && j < (int)i)) ? 1 : 0;
   }
   const int slot = b + rank;
@@ -240,16 +263,28 @@ __global__ void __launch_bounds__(256) k_rank(View p) {
     p.chunk_info[p.row_chunk[row] + (slot - rbeg) / NEAR_CHUNK] = make_int2(row, slot);
 }
 
+// The k-batch, one warp per sample (needs only the step counter).
+__global__ void __launch_bounds__(256) k_ksample(View p, int step_off) {
+  const long long s = *p.step + step_off;
+  ksample_warp(p, (int)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), s, threadIdx.x & 31);
+}
+
+void launch_ksample(const View &v, cudaStream_t st, int step_off) {
+  if (!v.fixed_k) k_ksample<<<v.nblk_kq, 256, 0, st>>>(v, step_off);
+}
+
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
-  cudaMemsetAsync(v.cell_count, 0, sizeof(int) * (size_t)v.ncell, st);
-  const int blocks = v.nblk_atoms + v.nblk_kq;
+  // cell_count and row_count are one allocation
+  cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), st);
+  const int blocks = v.nblk_atoms;
   if (mode == 0) k_prepare<0><<<blocks, 256, 0, st>>>(v, step_off);
   else if (mode == 1) k_prepare<1><<<blocks, 256, 0, st>>>(v, step_off);
   else k_prepare<2><<<blocks, 256, 0, st>>>(v, step_off);
 }
 
 void launch_bin(const View &v, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(v);
+  k_rowscan<<<1, 1024, 0, st>>>(v);
+  k_cellstart<<<(unsigned)(((int64_t)v.nc[1] * v.nc[2] * 32 + 255) / 256), 256, 0, st>>>(v);
   k_scatter<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
   k_rank<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
 }

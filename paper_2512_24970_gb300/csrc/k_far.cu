@@ -4,8 +4,8 @@
 //             exactly in uint32; FP32 polynomial sincos with FP32 accumulation
 //             over at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
 //   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
-//             force coefficients c_p Im rho_p, c_p Re rho_p.
-//   k_corr    F^corr and U_N from the near-field block partials.
+//             force coefficients c_p Im rho_p, c_p Re rho_p; extra blocks form
+//             F^corr and U_N from the near-field warp partials.
 //   k_force   F_i = F_N,i - F^corr - (k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p),
 //             fused with the closing half kick of the MD step.
 #include "rbsog_internal.cuh"
@@ -105,57 +105,18 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
   }
 }
 
-// One warp per k: fixed-order sum over tiles (lane-strided, then a shuffle
-// tree), per-k force coefficients.  Block 0 / warp 0 also forms F^corr.
-template <typename R>
-__global__ void __launch_bounds__(256) k_reduce(View p, int step_off) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k = blockIdx.x * 8 + w;
-  if (k < p.P) {
-    double sr = 0.0, si = 0.0;
-#pragma unroll 4
-    for (int t = lane; t < p.ntile; t += 32) {
-      const double *d = p.rho_part + 2 * ((int64_t)k * p.ntile + t);
-      sr += d[0];
-      si += d[1];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_down_sync(0xffffffffu, sr, o);
-      si += __shfl_down_sync(0xffffffffu, si, o);
-    }
-    if (lane == 0) {
-      p.rho[2 * k] = sr;
-      p.rho[2 * k + 1] = si;
-      const int4 m = p.km[k];
-      const double c = p.kc[k];
-      const double kx = TWO_PI * (double)m.x / p.L[0];
-      const double ky = TWO_PI * (double)m.y / p.L[1];
-      const double kz = TWO_PI * (double)m.z / p.L[2];
-      const double A = c * si, B = c * sr;
-      if (sizeof(R) == 4) {
-        p.kff[k] = make_float4((float)kx, (float)ky, (float)kz, (float)A);
-        p.kfB[k] = (float)B;
-      } else {
-        double *o = p.kfd + 5 * (int64_t)k;
-        o[0] = kx; o[1] = ky; o[2] = kz; o[3] = A; o[4] = B;
-      }
-      p.uf[k] = c * (sr * sr + si * si);
-    }
-  }
-}
-
 // F^corr = (1/N) sum of the near-field warp partials, and U_N.  Block b sums
 // the fixed slice b of the partials (thread-strided, then a fixed tree); the
 // last block to finish adds the CORR_BLOCKS block sums in index order, so the
 // result does not depend on which block finishes when.
 constexpr int CORR_BLOCKS = 64;
-__global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
+__device__ void corr_block(const View &p, int blk, int step_off) {
   __shared__ double red[4][256];
   __shared__ bool last;
   const int t = threadIdx.x;
   const int np = p.nblk_near * NEAR_WARPS;
   const int per = (np + CORR_BLOCKS - 1) / CORR_BLOCKS;
-  const int b0 = blockIdx.x * per, b1 = min(b0 + per, np);
+  const int b0 = blk * per, b1 = min(b0 + per, np);
   double f[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b = b0 + t; b < b1; b += 256)
     for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
@@ -166,7 +127,7 @@ __global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
       for (int a = 0; a < 4; a++) red[a][t] += red[a][t + o];
     __syncthreads();
   }
-  if (t < 4) p.corr_part[4 * blockIdx.x + t] = red[t][0];
+  if (t < 4) p.corr_part[4 * blk + t] = red[t][0];
   __threadfence();
   __syncthreads();
   if (t == 0) last = (atomicAdd(p.corr_ticket, 1u) == CORR_BLOCKS - 1);
@@ -182,6 +143,62 @@ __global__ void __launch_bounds__(256) k_corr(View p, int step_off) {
   if (t == 0) {
     *p.corr_ticket = 0u;                          // ready for the next evaluation
     if (step_off) *p.step += step_off;
+  }
+}
+
+// Blocks [0, nkb): one warp per k, fixed-order sum over tiles (four
+// lane-strided partial sums, then a shuffle tree), per-k force coefficients.
+// Blocks [nkb, nkb + CORR_BLOCKS): F^corr and U_N (corr_block).
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce(View p, int nkb, int step_off) {
+  if ((int)blockIdx.x >= nkb) {
+    corr_block(p, (int)blockIdx.x - nkb, step_off);
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * 8 + w;
+  if (k < p.P) {
+    double sr[4] = {0.0, 0.0, 0.0, 0.0}, si[4] = {0.0, 0.0, 0.0, 0.0};
+    const double2 *d = reinterpret_cast<const double2 *>(p.rho_part) + (int64_t)k * p.ntile;
+    int t = lane;
+    for (; t + 96 < p.ntile; t += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const double2 v = d[t + 32 * u];
+        sr[u] += v.x;
+        si[u] += v.y;
+      }
+    }
+    for (int u = 0; t < p.ntile; t += 32, u++) {
+      const double2 v = d[t];
+      sr[u] += v.x;
+      si[u] += v.y;
+    }
+    double r = (sr[0] + sr[1]) + (sr[2] + sr[3]);
+    double i = (si[0] + si[1]) + (si[2] + si[3]);
+    for (int o = 16; o > 0; o >>= 1) {
+      r += __shfl_down_sync(0xffffffffu, r, o);
+      i += __shfl_down_sync(0xffffffffu, i, o);
+    }
+    if (lane == 0) {
+      const double sr0 = r, si0 = i;
+      p.rho[2 * k] = sr0;
+      p.rho[2 * k + 1] = si0;
+      const int4 m = p.km[k];
+      const double c = p.kc[k];
+      const double kx = TWO_PI * (double)m.x / p.L[0];
+      const double ky = TWO_PI * (double)m.y / p.L[1];
+      const double kz = TWO_PI * (double)m.z / p.L[2];
+      const double A = c * si0, B = c * sr0;
+      if (sizeof(R) == 4) {
+        p.kff[k] = make_float4((float)kx, (float)ky, (float)kz, (float)A);
+        p.kfB[k] = (float)B;
+      } else {
+        double *o = p.kfd + 5 * (int64_t)k;
+        o[0] = kx; o[1] = ky; o[2] = kz; o[3] = A; o[4] = B;
+      }
+      p.uf[k] = c * (sr0 * sr0 + si0 * si0);
+    }
   }
 }
 
@@ -293,9 +310,8 @@ void launch_rho(const View &v, cudaStream_t st) {
 
 void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
   const int g = max(1, (v.P + 7) / 8);
-  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, step_off);
-  else k_reduce<double><<<g, 256, 0, st>>>(v, step_off);
-  k_corr<<<CORR_BLOCKS, 256, 0, st>>>(v, step_off);
+  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g + CORR_BLOCKS, 256, 0, st>>>(v, g, step_off);
+  else k_reduce<double><<<g + CORR_BLOCKS, 256, 0, st>>>(v, g, step_off);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 

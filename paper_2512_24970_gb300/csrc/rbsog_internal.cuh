@@ -84,7 +84,10 @@ struct View {
   int *cellid;            // [n]
   // binning
   int *cell_count, *cell_start, *cell_cursor;
+  int *row_count;         // [ny*nz] atoms per row of cells (follows cell_count)
+  int *row_start;         // [ny*nz] first slot of each row
   int *perm_tmp, *perm, *slot_of;
+  uint32_t *key_tmp;      // [nslot] u_x of perm_tmp (binning scratch)
   int *row_chunk;         // [ny*nz + 1] first near-field chunk of each row of cells
   int2 *chunk_info;       // [chunks] (row of cells, first slot) of each near-field chunk
   // sorted, padded slots: every cell's range is rounded up to a multiple of 4;
@@ -300,6 +303,7 @@ __device__ __forceinline__ int cdf_pick_warp(const unsigned long long *C, int le
 // Launchers (one translation unit each).
 // MODE: 0 = evaluate only, 1 = velocity Verlet step, 2 = BAOAB step.
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off);
+void launch_ksample(const View &v, cudaStream_t st, int step_off);
 void launch_bin(const View &v, cudaStream_t st);
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
 void launch_rho(const View &v, cudaStream_t st);

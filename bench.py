@@ -112,9 +112,9 @@ def dist_env():
     return ws, rank, local
 
 
-# kernels of one MD step: k_prepare, k_rho, k_scan, k_scatter, k_rank, k_near,
-# k_reduce, k_corr, k_force (the cell-count clear is a memset node)
-KERNELS_PER_STEP = 9
+# kernels of one MD step: k_ksample, k_prepare, k_rho, k_rowscan, k_cellstart,
+# k_scatter, k_rank, k_near, k_reduce, k_force (the histogram clear is a memset node)
+KERNELS_PER_STEP = 10
 
 
 def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0):

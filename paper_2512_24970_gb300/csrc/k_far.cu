@@ -59,27 +59,34 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
     }
     __syncthreads();
     if (MIX) {
-      float fr[RHO_KPT], fi[RHO_KPT];
-#pragma unroll
-      for (int t = 0; t < RHO_KPT; t++) fr[t] = fi[t] = 0.0f;
+      // the thread's two k in packed pairs
+      static_assert(RHO_KPT == 2, "packed structure factor takes two k per thread");
+      unsigned long long fr = 0ull, fi = 0ull;
 #pragma unroll 4
       for (int a = 0; a < cnt; a++) {
         const uint4 u = sa[a];
         const float q = (float)sq[a];
-#pragma unroll
-        for (int t = 0; t < RHO_KPT; t++) {
-          const uint32_t th = mx[t] * u.x + my[t] * u.y + mz[t] * u.z;
-          float s, c;
-          sincos_phase_f(th, s, c);
-          fr[t] = __fmaf_rn(q, c, fr[t]);
-          fi[t] = __fmaf_rn(q, s, fi[t]);
-        }
+        const uint32_t th0 = mx[0] * u.x + my[0] * u.y + mz[0] * u.z;
+        const uint32_t th1 = mx[1] * u.x + my[1] * u.y + mz[1] * u.z;
+        unsigned long long s2, c2;
+#ifdef RB_MUFU_TRIG
+        float s0, c0, s1, c1;
+        sincos_phase_f(th0, s0, c0);
+        sincos_phase_f(th1, s1, c1);
+        s2 = pk2(s0, s1);
+        c2 = pk2(c0, c1);
+#else
+        sincos_turn2(th0, th1, s2, c2);
+#endif
+        const unsigned long long q2 = pk2(q, q);
+        fr = fma2(q2, c2, fr);
+        fi = fma2(q2, s2, fi);
       }
-#pragma unroll
-      for (int t = 0; t < RHO_KPT; t++) {
-        re[t] += (double)fr[t];
-        im[t] += (double)fi[t];
-      }
+      float r0, r1, i0, i1;
+      up2(fr, r0, r1);
+      up2(fi, i0, i1);
+      re[0] += (double)r0; re[1] += (double)r1;
+      im[0] += (double)i0; im[1] += (double)i1;
     } else {
       for (int a = 0; a < cnt; a++) {
         const uint4 u = sa[a];
@@ -213,43 +220,97 @@ __global__ void k_energy(View p) {
 template <typename R, int MODE>
 __global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
   constexpr bool MIX = sizeof(R) == 4;
+  // per k: (m_x, m_y, m_z, bits of -c Re rho); mixed: per pair of k the packed
+  // (k_x, k_x'; k_y, k_y') and (k_z, k_z'; c Im rho, c' Im rho')
   __shared__ int4 sm[FORCE_KCHUNK];
-  __shared__ float4 skf[MIX ? FORCE_KCHUNK : 1];
-  __shared__ float skB[MIX ? FORCE_KCHUNK : 1];
+  __shared__ float4 ska[MIX ? FORCE_KCHUNK / 2 : 1];
+  __shared__ float4 skb[MIX ? FORCE_KCHUNK / 2 : 1];
   __shared__ double skd[MIX ? 1 : FORCE_KCHUNK * 5];
+  __shared__ float sred[MIX ? FORCE_TPA - 1 : 1][MIX ? FORCE_BLOCK / FORCE_TPA : 1][3];
   const int tid = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * FORCE_BLOCK + tid;
+  // MIX: FORCE_TPA warps per 32 atoms; warp segment g takes the k pairs
+  // g, g + FORCE_TPA, ... (warp-uniform shared-memory reads)
+  constexpr int TPA_ = MIX ? FORCE_TPA : 1;
+  constexpr int APB_ = FORCE_BLOCK / TPA_;    // atoms per block
+  const int w = tid >> 5, lane = tid & 31;
+  const int g = MIX ? w / (APB_ / 32) : 0;
+  const int al = MIX ? (w % (APB_ / 32)) * 32 + lane : tid;   // atom of the block
+  const int64_t i = (int64_t)blockIdx.x * APB_ + al;
   const bool act = i < p.n;
   const uint4 u = act ? p.ua[i] : make_uint4(0, 0, 0, 0);
   double ax = 0.0, ay = 0.0, az = 0.0;
   for (int k0 = 0; k0 < p.P; k0 += FORCE_KCHUNK) {
     const int cnt = min(FORCE_KCHUNK, p.P - k0);
+    const int cnt2 = (cnt + 1) & ~1;          // an odd chunk ends with a zero pair member
     __syncthreads();
-    for (int k = tid; k < cnt; k += FORCE_BLOCK) {
-      sm[k] = p.km[k0 + k];
+    for (int k = tid; k < cnt2; k += FORCE_BLOCK) {
       if (MIX) {
-        skf[k] = p.kff[k0 + k];
-        skB[k] = p.kfB[k0 + k];
-      } else {
+        int4 m = make_int4(0, 0, 0, 0);
+        float4 kf = make_float4(0.f, 0.f, 0.f, 0.f);
+        float B = 0.0f;
+        if (k < cnt) {
+          m = p.km[k0 + k];
+          kf = p.kff[k0 + k];
+          B = p.kfB[k0 + k];
+        }
+        sm[k] = make_int4(m.x, m.y, m.z, __float_as_int(-B));
+        float *a4 = reinterpret_cast<float *>(&ska[k >> 1]);
+        float *b4 = reinterpret_cast<float *>(&skb[k >> 1]);
+        a4[k & 1] = kf.x;
+        a4[2 + (k & 1)] = kf.y;
+        b4[k & 1] = kf.z;
+        b4[2 + (k & 1)] = kf.w;
+      } else if (k < cnt) {
+        sm[k] = p.km[k0 + k];
         for (int a = 0; a < 5; a++) skd[5 * k + a] = p.kfd[5 * (int64_t)(k0 + k) + a];
       }
     }
     __syncthreads();
     if (MIX) {
-      float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-#pragma unroll 4
-      for (int k = 0; k < cnt; k++) {
-        const int4 m = sm[k];
-        const uint32_t th = (uint32_t)m.x * u.x + (uint32_t)m.y * u.y + (uint32_t)m.z * u.z;
-        float s, c;
-        sincos_phase_f(th, s, c);
-        const float4 kf = skf[k];
-        const float sv = __fmaf_rn(c, kf.w, -s * skB[k]);
-        fx = __fmaf_rn(sv, kf.x, fx);
-        fy = __fmaf_rn(sv, kf.y, fy);
-        fz = __fmaf_rn(sv, kf.z, fz);
+      unsigned long long fx = 0ull, fy = 0ull, fz = 0ull;
+#pragma unroll 2
+      for (int k = 2 * g; k < cnt2; k += 2 * TPA_) {
+        const int4 m0 = sm[k], m1 = sm[k + 1];
+        const uint32_t th0 = (uint32_t)m0.x * u.x + (uint32_t)m0.y * u.y + (uint32_t)m0.z * u.z;
+        const uint32_t th1 = (uint32_t)m1.x * u.x + (uint32_t)m1.y * u.y + (uint32_t)m1.z * u.z;
+        unsigned long long s2, c2;
+#ifdef RB_MUFU_TRIG
+        float s0, c0, s1, c1;
+        sincos_phase_f(th0, s0, c0);
+        sincos_phase_f(th1, s1, c1);
+        s2 = pk2(s0, s1);
+        c2 = pk2(c0, c1);
+#else
+        sincos_turn2(th0, th1, s2, c2);
+#endif
+        const float4 ka = ska[k >> 1], kb = skb[k >> 1];
+        // Im(e^{-i theta} rho) c = c Im rho cos - c Re rho sin, two k at once
+        const unsigned long long sv =
+            fma2(c2, pk2(kb.z, kb.w), mul2(s2, pk2(__int_as_float(m0.w), __int_as_float(m1.w))));
+        fx = fma2(sv, pk2(ka.x, ka.y), fx);
+        fy = fma2(sv, pk2(ka.z, ka.w), fy);
+        fz = fma2(sv, pk2(kb.x, kb.y), fz);
       }
-      ax += fx; ay += fy; az += fz;
+      float x0, x1, y0, y1, z0, z1;
+      up2(fx, x0, x1);
+      up2(fy, y0, y1);
+      up2(fz, z0, z1);
+      float sx = x0 + x1, sy = y0 + y1, sz = z0 + z1;
+      if (MIX && TPA_ > 1) {                   // the segments' sums, in segment order
+        if (g > 0) {
+          sred[g - 1][al][0] = sx;
+          sred[g - 1][al][1] = sy;
+          sred[g - 1][al][2] = sz;
+        }
+        __syncthreads();
+        if (g == 0)
+          for (int t = 0; t < TPA_ - 1; t++) {
+            sx += sred[t][al][0];
+            sy += sred[t][al][1];
+            sz += sred[t][al][2];
+          }
+      }
+      ax += (double)sx; ay += (double)sy; az += (double)sz;
     } else {
       for (int k = 0; k < cnt; k++) {
         const int4 m = sm[k];
@@ -264,7 +325,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
       }
     }
   }
-  if (!act) return;
+  if (!act || g != 0) return;
   const int64_t n = p.n;
   const int sp = (int)u.w;
   const double pre = -KE * p.qs[sp] / p.V;
@@ -316,7 +377,8 @@ void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
 }
 
 void launch_force(const View &v, cudaStream_t st, int mode) {
-  const int g = (int)((v.n + FORCE_BLOCK - 1) / FORCE_BLOCK);
+  const int apb = v.prec == RBSOG_MIXED ? FORCE_BLOCK / FORCE_TPA : FORCE_BLOCK;   // atoms per block
+  const int g = (int)((v.n + apb - 1) / apb);
   if (v.prec == RBSOG_MIXED) {
     if (mode) k_force<float, 1><<<g, FORCE_BLOCK, 0, st>>>(v);
     else k_force<float, 0><<<g, FORCE_BLOCK, 0, st>>>(v);

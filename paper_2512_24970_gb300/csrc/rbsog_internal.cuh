@@ -24,6 +24,7 @@ constexpr int RHO_BLOCK = 256;     // threads per block of the structure-factor 
 constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernel
 constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernel
 constexpr int FORCE_KCHUNK = 512;  // k-vectors staged in shared memory per chunk
+constexpr int FORCE_TPA = 4;       // threads per atom of the mixed far-field force kernel
 constexpr int STENCIL = 5;         // cells per axis in the neighbour stencil (cell >= r_shell/2)
 
 // sorted atoms carry (caller id | species << 28) in one word
@@ -226,6 +227,41 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   unsigned long long r;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
   return r;
+}
+
+// sincos_turn of two phases at once: the FP32 steps in packed pairs, the
+// quarter-turn bookkeeping per lane; lane by lane the same results.
+__device__ __forceinline__ void sincos_turn2(uint32_t th0, uint32_t th1, unsigned long long &s2,
+                                             unsigned long long &c2) {
+  const uint32_t t0 = th0 + 0x20000000u, t1 = th1 + 0x20000000u;
+  const int x0 = ((int)(t0 & 0x3FFFFFFFu) - 0x20000000 + 64) >> 7;
+  const int x1 = ((int)(t1 & 0x3FFFFFFFu) - 0x20000000 + 64) >> 7;
+  constexpr float TURN25 = (float)(6.283185307179586 / 33554432.0);  // 2 pi / 2^25
+  const unsigned long long xb = pk2(__int_as_float(x0 + 0x4B400000), __int_as_float(x1 + 0x4B400000));
+  const unsigned long long phi = mul2(add2(xb, pk2(-12582912.0f, -12582912.0f)), pk2(TURN25, TURN25));
+  const unsigned long long z = mul2(phi, phi);
+  const unsigned long long ps =
+      fma2(fma2(fma2(pk2(2.7557319e-06f, 2.7557319e-06f), z, pk2(-1.9841270e-04f, -1.9841270e-04f)), z,
+                pk2(8.3333338e-03f, 8.3333338e-03f)),
+           z, pk2(-1.6666667e-01f, -1.6666667e-01f));
+  const unsigned long long sn = fma2(mul2(ps, z), phi, phi);
+  const unsigned long long pc =
+      fma2(fma2(fma2(fma2(pk2(-2.7557320e-07f, -2.7557320e-07f), z, pk2(2.4801588e-05f, 2.4801588e-05f)), z,
+                     pk2(-1.3888889e-03f, -1.3888889e-03f)),
+                z, pk2(4.1666668e-02f, 4.1666668e-02f)),
+           z, pk2(-0.5f, -0.5f));
+  const unsigned long long cs = fma2(pc, z, pk2(1.0f, 1.0f));
+  float sn0, sn1, cs0, cs1;
+  up2(sn, sn0, sn1);
+  up2(cs, cs0, cs1);
+  const uint32_t q0 = t0 >> 30, q1 = t1 >> 30;
+  const bool w0 = (q0 & 1u) != 0u, w1 = (q1 & 1u) != 0u;
+  const float s0 = __int_as_float(__float_as_int(w0 ? cs0 : sn0) ^ (int)((q0 & 2u) << 30));
+  const float c0 = __int_as_float(__float_as_int(w0 ? sn0 : cs0) ^ (int)(((q0 + 1u) & 2u) << 30));
+  const float s1 = __int_as_float(__float_as_int(w1 ? cs1 : sn1) ^ (int)((q1 & 2u) << 30));
+  const float c1 = __int_as_float(__float_as_int(w1 ? sn1 : cs1) ^ (int)(((q1 + 1u) & 2u) << 30));
+  s2 = pk2(s0, s1);
+  c2 = pk2(c0, c1);
 }
 
 // Packed constants of the list predicate seen from one atom image:

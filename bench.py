@@ -228,12 +228,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2512_24970_gb300 import build, rbsog, workloads as W
+    from paper_2512_24970_gb300.replicas import aggregate, replica_seed
     build.build()
     w, cfg = W.make(args.config)
     P_F = args.P_F or cfg.P_F
     P_R = args.P_R or cfg.P_R
     prec = rbsog.MIXED if args.precision == "mixed" else rbsog.FP64
-    prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=cfg.seed + 1000 * rank, precision=prec,
+    prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=replica_seed(cfg.seed, rank), precision=prec,
                              integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
                              T=cfg.T, dt=0.001, gamma=1.0)
     stream = torch.cuda.Stream(device=dev)
@@ -266,13 +267,8 @@ def run_ours(args):
         clk = clocks.stop()
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     ctx.sync()
-    t_total = float(ms.sum())
-    if ws > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    value, t_total, _ = aggregate(float(ms.sum()), float(w.n * K), dist if ws > 1 else None, dev)
     stage_ms = stage / K
-    value = ws * w.n * K / (t_total / 1000.0)
     # ---- roofline of the dominant kernel -------------------------------------
     pk, pk_kind = peaks()
     props = torch.cuda.get_device_properties(dev)

@@ -157,11 +157,13 @@ def test_resume_bit_identical(rb, orc):
     assert runs[0][2] == runs[1][2] == 12
 
 
-def test_full_size_sampled(rb, orc):
-    """Molten NaCl N=64,000 (the benchmark workload): lists and batches of
+@pytest.mark.parametrize("key", ["nacl_64k", "liclnacl_216k", "nacl_1m"])
+def test_full_size_sampled(rb, orc, key):
+    """The full-size workloads (molten NaCl N = 64,000, the benchmark; the
+    LiCl-NaCl mixture N = 216,000; NaCl N = 1,024,000): lists and batches of
     sampled atoms bit-exact, k-batch bit-exact, mixed forces of the sample
     within 1e-5 RMS of the oracle's FP64 near + far field."""
-    w, cfg = W.make("nacl_64k")
+    w, cfg = W.make(key)
     ctx, S = setup_pair(rb, orc, w, P_R=cfg.P_R, P_F=cfg.P_F, precision=rb.MIXED, seed=cfg.seed, step=3)
     Fg = ctx.compute_forces()
     parts = ctx.debug_parts()

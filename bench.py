@@ -112,9 +112,11 @@ def dist_env():
     return ws, rank, local
 
 
-# kernels of one MD step: k_ksample, k_prepare, k_rho, k_rowscan, k_cellstart,
-# k_scatter, k_rank, k_near, k_reduce, k_force (the histogram clear is a memset node)
-KERNELS_PER_STEP = 10
+# kernels of one MD step: main branch k_prepare, k_rowscan, k_cellstart, k_scatter, k_rank,
+# k_near, k_reduce (F^corr), k_finish; side branch k_ksample, k_rho, k_reduce (rho), k_farforce
+# (the histogram clear is a memset node)
+KERNELS_PER_STEP = 12
+KERNEL_LABEL = {"near": "k_near", "far": "k_rho + k_farforce (side stream)"}
 
 
 def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0):
@@ -127,14 +129,14 @@ def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0):
     n_sph = 4.0 / 3.0 * np.pi * r_shell ** 3 * rho_n
     n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
     return {"near": w.n * (8.0 * n_sph + 25.0 * (n_core + P_R)),
-            "rho": 15.0 * w.n * P_F, "force": 21.0 * w.n * P_F}
+            "far": (15.0 + 21.0) * w.n * P_F}
 
 
 def profiled_traffic(stage):
     """DRAM bytes per launch of the stage's kernel from the committed ncu summary,
     only while the kernel source is the one that was profiled (else None)."""
     import hashlib
-    src = {"near": "k_near.cu", "rho": "k_far.cu", "force": "k_far.cu"}.get(stage)
+    src = {"near": "k_near.cu", "far": "k_far.cu"}.get(stage)
     summ = os.path.join(ROOT, "profiles", "traffic_nacl64k.txt")
     if src is None or not os.path.exists(summ):
         return None
@@ -281,16 +283,20 @@ def run_ours(args):
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
     alg = algorithmic_ops(w, P_F, P_R)
-    # the dominant kernel: the longest of the stages that carry the arithmetic
-    # (near field, structure factor, far force); the bookkeeping stages are
-    # reported in stage_ms
-    dom = max((i for i, nm in enumerate(names) if nm in alg), key=lambda i: stage_ms[i])
+    # the dominant kernel: the near field, the longest stage of the critical path
+    # (the far-field branch runs concurrently on a side stream; its wall time
+    # there is shared with the near field, so it gets its own line below)
+    dom = names.index("near")
     peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
     achieved = alg[names[dom]] / (stage_ms[dom] * 1e-3)
-    roof = {"bound": "alu", "kernel": "k_" + names[dom], "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+    roof = {"bound": "alu", "kernel": KERNEL_LABEL[names[dom]], "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
             "unit": "Glane-op/s", "frac": achieved / peak_ops,
             "traffic": profiled_traffic(names[dom]),
             "peak_source": "4 warp-instructions/clk/SM x 32 lanes x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
+    fi = names.index("far")
+    far_roof = {"kernels": KERNEL_LABEL["far"], "achieved": alg["far"] / (stage_ms[fi] * 1e-3) / 1e9,
+                "unit": "Glane-op/s", "frac": alg["far"] / (stage_ms[fi] * 1e-3) / peak_ops,
+                "note": "wall time of the side-stream branch, concurrent with the near field"}
     step_ops = sum(alg.values())
     step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / peak_ops * 1e6,
                  "frac": (step_ops / peak_ops) / (t_total / K * 1e-3)}
@@ -335,7 +341,7 @@ def run_ours(args):
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
-            "roofline": roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "far_roofline": far_roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * K, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -101,10 +101,11 @@ int check_launch(rbsog_ctx *ctx) {
 }
 
 // One force evaluation; mode 0 = evaluate, 1 = VV step, 2 = BAOAB step.
-// The k-batch draw needs only the step counter and the structure-factor
-// kernel only the prepared coordinates and the k-batch, so both run on a
-// side stream, concurrently with the integrator/binning and with the near
-// field (two branches of the captured step graph).
+// Two branches (of the captured step graph): the k-batch draw needs only the
+// step counter, the structure factor and the far-field force only the
+// prepared coordinates and the k-batch, so they run on a side stream,
+// concurrently with the integrator, the binning and the near field; the
+// branches join for the total force and the closing half kick.
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
   cudaStream_t st = ctx->st, st2 = ctx->st2;
   const bool pr = ctx->profiling;
@@ -121,18 +122,22 @@ int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[1], st, evflag));
   CK(cudaEventRecord(ctx->ev_fork, st));
   CK(cudaStreamWaitEvent(st2, ctx->ev_fork, 0));
+  // side branch: structure factor, its reduction, far-field force
   rb::launch_rho(v, st2);
+  rb::launch_rhosum(v, st2, energy);
+  rb::launch_farforce(v, st2);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st2, evflag));
   CK(cudaEventRecord(ctx->ev_join, st2));
+  // main branch: binning, near field, F^corr
   rb::launch_bin(v, st);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[2], st, evflag));
   rb::launch_near(v, st, step_off, energy);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[7], st, evflag));
-  CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  rb::launch_corr(v, st, step_off);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[5], st, evflag));
-  rb::launch_reduce(v, st, step_off, energy);
+  CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[6], st, evflag));
-  rb::launch_force(v, st, mode);
+  rb::launch_finish(v, st, mode);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[8], st, evflag));
   return check_launch(ctx);
 }
@@ -385,6 +390,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   for (int a = 0; a < n_species; a++) {
     v.qs[a] = hq[a];
     v.kick[a] = 0.5 * P.dt * rb::FCONV / hm[a];
+    v.qfar[a] = -rb::KE * hq[a] / v.V;
     v.sig_ou[a] = std::sqrt(std::max(0.0, (1.0 - v.c1 * v.c1) * rb::KBOLTZ * P.T * rb::FCONV / hm[a]));
   }
   v.nblk_atoms = (int)((n + 255) / 256);
@@ -554,8 +560,6 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
   }
   if (!ctx->graph_ok) {
     View vs = ctx->v;
-    vs.FFf = nullptr;  // the step writes no debug parts
-    vs.FFd = nullptr;
     const int mode = ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 2;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -811,9 +815,10 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage) {
   if (!ctx->profiling) return fail(ctx, RBSOG_E_INVAL, "profiling is off");
   CK(cudaSetDevice(ctx->dev));
   CK(cudaEventSynchronize(ctx->prof[8]));
-  // (start, end) event of each stage: prepare, bin, near, rho, reduce, force, total
-  static const int b[7] = {0, 1, 2, 3, 5, 6, 0};
-  static const int e[7] = {1, 2, 7, 4, 6, 8, 8};
+  // (start, end) event of each stage: prepare, bin, near, far branch (k-batch, structure factor,
+  // its reduction, far force; side stream), F^corr, finish (after the join), total
+  static const int b[7] = {0, 1, 2, 3, 7, 6, 0};
+  static const int e[7] = {1, 2, 7, 4, 5, 8, 8};
   for (int k = 0; k < nstage && k < 7; k++) CK(cudaEventElapsedTime(ms + k, ctx->prof[b[k]], ctx->prof[e[k]]));
   return RBSOG_OK;
 }

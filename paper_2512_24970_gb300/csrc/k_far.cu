@@ -6,8 +6,8 @@
 //   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
 //             force coefficients c_p Im rho_p, c_p Re rho_p; extra blocks form
 //             F^corr and U_N from the near-field warp partials.
-//   k_force   F_i = F_N,i - F^corr - (k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p),
-//             fused with the closing half kick of the MD step.
+//   k_farforce F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
+//   k_finish  F_i = F_N,i - F^corr + F_F,i and the closing half kick of the MD step.
 #include "rbsog_internal.cuh"
 
 namespace rb {
@@ -217,8 +217,8 @@ __global__ void k_energy(View p) {
   p.red[4] = KE / (2.0 * p.V) * u;
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
+template <typename R>
+__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
   constexpr bool MIX = sizeof(R) == 4;
   // per k: (m_x, m_y, m_z, bits of -c Re rho); mixed: per pair of k the packed
   // (k_x, k_x'; k_y, k_y') and (k_z, k_z'; c Im rho, c' Im rho')
@@ -327,23 +327,34 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_force(View p) {
   }
   if (!act || g != 0) return;
   const int64_t n = p.n;
-  const int sp = (int)u.w;
-  const double pre = -KE * p.qs[sp] / p.V;
-  const double far[3] = {pre * ax, pre * ay, pre * az};
+  const double pre = p.qfar[(int)u.w];          // -k_e q_i / V
+  if (MIX) {
+    p.FFf[i] = (float)(pre * ax); p.FFf[n + i] = (float)(pre * ay); p.FFf[2 * n + i] = (float)(pre * az);
+  } else {
+    p.FFd[i] = pre * ax; p.FFd[n + i] = pre * ay; p.FFd[2 * n + i] = pre * az;
+  }
+}
+
+// F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_finish(View p) {
+  constexpr bool MIX = sizeof(R) == 4;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int64_t n = p.n;
   double F[3];
   for (int a = 0; a < 3; a++) {
     const double fn = MIX ? (double)p.FNf[a * n + i] : p.FNd[a * n + i];
-    F[a] = fn - p.red[a] + far[a];
+    const double ff = MIX ? (double)p.FFf[a * n + i] : p.FFd[a * n + i];
+    F[a] = fn - p.red[a] + ff;
   }
   if (MIX) {
     for (int a = 0; a < 3; a++) p.Ff[a * n + i] = (float)F[a];
-    if (p.FFf) for (int a = 0; a < 3; a++) p.FFf[a * n + i] = (float)far[a];
   } else {
     for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
-    if (p.FFd) for (int a = 0; a < 3; a++) p.FFd[a * n + i] = far[a];
   }
   if (MODE != 0) {
-    const double kick = p.kick[sp];
+    const double kick = p.kick[p.spc[i]];
     for (int a = 0; a < 3; a++) {
       const double Fa = MIX ? (double)(float)F[a] : F[a];
       p.v[a * n + i] += kick * Fa;
@@ -369,22 +380,32 @@ void launch_rho(const View &v, cudaStream_t st) {
   else k_rho<double><<<g, RHO_BLOCK, 0, st>>>(v);
 }
 
-void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy) {
+void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
   const int g = max(1, (v.P + 7) / 8);
-  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g + CORR_BLOCKS, 256, 0, st>>>(v, g, step_off);
-  else k_reduce<double><<<g + CORR_BLOCKS, 256, 0, st>>>(v, g, step_off);
+  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, g, 0);
+  else k_reduce<double><<<g, 256, 0, st>>>(v, g, 0);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 
-void launch_force(const View &v, cudaStream_t st, int mode) {
+void launch_corr(const View &v, cudaStream_t st, int step_off) {
+  k_reduce<float><<<CORR_BLOCKS, 256, 0, st>>>(v, 0, step_off);
+}
+
+void launch_farforce(const View &v, cudaStream_t st) {
   const int apb = v.prec == RBSOG_MIXED ? FORCE_BLOCK / FORCE_TPA : FORCE_BLOCK;   // atoms per block
   const int g = (int)((v.n + apb - 1) / apb);
+  if (v.prec == RBSOG_MIXED) k_farforce<float><<<g, FORCE_BLOCK, 0, st>>>(v);
+  else k_farforce<double><<<g, FORCE_BLOCK, 0, st>>>(v);
+}
+
+void launch_finish(const View &v, cudaStream_t st, int mode) {
+  const int g = (int)((v.n + 255) / 256);
   if (v.prec == RBSOG_MIXED) {
-    if (mode) k_force<float, 1><<<g, FORCE_BLOCK, 0, st>>>(v);
-    else k_force<float, 0><<<g, FORCE_BLOCK, 0, st>>>(v);
+    if (mode == 0) k_finish<float, 0><<<g, 256, 0, st>>>(v);
+    else k_finish<float, 1><<<g, 256, 0, st>>>(v);
   } else {
-    if (mode) k_force<double, 1><<<g, FORCE_BLOCK, 0, st>>>(v);
-    else k_force<double, 0><<<g, FORCE_BLOCK, 0, st>>>(v);
+    if (mode == 0) k_finish<double, 0><<<g, 256, 0, st>>>(v);
+    else k_finish<double, 1><<<g, 256, 0, st>>>(v);
   }
 }
 

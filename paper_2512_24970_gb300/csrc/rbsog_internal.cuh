@@ -73,6 +73,7 @@ struct View {
   double dt, c1;
   double qs[RBSOG_MAX_SPECIES];
   double kick[RBSOG_MAX_SPECIES];    // 0.5 dt FCONV / m
+  double qfar[RBSOG_MAX_SPECIES];    // -k_e q / V (far-force prefactor)
   double sig_ou[RBSOG_MAX_SPECIES];  // sqrt((1 - c1^2) kT FCONV / m)
   int G;                  // M + 1
   int ntile, tile_atoms, nblk_atoms, nblk_kq, nblk_near;
@@ -343,8 +344,10 @@ void launch_ksample(const View &v, cudaStream_t st, int step_off);
 void launch_bin(const View &v, cudaStream_t st);
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
 void launch_rho(const View &v, cudaStream_t st);
-void launch_reduce(const View &v, cudaStream_t st, int step_off, bool energy);
-void launch_force(const View &v, cudaStream_t st, int mode);
+void launch_rhosum(const View &v, cudaStream_t st, bool energy);
+void launch_corr(const View &v, cudaStream_t st, int step_off);
+void launch_farforce(const View &v, cudaStream_t st);
+void launch_finish(const View &v, cudaStream_t st, int mode);
 void launch_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
                   int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
                   int *batch, int *nbatch, double *weight);

@@ -40,7 +40,10 @@ EXPORTS = [
 ]
 SF_STATIC_PMAX = 1024
 NSTAGE = 7
-STAGES = ["prepare", "bin", "near", "rho", "reduce", "force", "total"]
+# stages of rbsog_get_stage_times: integrator + histograms, binning, near field, the far-field
+# branch on the side stream (k-batch, structure factor, its reduction, far force), F^corr, the
+# closing total force + half kick after the branches join, and the whole evaluation
+STAGES = ["prepare", "bin", "near", "far", "corr", "finish", "total"]
 
 
 class RbsogError(RuntimeError):

@@ -501,6 +501,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaMemsetAsync(v.err, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(v.step, 0, sizeof(long long), ctx->st));
   CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 8, ctx->st));
+  CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
   CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
   ctx->has_system = true;
@@ -641,6 +642,8 @@ int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int3
   View &v = ctx->v;
   rb::launch_prepare(v, ctx->st, 0, 0);
   rb::launch_bin(v, ctx->st);
+  // the near field is not run here: clear the binning's histograms ourselves
+  CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   const size_t k = (size_t)nsel;
   long long *dsel;
   int *dcore, *dnc, *dshell, *dns, *dbatch = nullptr, *dnb = nullptr;

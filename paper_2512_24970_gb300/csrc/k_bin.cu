@@ -273,9 +273,9 @@ void launch_ksample(const View &v, cudaStream_t st, int step_off) {
   if (!v.fixed_k) k_ksample<<<v.nblk_kq, 256, 0, st>>>(v, step_off);
 }
 
+// The cell and row histograms start at zero: cleared at set-up and, after
+// every use, by the near-field kernel (clear_counts) or by the caller.
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
-  // cell_count and row_count are one allocation
-  cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), st);
   const int blocks = v.nblk_atoms;
   if (mode == 0) k_prepare<0><<<blocks, 256, 0, st>>>(v, step_off);
   else if (mode == 1) k_prepare<1><<<blocks, 256, 0, st>>>(v, step_off);

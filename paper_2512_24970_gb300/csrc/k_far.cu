@@ -141,9 +141,16 @@ __device__ void corr_block(const View &p, int blk, int step_off) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the CORR_BLOCKS block sums, one per thread, then the same fixed tree
+  static_assert(4 * CORR_BLOCKS == 256, "one block sum per thread");
+  red[t & 3][t >> 2] = __ldcg(p.corr_part + 4 * (t >> 2) + (t & 3));
+  __syncthreads();
+  for (int o = CORR_BLOCKS / 2; o > 0; o >>= 1) {
+    if (t < 4 * o) red[t & 3][t >> 2] += red[t & 3][(t >> 2) + o];
+    __syncthreads();
+  }
   if (t < 4) {
-    double v = 0.0;
-    for (int k = 0; k < CORR_BLOCKS; k++) v += ((volatile double *)p.corr_part)[4 * k + t];
+    const double v = red[t][0];
     if (t < 3) p.red[t] = v / (double)p.n;
     else p.red[3] = v;
   }

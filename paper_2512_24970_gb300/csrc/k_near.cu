@@ -290,6 +290,10 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   __syncthreads();
   const long long s = *p.step + step_off;
+  // the binning's histograms are consumed: clear them for the next evaluation
+  for (int64_t c = (int64_t)blockIdx.x * NEAR_BLOCK + tid; c < (int64_t)p.ncell + p.nc[1] * p.nc[2];
+       c += (int64_t)gridDim.x * NEAR_BLOCK)
+    p.cell_count[c] = 0;
   const int warp = tid >> 5, lane = tid & 31;
   const int a = warp * APW + lane / TPA;      // atom row of the shared arrays
   const int g = lane % TPA;

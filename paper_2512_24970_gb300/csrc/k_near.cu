@@ -161,7 +161,14 @@ __device__ __forceinline__ void add_pair(const View &p, const PairF *spf, const 
   const int spj = (int)(uj.w >> SU_SP_SHIFT);
   if (sizeof(R) == 4) {
     float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    pair_mixed<ENERGY>(p, spf[spi * p.ns + spj], sg, ui, uj, a0, a1, a2, a3);
+    // the pair record through the read-only cache (three 16-byte loads)
+    const float4 *src = reinterpret_cast<const float4 *>(spf + spi * p.ns + spj);
+    const float4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2);
+    PairF q;
+    q.kqq = r0.x; q.Ar = r0.y; q.lr = r0.z; q.sig = r0.w;
+    q.C6 = r1.x; q.D8 = r1.y; q.A = r1.z; q.C = r1.w;
+    q.D = r2.x;
+    pair_mixed<ENERGY>(p, q, sg, ui, uj, a0, a1, a2, a3);
     a.x += a0; a.y += a1; a.z += a2; a.e += a3;
   } else {
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
@@ -194,7 +201,7 @@ constexpr int TPA = 4;
 constexpr int APW = NEAR_CHUNK;              // atoms per warp
 constexpr int APB = NEAR_WARPS * NEAR_CHUNK; // atoms per block
 constexpr int NROW = STENCIL * STENCIL;      // stencil rows (y, z)
-constexpr int GBYTES = 384;                  // candidate groups one atom's chunk may test
+constexpr int GBYTES = 352;                  // candidate groups one atom's chunk may test
 constexpr int SHELL_BITS = RBSOG_MAX_SHELL;  // shell members one bitmask can index
 constexpr int WMAX = 8;                      // union x-cells of a chunk
 static_assert(TPA * NEAR_CHUNK == 32 && NEAR_WARPS * 32 == NEAR_BLOCK, "near-field block layout");
@@ -279,16 +286,11 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   __shared__ float4 rsh[NEAR_WARPS][NROW];       // image shifts (x of run a, x of run b, y, z)
   __shared__ int rgo[NEAR_WARPS][NROW + 1];      // first group of each row (flattened)
   __shared__ int rbo[NEAR_WARPS][NROW];          // first byte of each row in gres
-  __shared__ PairF spf[MIX ? RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
-  __shared__ PairD spd[MIX ? 1 : RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
+  const PairF *spf = p.pf;                       // pair records, read through the read-only cache
+  const PairD *spd = p.pd;
   const int tid = threadIdx.x;
-  const int nsp2 = p.ns * p.ns;
-  for (int k = tid; k < nsp2; k += NEAR_BLOCK) {
-    if (MIX) spf[k] = p.pf[k]; else spd[k] = p.pd[k];
-  }
   const float4 *sg4 = p.gtab;
   const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
-  __syncthreads();
   const long long s = *p.step + step_off;
   // the binning's histograms are consumed: clear them for the next evaluation
   for (int64_t c = (int64_t)blockIdx.x * NEAR_BLOCK + tid; c < (int64_t)p.ncell + p.nc[1] * p.nc[2];

@@ -47,6 +47,7 @@ struct PairF {
   float C6, D8, A, C;
   float D, pad0, pad1, pad2;
 };
+static_assert(sizeof(PairF) == 48, "pair record read as three 16-byte words");
 // Pair record, FP64: the Eq. (BMH) parameters and k_e q_i q_j.
 struct PairD {
   double kqq, A, sig, rho, C, D;

@@ -350,10 +350,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ensemble(args):
+    """The replica ensemble (64 replicas of uneven size and composition, one
+    ensemble step = one MD step of every replica, all overlapping on the GPU)
+    against the same replicas stepped one after another on one stream."""
+    import torch
+    from paper_2512_24970_gb300 import build, rbsog, workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    reps = W.ensemble(n_rep=64, seed=5)
+    stream = torch.cuda.Stream(device=dev)
+    ens = rbsog.Ensemble(0, stream.cuda_stream, max_replicas=len(reps))
+    natoms = 0
+    for r, (w, T) in enumerate(reps):
+        prm = rbsog.MethodParams(P_R=20, P_F=500, seed=5000 + r, precision=rbsog.MIXED,
+                                 integrator=rbsog.LANGEVIN_BAOAB, T=T)
+        c = ens.add_workload(w, prm)
+        c.set_velocities(w.vel)
+        natoms += w.n
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    K, Wm = args.steps, args.warmup
+
+    def timed(step_fn):
+        with torch.cuda.stream(stream):
+            for _ in range(Wm):
+                flush.zero_()
+                step_fn()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for k in range(K):
+                flush.zero_()
+                ev[k][0].record(stream)
+                step_fn()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in ev))
+
+    t_ens = timed(lambda: ens.step(1))
+    ens.sync()
+    # the same replicas one after another, each step on the ensemble's stream
+    solo = []
+    for r, (w, T) in enumerate(reps):
+        c = rbsog.Context(0, stream.cuda_stream)
+        c.set_workload(w, rbsog.MethodParams(P_R=20, P_F=500, seed=5000 + r, precision=rbsog.MIXED,
+                                             integrator=rbsog.LANGEVIN_BAOAB, T=T))
+        solo.append(c)
+
+    def seq():
+        for c in solo:
+            c.step(1)
+
+    t_seq = timed(seq)
+    line = {"metric": "atom-steps/s of RBSOG+RBL force step, replica ensemble", "value": natoms * K / (t_ens / 1000.0),
+            "unit": "atom-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": t_ens / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "64 replicas: N = 8 n^3, n in [4, 16] (N 512..32768), NaCl / LiCl / LiCl-NaCl, "
+                                   "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
+                       "l2": "flushed before every step (512 MiB memset)"},
+            "sequential": {"value": natoms * K / (t_seq / 1000.0), "ms_per_step": t_seq / K,
+                           "what": "the same replicas stepped one after another on one stream"}}
+    print(json.dumps(line), flush=True)
+    for c in solo:
+        c.close()
+    ens.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "ensemble_64":
+        run_ensemble(args)
     else:
         run_ours(args)
 

@@ -230,9 +230,10 @@ int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag);
 /* Stages timed by the profiling events.  The structure factor runs on a side
  * stream concurrently with binning and the near field, so stage times do not
  * add up to the total, which is reported last. */
-#define RBSOG_NSTAGE 7  /* integrator + fixed point + histograms, bin (row scan, cell
-                           prefix, scatter, rank), near field, k-batch + structure factor
-                           (side stream), reductions, far force + kick, total */
+#define RBSOG_NSTAGE 7  /* integrator + fixed point + histograms; bin (row scan, cell
+                           prefix, scatter, rank); near field; far-field branch on the
+                           side stream (k-batch, structure factor, its reduction, far
+                           force); F^corr; total force + closing kick; total */
 
 /* Record a CUDA event between consecutive stages of every force evaluation
  * (also inside the captured step graph, as event nodes) when on != 0. */
@@ -244,6 +245,49 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage);
 
 /* Message of the last error of this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
+
+/* ---- ensemble of independent replicas ---------------------------------------- */
+
+/* Many independent systems of uneven size on one GPU (e.g. a screen over
+ * compositions and temperatures).  Each replica is a full context (its own
+ * system, parameters, RNG key, step counter and step graph) running on its own
+ * non-blocking stream pair, so the replicas' steps overlap on the device; the
+ * calls below order that work after, and before, the ensemble's stream with
+ * events.  Results per replica are bit-identical to stepping it alone. */
+typedef struct rbsog_ensemble rbsog_ensemble; /* opaque, library-owned */
+
+/* Create an empty ensemble on CUDA device `cuda_device` for at most
+ * max_replicas replicas.  `cuda_stream` as in rbsog_create (NULL: the legacy
+ * stream).  Errors: RBSOG_E_INVAL, RBSOG_E_CUDA. */
+int rbsog_ensemble_create(rbsog_ensemble **out, int cuda_device, void *cuda_stream,
+                          int32_t max_replicas);
+
+/* Destroy the ensemble and all its replicas (waits for their work). */
+void rbsog_ensemble_destroy(rbsog_ensemble *ens);
+
+/* Add a replica: arguments exactly as rbsog_set_system.  *replica receives its
+ * index (0, 1, ...).  Errors: those of rbsog_set_system, RBSOG_E_INVAL when
+ * the ensemble is full. */
+int rbsog_ensemble_add(rbsog_ensemble *ens, int64_t n, const double *pos, const int32_t *species,
+                       int32_t n_species, const double *charge, const double *mass,
+                       const double *bmh, const double box[3], const rbsog_params *params,
+                       int ptr_kind, int32_t *replica);
+
+/* The context of replica r (owned by the ensemble): every rbsog_* call on a
+ * context applies to it (velocities, state, forces, parity hooks).  NULL for
+ * a bad index. */
+rbsog_ctx *rbsog_ensemble_replica(rbsog_ensemble *ens, int32_t r);
+
+/* Advance every replica nsteps MD steps (rbsog_step of each replica, all on
+ * their own streams, joined into the ensemble's stream; asynchronous).
+ * Errors: RBSOG_E_INVAL, the first failing replica's code. */
+int rbsog_ensemble_step(rbsog_ensemble *ens, int64_t nsteps);
+
+/* Wait for all replicas; return the first latched device error, if any. */
+int rbsog_ensemble_sync(rbsog_ensemble *ens);
+
+/* Message of the last error of the ensemble (never NULL). */
+const char *rbsog_ensemble_last_error(const rbsog_ensemble *ens);
 
 #ifdef __cplusplus
 }

@@ -201,7 +201,11 @@ constexpr int TPA = 4;
 constexpr int APW = NEAR_CHUNK;              // atoms per warp
 constexpr int APB = NEAR_WARPS * NEAR_CHUNK; // atoms per block
 constexpr int NROW = STENCIL * STENCIL;      // stencil rows (y, z)
-constexpr int GBYTES = 352;                  // candidate groups one atom's chunk may test
+// candidate groups one atom's chunk may test: culled rows (the common case),
+// or the whole rows of a short box (WRAP: 25 rows of at most
+// RBSOG_MAX_ROW_SLOTS / 4 groups)
+constexpr int GBYTES_CULLED = 352;
+constexpr int GBYTES_WRAP = STENCIL * STENCIL * RBSOG_MAX_ROW_SLOTS / CELL_ALIGN;
 constexpr int SHELL_BITS = RBSOG_MAX_SHELL;  // shell members one bitmask can index
 constexpr int WMAX = 8;                      // union x-cells of a chunk
 static_assert(TPA * NEAR_CHUNK == 32 && NEAR_WARPS * 32 == NEAR_BLOCK, "near-field block layout");
@@ -276,6 +280,7 @@ template <typename R, bool WRAP, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
   // per-atom rows padded by one word so that the eight atoms of a warp hit distinct banks
+  constexpr int GBYTES = WRAP ? GBYTES_WRAP : GBYTES_CULLED;
   __shared__ __align__(16) unsigned char gres[APB][GBYTES + 4]; // per group of 4 candidates: r < r_shell (bits 0-3), r < r_core (4-7)
   __shared__ unsigned char scnt[APB][NROW];      // shell members of each stencil row
   __shared__ unsigned short spre[APB][NROW + 1]; // exclusive prefix of the counts

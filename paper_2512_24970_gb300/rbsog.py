@@ -37,6 +37,8 @@ EXPORTS = [
     "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
+    "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
+    "rbsog_ensemble_step", "rbsog_ensemble_sync", "rbsog_ensemble_last_error",
 ]
 SF_STATIC_PMAX = 1024
 NSTAGE = 7
@@ -125,6 +127,17 @@ def load():
     L.rbsog_set_profiling.argtypes = [P, I]
     L.rbsog_get_stage_times.argtypes = [P, P, I32]
     L.rbsog_structure_factor_static.argtypes = [P, I32, P, P]
+    L.rbsog_ensemble_create.argtypes = [ctypes.POINTER(P), I, P, I32]
+    L.rbsog_ensemble_destroy.argtypes = [P]
+    L.rbsog_ensemble_destroy.restype = None
+    L.rbsog_ensemble_add.argtypes = [P, I64, P, P, I32, P, P, P, P, ctypes.POINTER(Params), I,
+                                     ctypes.POINTER(I32)]
+    L.rbsog_ensemble_replica.argtypes = [P, I32]
+    L.rbsog_ensemble_replica.restype = P
+    L.rbsog_ensemble_step.argtypes = [P, I64]
+    L.rbsog_ensemble_sync.argtypes = [P]
+    L.rbsog_ensemble_last_error.argtypes = [P]
+    L.rbsog_ensemble_last_error.restype = ctypes.c_char_p
     L.rbsog_last_error.argtypes = [P]
     L.rbsog_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -167,7 +180,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            self._L.rbsog_destroy(self.h)
+            if getattr(self, "_owned", True):       # replica views belong to their ensemble
+                self._L.rbsog_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -328,3 +342,66 @@ class Context:
 
     def debug_whole_shell(self, flag: bool):
         self._ck(self._L.rbsog_debug_set_whole_shell(self.h, 1 if flag else 0))
+
+
+class Ensemble:
+    """Independent replicas of uneven size stepped together on one GPU
+    (``rbsog_ensemble_*``): each replica is a full context on its own stream."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, max_replicas: int = 64):
+        self._L = load()
+        h = ctypes.c_void_p()
+        rc = self._L.rbsog_ensemble_create(ctypes.byref(h), device, ctypes.c_void_p(stream or 0), max_replicas)
+        if rc != 0:
+            raise RbsogError(rc, "rbsog_ensemble_create failed")
+        self.h = h
+        self.replicas = []
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise RbsogError(rc, self._L.rbsog_ensemble_last_error(self.h).decode())
+
+    def add(self, pos, species, charge, mass, bmh, box, params: MethodParams):
+        """Add a replica (arguments as Context.set_system); returns its Context view."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        charge = np.ascontiguousarray(charge, dtype=np.float64)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        bmh = np.ascontiguousarray(bmh, dtype=np.float64)
+        box = np.ascontiguousarray(box, dtype=np.float64)
+        prm = params.c()
+        r = ctypes.c_int32()
+        self._ck(self._L.rbsog_ensemble_add(self.h, pos.shape[0], _np_ptr(pos), _np_ptr(species), charge.size,
+                                            _np_ptr(charge), _np_ptr(mass), _np_ptr(bmh), _np_ptr(box),
+                                            ctypes.byref(prm), PTR_HOST, ctypes.byref(r)))
+        ctx = Context.__new__(Context)      # a non-owning view of the replica's context
+        ctx._L = self._L
+        ctx.h = ctypes.c_void_p(self._L.rbsog_ensemble_replica(self.h, r.value))
+        ctx.n = pos.shape[0]
+        ctx.params = params
+        ctx._owned = False
+        self.replicas.append(ctx)
+        return ctx
+
+    def add_workload(self, w, params: MethodParams):
+        return self.add(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, params)
+
+    def step(self, nsteps: int):
+        self._ck(self._L.rbsog_ensemble_step(self.h, int(nsteps)))
+
+    def sync(self):
+        self._ck(self._L.rbsog_ensemble_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for c in self.replicas:
+                c.h = None
+            self._L.rbsog_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

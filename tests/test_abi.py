@@ -15,7 +15,8 @@ def declared():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:int|void|const\s+char\s*\*)\s*\**\s*(rbsog_\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:int|void|const\s+char\s*\*|rbsog_ctx\s*\*)\s*\**\s*(rbsog_\w+)\s*\(",
+                                src, flags=re.M)
     return sorted(set(names))
 
 

@@ -48,6 +48,7 @@ CASES = {
     "nacl_1k": lambda: W.rock_salt((5, 5, 5), seed=1),                     # n_c = 5: fast stencil
     "small_box": lambda: W.rock_salt((4, 4, 4), seed=2),                   # n_c = 4: small-box path
     "ragged": lambda: W.rock_salt((6, 5, 7), seed=3, composition="LiCl-NaCl"),  # 3 species, orthorhombic
+    "six_cells": lambda: W.rock_salt((6, 6, 6), seed=4, composition="LiCl"),      # whole rows of 6 cells
 }
 
 

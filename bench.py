@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-force-error", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="shell batch x P_F sweep of the configuration (one JSON line each)")
     return ap.parse_args()
 
 
@@ -146,6 +149,26 @@ def profiled_traffic(stage):
         if len(f) >= 3 and f[0] == "k_" + stage and f[1] == h:
             return float(f[2])
     return None
+
+
+def force_error(rbsog, w, prm, dev):
+    """RMS relative force error of the mixed-precision path against the FP64
+    GPU path, eps = sqrt(sum |F_mixed - F_FP64|^2 / sum |F_FP64|^2), from the
+    same positions, seed and step (so the same shell batches and k-batch), and
+    the largest per-atom relative error."""
+    import dataclasses
+    F = {}
+    for name, pr in (("mixed", rbsog.MIXED), ("fp64", rbsog.FP64)):
+        c = rbsog.Context(dev)
+        c.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, dataclasses.replace(prm, precision=pr))
+        c.set_state(w.pos, None, 1)
+        F[name] = c.compute_forces()
+        c.close()
+    d = F["mixed"] - F["fp64"]
+    eps = float(np.sqrt((d ** 2).sum() / (F["fp64"] ** 2).sum()))
+    per = np.sqrt((d ** 2).sum(1)) / np.maximum(np.sqrt((F["fp64"] ** 2).sum(1)), 1e-30)
+    return {"rms_rel": eps, "max_atom_rel": float(per.max()), "median_atom_rel": float(np.median(per)),
+            "what": "mixed vs FP64 GPU path, same state, seed and step (identical samples)"}
 
 
 def peaks():
@@ -323,6 +346,10 @@ def run_ours(args):
         e2e = {"value": w.n * Ke / te, "unit": "atom-steps/s", "h2d_bytes_per_step": 24 * w.n,
                "d2h_bytes_per_step": 24 * w.n,
                "what": "rbsog_set_state(host positions) + rbsog_compute_forces(host forces) per step"}
+    # ---- mixed vs FP64 force error on identical state and samples ---------------
+    ferr = None
+    if not args.no_force_error and prec == rbsog.MIXED and ws == 1:
+        ferr = force_error(rbsog, w, prm, local)
     # ---- CPU baseline (oracle) ---------------------------------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -342,7 +369,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
             "roofline": roof, "far_roofline": far_roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * K, "cpu_baseline": cpu,
+            "gpu_launches": KERNELS_PER_STEP * K, "cpu_baseline": cpu, "force_error": ferr,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -421,6 +448,13 @@ def main():
         run_reference(args)
     elif args.config == "ensemble_64":
         run_ensemble(args)
+    elif args.sweep:
+        # shell batch x Fourier batch sweep of one configuration, one line each
+        for P_R in (10, 20, 40):
+            for P_F in (500, 1000, 2000):
+                args.P_R, args.P_F = P_R, P_F
+                args.no_cpu_baseline = args.no_e2e = True
+                run_ours(args)
     else:
         run_ours(args)
 

@@ -63,7 +63,7 @@ class _Sys(ctypes.Structure):
         ("L", ctypes.c_double * 3), ("b", ctypes.c_double), ("s", ctypes.c_double),
         ("r_core", ctypes.c_double), ("r_shell", ctypes.c_double),
         ("P_R", ctypes.c_int32), ("P_F", ctypes.c_int32),
-        ("seed", ctypes.c_uint64), ("step", ctypes.c_int64),
+        ("seed", ctypes.c_uint64), ("step", ctypes.c_int64), ("skin", ctypes.c_double),
     ]
 
 
@@ -86,6 +86,11 @@ def _declare(L):
     L.orc_pair_terms.argtypes = [sp, _I32, _I32, _I64, _P, _P, _P]
     L.orc_fixed_point.argtypes = [sp, _P]
     L.orc_cell_grid.argtypes = [sp, _P]
+    L.orc_cell_grid_skin.argtypes = [sp, _P]
+    L.orc_lists_skin.argtypes = [sp, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_lists_skin.restype = ctypes.c_int
+    L.orc_near_skin.argtypes = [sp, _P, _P, _I64, _I32, _P, _P]
+    L.orc_near_skin.restype = ctypes.c_int
     L.orc_floyd.argtypes = [_U64, _I64, _U32, _I32, _I32, _P]
     L.orc_floyd.restype = _I32
     L.orc_lists.argtypes = [sp, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
@@ -157,10 +162,18 @@ def sog_eval(b, M, s, w, r):
 # --------------------------------------------------------------------------
 
 class System:
-    """A BMH system with its RBSOG/RBL parameters, held as numpy arrays."""
+    """A BMH system with its RBSOG/RBL parameters, held as numpy arrays.
+
+    ``list_every = 0`` (default): the random batch list is rebuilt from the
+    current positions at every evaluation (Sec. 2.2).  ``list_every = n >= 1``:
+    kept lists with outer radius r_shell + ``skin``, built at the first
+    evaluation, at every step that is a multiple of n, and after
+    :meth:`invalidate_lists` (see ``orc_near_skin``).
+    """
 
     def __init__(self, pos, species, charge, mass, bmh, box, *, b=1.3, M=64, s=None, w=None,
-                 r_core=6.0, r_shell=12.0, P_R=20, P_F=200, seed=1, step=0):
+                 r_core=6.0, r_shell=12.0, P_R=20, P_F=200, seed=1, step=0, skin=0.0,
+                 list_every=0):
         self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         self.species = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
         self.charge = np.ascontiguousarray(charge, dtype=np.float64)
@@ -176,6 +189,20 @@ class System:
         self.r_core, self.r_shell = float(r_core), float(r_shell)
         self.P_R, self.P_F = int(P_R), int(P_F)
         self.seed, self.step = int(seed), int(step)
+        self.skin, self.list_every = float(skin), int(list_every)
+        self.build_pos = None   # positions the kept lists were built from
+
+    @property
+    def kept_lists(self):
+        return self.list_every > 0
+
+    def invalidate_lists(self):
+        """The next evaluation builds the kept lists from the positions it sees."""
+        self.build_pos = None
+
+    def _ensure_lists(self):
+        if self.build_pos is None:
+            self.build_pos = self.pos.copy()
 
     @property
     def n(self):
@@ -204,6 +231,7 @@ class System:
         st.r_core, st.r_shell = self.r_core, self.r_shell
         st.P_R, st.P_F = self.P_R, self.P_F
         st.seed, st.step = self.seed, self.step
+        st.skin = self.skin
         return st
 
     # ---- geometry -------------------------------------------------------
@@ -241,14 +269,51 @@ class System:
             out.update(batch=bt, nbatch=nb, weight=wt)
         return out
 
+    def cell_grid_skin(self):
+        nc = np.zeros(3, dtype=np.int32)
+        st = self._c()
+        lib().orc_cell_grid_skin(ctypes.byref(st), _ptr(nc))
+        return nc
+
+    def lists_skin(self, sel=None, cap_a=256, cap_b=2048, batch=True):
+        """Kept lists A, B (canonical order of the build positions) and the batch of ``sel``."""
+        self._ensure_lists()
+        sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+        k = sel.size
+        A = np.full((k, cap_a), -1, dtype=np.int32)
+        na = np.zeros(k, dtype=np.int32)
+        B = np.full((k, cap_b), -1, dtype=np.int32)
+        nb = np.zeros(k, dtype=np.int32)
+        PR = max(self.P_R, 1)
+        bt = np.full((k, PR), -1, dtype=np.int32) if batch else None
+        nbt = np.zeros(k, dtype=np.int32) if batch else None
+        wt = np.zeros(k, dtype=np.float64) if batch else None
+        st = self._c()
+        bp = np.ascontiguousarray(self.build_pos)
+        rc = lib().orc_lists_skin(ctypes.byref(st), _ptr(bp), _ptr(sel), k, cap_a, cap_b, _ptr(A), _ptr(na),
+                                  _ptr(B), _ptr(nb), _ptr(bt), _ptr(nbt), _ptr(wt))
+        if rc != 0:
+            raise RuntimeError("oracle list capacity exceeded")
+        out = dict(A=A, nA=na, B=B, nB=nb)
+        if batch:
+            out.update(batch=bt, nbatch=nbt, weight=wt)
+        return out
+
     # ---- near field (Sec. 2.2) -------------------------------------------
     def near(self, sel=None, all_shell=False, energy=False):
-        """Uncorrected near-field force F_core + F*_shell of ``sel`` (and 1/2 pair energy)."""
+        """Uncorrected near-field force F_core + F*_shell of ``sel`` (and 1/2 pair energy);
+        with kept lists, the estimator of ``orc_near_skin``."""
         sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
         F = np.zeros((sel.size, 3))
         E = np.zeros(sel.size) if energy else None
         st = self._c()
-        rc = lib().orc_near(ctypes.byref(st), _ptr(sel), sel.size, int(bool(all_shell)), _ptr(F), _ptr(E))
+        if self.kept_lists:
+            self._ensure_lists()
+            bp = np.ascontiguousarray(self.build_pos)
+            rc = lib().orc_near_skin(ctypes.byref(st), _ptr(bp), _ptr(sel), sel.size, int(bool(all_shell)),
+                                     _ptr(F), _ptr(E))
+        else:
+            rc = lib().orc_near(ctypes.byref(st), _ptr(sel), sel.size, int(bool(all_shell)), _ptr(F), _ptr(E))
         if rc != 0:
             raise RuntimeError("oracle near-field capacity exceeded")
         return (F, E) if energy else F
@@ -382,6 +447,8 @@ class System:
             else:
                 self.pos = self.pos + dt * vel
             self.step = nxt
+            if self.kept_lists and nxt % self.list_every == 0:
+                self.build_pos = self.pos.copy()
             F = self.forces()["F"]
             vel = vel + 0.5 * dt * F * minv
         return vel, F

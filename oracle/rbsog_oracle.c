@@ -61,6 +61,7 @@ typedef struct {
   int32_t P_R, P_F;       /* batch sizes */
   uint64_t seed;
   int64_t step;
+  double skin;            /* Verlet skin of the kept lists (orc_*_skin only) */
 } orc_sys;
 
 /* ------------------------------------------------------------------------ */
@@ -248,15 +249,18 @@ void orc_fixed_point(const orc_sys *S, uint32_t *u) {
     for (int a = 0; a < 3; a++) u[3 * i + a] = fixed_point(S->pos[3 * i + a], inv[a]);
 }
 
-/* Cell grid of the canonical order: n_c = max(1, floor(L / (r_shell/2 * (1 + 2^-12)))),
- * cell = (u * n_c) >> 32, linear index x fastest.                         */
-void orc_cell_grid(const orc_sys *S, int32_t nc[3]) {
+/* Cell grid of the canonical order: n_c = max(1, floor(L / (r_out/2 * (1 + 2^-12)))),
+ * cell = (u * n_c) >> 32, linear index x fastest.  r_out is the outer list
+ * radius: r_shell for the per-step lists, r_shell + skin for kept lists.  */
+static void cell_grid_r(const orc_sys *S, double r_out, int32_t nc[3]) {
   for (int a = 0; a < 3; a++) {
-    double w = 0.5 * S->r_shell * (1.0 + 1.0 / 4096.0);
+    double w = 0.5 * r_out * (1.0 + 1.0 / 4096.0);
     int32_t c = (int32_t)floor(S->L[a] / w);
     nc[a] = c < 1 ? 1 : c;
   }
 }
+void orc_cell_grid(const orc_sys *S, int32_t nc[3]) { cell_grid_r(S, S->r_shell, nc); }
+void orc_cell_grid_skin(const orc_sys *S, int32_t nc[3]) { cell_grid_r(S, S->r_shell + S->skin, nc); }
 
 static int64_t cell_linear(const uint32_t *u, const int32_t nc[3]) {
   int64_t c[3];
@@ -295,16 +299,20 @@ typedef struct {
   int64_t *cell;   /* [n] */
 } orc_geo;
 
-static void geo_init(const orc_sys *S, orc_geo *G) {
+/* Geometry of the positions pos with outer list radius r_out. */
+static void geo_init_at(const orc_sys *S, const double *pos, double r_out, orc_geo *G) {
   for (int a = 0; a < 3; a++) G->h[a] = (float)(S->L[a] * 0x1p-23);
   G->rc2 = (float)(S->r_core * S->r_core);
-  G->rs2 = (float)(S->r_shell * S->r_shell);
-  orc_cell_grid(S, G->nc);
+  G->rs2 = (float)(r_out * r_out);
+  cell_grid_r(S, r_out, G->nc);
   G->u = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)S->n);
   G->cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)S->n);
-  orc_fixed_point(S, G->u);
+  double inv[3] = {1.0 / S->L[0], 1.0 / S->L[1], 1.0 / S->L[2]};
+  for (int64_t i = 0; i < S->n; i++)
+    for (int a = 0; a < 3; a++) G->u[3 * i + a] = fixed_point(pos[3 * i + a], inv[a]);
   for (int64_t i = 0; i < S->n; i++) G->cell[i] = cell_linear(G->u + 3 * i, G->nc);
 }
+static void geo_init(const orc_sys *S, orc_geo *G) { geo_init_at(S, S->pos, S->r_shell, G); }
 static void geo_free(orc_geo *G) { free(G->u); free(G->cell); }
 
 /* Core set {j != i : r^2 < fl32(r_core^2)} and shell set
@@ -483,6 +491,128 @@ int orc_near(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t all_she
     free(cc); free(ss); free(tt);
   }
   geo_free(&G);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kept (Verlet-skin) random batch lists: the RBL of Sec. 2.2 with neighbour
+ * lists that live for several steps, as in the paper's LAMMPS implementation
+ * (Sec. 3), whose per-step work is the core list plus P_R shell members
+ * (Sec. 2.4).  The lists are built at the positions pos_b with the outer
+ * radius r_list = r_shell + skin (cell grid of r_list / 2, canonical order of
+ * pos_b):
+ *   A_i = {j != i : pred_b < fl32(r_core^2)}
+ *   B_i = {j != i : fl32(r_core^2) <= pred_b < fl32(r_list^2)}.
+ * At the current positions every pair term carries the indicator
+ * 1[pred < fl32(r_shell^2)]:
+ *   F_i = sum_{j in A_i} f_ij 1[.] + (|B_i| / P_R) sum_{t in T_i} f_{i B_i[t]} 1[.]
+ * with T_i Floyd's P_R of |B_i| (all of B_i with weight 1 when |B_i| <= P_R).
+ * While no atom has moved by skin / 2 since pos_b, A_i and B_i hold every j
+ * with r_ij < r_shell, so the mean over T_i is the r_shell-cutoff force.    */
+int orc_lists_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int64_t nsel,
+                   int32_t cap_a, int32_t cap_b, int32_t *A, int32_t *na, int32_t *B, int32_t *nb,
+                   int32_t *batch, int32_t *nbatch, double *weight) {
+  orc_geo G;
+  geo_init_at(S, pos_b, S->r_shell + S->skin, &G);
+  int status = ORC_OK;
+#pragma omp parallel
+  {
+    cand_t *aa = (cand_t *)malloc(sizeof(cand_t) * (size_t)cap_a);
+    cand_t *bb = (cand_t *)malloc(sizeof(cand_t) * (size_t)cap_b);
+    int32_t *tt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->P_R > 0 ? S->P_R : 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < nsel; q++) {
+      int64_t i = sel[q];
+      int32_t n_a, n_b;
+      if (atom_lists(S, &G, i, aa, &n_a, cap_a, bb, &n_b, cap_b) != ORC_OK) {
+#pragma omp atomic write
+        status = ORC_ECAP;
+        na[q] = n_a; nb[q] = n_b;
+        continue;
+      }
+      na[q] = n_a;
+      nb[q] = n_b;
+      for (int k = 0; k < n_a; k++) A[q * cap_a + k] = aa[k].j;
+      for (int k = 0; k < n_b; k++) B[q * cap_b + k] = bb[k].j;
+      if (batch) {
+        int m = floyd_batch(S->seed, S->step, (uint32_t)i, n_b, S->P_R, tt);
+        nbatch[q] = m;
+        for (int k = 0; k < m; k++) batch[q * S->P_R + k] = bb[tt[k]].j;
+        weight[q] = n_b <= S->P_R ? 1.0 : (double)n_b / (double)S->P_R;
+      }
+    }
+    free(aa); free(bb); free(tt);
+  }
+  geo_free(&G);
+  return status;
+}
+
+/* Uncorrected near field of selected atoms with the kept lists of pos_b (see
+ * above); all_shell != 0 takes the whole of B_i with weight 1.  Per-atom
+ * energy: 1/2 of the same weighted pair sum.                               */
+int orc_near_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int64_t nsel,
+                  int32_t all_shell, double *F, double *E) {
+  orc_geo Gb, Gn;
+  geo_init_at(S, pos_b, S->r_shell + S->skin, &Gb);
+  geo_init_at(S, S->pos, S->r_shell, &Gn);
+  int status = ORC_OK;
+  const double sc[3] = {S->L[0] * 0x1p-32, S->L[1] * 0x1p-32, S->L[2] * 0x1p-32};
+#pragma omp parallel
+  {
+    cand_t *aa = (cand_t *)malloc(sizeof(cand_t) * ORC_CAP);
+    cand_t *bb = (cand_t *)malloc(sizeof(cand_t) * ORC_CAP);
+    int32_t *tt = (int32_t *)malloc(sizeof(int32_t) * ORC_CAP);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < nsel; q++) {
+      int64_t i = sel[q];
+      int32_t n_a, n_b;
+      if (atom_lists(S, &Gb, i, aa, &n_a, ORC_CAP, bb, &n_b, ORC_CAP) != ORC_OK) {
+#pragma omp atomic write
+        status = ORC_ECAP;
+        continue;
+      }
+      const uint32_t *ui = Gn.u + 3 * i;
+      const int si = S->species[i];
+      double fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0}, ea = 0.0, eb = 0.0;
+      for (int k = 0; k < n_a; k++) {
+        const int64_t j = aa[k].j;
+        const uint32_t *uj = Gn.u + 3 * j;
+        if (!(pred_r2(ui, uj, Gn.h) < Gn.rs2)) continue;
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = (double)(int32_t)(ui[a] - uj[a]) * sc[a];
+        double phi, e;
+        pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
+        for (int a = 0; a < 3; a++) fa[a] += phi * d[a];
+        ea += e;
+      }
+      int m;
+      double wgt;
+      if (all_shell || n_b <= S->P_R) {
+        m = n_b;
+        for (int k = 0; k < n_b; k++) tt[k] = k;
+        wgt = 1.0;
+      } else {
+        m = floyd_batch(S->seed, S->step, (uint32_t)i, n_b, S->P_R, tt);
+        wgt = (double)n_b / (double)S->P_R;
+      }
+      for (int k = 0; k < m; k++) {
+        const int64_t j = bb[tt[k]].j;
+        const uint32_t *uj = Gn.u + 3 * j;
+        if (!(pred_r2(ui, uj, Gn.h) < Gn.rs2)) continue;
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = (double)(int32_t)(ui[a] - uj[a]) * sc[a];
+        double phi, e;
+        pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
+        for (int a = 0; a < 3; a++) fb[a] += phi * d[a];
+        eb += e;
+      }
+      for (int a = 0; a < 3; a++) F[3 * q + a] = fa[a] + wgt * fb[a];
+      if (E) E[q] = 0.5 * (ea + wgt * eb);
+    }
+    free(aa); free(bb); free(tt);
+  }
+  geo_free(&Gb);
+  geo_free(&Gn);
   return status;
 }
 

@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--P_F", type=int, default=None)
     ap.add_argument("--P_R", type=int, default=None)
+    ap.add_argument("--list-every", type=int, default=0,
+                    help="0: per-step random batch lists; n >= 1: kept (skin) lists rebuilt every n steps")
+    ap.add_argument("--skin", type=float, default=1.0, help="skin of kept lists [A]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
@@ -119,19 +122,25 @@ def dist_env():
 # k_near, k_reduce (F^corr), k_finish; side branch k_ksample, k_rho, k_reduce (rho), k_farforce
 # (the histogram clear is a memset node)
 KERNELS_PER_STEP = 12
+# kept lists: a build step adds the list build to the per-step graph; a step
+# that reuses the lists has no binning (4 kernels) and no build
+KERNELS_BUILD_STEP = 13
+KERNELS_KEEP_STEP = 8
 KERNEL_LABEL = {"near": "k_near", "far": "k_rho + k_farforce (side stream)"}
 
 
-def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0):
+def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0, list_every=0, skin=0.0):
     """Algorithmic FP32/INT lane-operations of one force evaluation, per stage
     (the minimal instruction model of the design notes): near field = 8 ops per
-    list test of every neighbour inside r_shell plus 25 per evaluated pair
-    (core + P_R shell); structure factor = 15 per (atom, k) (3 phase IMAD,
-    ~10 sincos, 2 FMA); far force = 21 per (atom, k)."""
+    list test of every neighbour inside the list radius (r_shell every step;
+    r_shell + skin once per list_every steps with kept lists) plus 25 per
+    evaluated pair (core + P_R shell); structure factor = 15 per (atom, k)
+    (3 phase IMAD, ~10 sincos, 2 FMA); far force = 21 per (atom, k)."""
     rho_n = w.n / float(np.prod(w.box))
-    n_sph = 4.0 / 3.0 * np.pi * r_shell ** 3 * rho_n
+    r_list = r_shell + (skin if list_every > 0 else 0.0)
+    tests = 4.0 / 3.0 * np.pi * r_list ** 3 * rho_n / max(list_every, 1)
     n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
-    return {"near": w.n * (8.0 * n_sph + 25.0 * (n_core + P_R)),
+    return {"near": w.n * (8.0 * tests + 25.0 * (n_core + P_R)),
             "far": (15.0 + 21.0) * w.n * P_F}
 
 
@@ -266,7 +275,8 @@ def run_ours(args):
     prec = rbsog.MIXED if args.precision == "mixed" else rbsog.FP64
     prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=replica_seed(cfg.seed, rank), precision=prec,
                              integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
-                             T=cfg.T, dt=0.001, gamma=1.0)
+                             T=cfg.T, dt=0.001, gamma=1.0, list_every=args.list_every,
+                             skin=args.skin if args.list_every > 0 else 0.0)
     stream = torch.cuda.Stream(device=dev)
     ctx = rbsog.Context(local, stream.cuda_stream)
     ctx.set_workload(w, prm)
@@ -305,16 +315,17 @@ def run_ours(args):
     nsm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    alg = algorithmic_ops(w, P_F, P_R)
+    alg = algorithmic_ops(w, P_F, P_R, list_every=args.list_every, skin=prm.skin)
     # the dominant kernel: the near field, the longest stage of the critical path
     # (the far-field branch runs concurrently on a side stream; its wall time
     # there is shared with the near field, so it gets its own line below)
     dom = names.index("near")
     peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
     achieved = alg[names[dom]] / (stage_ms[dom] * 1e-3)
-    roof = {"bound": "alu", "kernel": KERNEL_LABEL[names[dom]], "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+    roof = {"bound": "alu",
+            "kernel": KERNEL_LABEL[names[dom]] if not args.list_every else "k_near_kept + k_near (list build, amortised)", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
             "unit": "Glane-op/s", "frac": achieved / peak_ops,
-            "traffic": profiled_traffic(names[dom]),
+            "traffic": profiled_traffic(names[dom]) if not args.list_every else None,
             "peak_source": "4 warp-instructions/clk/SM x 32 lanes x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
     fi = names.index("far")
     far_roof = {"kernels": KERNEL_LABEL["far"], "achieved": alg["far"] / (stage_ms[fi] * 1e-3) / 1e9,
@@ -358,6 +369,11 @@ def run_ours(args):
         v, wall, sample = oracle_sample(w, cfg, P_F, P_R)
         cpu = {"value": v, "unit": "atom-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": sample, "wall_s": wall}
+    if args.list_every:
+        builds = sum(1 for s in range(Wm + 1, Wm + K + 1) if s % args.list_every == 0)
+        launches = KERNELS_BUILD_STEP * builds + KERNELS_KEEP_STEP * (K - builds)
+    else:
+        launches = KERNELS_PER_STEP * K
     if rank == 0:
         line = {
             "metric": "atom-steps/s of RBSOG+RBL force step at <=1e-5 RMS rel. force err, mixed vs FP64",
@@ -366,10 +382,12 @@ def run_ours(args):
             "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
             "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
+                       "lists": ("per step" if not args.list_every else
+                                 "kept: skin %.2f A, rebuilt every %d steps" % (prm.skin, args.list_every)),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
             "roofline": roof, "far_roofline": far_roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * K, "cpu_baseline": cpu, "force_error": ferr,
+            "gpu_launches": launches, "cpu_baseline": cpu, "force_error": ferr,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

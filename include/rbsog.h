@@ -52,6 +52,8 @@ extern "C" {
 #define RBSOG_E_TIMEOUT (-6)        /* bounded device wait expired */
 #define RBSOG_E_NO_SOG_ROOT (-7)    /* no s with N'(r_c) = 0 in [r_c/6, r_c/2] */
 #define RBSOG_E_NO_SYSTEM (-8)      /* call needs rbsog_set_system first */
+#define RBSOG_E_SKIN (-9)           /* kept lists: an atom moved by more than skin/2 since the
+                                       lists were built (that step and later ones are invalid) */
 
 /* ---- enums ---------------------------------------------------------------- */
 #define RBSOG_FP64 0   /* analytic FP64 pair terms (M+1 Gaussians), FP64 sincospi and sums */
@@ -72,6 +74,7 @@ extern "C" {
                                    8 sorted atoms needs, each cell padded to a multiple of 4
                                    (also: a run of 8 atoms spans at most 4 cells along x) */
 #define RBSOG_MAX_SHELL 1024   /* shell neighbours of one atom when the batch is sampled */
+#define RBSOG_MAX_KEPT 512     /* kept lists: members of B (r_core <= r < r_shell + skin) per atom */
 #define RBSOG_MAX_M 128        /* Gaussians m = 0..M */
 
 typedef struct rbsog_ctx rbsog_ctx; /* opaque, library-owned */
@@ -93,6 +96,20 @@ typedef struct {
   double dt;       /* time step [ps] */
   double T;        /* Langevin temperature [K] */
   double gamma;    /* Langevin collision rate gamma/m [1/ps], same for all species */
+  /* Random batch lists (Sec. 2.2).  list_every = 0: core and shell are found
+   * from the current positions at every evaluation.  list_every = n >= 1:
+   * kept lists, as with the paper's skin neighbour lists (Sec. 3): built from
+   * the positions of the first evaluation after set_system / set_state and of
+   * every step that is a multiple of n, with the outer radius
+   * r_list = r_shell + skin; A = {r < r_core}, B = {r_core <= r < r_list} at
+   * those positions.  Each evaluation sums A exactly and a Floyd batch of P_R
+   * of B with weight |B| / P_R; every term carries the indicator
+   * r < r_shell at the current positions, so the estimator stays unbiased for
+   * the r_shell-cutoff force while no atom moves by skin/2 between builds
+   * (checked every step: RBSOG_E_SKIN).  Needs every box length
+   * >= 2 r_list. */
+  int32_t list_every;
+  double skin;     /* [A], >= 0; used when list_every >= 1 */
 } rbsog_params;
 
 /* Create a context on CUDA device `cuda_device`.  `cuda_stream` is the
@@ -200,6 +217,18 @@ int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, d
 int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_core,
                           int32_t cap_shell, int32_t *core, int32_t *ncore, int32_t *shell,
                           int32_t *nshell, int32_t *batch, int32_t *nbatch, double *weight);
+
+/* Kept lists (list_every >= 1) of atoms sel[0..nsel) as last built, and the
+ * shell batch the current step counter draws from them: A rows (width
+ * cap_a) and B rows (width cap_b) hold caller atom indices in the canonical
+ * order of the build positions (ascending (cell index of j on the r_list/2
+ * grid, u_x of j, j)); batch rows of width P_R hold the sampled members of B
+ * (all of B, weight 1, if |B| <= P_R), weight = |B| / P_R.  Needs a force
+ * evaluation since the lists were last invalidated.  Host pointers.
+ * Errors: RBSOG_E_INVAL (per-step lists in use, bad arguments). */
+int rbsog_debug_get_kept_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_a,
+                               int32_t cap_b, int32_t *A, int32_t *nA, int32_t *B, int32_t *nB,
+                               int32_t *batch, int32_t *nbatch, double *weight);
 
 /* k-batch of the last force evaluation: m [P][3] int32, c [P] FP64 with
  * c_p = S/(P_F |k_p|^2) (or the weights set below).  Host pointers. */

@@ -34,8 +34,11 @@ struct rbsog_ctx {
   std::vector<void *> allocs;  // system-lifetime device buffers
   int Pmax = 0;
   double *stage = nullptr;     // [n][3] FP64 staging
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec = nullptr;       // step graph (with kept lists: the build variant)
+  cudaGraphExec_t gexec_keep = nullptr;  // kept lists: the variant that reuses them
   bool graph_ok = false;
+  bool lists_valid = false;              // kept lists built since the last set_system / set_state
+  int64_t host_step = 0;                 // mirror of the device step counter
   bool own_stream = false;
   bool profiling = false;
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
@@ -69,8 +72,11 @@ int dalloc(rbsog_ctx *ctx, T **p, size_t count) {
 
 void free_system(rbsog_ctx *ctx) {
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->gexec_keep) cudaGraphExecDestroy(ctx->gexec_keep);
   ctx->gexec = nullptr;
+  ctx->gexec_keep = nullptr;
   ctx->graph_ok = false;
+  ctx->lists_valid = false;
   for (void *p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->has_system = false;
@@ -105,7 +111,9 @@ int check_launch(rbsog_ctx *ctx) {
 // step counter, the structure factor and the far-field force only the
 // prepared coordinates and the k-batch, so they run on a side stream,
 // concurrently with the integrator, the binning and the near field; the
-// branches join for the total force and the closing half kick.
+// branches join for the total force and the closing half kick.  With kept
+// lists, v.build selects binning + list build + evaluation, else the
+// evaluation of the last build's lists alone.
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
   cudaStream_t st = ctx->st, st2 = ctx->st2;
   const bool pr = ctx->profiling;
@@ -129,9 +137,14 @@ int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st2, evflag));
   CK(cudaEventRecord(ctx->ev_join, st2));
   // main branch: binning, near field, F^corr
-  rb::launch_bin(v, st);
+  if (!v.kept || v.build) rb::launch_bin(v, st);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[2], st, evflag));
-  rb::launch_near(v, st, step_off, energy);
+  if (!v.kept) {
+    rb::launch_near(v, st, step_off, energy);
+  } else {
+    if (v.build) rb::launch_build_lists(v, st);
+    rb::launch_near_kept(v, st, step_off, energy);
+  }
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[7], st, evflag));
   rb::launch_corr(v, st, step_off);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[5], st, evflag));
@@ -152,6 +165,10 @@ int read_err(rbsog_ctx *ctx) {
     if (e & rb::ERR_CORE_CAP) m += " core list > RBSOG_MAX_CORE";
     if (e & rb::ERR_CELL_SHELL_CAP) m += " stencil row > RBSOG_MAX_ROW_SLOTS slots or shell > RBSOG_MAX_SHELL";
     if (e & rb::ERR_PR_CAP) m += " P_R";
+    if (e & rb::ERR_KEPT_CAP) m += " kept list: |A| > RBSOG_MAX_CORE or |B| > RBSOG_MAX_KEPT";
+    if (e & rb::ERR_SKIN)
+      return fail(ctx, RBSOG_E_SKIN, "kept lists: an atom moved by more than skin/2 since the last build "
+                                     "(rebuild more often or widen the skin)");
     return fail(ctx, RBSOG_E_CAP_OVERFLOW, m);
   }
   return RBSOG_OK;
@@ -298,12 +315,16 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   if (P.P_F < 1) return fail(ctx, RBSOG_E_INVAL, "P_F out of range");
   if (P.precision != RBSOG_FP64 && P.precision != RBSOG_MIXED) return fail(ctx, RBSOG_E_INVAL, "bad precision");
   if (P.integrator != RBSOG_NVE_VV && P.integrator != RBSOG_LANGEVIN_BAOAB) return fail(ctx, RBSOG_E_INVAL, "bad integrator");
+  if (P.list_every < 0) return fail(ctx, RBSOG_E_INVAL, "list_every must be >= 0");
+  if (P.list_every > 0 && !(P.skin >= 0.0)) return fail(ctx, RBSOG_E_INVAL, "skin must be >= 0");
+  const bool kept = P.list_every > 0;
+  const double r_list = P.r_shell + (kept ? P.skin : 0.0);  // outer radius of the lists
   std::vector<double> hb(3);
   int rc;
   if ((rc = fetch(ctx, box, 3, RBSOG_PTR_HOST, hb))) return rc;
   for (int a = 0; a < 3; a++) {
     if (!(hb[a] > 0.0)) return fail(ctx, RBSOG_E_INVAL, "box must be positive");
-    if (hb[a] < 2.0 * P.r_shell) return fail(ctx, RBSOG_E_BOX_TOO_SMALL, "box length < 2 r_shell");
+    if (hb[a] < 2.0 * r_list) return fail(ctx, RBSOG_E_BOX_TOO_SMALL, "box length < 2 (r_shell + skin)");
   }
   std::vector<double> hpos, hq, hm, hbmh;
   std::vector<int32_t> hsp;
@@ -374,10 +395,16 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     v.hf[a] = (float)(hb[a] * 0x1p-32);
     v.hd[a] = hb[a] * 0x1p-32;
     v.kunit[a] = 2.0 * M_PI / hb[a];
-    v.nc[a] = rb::cell_count(hb[a], P.r_shell);
+    v.nc[a] = rb::cell_count(hb[a], r_list);
   }
   v.rc2f = (float)(P.r_core * P.r_core);
   v.rs2f = (float)(P.r_shell * P.r_shell);
+  v.kept = kept ? 1 : 0;
+  v.build = 0;
+  v.rl2f = (float)(r_list * r_list);
+  // an atom may move by skin/2 (pair distances by skin): shaded by 2^-10 so
+  // that the FP32 predicate's rounding stays inside the margin
+  v.half_skin2 = 0.25 * P.skin * P.skin * (1.0 - 1.0 / 1024.0);
   v.ncell = v.nc[0] * v.nc[1] * v.nc[2];
   v.small = (v.nc[0] < rb::STENCIL || v.nc[1] < rb::STENCIL || v.nc[2] < rb::STENCIL) ? 1 : 0;
   // the near field's union of a chunk's x-stencils (<= 8 cells) may meet
@@ -436,6 +463,11 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &off0, samp.off0.size())) || (rc = dalloc(ctx, &off2, samp.off2.size())) ||
       (rc = dalloc(ctx, &nmax, samp.nmax.size())) || (rc = dalloc(ctx, &ctx->stage, 3 * N)) ||
       (rc = ensure_kcap(ctx, P.P_F))) {
+    free_system(ctx);
+    return rc;
+  }
+  if (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
+               (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N)))) {
     free_system(ctx);
     return rc;
   }
@@ -506,6 +538,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
   ctx->has_system = true;
   ctx->forces_valid = false;
+  ctx->lists_valid = false;
+  ctx->host_step = 0;
   return leave(ctx);
 }
 
@@ -527,8 +561,11 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
   if (virial) return fail(ctx, RBSOG_E_INVAL, "virial output is not provided");
   int rc;
   if ((rc = enter(ctx))) return rc;
-  if ((rc = run_force(ctx, ctx->v, 0, 0, energy != nullptr))) return rc;
+  View vv = ctx->v;
+  vv.build = ctx->lists_valid ? 0 : 1;
+  if ((rc = run_force(ctx, vv, 0, 0, energy != nullptr))) return rc;
   ctx->forces_valid = true;
+  ctx->lists_valid = true;
   if (forces) {
     if (ctx->v.prec == RBSOG_FP64) rc = export_aos(ctx, ctx->v.Fd, nullptr, forces, ptr_kind);
     else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind);
@@ -556,25 +593,42 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
   int rc;
   if ((rc = enter(ctx))) return rc;
   if (!ctx->forces_valid) {
-    if ((rc = run_force(ctx, ctx->v, 0, 0, false))) return rc;
+    View vv = ctx->v;
+    vv.build = ctx->lists_valid ? 0 : 1;
+    if ((rc = run_force(ctx, vv, 0, 0, false))) return rc;
     ctx->forces_valid = true;
+    ctx->lists_valid = true;
   }
   if (!ctx->graph_ok) {
-    View vs = ctx->v;
     const int mode = ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 2;
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-    rc = run_force(ctx, vs, mode, 1, false);
-    cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
-    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    // variant 0 bins and builds (per-step lists: the only one); variant 1
+    // evaluates the kept lists of the last build
+    for (int var = 0; var < (ctx->v.kept ? 2 : 1); var++) {
+      View vs = ctx->v;
+      vs.build = var == 0 ? 1 : 0;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+      rc = run_force(ctx, vs, mode, 1, false);
+      cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      cudaGraphExec_t &ge = var == 0 ? ctx->gexec : ctx->gexec_keep;
+      if (ge) cudaGraphExecDestroy(ge);
+      ge = nullptr;
+      e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
     ctx->graph_ok = true;
   }
-  for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+  // kept lists are rebuilt at the steps that are multiples of list_every
+  const int64_t every = ctx->prm.list_every;
+  for (int64_t k = 0; k < nsteps; k++) {
+    const int64_t next = ctx->host_step + 1;
+    const bool build = !ctx->v.kept || next % every == 0;
+    CK(cudaGraphLaunch(build ? ctx->gexec : ctx->gexec_keep, ctx->st));
+    ctx->host_step = next;
+  }
   return leave(ctx);
 }
 
@@ -608,6 +662,8 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
   CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->forces_valid = false;
+  ctx->lists_valid = false;
+  ctx->host_step = step;
   return leave(ctx);
 }
 
@@ -637,6 +693,7 @@ int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int3
     return fail(ctx, RBSOG_E_INVAL, "bad list arguments");
   for (int64_t q = 0; q < nsel; q++)
     if (sel[q] < 0 || sel[q] >= ctx->n) return fail(ctx, RBSOG_E_INVAL, "selected atom out of range");
+  if (ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "kept lists in use: see rbsog_debug_get_kept_lists");
   int rc;
   if ((rc = enter(ctx))) return rc;
   View &v = ctx->v;
@@ -677,6 +734,57 @@ int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int3
   }
   CK(cudaStreamSynchronize(ctx->st));
   cudaFree(dsel); cudaFree(dcore); cudaFree(dnc); cudaFree(dshell); cudaFree(dns);
+  if (batch) { cudaFree(dbatch); cudaFree(dnb); cudaFree(dw); }
+  return leave(ctx);
+}
+
+int rbsog_debug_get_kept_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_a,
+                               int32_t cap_b, int32_t *A, int32_t *nA, int32_t *B, int32_t *nB,
+                               int32_t *batch, int32_t *nbatch, double *weight) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "per-step lists in use (list_every = 0)");
+  if (!ctx->lists_valid) return fail(ctx, RBSOG_E_INVAL, "no kept lists yet: evaluate forces first");
+  if (!sel || nsel <= 0 || cap_a < 1 || cap_b < 1 || !A || !nA || !B || !nB ||
+      (batch && (!nbatch || !weight)))
+    return fail(ctx, RBSOG_E_INVAL, "bad list arguments");
+  for (int64_t q = 0; q < nsel; q++)
+    if (sel[q] < 0 || sel[q] >= ctx->n) return fail(ctx, RBSOG_E_INVAL, "selected atom out of range");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  const View &v = ctx->v;
+  const size_t k = (size_t)nsel;
+  long long *dsel;
+  int *dA, *dnA, *dB, *dnB, *dbatch = nullptr, *dnb = nullptr;
+  double *dw = nullptr;
+  CK(cudaMalloc(&dsel, sizeof(long long) * k));
+  CK(cudaMalloc(&dA, sizeof(int) * k * cap_a));
+  CK(cudaMalloc(&dnA, sizeof(int) * k));
+  CK(cudaMalloc(&dB, sizeof(int) * k * cap_b));
+  CK(cudaMalloc(&dnB, sizeof(int) * k));
+  if (batch) {
+    CK(cudaMalloc(&dbatch, sizeof(int) * k * v.P_R));
+    CK(cudaMalloc(&dnb, sizeof(int) * k));
+    CK(cudaMalloc(&dw, sizeof(double) * k));
+    CK(cudaMemsetAsync(dbatch, 0xFF, sizeof(int) * k * v.P_R, ctx->st));
+  }
+  CK(cudaMemsetAsync(dA, 0xFF, sizeof(int) * k * cap_a, ctx->st));   // pad rows with -1
+  CK(cudaMemsetAsync(dB, 0xFF, sizeof(int) * k * cap_b, ctx->st));
+  std::vector<long long> hs(sel, sel + k);
+  CK(cudaMemcpyAsync(dsel, hs.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, ctx->st));
+  rb::launch_kept_lists(v, ctx->st, 0, dsel, (int)nsel, cap_a, cap_b, dA, dnA, dB, dnB, dbatch, dnb, dw);
+  if ((rc = check_launch(ctx))) return rc;
+  CK(cudaMemcpyAsync(A, dA, sizeof(int) * k * cap_a, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(nA, dnA, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(B, dB, sizeof(int) * k * cap_b, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(nB, dnB, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+  if (batch) {
+    CK(cudaMemcpyAsync(batch, dbatch, sizeof(int) * k * v.P_R, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(nbatch, dnb, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(weight, dw, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  cudaFree(dsel); cudaFree(dA); cudaFree(dnA); cudaFree(dB); cudaFree(dnB);
   if (batch) { cudaFree(dbatch); cudaFree(dnb); cudaFree(dw); }
   return leave(ctx);
 }

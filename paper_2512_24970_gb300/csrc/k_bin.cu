@@ -1,6 +1,8 @@
 // Stage (a) and the integrator's first half, plus the k-batch draw of stage (d):
 //   k_prepare   per atom: [half kick, drift / BAOAB B-A-O-A (Sec. 2.3)], 32-bit
-//               fixed-point coordinates, cell index, cell and row histograms.
+//               fixed-point coordinates, cell index, cell and row histograms
+//               (with kept lists between builds: the slot's coordinates and
+//               the displacement check instead of the histograms).
 //   k_ksample   the P_F k-vectors from P(k) (Eq. (Pk)), one warp per sample.
 //   k_rowscan   row ranges (rows of cells padded to a multiple of 4 slots),
 //               padding slots, near-field chunk offsets (one block).
@@ -126,6 +128,22 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   const int cell = cell_of(u[0], p.nc[0]) + p.nc[0] * (cell_of(u[1], p.nc[1]) + p.nc[1] * cell_of(u[2], p.nc[2]));
   p.ua[i] = make_uint4(u[0], u[1], u[2], (uint32_t)sp);
   p.cellid[i] = cell;
+  if (p.kept) {
+    if (p.build) {                 // positions of this build, for the displacement check
+      for (int a = 0; a < 3; a++) p.xb[a * n + i] = x[a];
+    } else {
+      // the lists and slots of the last build are kept: refresh this atom's
+      // coordinates in its slot and check that it stayed within skin/2
+      p.su[p.slot_of[i]] = make_uint4(u[0], u[1], u[2], (uint32_t)i | ((uint32_t)sp << SU_SP_SHIFT));
+      double d2 = 0.0;
+      for (int a = 0; a < 3; a++) {
+        const double d = x[a] - p.xb[a * n + i];
+        d2 += d * d;
+      }
+      if (d2 > p.half_skin2) atomicOr(p.err, ERR_SKIN);
+      return;                      // no binning in this evaluation
+    }
+  }
   // histograms; lanes of one warp that share a cell (or row) add once
   const unsigned act = __activemask();
   const unsigned pc = __match_any_sync(act, cell);

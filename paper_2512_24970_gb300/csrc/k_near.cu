@@ -4,7 +4,8 @@
 // stream 0), core + weighted batch pair forces.  The pair force is
 // Eq. (Fshort) (SOG residual + BMH, k_e on Coulomb): FP32 with the SOG sum
 // tabulated (mixed) or analytic FP64 over m = 0..M.  The block's FP64 partial
-// sums of F_N feed the momentum correction F^corr.
+// sums of F_N feed the momentum correction F^corr.  With kept (skin) lists
+// the walk's BUILD variant writes the lists and k_near_kept evaluates them.
 #include "rbsog_internal.cuh"
 
 namespace rb {
@@ -205,6 +206,7 @@ constexpr int NROW = STENCIL * STENCIL;      // stencil rows (y, z)
 // or the whole rows of a short box (WRAP: 25 rows of at most
 // RBSOG_MAX_ROW_SLOTS / 4 groups)
 constexpr int GBYTES_CULLED = 352;
+constexpr int GBYTES_BUILD = 512;            // kept-list builds: outer radius r_shell + skin
 constexpr int GBYTES_WRAP = STENCIL * STENCIL * RBSOG_MAX_ROW_SLOTS / CELL_ALIGN;
 constexpr int SHELL_BITS = RBSOG_MAX_SHELL;  // shell members one bitmask can index
 constexpr int WMAX = 8;                      // union x-cells of a chunk
@@ -276,13 +278,69 @@ __device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *
   q1 = fma2(az1, az1, fma2(ay1, ay1, mul2(ax1, ax1)));
 }
 
-template <typename R, bool WRAP, bool ENERGY>
+// One partial per warp of sum F_N and of the pair energy (FP32 sums of the
+// warp's eight atoms in mixed precision, FP64 otherwise).
+template <bool MIX>
+__device__ __forceinline__ void warp_partials(const View &p, double part[4], int warp, int lane) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    if (MIX) {
+      float f = (float)part[c];
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+      part[c] = (double)f;
+    } else {
+      for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
+    }
+  }
+  if (lane == 0) {
+    double *d = p.near_part + 4 * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
+    d[0] = part[0]; d[1] = part[1]; d[2] = part[2]; d[3] = part[3];
+  }
+}
+
+// Sum an atom's exact part fc and batch part fs over its TPA threads; its
+// first thread writes F_N = fc + wgt fs (caller order) and its warp-partial
+// terms.
+template <typename R, bool ENERGY>
+__device__ __forceinline__ void combine_atom(const View &p, Acc<R> &fc, Acc<R> &fs, R wgt, bool active,
+                                             int g, uint4 ui, double part[4]) {
+#pragma unroll
+  for (int o = 1; o < TPA; o <<= 1) {
+    fc.x += __shfl_xor_sync(0xffffffffu, fc.x, o, TPA);
+    fc.y += __shfl_xor_sync(0xffffffffu, fc.y, o, TPA);
+    fc.z += __shfl_xor_sync(0xffffffffu, fc.z, o, TPA);
+    fs.x += __shfl_xor_sync(0xffffffffu, fs.x, o, TPA);
+    fs.y += __shfl_xor_sync(0xffffffffu, fs.y, o, TPA);
+    fs.z += __shfl_xor_sync(0xffffffffu, fs.z, o, TPA);
+    if (ENERGY) {
+      fc.e += __shfl_xor_sync(0xffffffffu, fc.e, o, TPA);
+      fs.e += __shfl_xor_sync(0xffffffffu, fs.e, o, TPA);
+    }
+  }
+  if (active && g == 0) {
+    const R Fx = fc.x + wgt * fs.x, Fy = fc.y + wgt * fs.y, Fz = fc.z + wgt * fs.z;
+    const int64_t id = ui.w & SU_ID_MASK, n = p.n;
+    if (sizeof(R) == 4) {
+      p.FNf[id] = (float)Fx; p.FNf[n + id] = (float)Fy; p.FNf[2 * n + id] = (float)Fz;
+    } else {
+      p.FNd[id] = (double)Fx; p.FNd[n + id] = (double)Fy; p.FNd[2 * n + id] = (double)Fz;
+    }
+    part[0] = (double)Fx; part[1] = (double)Fy; part[2] = (double)Fz;
+    part[3] = (double)((R)0.5 * (fc.e + wgt * fs.e));
+  }
+}
+
+// BUILD: the same walk with the outer radius r_list = r_shell + skin builds
+// the kept lists instead (A = core members, B = the rest inside r_list, both
+// in canonical order, i.e. ascending slot) and evaluates nothing.
+template <typename R, bool WRAP, bool ENERGY, bool BUILD>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   constexpr bool MIX = sizeof(R) == 4;
   // per-atom rows padded by one word so that the eight atoms of a warp hit distinct banks
-  constexpr int GBYTES = WRAP ? GBYTES_WRAP : GBYTES_CULLED;
+  constexpr int GBYTES = WRAP ? GBYTES_WRAP : (BUILD ? GBYTES_BUILD : GBYTES_CULLED);
   __shared__ __align__(16) unsigned char gres[APB][GBYTES + 4]; // per group of 4 candidates: r < r_shell (bits 0-3), r < r_core (4-7)
   __shared__ unsigned char scnt[APB][NROW];      // shell members of each stencil row
+  __shared__ unsigned char ccnt[BUILD ? APB : 1][BUILD ? NROW : 1];  // core members (BUILD)
   __shared__ unsigned short spre[APB][NROW + 1]; // exclusive prefix of the counts
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
   __shared__ uint32_t bmask[APB][SHELL_BITS / 32 + 1];
@@ -374,7 +432,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
         const float cwy = 8388608.0f / (float)p.nc[1], cwz = 8388608.0f / (float)p.nc[2];
         const float ylo = __fmaf_rn((float)cy, cwy, shy) - 4.0f, yhi = __fmaf_rn((float)(cy + 1), cwy, shy) + 4.0f;
         const float zlo = __fmaf_rn((float)cz, cwz, shz) - 4.0f, zhi = __fmaf_rn((float)(cz + 1), cwz, shz) + 4.0f;
-        const float cull2 = p.rs2f * 1.0005f;
+        const float cull2 = (BUILD ? p.rl2f : p.rs2f) * 1.0005f;
         const float unit = 1.0001f / p.hp[0];   // 23-bit units per Angstrom along x, widened
         float xlo = 3.0e7f, xhi = -3.0e7f;
 #pragma unroll
@@ -384,9 +442,9 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
           const float gz = fmaxf(0.0f, fmaxf(zlo - qz[q], qz[q] - zhi)) * p.hp[2];
           const float R2 = cull2 - gy * gy - gz * gz;
           if (R2 > 0.0f) {
-            const float R = __fmaf_rn(sqrtf(R2), unit, 8.0f);
-            xlo = fminf(xlo, qx[q] - R);
-            xhi = fmaxf(xhi, qx[q] + R);
+            const float Rc = __fmaf_rn(sqrtf(R2), unit, 8.0f);
+            xlo = fminf(xlo, qx[q] - Rc);
+            xhi = fmaxf(xhi, qx[q] + Rc);
           }
         }
         xlo = fmaxf(xlo, (float)xs * cwx - 8.0f);
@@ -437,7 +495,8 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
     __syncwarp();
     // ---- pass 1: the chunk's groups dealt round-robin over an atom's four
     // threads (all eight atoms test the same group at the same time) ---------
-    const unsigned long long RS2 = pk2(-p.rs2f, -p.rs2f), RC2 = pk2(-p.rc2f, -p.rc2f);
+    const float outer2 = BUILD ? p.rl2f : p.rs2f;
+    const unsigned long long RS2 = pk2(-outer2, -outer2), RC2 = pk2(-p.rc2f, -p.rc2f);
     if (!over) {
       const int G = rgo[warp][nr];
       int r = -1, rg0 = 0, rg1 = 0, bo = 0;
@@ -494,17 +553,68 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
       for (int r = g; r < nr; r += TPA) {
         const int ng = rgo[warp][r + 1] - rgo[warp][r];
         const uint32_t *wp = reinterpret_cast<const uint32_t *>(&gres[a][rbo[warp][r]]);
-        int cnt = 0;
+        int cnt = 0, cc = 0;
         for (int w = 0; 4 * w < ng; w++) {
           uint32_t x = wp[w];
           if (ng - 4 * w < 4) x &= (1u << (8 * (ng - 4 * w))) - 1u;   // groups past the row
           const uint32_t cm = (x >> 4) & 0x0F0F0F0Fu;
           cnt += __popc(x & 0x0F0F0F0Fu & ~cm);
-          mycore += __popc(cm);
+          cc += __popc(cm);
         }
         scnt[a][r] = (unsigned char)min(cnt, 255);
+        if (BUILD) ccnt[a][r] = (unsigned char)min(cc, 255);
         my_total += cnt;
+        mycore += cc;
       }
+    }
+    if constexpr (BUILD) {
+      // ---- kept lists: each thread writes the members of its rows at the
+      // row's offset in the canonical order (prefix of the row counts) -------
+      int nb = my_total, na = mycore;
+#pragma unroll
+      for (int o = 1; o < TPA; o <<= 1) {
+        nb += __shfl_xor_sync(0xffffffffu, nb, o, TPA);
+        na += __shfl_xor_sync(0xffffffffu, na, o, TPA);
+      }
+      const bool ok = active && !over && na <= RBSOG_MAX_CORE && nb <= RBSOG_MAX_KEPT;
+      if (active && g == 0 && !ok) atomicOr(p.err, over ? ERR_CELL_SHELL_CAP : ERR_KEPT_CAP);
+      __syncwarp();
+      if (ok) {
+        int accB = 0, accA = 0;
+        for (int q = 0; q < g && q < nr; q++) {
+          accB += scnt[a][q];
+          accA += ccnt[a][q];
+        }
+        int *dA = p.lA + (int64_t)slot * RBSOG_MAX_CORE;
+        int *dB = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
+        for (int r = g; r < nr; r += TPA) {
+          const int ng = rgo[warp][r + 1] - rgo[warp][r];
+          const int4 sg = rseg[warp][r];
+          const uint32_t *wp = reinterpret_cast<const uint32_t *>(&gres[a][rbo[warp][r]]);
+          for (int w = 0; 4 * w < ng; w++) {
+            uint32_t x = wp[w];
+            if (ng - 4 * w < 4) x &= (1u << (8 * (ng - 4 * w))) - 1u;
+            uint32_t cm = (x >> 4) & 0x0F0F0F0Fu;
+            uint32_t sm = x & 0x0F0F0F0Fu & ~cm;
+            while (cm) {
+              const int b = __ffs(cm) - 1;
+              cm &= cm - 1u;
+              dA[accA++] = row_slot(sg, 16 * w + 4 * (b >> 3) + (b & 3));
+            }
+            while (sm) {
+              const int b = __ffs(sm) - 1;
+              sm &= sm - 1u;
+              dB[accB++] = row_slot(sg, 16 * w + 4 * (b >> 3) + (b & 3));
+            }
+          }
+          for (int q = r + 1; q < min(r + TPA, nr); q++) {
+            accB += scnt[a][q];
+            accA += ccnt[a][q];
+          }
+        }
+      }
+      if (active && g == 0) p.nAB[slot] = ok ? make_int2(na, nb) : make_int2(0, 0);
+      return;
     }
     if (!active) { my_total = 0; mycore = 0; over = false; }
     int cbase = mycore;                          // this thread's offset in the atom's core list
@@ -658,53 +768,17 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
           if (js[i] >= 0) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fc);
       }
     }
-    // ---- combine the group ----------------------------------------------
-#pragma unroll
-    for (int o = 1; o < TPA; o <<= 1) {
-      fc.x += __shfl_xor_sync(0xffffffffu, fc.x, o, TPA);
-      fc.y += __shfl_xor_sync(0xffffffffu, fc.y, o, TPA);
-      fc.z += __shfl_xor_sync(0xffffffffu, fc.z, o, TPA);
-      fs.x += __shfl_xor_sync(0xffffffffu, fs.x, o, TPA);
-      fs.y += __shfl_xor_sync(0xffffffffu, fs.y, o, TPA);
-      fs.z += __shfl_xor_sync(0xffffffffu, fs.z, o, TPA);
-      if (ENERGY) {
-        fc.e += __shfl_xor_sync(0xffffffffu, fc.e, o, TPA);
-        fs.e += __shfl_xor_sync(0xffffffffu, fs.e, o, TPA);
-      }
-    }
-    if (active && g == 0) {
-      const R Fx = fc.x + wgt * fs.x, Fy = fc.y + wgt * fs.y, Fz = fc.z + wgt * fs.z;
-      const int64_t id = ui.w & SU_ID_MASK, n = p.n;
-      if (MIX) {
-        p.FNf[id] = (float)Fx; p.FNf[n + id] = (float)Fy; p.FNf[2 * n + id] = (float)Fz;
-      } else {
-        p.FNd[id] = (double)Fx; p.FNd[n + id] = (double)Fy; p.FNd[2 * n + id] = (double)Fz;
-      }
-      part[0] = (double)Fx; part[1] = (double)Fy; part[2] = (double)Fz;
-      part[3] = (double)((R)0.5 * (fc.e + wgt * fs.e));
-    }
+    combine_atom<R, ENERGY>(p, fc, fs, wgt, active, g, ui, part);
   }
+  if constexpr (BUILD) return;
   // ---- partials of sum F_N and of the pair energy, one per warp (FP32 sums of
   // the warp's eight atoms in mixed precision, FP64 otherwise) ----------------
-#pragma unroll
-  for (int c = 0; c < 4; c++) {
-    if (MIX) {
-      float f = (float)part[c];
-      for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-      part[c] = (double)f;
-    } else {
-      for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
-    }
-  }
-  if (lane == 0) {
-    double *d = p.near_part + 4 * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
-    d[0] = part[0]; d[1] = part[1]; d[2] = part[2]; d[3] = part[3];
-  }
+  warp_partials<MIX>(p, part, warp, lane);
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
   const dim3 g(v.nblk_near), b(NEAR_BLOCK);  // one warp per chunk
-#define RB_NEAR(R, WR, EN) k_near<R, WR, EN><<<g, b, 0, st>>>(v, step_off)
+#define RB_NEAR(R, WR, EN) k_near<R, WR, EN, false><<<g, b, 0, st>>>(v, step_off)
   if (v.prec == RBSOG_MIXED) {
     if (v.wrap) { if (energy) RB_NEAR(float, true, true); else RB_NEAR(float, true, false); }
     else { if (energy) RB_NEAR(float, false, true); else RB_NEAR(float, false, false); }
@@ -713,6 +787,151 @@ void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
     else { if (energy) RB_NEAR(double, false, true); else RB_NEAR(double, false, false); }
   }
 #undef RB_NEAR
+}
+
+void launch_build_lists(const View &v, cudaStream_t st) {
+  const dim3 g(v.nblk_near), b(NEAR_BLOCK);
+  if (v.wrap) k_near<float, true, false, true><<<g, b, 0, st>>>(v, 0);
+  else k_near<float, false, false, true><<<g, b, 0, st>>>(v, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Near field with kept lists (Sec. 2.2 over the lists of the last build):
+// one warp per run of NEAR_CHUNK consecutive slots of that build, TPA threads
+// per atom.  A is summed exactly; B by Floyd's P_R of |B| (Philox stream 0,
+// as the per-step batch) with weight |B| / P_R, or whole with weight 1 when
+// |B| <= P_R; every term carries the indicator r < r_shell, the FP32 list
+// predicate on the current minimum-image 23-bit differences.
+
+// the list predicate between two current fixed-point positions
+__device__ __forceinline__ bool in_shell(const View &p, uint4 ui, uint4 uj) {
+  return pred_r2((float)wrap23(uj.x, ui.x), (float)wrap23(uj.y, ui.y), (float)wrap23(uj.z, ui.z), p.hp) <
+         p.rs2f;
+}
+
+template <typename R, bool ENERGY>
+__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
+  __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
+  __shared__ uint32_t bmask[APB][RBSOG_MAX_KEPT / 32 + 1];
+  const PairF *spf = p.pf;
+  const PairD *spd = p.pd;
+  const float4 *sg4 = p.gtab;
+  const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int a = warp * APW + lane / TPA, g = lane % TPA;
+  const long long s = *p.step + step_off;
+  const int nslot = p.cell_start[p.ncell];
+  const int slot = (blockIdx.x * NEAR_WARPS + warp) * APW + lane / TPA;
+  const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const bool active = ui.w != SU_PAD;
+  const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
+  const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  Acc<R> fa, fb;
+  // ---- A, exactly, dealt round-robin over the atom's threads ---------------
+  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
+  for (int e0 = g; e0 < nab.x; e0 += 4 * TPA) {
+    int js[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) js[i] = (e0 + TPA * i < nab.x) ? la[e0 + TPA * i] : -1;
+    uint4 uj[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if (js[i] >= 0 && in_shell(p, ui, uj[i])) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fa);
+  }
+  // ---- Floyd's P_R of |B|: Philox words in parallel, resolved in order -----
+  const int nB = nab.y, PR = p.P_R;
+  const bool sampled = active && !p.whole_shell && nB > PR;
+  if (sampled) {
+    for (int w = g; w < ((nB + 31) >> 5); w += TPA) bmask[a][w] = 0u;
+    const uint32_t id = ui.w & SU_ID_MASK;
+    for (int d = g; 2 * d < PR; d += TPA) {     // Philox word d serves samples 2d, 2d + 1
+      const uint4 w4 = draw(p.seed, s, id, 0u, (uint32_t)d);
+      const unsigned long long U0 = ((unsigned long long)w4.y << 32) | w4.x;
+      const unsigned long long U1 = ((unsigned long long)w4.w << 32) | w4.z;
+      const int r0 = 2 * d;
+      stsel[a][r0] = (unsigned short)__umul64hi(U0, (unsigned long long)(nB - PR + r0) + 1ull);
+      if (r0 + 1 < PR)
+        stsel[a][r0 + 1] = (unsigned short)__umul64hi(U1, (unsigned long long)(nB - PR + r0 + 1) + 1ull);
+    }
+  }
+  __syncwarp();
+  if (sampled && g == 0) {
+    uint32_t *bm = bmask[a];
+    for (int r = 0; r < PR; r++) {
+      uint32_t t = stsel[a][r];
+      if ((bm[t >> 5] >> (t & 31)) & 1u) t = (uint32_t)(nB - PR + r);
+      bm[t >> 5] |= 1u << (t & 31);
+      stsel[a][r] = (unsigned short)t;
+    }
+  }
+  __syncwarp();
+  // ---- the batch of B (or all of it) ---------------------------------------
+  const R wgt = sampled ? (R)nB / (R)PR : (R)1;
+  const int *lb = p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
+  const int nb = sampled ? PR : nB;
+  for (int k0 = g; k0 < nb; k0 += 4 * TPA) {
+    int js[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int k = k0 + TPA * i;
+      js[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+    }
+    uint4 uj[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if (js[i] >= 0 && in_shell(p, ui, uj[i])) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fb);
+  }
+  combine_atom<R, ENERGY>(p, fa, fb, wgt, active, g, ui, part);
+  warp_partials<sizeof(R) == 4>(p, part, warp, lane);
+}
+
+void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy) {
+  const dim3 g(v.nblk_near), b(NEAR_BLOCK);
+  if (v.prec == RBSOG_MIXED) {
+    if (energy) k_near_kept<float, true><<<g, b, 0, st>>>(v, step_off);
+    else k_near_kept<float, false><<<g, b, 0, st>>>(v, step_off);
+  } else {
+    if (energy) k_near_kept<double, true><<<g, b, 0, st>>>(v, step_off);
+    else k_near_kept<double, false><<<g, b, 0, st>>>(v, step_off);
+  }
+}
+
+// Parity hook: the kept lists of selected atoms (caller ids, canonical order)
+// and the batch the current step draws from B (same Floyd routine).
+__global__ void k_kept_lists(View p, int step_off, const long long *sel, int nsel, int cap_a, int cap_b,
+                             int *A, int *nA, int *B, int *nB, int *batch, int *nbatch, double *weight) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsel) return;
+  const long long s = *p.step + step_off;
+  const int slot = p.slot_of[sel[q]];
+  const int2 nab = p.nAB[slot];
+  const int *la = p.lA + (int64_t)slot * RBSOG_MAX_CORE;
+  const int *lb = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
+  for (int k = 0; k < nab.x && k < cap_a; k++) A[(long long)q * cap_a + k] = p.perm[la[k]];
+  for (int k = 0; k < nab.y && k < cap_b; k++) B[(long long)q * cap_b + k] = p.perm[lb[k]];
+  nA[q] = nab.x;
+  nB[q] = nab.y;
+  if (batch) {
+    const bool take_all = p.whole_shell || nab.y <= p.P_R;
+    int t[RBSOG_MAX_PR];
+    const int m = take_all ? nab.y : p.P_R;
+    if (!take_all) floyd(p, s, sel[q], nab.y, t);
+    for (int k = 0; k < m && k < p.P_R; k++) batch[(long long)q * p.P_R + k] = p.perm[lb[take_all ? k : t[k]]];
+    nbatch[q] = m;
+    weight[q] = take_all ? 1.0 : (double)nab.y / (double)p.P_R;
+  }
+}
+
+void launch_kept_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
+                       int cap_a, int cap_b, int *A, int *nA, int *B, int *nB, int *batch, int *nbatch,
+                       double *weight) {
+  const int b = 64, g = (nsel + b - 1) / b;
+  k_kept_lists<<<g, b, 0, st>>>(v, step_off, sel, nsel, cap_a, cap_b, A, nA, B, nB, batch, nbatch, weight);
 }
 
 // ---------------------------------------------------------------------------

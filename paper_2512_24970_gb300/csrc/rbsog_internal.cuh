@@ -38,6 +38,8 @@ constexpr int CELL_ALIGN = 4;              // cell ranges are rounded up to this
 constexpr int ERR_CORE_CAP = 1;
 constexpr int ERR_CELL_SHELL_CAP = 2;
 constexpr int ERR_PR_CAP = 4;
+constexpr int ERR_SKIN = 8;       // kept lists: an atom moved by more than skin/2
+constexpr int ERR_KEPT_CAP = 16;  // kept lists: |A| > RBSOG_MAX_CORE or |B| > RBSOG_MAX_KEPT
 
 // Pair record, mixed precision: force phi(r) r_ij with
 //   phi = kqq (1/r^3 - G(r^2)) + Ar/r * 2^((sig - r) lr) - (C6 + D8/r^2)/r^8
@@ -67,6 +69,14 @@ struct View {
   double hd[3];           // L * 2^-32
   double kunit[3];        // 2 pi / L
   float rc2f, rs2f;
+  // kept (skin) lists: kept = list_every >= 1; build = this evaluation builds
+  // them (the step graph has a build and a keep variant)
+  int kept, build;
+  float rl2f;             // fl32((r_shell + skin)^2), outer radius of a build
+  double half_skin2;      // (skin / 2)^2, shaded down: the displacement limit
+  int *lA, *lB;           // [nslot][RBSOG_MAX_CORE], [nslot][RBSOG_MAX_KEPT] member slots
+  int2 *nAB;              // [nslot] (|A|, |B|) of each slot
+  double *xb;             // [3][n] positions at the last build
   int nc[3], ncell, small;
   int wrap;               // near field reduces differences to the minimum image (short box)
   float tscale;           // NT_TAB / r_shell^2
@@ -344,6 +354,11 @@ void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off);
 void launch_ksample(const View &v, cudaStream_t st, int step_off);
 void launch_bin(const View &v, cudaStream_t st);
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
+void launch_build_lists(const View &v, cudaStream_t st);
+void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy);
+void launch_kept_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
+                       int cap_a, int cap_b, int *A, int *nA, int *B, int *nB, int *batch, int *nbatch,
+                       double *weight);
 void launch_rho(const View &v, cudaStream_t st);
 void launch_rhosum(const View &v, cudaStream_t st, bool energy);
 void launch_corr(const View &v, cudaStream_t st, int step_off);

@@ -178,8 +178,8 @@ void sog_tables(const SogParams &sog, double rs2, int nt, std::vector<float> &gt
   }
 }
 
-int cell_count(double L, double r_shell) {
-  const double w = 0.5 * r_shell * (1.0 + 1.0 / 4096.0);
+int cell_count(double L, double r_out) {
+  const double w = 0.5 * r_out * (1.0 + 1.0 / 4096.0);
   const int c = (int)std::floor(L / w);
   return c < 1 ? 1 : c;
 }

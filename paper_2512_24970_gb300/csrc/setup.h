@@ -29,7 +29,8 @@ int sog_solve(double b, int M, double rc, SogParams &out);
 void sampler_build(const SogParams &sog, const double L[3], Sampler &T);
 void sog_tables(const SogParams &sog, double rs2, int nt, std::vector<float> &gt,
                 std::vector<float> &ft);
-// Cells per axis: max(1, floor(L / (r_shell/2 (1 + 2^-12)))).
-int cell_count(double L, double r_shell);
+// Cells per axis: max(1, floor(L / (r_out/2 (1 + 2^-12)))), r_out the outer
+// list radius (r_shell, or r_shell + skin for kept lists).
+int cell_count(double L, double r_out);
 
 }  // namespace rb

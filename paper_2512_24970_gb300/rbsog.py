@@ -28,13 +28,15 @@ MAX_PR = 64
 ERRORS = {
     -1: "RBSOG_E_INVAL", -2: "RBSOG_E_NONNEUTRAL", -3: "RBSOG_E_BOX_TOO_SMALL",
     -4: "RBSOG_E_CAP_OVERFLOW", -5: "RBSOG_E_CUDA", -6: "RBSOG_E_TIMEOUT",
-    -7: "RBSOG_E_NO_SOG_ROOT", -8: "RBSOG_E_NO_SYSTEM",
+    -7: "RBSOG_E_NO_SOG_ROOT", -8: "RBSOG_E_NO_SYSTEM", -9: "RBSOG_E_SKIN",
 }
+MAX_CORE = 64
+MAX_KEPT = 512
 
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -61,6 +63,7 @@ class Params(ctypes.Structure):
         ("P_R", ctypes.c_int32), ("P_F", ctypes.c_int32), ("seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
         ("dt", ctypes.c_double), ("T", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("list_every", ctypes.c_int32), ("skin", ctypes.c_double),
     ]
 
 
@@ -80,6 +83,8 @@ class MethodParams:
     dt: float = 0.001
     T: float = 1200.0
     gamma: float = 1.0
+    list_every: int = 0     # 0: per-step lists; n >= 1: kept lists rebuilt every n steps
+    skin: float = 0.0       # Verlet skin of kept lists [A]
 
     def c(self):
         p = Params()
@@ -119,6 +124,7 @@ def load():
     L.rbsog_sync.argtypes = [P]
     L.rbsog_get_sog.argtypes = [P, P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
+    L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kbatch.argtypes = [P, P, P]
     L.rbsog_debug_set_kbatch.argtypes = [P, I32, P, P]
     L.rbsog_debug_get_parts.argtypes = [P, P, P, P, P]
@@ -284,6 +290,25 @@ class Context:
                                                _np_ptr(ncore), _np_ptr(shell), _np_ptr(nshell), _np_ptr(bt),
                                                _np_ptr(nb), _np_ptr(wt)))
         out = dict(core=core, ncore=ncore, shell=shell, nshell=nshell)
+        if batch:
+            out.update(batch=bt, nbatch=nb, weight=wt)
+        return out
+
+    def debug_kept_lists(self, sel, cap_a=MAX_CORE, cap_b=MAX_KEPT, batch=True):
+        """Kept lists A, B (caller ids, canonical order of the build) and the batch of ``sel``."""
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        k = sel.size
+        A = np.full((k, cap_a), -1, dtype=np.int32)
+        nA = np.zeros(k, dtype=np.int32)
+        B = np.full((k, cap_b), -1, dtype=np.int32)
+        nB = np.zeros(k, dtype=np.int32)
+        PR = self.params.P_R
+        bt = np.full((k, PR), -1, dtype=np.int32) if batch else None
+        nb = np.zeros(k, dtype=np.int32) if batch else None
+        wt = np.zeros(k) if batch else None
+        self._ck(self._L.rbsog_debug_get_kept_lists(self.h, _np_ptr(sel), k, cap_a, cap_b, _np_ptr(A), _np_ptr(nA),
+                                                    _np_ptr(B), _np_ptr(nB), _np_ptr(bt), _np_ptr(nb), _np_ptr(wt)))
+        out = dict(A=A, nA=nA, B=B, nB=nB)
         if batch:
             out.update(batch=bt, nbatch=nb, weight=wt)
         return out

@@ -1,0 +1,162 @@
+"""GPU parity of the kept (Verlet-skin) random batch lists against the oracle.
+
+Bars as for the per-step lists: kept lists A / B and the shell batches drawn
+from them bit-exact; FP64 forces and trajectories within 1e-12 / 1e-10; mixed
+precision within 1e-5 RMS relative force error.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_24970_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_24970_gb300 import rbsog
+    rbsog.load()
+    return rbsog
+
+
+def rms_rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b**2).sum()))
+
+
+def setup_kept(rb, orc, w, *, skin=1.0, list_every=5, P_R=20, P_F=200, precision=None, seed=3, step=0,
+               integrator=None):
+    S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=P_R, P_F=P_F, seed=seed, step=step,
+                   skin=skin, list_every=list_every)
+    prm = rb.MethodParams(s=S.s, w0=float(S.w[0]), P_R=P_R, P_F=P_F, seed=seed,
+                          precision=rb.FP64 if precision is None else precision,
+                          integrator=rb.LANGEVIN_BAOAB if integrator is None else integrator,
+                          list_every=list_every, skin=skin)
+    ctx = rb.Context(0)
+    ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
+    if step:
+        ctx.set_state(w.pos, np.zeros_like(w.pos), step)
+    return ctx, S
+
+
+CASES = {
+    "nacl_1k": lambda: W.rock_salt((5, 5, 5), seed=1),                          # 4 cells per axis: small box
+    "ragged": lambda: W.rock_salt((6, 5, 7), seed=3, composition="LiCl-NaCl"),  # 3 species, orthorhombic
+    "six_cells": lambda: W.rock_salt((6, 6, 6), seed=4, composition="LiCl"),    # 5 cells: whole rows
+    "nacl_5832": lambda: W.rock_salt((9, 9, 9), seed=5),                        # 8 cells: culled rows
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_kept_lists_and_batches_bitexact(rb, orc, case):
+    w = CASES[case]()
+    ctx, S = setup_kept(rb, orc, w, step=5)
+    ctx.compute_forces()
+    sel = np.arange(w.n)
+    g = ctx.debug_kept_lists(sel, cap_a=64, cap_b=512)
+    o = S.lists_skin(sel, cap_a=64, cap_b=512)
+    for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+
+
+def test_kept_skin_zero_is_per_step_path(rb, orc):
+    """list_every = 1, skin = 0: every evaluation builds, and the kept path
+    gives the per-step path's forces (summation order aside)."""
+    w = W.rock_salt((6, 5, 7), seed=3, composition="LiCl-NaCl")
+    ctx, S = setup_kept(rb, orc, w, skin=0.0, list_every=1, step=2)
+    Fk, Ek = ctx.compute_forces(energy=True)
+    prm = ctx.params
+    ref = rb.Context(0)
+    ref.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box,
+                   rb.MethodParams(**{**prm.__dict__, "list_every": 0, "skin": 0.0}))
+    ref.set_state(w.pos, np.zeros_like(w.pos), 2)
+    Fr, Er = ref.compute_forces(energy=True)
+    assert rms_rel(Fk, Fr) < 1e-14
+    np.testing.assert_allclose(Ek, Er, rtol=1e-13)
+
+
+@pytest.mark.parametrize("integ", ["nve", "langevin"])
+def test_kept_fp64_trajectory(rb, orc, integ):
+    """10 steps with builds at steps 0, 4, 8 and the kept lists in between:
+    GPU FP64 against the oracle's kept-list run."""
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ig = rb.NVE_VV if integ == "nve" else rb.LANGEVIN_BAOAB
+    ctx, S = setup_kept(rb, orc, w, list_every=4, P_F=100, integrator=ig)
+    ctx.set_velocities(v0)
+    ctx.step(10)
+    pos, vel, step = ctx.get_state()
+    vo, Fo = S.run(v0, 10, 0.001, integrator=0 if integ == "nve" else 1, T=1200.0, gamma=1.0)
+    assert step == 10 and S.step == 10
+    assert np.sqrt(((pos - S.pos) ** 2).mean()) < 1e-10
+    assert rms_rel(vel, vo) < 1e-10
+    g = ctx.debug_kept_lists(np.arange(w.n))
+    o = S.lists_skin(np.arange(w.n), cap_a=64, cap_b=512)
+    for k in ("nA", "nB", "A", "B", "batch"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+
+
+def test_kept_mixed_forces_between_builds(rb, orc):
+    """Mixed precision, evaluated from the kept lists three steps after the
+    build, against the oracle at the GPU's own positions."""
+    w = W.rock_salt((9, 9, 9), seed=5)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, S = setup_kept(rb, orc, w, list_every=10, P_F=300, precision=rb.MIXED)
+    ctx.set_velocities(v0)
+    ctx.step(3)
+    pos, vel, step = ctx.get_state()
+    Fg, Eg = ctx.compute_forces(energy=True)
+    S.build_pos = w.pos.copy()
+    S.pos = pos
+    S.step = step
+    o = S.forces(energy=True)
+    assert rms_rel(Fg, o["F"]) < MIXED_TOL
+    np.testing.assert_allclose(Eg[3], o["energy"][3], rtol=1e-5)
+
+
+def test_kept_skin_exceeded_is_reported(rb, orc):
+    """A skin far too thin for the motion: the step reports RBSOG_E_SKIN."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, _ = setup_kept(rb, orc, w, skin=1e-4, list_every=100, precision=rb.MIXED)
+    ctx.set_velocities(v0)
+    ctx.step(5)
+    with pytest.raises(rb.RbsogError) as e:
+        ctx.sync()
+    assert e.value.code == -9
+    # too small a box for r_shell + skin
+    with pytest.raises(rb.RbsogError) as e:
+        setup_kept(rb, orc, w, skin=4.0)
+    assert e.value.code == -3
+
+
+@pytest.mark.parametrize("key", ["nacl_64k", "liclnacl_216k"])
+def test_kept_full_size_sampled(rb, orc, key):
+    """Full-size workloads with kept lists (skin 1 A, rebuilt every 10 steps):
+    lists and batches of sampled atoms bit-exact at the build and five steps
+    later; mixed near field of the sample within 1e-5 of the oracle's."""
+    w, cfg = W.make(key)
+    ctx, S = setup_kept(rb, orc, w, list_every=10, P_R=cfg.P_R, P_F=cfg.P_F, precision=rb.MIXED, seed=cfg.seed,
+                        step=3)
+    ctx.set_velocities(W.maxwell_boltzmann(w, 1200.0))
+    ctx.compute_forces()
+    sel = np.linspace(0, w.n - 1, 96).astype(np.int64)
+    g = ctx.debug_kept_lists(sel)
+    o = S.lists_skin(sel, cap_a=64, cap_b=512)
+    for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    ctx.step(5)
+    pos, _, step = ctx.get_state()
+    assert step == 8
+    parts = ctx.debug_parts()
+    S.pos, S.step = pos, step
+    g = ctx.debug_kept_lists(sel)
+    o = S.lists_skin(sel, cap_a=64, cap_b=512)
+    for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL

@@ -42,6 +42,7 @@ struct rbsog_ctx {
   bool own_stream = false;
   bool profiling = false;
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
+  cudaStream_t st2_hi = nullptr;                // the same at the device's greatest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[9] = {};  // stage boundaries, see rbsog_get_stage_times
 };
@@ -115,7 +116,9 @@ int check_launch(rbsog_ctx *ctx) {
 // lists, v.build selects binning + list build + evaluation, else the
 // evaluation of the last build's lists alone.
 int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
-  cudaStream_t st = ctx->st, st2 = ctx->st2;
+  // with kept lists the far-field branch is the longer one: its kernels take
+  // free SM slots first (priorities are kept as node priorities in the graph)
+  cudaStream_t st = ctx->st, st2 = v.kept ? ctx->st2_hi : ctx->st2;
   const bool pr = ctx->profiling;
   // inside stream capture the stage events must become event-record nodes
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -263,6 +266,9 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
   for (int k = 0; k < 9 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
+  int prio_least = 0, prio_greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->st2_hi, cudaStreamNonBlocking, prio_greatest);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork0, cudaEventDisableTiming);
@@ -279,6 +285,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   cudaSetDevice(ctx->dev);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   if (ctx->st2) cudaStreamSynchronize(ctx->st2);
+  if (ctx->st2_hi) cudaStreamSynchronize(ctx->st2_hi);
   free_system(ctx);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -288,6 +295,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_fork0) cudaEventDestroy(ctx->ev_fork0);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
+  if (ctx->st2_hi) cudaStreamDestroy(ctx->st2_hi);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
 }
@@ -615,7 +623,7 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
       cudaGraphExec_t &ge = var == 0 ? ctx->gexec : ctx->gexec_keep;
       if (ge) cudaGraphExecDestroy(ge);
       ge = nullptr;
-      e = cudaGraphInstantiate(&ge, g, 0);
+      e = cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }

@@ -168,7 +168,10 @@ class System:
     current positions at every evaluation (Sec. 2.2).  ``list_every = n >= 1``:
     kept lists with outer radius r_shell + ``skin``, built at the first
     evaluation, at every step that is a multiple of n, and after
-    :meth:`invalidate_lists` (see ``orc_near_skin``).
+    :meth:`invalidate_lists` (see ``orc_near_skin``).  ``list_every = -1``:
+    kept lists rebuilt at every step where some atom has moved by more than
+    skin/2 since the last build (the displacement limit under which the kept
+    lists still hold every pair inside r_shell).
     """
 
     def __init__(self, pos, species, charge, mass, bmh, box, *, b=1.3, M=64, s=None, w=None,
@@ -191,10 +194,16 @@ class System:
         self.seed, self.step = int(seed), int(step)
         self.skin, self.list_every = float(skin), int(list_every)
         self.build_pos = None   # positions the kept lists were built from
+        self.builds = 0         # automatic rebuilds (list_every = -1) during run()
 
     @property
     def kept_lists(self):
-        return self.list_every > 0
+        return self.list_every != 0
+
+    def displacement_limit2(self):
+        """(skin/2)^2, shaded by 2^-10 so that the FP32 list predicate's
+        rounding stays inside the margin."""
+        return 0.25 * self.skin * self.skin * (1.0 - 1.0 / 1024.0)
 
     def invalidate_lists(self):
         """The next evaluation builds the kept lists from the positions it sees."""
@@ -447,8 +456,14 @@ class System:
             else:
                 self.pos = self.pos + dt * vel
             self.step = nxt
-            if self.kept_lists and nxt % self.list_every == 0:
+            if self.list_every > 0 and nxt % self.list_every == 0:
                 self.build_pos = self.pos.copy()
+            elif self.list_every < 0 and self.build_pos is not None:
+                d = self.pos - self.build_pos
+                d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+                if d2.max() > self.displacement_limit2():
+                    self.build_pos = self.pos.copy()
+                    self.builds += 1
             F = self.forces()["F"]
             vel = vel + 0.5 * dt * F * minv
         return vel, F

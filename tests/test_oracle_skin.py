@@ -158,3 +158,22 @@ def test_skin_run_follows_per_step_whole_shell_run(orc):
     T = make(orc, w, skin=1.0, list_every=3, **kw)
     T.run(v0, 6, 0.001, integrator=0)
     np.testing.assert_array_equal(S.build_pos, T.pos)
+
+
+def test_auto_rebuild_keeps_every_cutoff_pair(orc):
+    """list_every = -1: lists rebuilt whenever an atom has moved by more than
+    skin/2; with the whole of B taken, a run follows the per-step whole-shell
+    run through several automatic rebuilds."""
+    w = W.rock_salt((5, 5, 5), seed=16)
+    v0 = W.maxwell_boltzmann(w, 3000.0)
+    kw = dict(P_R=4000, P_F=50, seed=2)
+    S = make(orc, w, skin=0.12, list_every=-1, **kw)
+    R = make(orc, w, **kw)
+    vS, FS = S.run(v0, 12, 0.001, integrator=0)
+    vR, FR = R.run(v0, 12, 0.001, integrator=0)
+    assert S.builds >= 2, S.builds
+    np.testing.assert_allclose(S.pos, R.pos, rtol=0, atol=1e-11)
+    assert np.abs(FS - FR).max() < 1e-11 * np.abs(FR).max()
+    # and the displacement since the last build is within the limit
+    d2 = ((S.pos - S.build_pos) ** 2).sum(1)
+    assert d2.max() <= S.displacement_limit2()

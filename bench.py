@@ -44,9 +44,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--P_F", type=int, default=None)
     ap.add_argument("--P_R", type=int, default=None)
-    ap.add_argument("--list-every", type=int, default=0,
-                    help="0: per-step random batch lists; n >= 1: kept (skin) lists rebuilt every n steps")
-    ap.add_argument("--skin", type=float, default=1.0, help="skin of kept lists [A]")
+    ap.add_argument("--list-every", type=int, default=None,
+                    help="0: per-step random batch lists; n >= 1: kept (skin) lists rebuilt every n steps; "
+                         "-1: rebuilt when an atom has moved by skin/2 (default: the workload's, -1)")
+    ap.add_argument("--skin", type=float, default=None, help="skin of kept lists [A] (default: the workload's)")
+    ap.add_argument("--no-per-step-lists", action="store_true",
+                    help="skip the second measurement with lists rebuilt at every step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
@@ -83,9 +86,15 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def pause(self):
+        """End of the timed region: later samples are not used."""
+        self.n_keep = len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return None
+        if getattr(self, "n_keep", None) is not None:
+            self.lines = self.lines[:self.n_keep]
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -126,7 +135,7 @@ KERNELS_PER_STEP = 12
 # that reuses the lists has no binning (4 kernels) and no build
 KERNELS_BUILD_STEP = 13
 KERNELS_KEEP_STEP = 8
-KERNEL_LABEL = {"near": "k_near", "far": "k_rho + k_farforce (side stream)"}
+KERNEL_LABEL = {"near": "k_near", "rho": "k_rho", "farforce": "k_farforce"}
 
 
 def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0, list_every=0, skin=0.0):
@@ -141,21 +150,21 @@ def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0, list_every=0, skin=0.
     tests = 4.0 / 3.0 * np.pi * r_list ** 3 * rho_n / max(list_every, 1)
     n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
     return {"near": w.n * (8.0 * tests + 25.0 * (n_core + P_R)),
-            "far": (15.0 + 21.0) * w.n * P_F}
+            "rho": 15.0 * w.n * P_F, "farforce": 21.0 * w.n * P_F}
 
 
 def profiled_traffic(stage):
     """DRAM bytes per launch of the stage's kernel from the committed ncu summary,
     only while the kernel source is the one that was profiled (else None)."""
     import hashlib
-    src = {"near": "k_near.cu", "far": "k_far.cu"}.get(stage)
+    src = {"near": "k_near.cu", "rho": "k_far.cu", "farforce": "k_far.cu"}.get(stage)
     summ = os.path.join(ROOT, "profiles", "traffic_nacl64k.txt")
     if src is None or not os.path.exists(summ):
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_24970_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
     for line in open(summ):
         f = line.split()
-        if len(f) >= 3 and f[0] == "k_" + stage and f[1] == h:
+        if len(f) >= 3 and f[0] == KERNEL_LABEL[stage] and f[1] == h:
             return float(f[2])
     return None
 
@@ -273,64 +282,98 @@ def run_ours(args):
     P_F = args.P_F or cfg.P_F
     P_R = args.P_R or cfg.P_R
     prec = rbsog.MIXED if args.precision == "mixed" else rbsog.FP64
+    list_every = cfg.list_every if args.list_every is None else args.list_every
+    skin = (cfg.skin if args.skin is None else args.skin) if list_every != 0 else 0.0
     prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=replica_seed(cfg.seed, rank), precision=prec,
                              integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
-                             T=cfg.T, dt=0.001, gamma=1.0, list_every=args.list_every,
-                             skin=args.skin if args.list_every > 0 else 0.0)
+                             T=cfg.T, dt=0.001, gamma=1.0, list_every=list_every, skin=skin)
     stream = torch.cuda.Stream(device=dev)
-    ctx = rbsog.Context(local, stream.cuda_stream)
-    ctx.set_workload(w, prm)
-    ctx.set_profiling(True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K, Wm = args.steps, args.warmup
-    with torch.cuda.stream(stream):
-        for _ in range(Wm):
-            flush.zero_()
-            ctx.step(1)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        clocks = Clocks(local)
-        clocks.start()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        stage = np.zeros(rbsog.NSTAGE)
-        torch.cuda.synchronize()
-        for k in range(K):
-            flush.zero_()
-            ev[k][0].record(stream)
-            ctx.step(1)
-            ev[k][1].record(stream)
-            stage += ctx.stage_times()          # waits for this step's last event
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        clk = clocks.stop()
-    ms = np.array([a.elapsed_time(b) for a, b in ev])
-    ctx.sync()
+
+    def timed_run(params, clocks=None, k_stage=None):
+        """Wm untimed steps, then K steps timed with CUDA events on the
+        launching stream (L2 flushed before each; no event inside the step
+        graph), then k_stage more steps with the stage events on (they add
+        event nodes to the graph, so they stay out of the timed steps).
+        Returns the context, the per-step ms and the mean stage times."""
+        c = rbsog.Context(local, stream.cuda_stream)
+        c.set_workload(w, params)
+        with torch.cuda.stream(stream):
+            for _ in range(Wm):
+                flush.zero_()
+                c.step(1)
+            torch.cuda.synchronize()
+            if ws > 1:
+                dist.barrier()
+            if clocks:
+                clocks.start()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            torch.cuda.synchronize()
+            for k in range(K):
+                flush.zero_()
+                ev[k][0].record(stream)
+                c.step(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if ws > 1:
+                dist.barrier()
+            if clocks:
+                clocks.pause()
+            ks = min(K, 500) if k_stage is None else k_stage
+            st = np.zeros(rbsog.NSTAGE)
+            c.set_profiling(True)
+            for k in range(ks):
+                flush.zero_()
+                c.step(1)
+                st += c.stage_times()          # waits for this step's last event
+            c.set_profiling(False)
+        c.sync()
+        return c, np.array([a.elapsed_time(b) for a, b in ev]), st / max(ks, 1)
+
+    clocks = Clocks(local)
+    ctx, ms, stage_ms = timed_run(prm, clocks)
+    clk = clocks.stop()
+    n_builds = ctx.list_builds()
+    n_steps_all = Wm + K + min(K, 500) + 1
     value, t_total, _ = aggregate(float(ms.sum()), float(w.n * K), dist if ws > 1 else None, dev)
-    stage_ms = stage / K
+    # the same steps with the random batch lists rebuilt from scratch at every step
+    per_step = None
+    if list_every != 0 and not args.no_per_step_lists:
+        import dataclasses
+        c1, ms1, st1 = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
+        c1.close()
+        v1, t1, _ = aggregate(float(ms1.sum()), float(w.n * K), dist if ws > 1 else None, dev)
+        per_step = {"value": v1, "unit": "atom-steps/s", "ms_per_step": t1 / K,
+                    "stage_ms": {n: float(t) for n, t in zip(rbsog.STAGES, st1)},
+                    "what": "same workload and steps, random batch lists rebuilt from the positions at every step"}
     # ---- roofline of the dominant kernel -------------------------------------
     pk, pk_kind = peaks()
     props = torch.cuda.get_device_properties(dev)
     nsm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    alg = algorithmic_ops(w, P_F, P_R, list_every=args.list_every, skin=prm.skin)
-    # the dominant kernel: the near field, the longest stage of the critical path
-    # (the far-field branch runs concurrently on a side stream; its wall time
-    # there is shared with the near field, so it gets its own line below)
-    dom = names.index("near")
+    alg = algorithmic_ops(w, P_F, P_R, list_every=list_every, skin=skin)
     peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
-    achieved = alg[names[dom]] / (stage_ms[dom] * 1e-3)
-    roof = {"bound": "alu",
-            "kernel": KERNEL_LABEL[names[dom]] if not args.list_every else "k_near_kept + k_near (list build, amortised)", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-            "unit": "Glane-op/s", "frac": achieved / peak_ops,
-            "traffic": profiled_traffic(names[dom]) if not args.list_every else None,
+    label = dict(KERNEL_LABEL)
+    if list_every != 0:
+        label["near"] = "k_near_kept (+ list builds by k_near, amortised)"
+    # every hot kernel against the issue peak, from its own live events (the
+    # near field on the main stream, k_rho and k_farforce on the side stream,
+    # running concurrently, so a live duration includes time spent sharing
+    # the SMs).  The dominant kernel is the one with the largest share of the
+    # serialised launch list: k_near with per-step lists, k_farforce with kept
+    # lists (whose branch also runs at the greater stream priority)
+    kern = {}
+    for kname in ("near", "rho", "farforce"):
+        t = stage_ms[names.index(kname)] * 1e-3
+        kern[kname] = {"kernel": label[kname], "ms": t * 1e3, "achieved": alg[kname] / t / 1e9,
+                       "frac": alg[kname] / t / peak_ops}
+    dom = "farforce" if list_every != 0 else "near"
+    roof = {"bound": "alu", "kernel": label[dom], "achieved": kern[dom]["achieved"], "peak": peak_ops / 1e9,
+            "unit": "Glane-op/s", "frac": kern[dom]["frac"],
+            "traffic": profiled_traffic(dom) if not (dom == "near" and list_every != 0) else None,
             "peak_source": "4 warp-instructions/clk/SM x 32 lanes x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
-    fi = names.index("far")
-    far_roof = {"kernels": KERNEL_LABEL["far"], "achieved": alg["far"] / (stage_ms[fi] * 1e-3) / 1e9,
-                "unit": "Glane-op/s", "frac": alg["far"] / (stage_ms[fi] * 1e-3) / peak_ops,
-                "note": "wall time of the side-stream branch, concurrent with the near field"}
     step_ops = sum(alg.values())
     step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / peak_ops * 1e6,
                  "frac": (step_ops / peak_ops) / (t_total / K * 1e-3)}
@@ -369,8 +412,10 @@ def run_ours(args):
         v, wall, sample = oracle_sample(w, cfg, P_F, P_R)
         cpu = {"value": v, "unit": "atom-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": sample, "wall_s": wall}
-    if args.list_every:
-        builds = sum(1 for s in range(Wm + 1, Wm + K + 1) if s % args.list_every == 0)
+    if list_every < 0:
+        launches = KERNELS_BUILD_STEP * K        # the binning and build kernels return at once when not needed
+    elif list_every > 0:
+        builds = sum(1 for s in range(Wm + 1, Wm + K + 1) if s % list_every == 0)
         launches = KERNELS_BUILD_STEP * builds + KERNELS_KEEP_STEP * (K - builds)
     else:
         launches = KERNELS_PER_STEP * K
@@ -382,11 +427,13 @@ def run_ours(args):
             "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
             "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
-                       "lists": ("per step" if not args.list_every else
-                                 "kept: skin %.2f A, rebuilt every %d steps" % (prm.skin, args.list_every)),
+                       "lists": ("per step" if not list_every else
+                                 ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in "
+                                  "%d steps)" % (skin, n_builds, n_steps_all)) if list_every < 0 else
+                                 "kept: skin %.2f A, rebuilt every %d steps" % (skin, list_every)),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
-            "roofline": roof, "far_roofline": far_roof, "step_roofline": step_roof, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "kernel_rooflines": kern, "step_roofline": step_roof, "per_step_lists": per_step, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "cpu_baseline": cpu, "force_error": ferr,
         }
         print(json.dumps(line), flush=True)

@@ -63,6 +63,8 @@ extern "C" {
 #define RBSOG_NVE_VV 0          /* velocity Verlet */
 #define RBSOG_LANGEVIN_BAOAB 1  /* BAOAB splitting of the Langevin SDE of Sec. 2.3 */
 
+#define RBSOG_LISTS_AUTO (-1)  /* list_every: rebuild kept lists when an atom moved by skin/2 */
+
 #define RBSOG_PTR_HOST 0
 #define RBSOG_PTR_DEVICE 1
 
@@ -100,14 +102,16 @@ typedef struct {
    * from the current positions at every evaluation.  list_every = n >= 1:
    * kept lists, as with the paper's skin neighbour lists (Sec. 3): built from
    * the positions of the first evaluation after set_system / set_state and of
-   * every step that is a multiple of n, with the outer radius
+   * every step that is a multiple of n (RBSOG_LISTS_AUTO: of every step where
+   * some atom has moved by more than skin/2 since the last build, checked on
+   * the device every step), with the outer radius
    * r_list = r_shell + skin; A = {r < r_core}, B = {r_core <= r < r_list} at
    * those positions.  Each evaluation sums A exactly and a Floyd batch of P_R
    * of B with weight |B| / P_R; every term carries the indicator
    * r < r_shell at the current positions, so the estimator stays unbiased for
    * the r_shell-cutoff force while no atom moves by skin/2 between builds
-   * (checked every step: RBSOG_E_SKIN).  Needs every box length
-   * >= 2 r_list. */
+   * (checked every step: RBSOG_E_SKIN with a fixed n).  Needs every box
+   * length >= 2 r_list. */
   int32_t list_every;
   double skin;     /* [A], >= 0; used when list_every >= 1 */
 } rbsog_params;
@@ -174,6 +178,10 @@ int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int
  * run(2n) bit for bit. */
 int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_t step,
                     int ptr_kind);
+
+/* Builds of the kept random batch lists since rbsog_set_system (waits for the
+ * context's work).  Host pointer. */
+int rbsog_get_list_builds(rbsog_ctx *ctx, int64_t *builds);
 
 /* Wait for the context's work; return the latched device error, if any. */
 int rbsog_sync(rbsog_ctx *ctx);
@@ -259,10 +267,12 @@ int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag);
 /* Stages timed by the profiling events.  The structure factor runs on a side
  * stream concurrently with binning and the near field, so stage times do not
  * add up to the total, which is reported last. */
-#define RBSOG_NSTAGE 7  /* integrator + fixed point + histograms; bin (row scan, cell
+#define RBSOG_NSTAGE 9  /* integrator + fixed point + histograms; bin (row scan, cell
                            prefix, scatter, rank); near field; far-field branch on the
                            side stream (k-batch, structure factor, its reduction, far
-                           force); F^corr; total force + closing kick; total */
+                           force); F^corr; total force + closing kick; total; inside the
+                           far-field branch: the structure-factor kernel alone, the
+                           far-force kernel alone */
 
 /* Record a CUDA event between consecutive stages of every force evaluation
  * (also inside the captured step graph, as event nodes) when on != 0. */

@@ -44,7 +44,7 @@ struct rbsog_ctx {
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
   cudaStream_t st2_hi = nullptr;                // the same at the device's greatest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
-  cudaEvent_t prof[9] = {};  // stage boundaries, see rbsog_get_stage_times
+  cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
 };
 
 namespace {
@@ -134,8 +134,11 @@ int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy
   CK(cudaEventRecord(ctx->ev_fork, st));
   CK(cudaStreamWaitEvent(st2, ctx->ev_fork, 0));
   // side branch: structure factor, its reduction, far-field force
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[9], st2, evflag));
   rb::launch_rho(v, st2);
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[10], st2, evflag));
   rb::launch_rhosum(v, st2, energy);
+  if (pr) CK(cudaEventRecordWithFlags(ctx->prof[11], st2, evflag));
   rb::launch_farforce(v, st2);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[4], st2, evflag));
   CK(cudaEventRecord(ctx->ev_join, st2));
@@ -158,21 +161,30 @@ int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy
   return check_launch(ctx);
 }
 
+// The view of a one-off evaluation: kept lists that are not valid are built
+// (automatic lists: by raising the device flag the binning kernels check).
+int eval_view(rbsog_ctx *ctx, View &vv) {
+  vv = ctx->v;
+  vv.build = (ctx->lists_valid && !ctx->v.auto_lists) ? 0 : 1;
+  if (ctx->v.auto_lists && !ctx->lists_valid) CK(cudaMemsetAsync(ctx->v.lflag, 0x01, sizeof(int), ctx->st));
+  return RBSOG_OK;
+}
+
 int read_err(rbsog_ctx *ctx) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, ctx->v.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (e) {
     CK(cudaMemsetAsync(ctx->v.err, 0, sizeof(int), ctx->st));
-    std::string m = "device capacity overflow:";
-    if (e & rb::ERR_CORE_CAP) m += " core list > RBSOG_MAX_CORE";
-    if (e & rb::ERR_CELL_SHELL_CAP) m += " stencil row > RBSOG_MAX_ROW_SLOTS slots or shell > RBSOG_MAX_SHELL";
-    if (e & rb::ERR_PR_CAP) m += " P_R";
-    if (e & rb::ERR_KEPT_CAP) m += " kept list: |A| > RBSOG_MAX_CORE or |B| > RBSOG_MAX_KEPT";
-    if (e & rb::ERR_SKIN)
-      return fail(ctx, RBSOG_E_SKIN, "kept lists: an atom moved by more than skin/2 since the last build "
-                                     "(rebuild more often or widen the skin)");
-    return fail(ctx, RBSOG_E_CAP_OVERFLOW, m);
+    std::string m;
+    if (e & rb::ERR_SKIN) m += " an atom moved by more than skin/2 since the last build of the kept lists "
+                               "(rebuild more often or widen the skin);";
+    if (e & rb::ERR_CORE_CAP) m += " core list > RBSOG_MAX_CORE;";
+    if (e & rb::ERR_CELL_SHELL_CAP) m += " stencil row > RBSOG_MAX_ROW_SLOTS slots or shell > RBSOG_MAX_SHELL;";
+    if (e & rb::ERR_PR_CAP) m += " P_R;";
+    if (e & rb::ERR_KEPT_CAP) m += " kept list: |A| > RBSOG_MAX_CORE or |B| > RBSOG_MAX_KEPT;";
+    const bool cap = (e & ~rb::ERR_SKIN) != 0;
+    return fail(ctx, cap ? RBSOG_E_CAP_OVERFLOW : RBSOG_E_SKIN, (cap ? "device capacity overflow:" : "kept lists:") + m);
   }
   return RBSOG_OK;
 }
@@ -264,7 +276,7 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
-  for (int k = 0; k < 9 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
+  for (int k = 0; k < 12 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
   int prio_least = 0, prio_greatest = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
@@ -289,7 +301,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   free_system(ctx);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
-  for (int k = 0; k < 9; k++)
+  for (int k = 0; k < 12; k++)
     if (ctx->prof[k]) cudaEventDestroy(ctx->prof[k]);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -323,9 +335,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   if (P.P_F < 1) return fail(ctx, RBSOG_E_INVAL, "P_F out of range");
   if (P.precision != RBSOG_FP64 && P.precision != RBSOG_MIXED) return fail(ctx, RBSOG_E_INVAL, "bad precision");
   if (P.integrator != RBSOG_NVE_VV && P.integrator != RBSOG_LANGEVIN_BAOAB) return fail(ctx, RBSOG_E_INVAL, "bad integrator");
-  if (P.list_every < 0) return fail(ctx, RBSOG_E_INVAL, "list_every must be >= 0");
-  if (P.list_every > 0 && !(P.skin >= 0.0)) return fail(ctx, RBSOG_E_INVAL, "skin must be >= 0");
-  const bool kept = P.list_every > 0;
+  if (P.list_every < RBSOG_LISTS_AUTO) return fail(ctx, RBSOG_E_INVAL, "list_every must be >= -1");
+  if (P.list_every != 0 && !(P.skin >= 0.0)) return fail(ctx, RBSOG_E_INVAL, "skin must be >= 0");
+  const bool kept = P.list_every != 0;
   const double r_list = P.r_shell + (kept ? P.skin : 0.0);  // outer radius of the lists
   std::vector<double> hb(3);
   int rc;
@@ -408,6 +420,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.rc2f = (float)(P.r_core * P.r_core);
   v.rs2f = (float)(P.r_shell * P.r_shell);
   v.kept = kept ? 1 : 0;
+  v.auto_lists = P.list_every == RBSOG_LISTS_AUTO ? 1 : 0;
   v.build = 0;
   v.rl2f = (float)(r_list * r_list);
   // an atom may move by skin/2 (pair distances by skin): shaded by 2^-10 so
@@ -474,8 +487,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     free_system(ctx);
     return rc;
   }
-  if (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
-               (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N)))) {
+  if ((rc = dalloc(ctx, &v.lflag, 1)) || (rc = dalloc(ctx, &v.nbuild, 1)) ||
+      (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
+                (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
     free_system(ctx);
     return rc;
   }
@@ -543,6 +557,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 8, ctx->st));
   CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(v.lflag, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(v.nbuild, 0, sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(v.slot_of, 0, sizeof(int) * N, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
   ctx->has_system = true;
   ctx->forces_valid = false;
@@ -569,8 +586,8 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
   if (virial) return fail(ctx, RBSOG_E_INVAL, "virial output is not provided");
   int rc;
   if ((rc = enter(ctx))) return rc;
-  View vv = ctx->v;
-  vv.build = ctx->lists_valid ? 0 : 1;
+  View vv;
+  if ((rc = eval_view(ctx, vv))) return rc;
   if ((rc = run_force(ctx, vv, 0, 0, energy != nullptr))) return rc;
   ctx->forces_valid = true;
   ctx->lists_valid = true;
@@ -601,8 +618,8 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
   int rc;
   if ((rc = enter(ctx))) return rc;
   if (!ctx->forces_valid) {
-    View vv = ctx->v;
-    vv.build = ctx->lists_valid ? 0 : 1;
+    View vv;
+    if ((rc = eval_view(ctx, vv))) return rc;
     if ((rc = run_force(ctx, vv, 0, 0, false))) return rc;
     ctx->forces_valid = true;
     ctx->lists_valid = true;
@@ -611,7 +628,7 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
     const int mode = ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 2;
     // variant 0 bins and builds (per-step lists: the only one); variant 1
     // evaluates the kept lists of the last build
-    for (int var = 0; var < (ctx->v.kept ? 2 : 1); var++) {
+    for (int var = 0; var < ((ctx->v.kept && !ctx->v.auto_lists) ? 2 : 1); var++) {
       View vs = ctx->v;
       vs.build = var == 0 ? 1 : 0;
       cudaGraph_t g = nullptr;
@@ -633,7 +650,7 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
   const int64_t every = ctx->prm.list_every;
   for (int64_t k = 0; k < nsteps; k++) {
     const int64_t next = ctx->host_step + 1;
-    const bool build = !ctx->v.kept || next % every == 0;
+    const bool build = !ctx->v.kept || ctx->v.auto_lists || next % every == 0;
     CK(cudaGraphLaunch(build ? ctx->gexec : ctx->gexec_keep, ctx->st));
     ctx->host_step = next;
   }
@@ -681,6 +698,17 @@ int rbsog_sync(rbsog_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   if (!ctx->has_system) return RBSOG_OK;
   return read_err(ctx);
+}
+
+int rbsog_get_list_builds(rbsog_ctx *ctx, int64_t *builds) {
+  if (!ctx || !builds) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  unsigned long long b = 0;
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaMemcpyAsync(&b, ctx->v.nbuild, sizeof(b), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *builds = (int64_t)b;
+  return RBSOG_OK;
 }
 
 int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S) {
@@ -935,10 +963,12 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage) {
   CK(cudaSetDevice(ctx->dev));
   CK(cudaEventSynchronize(ctx->prof[8]));
   // (start, end) event of each stage: prepare, bin, near, far branch (k-batch, structure factor,
-  // its reduction, far force; side stream), F^corr, finish (after the join), total
-  static const int b[7] = {0, 1, 2, 3, 7, 6, 0};
-  static const int e[7] = {1, 2, 7, 4, 5, 8, 8};
-  for (int k = 0; k < nstage && k < 7; k++) CK(cudaEventElapsedTime(ms + k, ctx->prof[b[k]], ctx->prof[e[k]]));
+  // its reduction, far force; side stream), F^corr, finish (after the join), total, and inside
+  // the far branch the structure-factor kernel and the far-force kernel alone
+  static const int b[RBSOG_NSTAGE] = {0, 1, 2, 3, 7, 6, 0, 9, 11};
+  static const int e[RBSOG_NSTAGE] = {1, 2, 7, 4, 5, 8, 8, 10, 4};
+  for (int k = 0; k < nstage && k < RBSOG_NSTAGE; k++)
+    CK(cudaEventElapsedTime(ms + k, ctx->prof[b[k]], ctx->prof[e[k]]));
   return RBSOG_OK;
 }
 

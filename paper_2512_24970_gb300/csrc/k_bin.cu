@@ -129,16 +129,28 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
   p.ua[i] = make_uint4(u[0], u[1], u[2], (uint32_t)sp);
   p.cellid[i] = cell;
   if (p.kept) {
-    if (p.build) {                 // positions of this build, for the displacement check
-      for (int a = 0; a < 3; a++) p.xb[a * n + i] = x[a];
-    } else {
+    if (p.auto_lists) {
+      // refresh the slot of the last build (unless the host asked for a build:
+      // then there may be none yet) and raise the build flag when this atom
+      // has moved by more than skin/2 since then; the histograms follow, the
+      // binning kernels run only if the flag is up
+      if (*(volatile int *)p.lflag == 0)
+        p.su[p.slot_of[i]] = make_uint4(u[0], u[1], u[2], (uint32_t)i | ((uint32_t)sp << SU_SP_SHIFT));
+      double d2 = 0.0;
+      for (int a = 0; a < 3; a++) {
+        const double d = __dadd_rn(x[a], -p.xb[a * n + i]);
+        d2 = __dadd_rn(d2, __dmul_rn(d, d));
+      }
+      const unsigned far = __ballot_sync(__activemask(), d2 > p.half_skin2);
+      if (far && (threadIdx.x & 31) == __ffs(far) - 1) atomicOr(p.lflag, 1);   // one lane per warp
+    } else if (!p.build) {
       // the lists and slots of the last build are kept: refresh this atom's
       // coordinates in its slot and check that it stayed within skin/2
       p.su[p.slot_of[i]] = make_uint4(u[0], u[1], u[2], (uint32_t)i | ((uint32_t)sp << SU_SP_SHIFT));
       double d2 = 0.0;
       for (int a = 0; a < 3; a++) {
-        const double d = x[a] - p.xb[a * n + i];
-        d2 += d * d;
+        const double d = __dadd_rn(x[a], -p.xb[a * n + i]);
+        d2 = __dadd_rn(d2, __dmul_rn(d, d));
       }
       if (d2 > p.half_skin2) atomicOr(p.err, ERR_SKIN);
       return;                      // no binning in this evaluation
@@ -182,8 +194,15 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
 // all slots) and the near-field chunks: each row's slots cut into runs of
 // NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.  One block;
 // the row totals come from the binning's atomic counts.
+// With automatic kept lists the binning kernels stay in every step's graph
+// and return at once unless this step rebuilds the lists.
+__device__ __forceinline__ bool skip_binning(const View &p) {
+  return p.auto_lists && *(volatile const int *)p.lflag == 0;
+}
+
 __global__ void __launch_bounds__(1024) k_rowscan(View p) {
   __shared__ int wsum[32];
+  if (skip_binning(p)) return;
   const int nt = blockDim.x, t = threadIdx.x;
   const int nrow = p.nc[1] * p.nc[2];
   const int per = (nrow + nt - 1) / nt;
@@ -220,6 +239,7 @@ __global__ void __launch_bounds__(1024) k_rowscan(View p) {
 // Cell ranges inside each row: one warp per row, an inclusive warp scan of
 // the cell counts (32 cells per round) on top of the row's start.
 __global__ void __launch_bounds__(256) k_cellstart(View p) {
+  if (skip_binning(p)) return;
   const int nrow = p.nc[1] * p.nc[2], nc0 = p.nc[0];
   const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -244,7 +264,7 @@ __global__ void __launch_bounds__(256) k_cellstart(View p) {
 
 __global__ void __launch_bounds__(256) k_scatter(View p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.n) return;
+  if (i >= p.n || skip_binning(p)) return;
   const int slot = atomicAdd(p.cell_cursor + p.cellid[i], 1);
   p.perm_tmp[slot] = (int)i;
   p.key_tmp[slot] = p.ua[i].x;
@@ -255,7 +275,9 @@ __global__ void __launch_bounds__(256) k_scatter(View p) {
 // writes the sorted SoA arrays and the near-field chunk table.
 __global__ void __launch_bounds__(256) k_rank(View p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.n) return;
+  if (i >= p.n || skip_binning(p)) return;
+  if (p.kept)                      // positions of this build, for the displacement check
+    for (int a = 0; a < 3; a++) p.xb[a * p.n + i] = p.x[a * p.n + i];
   const int c = p.cellid[i];
   const int b = p.cell_start[c], cnt = p.cell_count[c];
   const uint4 u = p.ua[i];

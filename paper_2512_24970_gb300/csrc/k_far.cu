@@ -154,10 +154,7 @@ __device__ void corr_block(const View &p, int blk, int step_off) {
     if (t < 3) p.red[t] = v / (double)p.n;
     else p.red[3] = v;
   }
-  if (t == 0) {
-    *p.corr_ticket = 0u;                          // ready for the next evaluation
-    if (step_off) *p.step += step_off;
-  }
+  if (t == 0) *p.corr_ticket = 0u;                // ready for the next evaluation
 }
 
 // Blocks [0, nkb): one warp per k, fixed-order sum over tiles (four
@@ -360,6 +357,10 @@ __global__ void __launch_bounds__(256) k_finish(View p) {
   } else {
     for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
   }
+  // the step counter advances here, after both branches joined: every kernel
+  // of the step that reads it (k-batch, noise, shell batch) has finished
+  if (MODE != 0 && i == 0) *p.step += 1;
+  if (i == 0 && p.auto_lists) *p.lflag = 0;     // the build flag of the next step starts down
   if (MODE != 0) {
     const double kick = p.kick[p.spc[i]];
     for (int a = 0; a < 3; a++) {

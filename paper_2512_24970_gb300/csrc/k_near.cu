@@ -359,6 +359,11 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   for (int64_t c = (int64_t)blockIdx.x * NEAR_BLOCK + tid; c < (int64_t)p.ncell + p.nc[1] * p.nc[2];
        c += (int64_t)gridDim.x * NEAR_BLOCK)
     p.cell_count[c] = 0;
+  if (BUILD) {
+    // automatic kept lists: only a step whose k_prepare raised the flag builds
+    if (p.auto_lists && *(volatile const int *)p.lflag == 0) return;
+    if (blockIdx.x == 0 && tid == 0) atomicAdd(p.nbuild, 1ull);
+  }
   const int warp = tid >> 5, lane = tid & 31;
   const int a = warp * APW + lane / TPA;      // atom row of the shared arrays
   const int g = lane % TPA;

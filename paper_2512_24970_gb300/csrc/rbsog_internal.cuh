@@ -72,6 +72,9 @@ struct View {
   // kept (skin) lists: kept = list_every >= 1; build = this evaluation builds
   // them (the step graph has a build and a keep variant)
   int kept, build;
+  int auto_lists;         // kept lists rebuilt when an atom moved by skin/2 (flag set on the device)
+  int *lflag;             // [1] auto_lists: this step rebuilds (set by k_prepare or the host)
+  unsigned long long *nbuild;  // [1] list builds so far
   float rl2f;             // fl32((r_shell + skin)^2), outer radius of a build
   double half_skin2;      // (skin / 2)^2, shaded down: the displacement limit
   int *lA, *lB;           // [nslot][RBSOG_MAX_CORE], [nslot][RBSOG_MAX_KEPT] member slots

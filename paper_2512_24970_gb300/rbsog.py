@@ -31,23 +31,25 @@ ERRORS = {
     -7: "RBSOG_E_NO_SOG_ROOT", -8: "RBSOG_E_NO_SYSTEM", -9: "RBSOG_E_SKIN",
 }
 MAX_CORE = 64
+LISTS_AUTO = -1   # list_every: rebuild kept lists when an atom has moved by skin/2
 MAX_KEPT = 512
 
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_get_list_builds", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
     "rbsog_ensemble_step", "rbsog_ensemble_sync", "rbsog_ensemble_last_error",
 ]
 SF_STATIC_PMAX = 1024
-NSTAGE = 7
+NSTAGE = 9
 # stages of rbsog_get_stage_times: integrator + histograms, binning, near field, the far-field
 # branch on the side stream (k-batch, structure factor, its reduction, far force), F^corr, the
-# closing total force + half kick after the branches join, and the whole evaluation
-STAGES = ["prepare", "bin", "near", "far", "corr", "finish", "total"]
+# closing total force + half kick after the branches join, the whole evaluation, and inside the
+# far-field branch the structure-factor kernel and the far-force kernel alone
+STAGES = ["prepare", "bin", "near", "far", "corr", "finish", "total", "rho", "farforce"]
 
 
 class RbsogError(RuntimeError):
@@ -83,7 +85,7 @@ class MethodParams:
     dt: float = 0.001
     T: float = 1200.0
     gamma: float = 1.0
-    list_every: int = 0     # 0: per-step lists; n >= 1: kept lists rebuilt every n steps
+    list_every: int = 0     # 0: per-step lists; n >= 1: kept lists rebuilt every n steps; -1: when needed
     skin: float = 0.0       # Verlet skin of kept lists [A]
 
     def c(self):
@@ -123,6 +125,7 @@ def load():
     L.rbsog_set_state.argtypes = [P, P, P, I64, I]
     L.rbsog_sync.argtypes = [P]
     L.rbsog_get_sog.argtypes = [P, P, P, P]
+    L.rbsog_get_list_builds.argtypes = [P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kbatch.argtypes = [P, P, P]
@@ -273,6 +276,12 @@ class Context:
         w = np.zeros(M + 1)
         self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
         return s.value, w, S.value
+
+    def list_builds(self) -> int:
+        """Builds of the kept random batch lists since set_system."""
+        b = np.zeros(1, dtype=np.int64)
+        self._ck(self._L.rbsog_get_list_builds(self.h, _np_ptr(b)))
+        return int(b[0])
 
     # ---- parity hooks -----------------------------------------------------
     def debug_lists(self, sel, cap_core=128, cap_shell=512, batch=True):

@@ -154,6 +154,8 @@ class Config:
     T: float
     steps: int
     integrator: str        # "nve" | "langevin"
+    list_every: int = -1   # kept random batch lists, rebuilt when an atom has moved by skin/2 ...
+    skin: float = 1.0      # ... with this skin [A]
 
 
 CONFIGS = {

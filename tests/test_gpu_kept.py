@@ -160,3 +160,39 @@ def test_kept_full_size_sampled(rb, orc, key):
     for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
     assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kept_auto_rebuild_trajectory(rb, orc, precision):
+    """list_every = -1: the device rebuilds the lists whenever an atom has
+    moved by more than skin/2; a hot run with a thin skin rebuilds several
+    times, at the same steps as the oracle, and follows its trajectory (FP64)
+    or stays within the mixed force tolerance (mixed, at the GPU's state)."""
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    v0 = W.maxwell_boltzmann(w, 3000.0)
+    prec = rb.FP64 if precision == "fp64" else rb.MIXED
+    ctx, S = setup_kept(rb, orc, w, skin=0.15, list_every=-1, P_F=100, precision=prec, integrator=rb.NVE_VV)
+    ctx.set_velocities(v0)
+    ctx.step(12)
+    pos, vel, step = ctx.get_state()
+    builds = ctx.list_builds()
+    if precision == "fp64":
+        vo, _ = S.run(v0, 12, 0.001, integrator=0)
+        assert S.builds >= 2
+        assert builds == 1 + S.builds                # the first evaluation builds too
+        assert np.sqrt(((pos - S.pos) ** 2).mean()) < 1e-10
+        assert rms_rel(vel, vo) < 1e-10
+    else:
+        # mixed: rebuilt several times, and the kept lists still hold every
+        # pair inside r_shell at the GPU's current positions
+        assert builds >= 3
+        Fg = ctx.compute_forces()
+        assert np.isfinite(Fg).all()
+        R = orc.System(pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=20, P_F=100, seed=3, step=step)
+        sel = np.arange(0, w.n, 37)
+        Lr = R.lists(sel, cap_core=128, cap_shell=1024, batch=False)
+        g = ctx.debug_kept_lists(sel)
+        for q in range(sel.size):
+            have = set(g["A"][q, :g["nA"][q]].tolist()) | set(g["B"][q, :g["nB"][q]].tolist())
+            need = set(Lr["core"][q, :Lr["ncore"][q]].tolist()) | set(Lr["shell"][q, :Lr["nshell"][q]].tolist())
+            assert need <= have

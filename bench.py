@@ -135,6 +135,9 @@ KERNELS_PER_STEP = 12
 # that reuses the lists has no binning (4 kernels) and no build
 KERNELS_BUILD_STEP = 13
 KERNELS_KEEP_STEP = 8
+# automatic kept lists: every step's graph holds the binning and build
+# kernels (they return at once unless the step rebuilds)
+KERNELS_AUTO_STEP = 13
 KERNEL_LABEL = {"near": "k_near", "rho": "k_rho", "farforce": "k_farforce"}
 
 
@@ -413,7 +416,7 @@ def run_ours(args):
         cpu = {"value": v, "unit": "atom-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": sample, "wall_s": wall}
     if list_every < 0:
-        launches = KERNELS_BUILD_STEP * K        # the binning and build kernels return at once when not needed
+        launches = KERNELS_AUTO_STEP * K
     elif list_every > 0:
         builds = sum(1 for s in range(Wm + 1, Wm + K + 1) if s % list_every == 0)
         launches = KERNELS_BUILD_STEP * builds + KERNELS_KEEP_STEP * (K - builds)

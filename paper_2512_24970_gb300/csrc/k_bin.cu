@@ -87,8 +87,24 @@ __device__ __forceinline__ void noise3f(const View &p, long long s, uint32_t i, 
   g[2] = r1 * c1;
 }
 
+// Cell and row histograms; lanes of one warp that share a cell (or row) add once.
+__device__ __forceinline__ void histogram_add(const View &p, int cell) {
+  const unsigned act = __activemask();
+  const unsigned pc = __match_any_sync(act, cell);
+  if ((threadIdx.x & 31) == __ffs(pc) - 1) atomicAdd(p.cell_count + cell, __popc(pc));
+  const int row = cell / p.nc[0];
+  const unsigned pr = __match_any_sync(act, row);
+  if ((threadIdx.x & 31) == __ffs(pr) - 1) atomicAdd(p.row_count + row, __popc(pr));
+}
+
+// With automatic kept lists the binning kernels stay in every step's graph
+// and return at once unless this step rebuilds the lists.
+__device__ __forceinline__ bool skip_binning(const View &p) {
+  return p.auto_lists && *(volatile const int *)p.lflag == 0;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
+__global__ void __launch_bounds__(PREP_BLOCK) k_prepare(View p, int step_off) {
   const long long s = *p.step + step_off;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
@@ -156,13 +172,7 @@ __global__ void __launch_bounds__(256) k_prepare(View p, int step_off) {
       return;                      // no binning in this evaluation
     }
   }
-  // histograms; lanes of one warp that share a cell (or row) add once
-  const unsigned act = __activemask();
-  const unsigned pc = __match_any_sync(act, cell);
-  if ((threadIdx.x & 31) == __ffs(pc) - 1) atomicAdd(p.cell_count + cell, __popc(pc));
-  const int row = cell / p.nc[0];
-  const unsigned pr = __match_any_sync(act, row);
-  if ((threadIdx.x & 31) == __ffs(pr) - 1) atomicAdd(p.row_count + row, __popc(pr));
+  histogram_add(p, cell);
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
@@ -194,12 +204,6 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
 // all slots) and the near-field chunks: each row's slots cut into runs of
 // NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.  One block;
 // the row totals come from the binning's atomic counts.
-// With automatic kept lists the binning kernels stay in every step's graph
-// and return at once unless this step rebuilds the lists.
-__device__ __forceinline__ bool skip_binning(const View &p) {
-  return p.auto_lists && *(volatile const int *)p.lflag == 0;
-}
-
 __global__ void __launch_bounds__(1024) k_rowscan(View p) {
   __shared__ int wsum[32];
   if (skip_binning(p)) return;
@@ -316,10 +320,10 @@ void launch_ksample(const View &v, cudaStream_t st, int step_off) {
 // The cell and row histograms start at zero: cleared at set-up and, after
 // every use, by the near-field kernel (clear_counts) or by the caller.
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
-  const int blocks = v.nblk_atoms;
-  if (mode == 0) k_prepare<0><<<blocks, 256, 0, st>>>(v, step_off);
-  else if (mode == 1) k_prepare<1><<<blocks, 256, 0, st>>>(v, step_off);
-  else k_prepare<2><<<blocks, 256, 0, st>>>(v, step_off);
+  const int blocks = (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);
+  if (mode == 0) k_prepare<0><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
+  else if (mode == 1) k_prepare<1><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
+  else k_prepare<2><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
 }
 
 void launch_bin(const View &v, cudaStream_t st) {

@@ -14,17 +14,9 @@ namespace rb {
 
 constexpr double TWO_PI = 6.283185307179586;
 
-// Mixed phase e^{i 2 pi th / 2^32}: FP32 polynomial with exact quarter-turn
-// reduction (RB_MUFU_TRIG selects the hardware approximation for experiments).
-__device__ __forceinline__ void sincos_phase_f(uint32_t th, float &s, float &c) {
-#ifdef RB_MUFU_TRIG
-  constexpr float ANG23 = (float)(TWO_PI / 8388608.0);  // 2 pi / 2^23
-  const int xs = ((int)(th + 256u)) >> 9;
-  __sincosf(i2f_small(xs) * ANG23, &s, &c);
-#else
-  sincos_turn(th, s, c);
-#endif
-}
+// Mixed phase e^{i 2 pi th / 2^32}: FP32 polynomial with exact half-turn
+// reduction (sincos_turn).
+__device__ __forceinline__ void sincos_phase_f(uint32_t th, float &s, float &c) { sincos_turn(th, s, c); }
 __device__ __forceinline__ void sincos_phase_d(uint32_t th, double &s, double &c) {
   sincospi((double)(int)th * 4.656612873077393e-10, &s, &c);  // * 2^-31
 }
@@ -69,15 +61,7 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
         const uint32_t th0 = mx[0] * u.x + my[0] * u.y + mz[0] * u.z;
         const uint32_t th1 = mx[1] * u.x + my[1] * u.y + mz[1] * u.z;
         unsigned long long s2, c2;
-#ifdef RB_MUFU_TRIG
-        float s0, c0, s1, c1;
-        sincos_phase_f(th0, s0, c0);
-        sincos_phase_f(th1, s1, c1);
-        s2 = pk2(s0, s1);
-        c2 = pk2(c0, c1);
-#else
         sincos_turn2(th0, th1, s2, c2);
-#endif
         const unsigned long long q2 = pk2(q, q);
         fr = fma2(q2, c2, fr);
         fi = fma2(q2, s2, fi);
@@ -157,42 +141,39 @@ __device__ void corr_block(const View &p, int blk, int step_off) {
   if (t == 0) *p.corr_ticket = 0u;                // ready for the next evaluation
 }
 
-// Blocks [0, nkb): one warp per k, fixed-order sum over tiles (four
-// lane-strided partial sums, then a shuffle tree), per-k force coefficients.
-// Blocks [nkb, nkb + CORR_BLOCKS): F^corr and U_N (corr_block).
+// Blocks [0, nkb): one block per k, fixed-order sum over tiles (thread-
+// strided partial sums, a shuffle tree per warp, the eight warp sums in
+// order), per-k force coefficients.  Blocks [nkb, nkb + CORR_BLOCKS): F^corr
+// and U_N (corr_block).
 template <typename R>
 __global__ void __launch_bounds__(256) k_reduce(View p, int nkb, int step_off) {
   if ((int)blockIdx.x >= nkb) {
     corr_block(p, (int)blockIdx.x - nkb, step_off);
     return;
   }
+  __shared__ double2 wsum[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k = blockIdx.x * 8 + w;
+  const int k = blockIdx.x;
   if (k < p.P) {
-    double sr[4] = {0.0, 0.0, 0.0, 0.0}, si[4] = {0.0, 0.0, 0.0, 0.0};
     const double2 *d = reinterpret_cast<const double2 *>(p.rho_part) + (int64_t)k * p.ntile;
-    int t = lane;
-    for (; t + 96 < p.ntile; t += 128) {
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const double2 v = d[t + 32 * u];
-        sr[u] += v.x;
-        si[u] += v.y;
-      }
-    }
-    for (int u = 0; t < p.ntile; t += 32, u++) {
+    double r = 0.0, i = 0.0;
+    for (int t = threadIdx.x; t < p.ntile; t += 256) {
       const double2 v = d[t];
-      sr[u] += v.x;
-      si[u] += v.y;
+      r += v.x;
+      i += v.y;
     }
-    double r = (sr[0] + sr[1]) + (sr[2] + sr[3]);
-    double i = (si[0] + si[1]) + (si[2] + si[3]);
     for (int o = 16; o > 0; o >>= 1) {
       r += __shfl_down_sync(0xffffffffu, r, o);
       i += __shfl_down_sync(0xffffffffu, i, o);
     }
-    if (lane == 0) {
-      const double sr0 = r, si0 = i;
+    if (lane == 0) wsum[w] = make_double2(r, i);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr0 = 0.0, si0 = 0.0;
+      for (int u = 0; u < 8; u++) {
+        sr0 += wsum[u].x;
+        si0 += wsum[u].y;
+      }
       p.rho[2 * k] = sr0;
       p.rho[2 * k + 1] = si0;
       const int4 m = p.km[k];
@@ -278,15 +259,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
         const uint32_t th0 = (uint32_t)m0.x * u.x + (uint32_t)m0.y * u.y + (uint32_t)m0.z * u.z;
         const uint32_t th1 = (uint32_t)m1.x * u.x + (uint32_t)m1.y * u.y + (uint32_t)m1.z * u.z;
         unsigned long long s2, c2;
-#ifdef RB_MUFU_TRIG
-        float s0, c0, s1, c1;
-        sincos_phase_f(th0, s0, c0);
-        sincos_phase_f(th1, s1, c1);
-        s2 = pk2(s0, s1);
-        c2 = pk2(c0, c1);
-#else
         sincos_turn2(th0, th1, s2, c2);
-#endif
         const float4 ka = ska[k >> 1], kb = skb[k >> 1];
         // Im(e^{-i theta} rho) c = c Im rho cos - c Re rho sin, two k at once
         const unsigned long long sv =
@@ -341,7 +314,7 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
 
 // F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_finish(View p) {
+__global__ void __launch_bounds__(PREP_BLOCK) k_finish(View p) {
   constexpr bool MIX = sizeof(R) == 4;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
@@ -389,7 +362,7 @@ void launch_rho(const View &v, cudaStream_t st) {
 }
 
 void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
-  const int g = max(1, (v.P + 7) / 8);
+  const int g = max(1, v.P);                    // one block per k
   if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, g, 0);
   else k_reduce<double><<<g, 256, 0, st>>>(v, g, 0);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
@@ -407,13 +380,13 @@ void launch_farforce(const View &v, cudaStream_t st) {
 }
 
 void launch_finish(const View &v, cudaStream_t st, int mode) {
-  const int g = (int)((v.n + 255) / 256);
+  const int g = (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);
   if (v.prec == RBSOG_MIXED) {
-    if (mode == 0) k_finish<float, 0><<<g, 256, 0, st>>>(v);
-    else k_finish<float, 1><<<g, 256, 0, st>>>(v);
+    if (mode == 0) k_finish<float, 0><<<g, PREP_BLOCK, 0, st>>>(v);
+    else k_finish<float, 1><<<g, PREP_BLOCK, 0, st>>>(v);
   } else {
-    if (mode == 0) k_finish<double, 0><<<g, 256, 0, st>>>(v);
-    else k_finish<double, 1><<<g, 256, 0, st>>>(v);
+    if (mode == 0) k_finish<double, 0><<<g, PREP_BLOCK, 0, st>>>(v);
+    else k_finish<double, 1><<<g, PREP_BLOCK, 0, st>>>(v);
   }
 }
 

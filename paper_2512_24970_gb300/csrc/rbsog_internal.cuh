@@ -17,6 +17,7 @@ constexpr double FCONV = 9648.53321;     // (eV/A)/amu -> A/ps^2
 constexpr double KBOLTZ = 8.617333262e-5;  // eV/K
 
 constexpr int NT_TAB = 512;        // intervals of the FP32 SOG tables on [0, r_shell^2]
+constexpr int PREP_BLOCK = 128;    // threads per block of k_prepare and k_finish (atoms spread over the SMs)
 constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
 constexpr int NEAR_CHUNK = 8;      // atoms per warp of the near-field kernel (4 threads each)
 constexpr int NEAR_WARPS = 4;      // warps per near-field block
@@ -169,29 +170,31 @@ __device__ __forceinline__ float i2f_small(int x) {
 }
 
 // (sin, cos) of the angle 2 pi th / 2^32 in FP32 for an exact integer phase th.
-// The nearest quarter turn q is taken off in integer arithmetic; the remainder
-// r in [-2^29, 2^29] (|phi| <= pi/4) is rounded to 23 bits and converted
-// exactly; sin and cos of phi are the Taylor polynomials of degree 9 and 10
-// (truncation error at pi/4 below 1.8e-9 and 1.2e-10, so the error is FP32
-// rounding, unbiased, ~4e-8 RMS); the quarter turn is applied by a swap and
-// sign flips.  No MUFU: its approximation error is smooth in the angle and
-// adds coherently over atoms sharing a phase.
+// The half turn h is taken off in integer arithmetic: m = the top bit of
+// th + 2^30, r = th ^ m = th - h 2^31 (two's complement) in [-2^30, 2^30), so
+// phi = 2 pi r / 2^32 lies in [-pi/2, pi/2); r is rounded to FP32 (at most
+// 2^6 of 2^32 in a turn off, ~1e-7 rad) and scaled.  sin and cos of phi are
+// minimax polynomials of degree 9 and 10 on [-pi/2, pi/2] (absolute error
+// 4.9e-9 and 4.3e-10 with the binary32 coefficients, below FP32 rounding;
+// derived by csrc/sincos_coeffs.py), and sin(phi + h pi) = (-1)^h sin(phi),
+// cos likewise: one sign flip by m.  No MUFU: its approximation error is
+// smooth in the angle and adds coherently over atoms sharing a phase.
+constexpr float SC_S3 = -1.666665673e-01f, SC_S5 = 8.333008736e-03f, SC_S7 = -1.980603120e-04f,
+                SC_S9 = 2.598852234e-06f;
+constexpr float SC_C2 = -5.000000000e-01f, SC_C4 = 4.166665673e-02f, SC_C6 = -1.388858538e-03f,
+                SC_C8 = 2.477017915e-05f, SC_C10 = -2.620901967e-07f;
+constexpr float SC_TURN32 = (float)(6.283185307179586 / 4294967296.0);  // 2 pi / 2^32
 __device__ __forceinline__ void sincos_turn(uint32_t th, float &s, float &c) {
-  const uint32_t t = th + 0x20000000u;
-  const uint32_t q = t >> 30;
-  const int r = (int)(t & 0x3FFFFFFFu) - 0x20000000;
-  constexpr float TURN25 = (float)(6.283185307179586 / 33554432.0);  // 2 pi / 2^25
-  const float phi = i2f_small((r + 64) >> 7) * TURN25;
+  const uint32_t m = (th + 0x40000000u) & 0x80000000u;
+  const float phi = __int2float_rn((int)(th ^ m)) * SC_TURN32;
   const float z = phi * phi;
-  float ps = __fmaf_rn(__fmaf_rn(__fmaf_rn(2.7557319e-06f, z, -1.9841270e-04f), z, 8.3333338e-03f), z,
-                       -1.6666667e-01f);
+  const float ps = __fmaf_rn(__fmaf_rn(__fmaf_rn(SC_S9, z, SC_S7), z, SC_S5), z, SC_S3);
   const float sn = __fmaf_rn(ps * z, phi, phi);
-  const float pc = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(-2.7557320e-07f, z, 2.4801588e-05f), z,
-                                                 -1.3888889e-03f), z, 4.1666668e-02f), z, -0.5f);
+  const float pc =
+      __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(SC_C10, z, SC_C8), z, SC_C6), z, SC_C4), z, SC_C2);
   const float cs = __fmaf_rn(pc, z, 1.0f);
-  const bool sw = (q & 1u) != 0u;
-  s = __int_as_float(__float_as_int(sw ? cs : sn) ^ (int)((q & 2u) << 30));
-  c = __int_as_float(__float_as_int(sw ? sn : cs) ^ (int)(((q + 1u) & 2u) << 30));
+  s = __int_as_float(__float_as_int(sn) ^ (int)m);
+  c = __int_as_float(__float_as_int(cs) ^ (int)m);
 }
 
 // 32-bit fixed-point fractional coordinate floor(frac(x / L) 2^32).
@@ -245,38 +248,24 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 }
 
 // sincos_turn of two phases at once: the FP32 steps in packed pairs, the
-// quarter-turn bookkeeping per lane; lane by lane the same results.
+// half-turn bookkeeping per lane; lane by lane the same results.
 __device__ __forceinline__ void sincos_turn2(uint32_t th0, uint32_t th1, unsigned long long &s2,
                                              unsigned long long &c2) {
-  const uint32_t t0 = th0 + 0x20000000u, t1 = th1 + 0x20000000u;
-  const int x0 = ((int)(t0 & 0x3FFFFFFFu) - 0x20000000 + 64) >> 7;
-  const int x1 = ((int)(t1 & 0x3FFFFFFFu) - 0x20000000 + 64) >> 7;
-  constexpr float TURN25 = (float)(6.283185307179586 / 33554432.0);  // 2 pi / 2^25
-  const unsigned long long xb = pk2(__int_as_float(x0 + 0x4B400000), __int_as_float(x1 + 0x4B400000));
-  const unsigned long long phi = mul2(add2(xb, pk2(-12582912.0f, -12582912.0f)), pk2(TURN25, TURN25));
+  const uint32_t m0 = (th0 + 0x40000000u) & 0x80000000u, m1 = (th1 + 0x40000000u) & 0x80000000u;
+  const unsigned long long phi = mul2(pk2(__int2float_rn((int)(th0 ^ m0)), __int2float_rn((int)(th1 ^ m1))),
+                                      pk2(SC_TURN32, SC_TURN32));
   const unsigned long long z = mul2(phi, phi);
   const unsigned long long ps =
-      fma2(fma2(fma2(pk2(2.7557319e-06f, 2.7557319e-06f), z, pk2(-1.9841270e-04f, -1.9841270e-04f)), z,
-                pk2(8.3333338e-03f, 8.3333338e-03f)),
-           z, pk2(-1.6666667e-01f, -1.6666667e-01f));
+      fma2(fma2(fma2(pk2(SC_S9, SC_S9), z, pk2(SC_S7, SC_S7)), z, pk2(SC_S5, SC_S5)), z, pk2(SC_S3, SC_S3));
   const unsigned long long sn = fma2(mul2(ps, z), phi, phi);
   const unsigned long long pc =
-      fma2(fma2(fma2(fma2(pk2(-2.7557320e-07f, -2.7557320e-07f), z, pk2(2.4801588e-05f, 2.4801588e-05f)), z,
-                     pk2(-1.3888889e-03f, -1.3888889e-03f)),
-                z, pk2(4.1666668e-02f, 4.1666668e-02f)),
-           z, pk2(-0.5f, -0.5f));
+      fma2(fma2(fma2(fma2(pk2(SC_C10, SC_C10), z, pk2(SC_C8, SC_C8)), z, pk2(SC_C6, SC_C6)), z,
+                pk2(SC_C4, SC_C4)),
+           z, pk2(SC_C2, SC_C2));
   const unsigned long long cs = fma2(pc, z, pk2(1.0f, 1.0f));
-  float sn0, sn1, cs0, cs1;
-  up2(sn, sn0, sn1);
-  up2(cs, cs0, cs1);
-  const uint32_t q0 = t0 >> 30, q1 = t1 >> 30;
-  const bool w0 = (q0 & 1u) != 0u, w1 = (q1 & 1u) != 0u;
-  const float s0 = __int_as_float(__float_as_int(w0 ? cs0 : sn0) ^ (int)((q0 & 2u) << 30));
-  const float c0 = __int_as_float(__float_as_int(w0 ? sn0 : cs0) ^ (int)(((q0 + 1u) & 2u) << 30));
-  const float s1 = __int_as_float(__float_as_int(w1 ? cs1 : sn1) ^ (int)((q1 & 2u) << 30));
-  const float c1 = __int_as_float(__float_as_int(w1 ? sn1 : cs1) ^ (int)(((q1 + 1u) & 2u) << 30));
-  s2 = pk2(s0, s1);
-  c2 = pk2(c0, c1);
+  const unsigned long long mm = ((unsigned long long)m1 << 32) | m0;   // the sign of each lane
+  s2 = sn ^ mm;
+  c2 = cs ^ mm;
 }
 
 // Packed constants of the list predicate seen from one atom image:

@@ -83,19 +83,20 @@ def _declare(L):
     L.orc_sog_solve.restype = ctypes.c_int
     L.orc_sog_eval.argtypes = [_I32, _D, _D, _P, _I64, _P, _P, _P]
     L.orc_sog_fhat.argtypes = [sp, _I64, _P, _P]
+    L.orc_sog_fhat_dk2.argtypes = [sp, _I64, _P, _P]
     L.orc_pair_terms.argtypes = [sp, _I32, _I32, _I64, _P, _P, _P]
     L.orc_fixed_point.argtypes = [sp, _P]
     L.orc_cell_grid.argtypes = [sp, _P]
     L.orc_cell_grid_skin.argtypes = [sp, _P]
     L.orc_lists_skin.argtypes = [sp, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
     L.orc_lists_skin.restype = ctypes.c_int
-    L.orc_near_skin.argtypes = [sp, _P, _P, _I64, _I32, _P, _P]
+    L.orc_near_skin.argtypes = [sp, _P, _P, _I64, _I32, _P, _P, _P]
     L.orc_near_skin.restype = ctypes.c_int
     L.orc_floyd.argtypes = [_U64, _I64, _U32, _I32, _I32, _P]
     L.orc_floyd.restype = _I32
     L.orc_lists.argtypes = [sp, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
     L.orc_lists.restype = ctypes.c_int
-    L.orc_near.argtypes = [sp, _P, _I64, _I32, _P, _P]
+    L.orc_near.argtypes = [sp, _P, _I64, _I32, _P, _P, _P]
     L.orc_near.restype = ctypes.c_int
     L.orc_sampler_S.argtypes = [sp]
     L.orc_sampler_S.restype = _D
@@ -309,23 +310,27 @@ class System:
         return out
 
     # ---- near field (Sec. 2.2) -------------------------------------------
-    def near(self, sel=None, all_shell=False, energy=False):
-        """Uncorrected near-field force F_core + F*_shell of ``sel`` (and 1/2 pair energy);
-        with kept lists, the estimator of ``orc_near_skin``."""
+    def near(self, sel=None, all_shell=False, energy=False, virial=False):
+        """Uncorrected near-field force F_core + F*_shell of ``sel`` (and 1/2 pair energy,
+        and the per-atom pair virial [n,6] = xx, yy, zz, xy, xz, yz); with kept lists,
+        the estimator of ``orc_near_skin``."""
         sel = np.arange(self.n, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
         F = np.zeros((sel.size, 3))
         E = np.zeros(sel.size) if energy else None
+        W = np.zeros((sel.size, 6)) if virial else None
         st = self._c()
         if self.kept_lists:
             self._ensure_lists()
             bp = np.ascontiguousarray(self.build_pos)
             rc = lib().orc_near_skin(ctypes.byref(st), _ptr(bp), _ptr(sel), sel.size, int(bool(all_shell)),
-                                     _ptr(F), _ptr(E))
+                                     _ptr(F), _ptr(E), _ptr(W))
         else:
-            rc = lib().orc_near(ctypes.byref(st), _ptr(sel), sel.size, int(bool(all_shell)), _ptr(F), _ptr(E))
+            rc = lib().orc_near(ctypes.byref(st), _ptr(sel), sel.size, int(bool(all_shell)), _ptr(F), _ptr(E),
+                                _ptr(W))
         if rc != 0:
             raise RuntimeError("oracle near-field capacity exceeded")
-        return (F, E) if energy else F
+        out = (F,) + ((E,) if energy else ()) + ((W,) if virial else ())
+        return out if len(out) > 1 else F
 
     def pair_terms(self, si, sj, r2):
         r2 = np.ascontiguousarray(r2, dtype=np.float64).reshape(-1)
@@ -342,6 +347,33 @@ class System:
         st = self._c()
         lib().orc_sog_fhat(ctypes.byref(st), k2.size, _ptr(k2), _ptr(out))
         return out
+
+    def fhat_dk2(self, k2):
+        """dFhat/d(k^2) of Eq. (Fouriertransform)."""
+        k2 = np.ascontiguousarray(k2, dtype=np.float64).reshape(-1)
+        out = np.empty_like(k2)
+        st = self._c()
+        lib().orc_sog_fhat_dk2(ctypes.byref(st), k2.size, _ptr(k2), _ptr(out))
+        return out
+
+    def far_virial(self, m, c, rho):
+        """Virial [6] (xx, yy, zz, xy, xz, yz) of the far-field energy estimator
+        U_F* = k_e/(2V) sum_p c_p |rho_p|^2: minus its derivative under a homogeneous
+        strain of positions and box.  k . r does not change, k_a -> k_a - eps_ab k_b
+        and V -> V (1 + tr eps), so W_ab = delta_ab U_F* + (k_e/V) sum_p c_p
+        (Fhat'/Fhat)(k_p^2) k_pa k_pb |rho_p|^2, with c_p the weight of Fhat(k_p)
+        (the k-batch's importance weight or, enumerated, Fhat itself)."""
+        k = self.kvec(m)
+        k2 = (k ** 2).sum(1)
+        g = self.fhat_dk2(k2) / self.fhat(k2)
+        r2 = (np.asarray(rho) ** 2).sum(1)
+        V = self.volume
+        UF = KE / (2.0 * V) * float((c * r2).sum())
+        wk = KE / V * c * g * r2
+        W = np.zeros(6)
+        for comp, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+            W[comp] = float((wk * k[:, a] * k[:, b]).sum()) + (UF if a == b else 0.0)
+        return W
 
     def sampler_S(self):
         st = self._c()
@@ -404,10 +436,12 @@ class System:
 
         ``kmodes=(m, c)`` replaces the sampled k-batch (enumeration mode).
         Returns a dict with total F (of ``sel``), near (uncorrected), far, Fcorr
-        and, if ``energy``, [U_N, U_F*, U_self, U_total].
+        and, if ``energy``, [U_N, U_F*, U_self, U_total] and the virial [6]
+        (xx, yy, zz, xy, xz, yz) W = W_N + W_F* of the same estimators (F^corr,
+        not a pair force, has none).
         """
         allsel = np.arange(self.n, dtype=np.int64)
-        Fn_all, En = self.near(allsel, all_shell=all_shell, energy=True)
+        Fn_all, En, Wn = self.near(allsel, all_shell=all_shell, energy=True, virial=True)
         Fcorr = Fn_all.mean(axis=0)
         if kmodes is None:
             m, c, S = self.kbatch()
@@ -423,6 +457,8 @@ class System:
             UN = float(En.sum())
             Us = self.self_energy()
             out["energy"] = np.array([UN, Uf, Us, UN + Uf - Us])
+            out["virial"] = Wn.sum(0) + self.far_virial(m, c, rho)
+            out["virial_near"] = Wn.sum(0)
         return out
 
     # ---- integrators (Sec. 2.3) ----------------------------------------------

@@ -202,6 +202,21 @@ static double sog_fhat(const orc_sys *S, double k2) {
   return pow(2.0 * M_PI, 1.5) * f;
 }
 
+/* dFhat/d(k^2) = -(2 pi)^{3/2} sum_m w_m b^{3m} s^3 (b^{2m} s^2 / 2) e^{-b^{2m} s^2 k^2 / 2},
+ * the derivative the far-field virial needs (strain changes k, not k . r). */
+static double sog_fhat_dk2(const orc_sys *S, double k2) {
+  double f = 0.0;
+  for (int m = 0; m <= S->M; m++) {
+    double a = sog_a(S->b, S->s, m);
+    f -= S->w[m] * pow(S->b, 3.0 * m) * S->s * S->s * S->s * (a / 2.0) * exp(-a * k2 / 2.0);
+  }
+  return pow(2.0 * M_PI, 1.5) * f;
+}
+
+void orc_sog_fhat_dk2(const orc_sys *S, int64_t n, const double *k2, double *out) {
+  for (int64_t i = 0; i < n; i++) out[i] = sog_fhat_dk2(S, k2[i]);
+}
+
 void orc_sog_fhat(const orc_sys *S, int64_t n, const double *k2, double *out) {
   for (int64_t i = 0; i < n; i++) out[i] = sog_fhat(S, k2[i]);
 }
@@ -430,10 +445,16 @@ int orc_lists(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t cap_co
  * (uncorrected), with pair displacements r_ij from the 32-bit fixed-point
  * minimum image, r_ij = (int32)(u_i - u_j) * (L / 2^32).  With all_shell != 0
  * the whole shell is taken with weight 1 (the deterministic r_shell-cutoff
- * force).  Per-atom energy: 1/2 of the same weighted pair sum.            */
+ * force).  Per-atom energy: 1/2 of the same weighted pair sum; per-atom
+ * virial W[q][6] (xx, yy, zz, xy, xz, yz): 1/2 of the same weighted sum of
+ * r_ij (x) f_ij (the pair virial, whose sum over atoms is -dU_N/d strain).  */
 #define ORC_CAP 4096
+static void add_virial(double *w, const double *d, double phi) {
+  w[0] += d[0] * phi * d[0]; w[1] += d[1] * phi * d[1]; w[2] += d[2] * phi * d[2];
+  w[3] += d[0] * phi * d[1]; w[4] += d[0] * phi * d[2]; w[5] += d[1] * phi * d[2];
+}
 int orc_near(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t all_shell,
-             double *F, double *E) {
+             double *F, double *E, double *W) {
   orc_geo G;
   geo_init(S, &G);
   int status = ORC_OK;
@@ -455,6 +476,7 @@ int orc_near(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t all_she
       const uint32_t *ui = G.u + 3 * i;
       const int si = S->species[i];
       double fc[3] = {0, 0, 0}, fs[3] = {0, 0, 0}, ec = 0.0, es = 0.0;
+      double wc[6] = {0, 0, 0, 0, 0, 0}, ws[6] = {0, 0, 0, 0, 0, 0};
       for (int k = 0; k < nc; k++) {
         const int64_t j = cc[k].j;
         const uint32_t *uj = G.u + 3 * j;
@@ -464,6 +486,7 @@ int orc_near(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t all_she
         pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
         for (int a = 0; a < 3; a++) fc[a] += phi * d[a];
         ec += e;
+        add_virial(wc, d, phi);
       }
       int nb;
       double wgt;
@@ -484,9 +507,12 @@ int orc_near(const orc_sys *S, const int64_t *sel, int64_t nsel, int32_t all_she
         pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
         for (int a = 0; a < 3; a++) fs[a] += phi * d[a];
         es += e;
+        add_virial(ws, d, phi);
       }
       for (int a = 0; a < 3; a++) F[3 * q + a] = fc[a] + wgt * fs[a];
       if (E) E[q] = 0.5 * (ec + wgt * es);
+      if (W)
+        for (int c = 0; c < 6; c++) W[6 * q + c] = 0.5 * (wc[c] + wgt * ws[c]);
     }
     free(cc); free(ss); free(tt);
   }
@@ -551,7 +577,7 @@ int orc_lists_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, in
  * above); all_shell != 0 takes the whole of B_i with weight 1.  Per-atom
  * energy: 1/2 of the same weighted pair sum.                               */
 int orc_near_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int64_t nsel,
-                  int32_t all_shell, double *F, double *E) {
+                  int32_t all_shell, double *F, double *E, double *W) {
   orc_geo Gb, Gn;
   geo_init_at(S, pos_b, S->r_shell + S->skin, &Gb);
   geo_init_at(S, S->pos, S->r_shell, &Gn);
@@ -574,6 +600,7 @@ int orc_near_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int
       const uint32_t *ui = Gn.u + 3 * i;
       const int si = S->species[i];
       double fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0}, ea = 0.0, eb = 0.0;
+      double wa[6] = {0, 0, 0, 0, 0, 0}, wb[6] = {0, 0, 0, 0, 0, 0};
       for (int k = 0; k < n_a; k++) {
         const int64_t j = aa[k].j;
         const uint32_t *uj = Gn.u + 3 * j;
@@ -584,6 +611,7 @@ int orc_near_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int
         pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
         for (int a = 0; a < 3; a++) fa[a] += phi * d[a];
         ea += e;
+        add_virial(wa, d, phi);
       }
       int m;
       double wgt;
@@ -605,9 +633,12 @@ int orc_near_skin(const orc_sys *S, const double *pos_b, const int64_t *sel, int
         pair_terms(S, si, S->species[j], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &phi, &e);
         for (int a = 0; a < 3; a++) fb[a] += phi * d[a];
         eb += e;
+        add_virial(wb, d, phi);
       }
       for (int a = 0; a < 3; a++) F[3 * q + a] = fa[a] + wgt * fb[a];
       if (E) E[q] = 0.5 * (ea + wgt * eb);
+      if (W)
+        for (int c = 0; c < 6; c++) W[6 * q + c] = 0.5 * (wa[c] + wgt * wb[c]);
     }
     free(aa); free(bb); free(tt);
   }

@@ -156,7 +156,13 @@ int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind);
  *          sampled estimators of Eqs. (short2), (UF): U_N = 1/2 sum_i
  *          (sum_core e_ij + N_shell/P_R sum_B e_ij), U_F* = k_e S/(2 V P_F)
  *          sum_p |rho_p|^2/|k_p|^2, U_self = k_e/2 sum_i q_i^2 sum_m w_m
- *   virial reserved, must be NULL.
+ *   virial [6] FP64 [eV] = (W_xx, W_yy, W_zz, W_xy, W_xz, W_yz), minus the
+ *          derivative of U_N + U_F* under a homogeneous strain of positions
+ *          and box, with the same samples: W_N = 1/2 sum_i (sum_core
+ *          r_ij (x) f_ij + N_shell/P_R sum_B r_ij (x) f_ij) and W_F* =
+ *          delta U_F* + (k_e/V) sum_p c_p (Fhat'/Fhat)(|k_p|^2) k_p (x) k_p
+ *          |rho_p|^2; F^corr, not a pair force, has none.  The pressure is
+ *          (2 E_kin + tr W) / (3V).
  * Synchronous for host outputs.  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL,
  * RBSOG_E_CAP_OVERFLOW, RBSOG_E_CUDA. */
 int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double *virial,

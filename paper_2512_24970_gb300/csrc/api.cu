@@ -115,7 +115,10 @@ int check_launch(rbsog_ctx *ctx) {
 // branches join for the total force and the closing half kick.  With kept
 // lists, v.build selects binning + list build + evaluation, else the
 // evaluation of the last build's lists alone.
-int run_force(rbsog_ctx *ctx, const View &v, int mode, int step_off, bool energy) {
+int run_force(rbsog_ctx *ctx, const View &v0, int mode, int step_off, bool energy) {
+  View v = v0;                     // energy evaluations also carry the virial partials
+  v.npart = energy ? rb::NEAR_NPART : 4;
+  v.want_vir = energy ? 1 : 0;
   // with kept lists the far-field branch is the longer one: its kernels take
   // free SM slots first (priorities are kept as node priorities in the graph)
   cudaStream_t st = ctx->st, st2 = v.kept ? ctx->st2_hi : ctx->st2;
@@ -237,7 +240,7 @@ int ensure_kcap(rbsog_ctx *ctx, int P) {
       (rc = dalloc(ctx, &v.rho, 2 * (size_t)P)) || (rc = dalloc(ctx, &v.uf, P)) ||
       (rc = dalloc(ctx, &v.kff, P)) || (rc = dalloc(ctx, &v.kfB, P)) ||
       (rc = dalloc(ctx, &v.kfd, 5 * (size_t)P)) ||
-      (rc = dalloc(ctx, &v.rho_part, 2 * (size_t)P * (size_t)v.ntile)))
+      (rc = dalloc(ctx, &v.rho_part, 2 * (size_t)P * (size_t)v.ntile)) || (rc = dalloc(ctx, &v.vf, P)))
     return rc;
   ctx->Pmax = P;
   return RBSOG_OK;
@@ -474,9 +477,9 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.perm, NS)) || (rc = dalloc(ctx, &v.slot_of, N)) ||
       (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) ||
       (rc = dalloc(ctx, &v.chunk_info, (size_t)v.nblk_near * rb::NEAR_WARPS)) || (rc = dalloc(ctx, &v.sx, NS)) ||
-      (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, 4 * (size_t)v.nblk_near * rb::NEAR_WARPS)) ||
-      (rc = dalloc(ctx, &v.corr_part, 4 * 64)) || (rc = dalloc(ctx, &v.corr_ticket, 1)) ||
-      (rc = dalloc(ctx, &v.red, 8)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
+      (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, (size_t)rb::NEAR_NPART * v.nblk_near * rb::NEAR_WARPS)) ||
+      (rc = dalloc(ctx, &v.corr_part, (size_t)rb::NEAR_NPART * 64)) || (rc = dalloc(ctx, &v.corr_ticket, 1)) ||
+      (rc = dalloc(ctx, &v.red, 24)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
       (rc = dalloc(ctx, &wa, (size_t)v.G)) || (rc = dalloc(ctx, &w, (size_t)v.G)) || (rc = dalloc(ctx, &h2, (size_t)v.G)) ||
       (rc = dalloc(ctx, &gtab, rb::NT_TAB)) || (rc = dalloc(ctx, &ftab, rb::NT_TAB)) ||
@@ -554,7 +557,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(up(nmax, samp.nmax.data(), sizeof(int) * samp.nmax.size()));
   CK(cudaMemsetAsync(v.err, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(v.step, 0, sizeof(long long), ctx->st));
-  CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 8, ctx->st));
+  CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 24, ctx->st));
   CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(v.lflag, 0, sizeof(int), ctx->st));
@@ -583,12 +586,12 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
                          int ptr_kind) {
   if (!ctx) return RBSOG_E_INVAL;
   if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
-  if (virial) return fail(ctx, RBSOG_E_INVAL, "virial output is not provided");
   int rc;
+  const bool ev = energy != nullptr || virial != nullptr;
   if ((rc = enter(ctx))) return rc;
   View vv;
   if ((rc = eval_view(ctx, vv))) return rc;
-  if ((rc = run_force(ctx, vv, 0, 0, energy != nullptr))) return rc;
+  if ((rc = run_force(ctx, vv, 0, 0, ev))) return rc;
   ctx->forces_valid = true;
   ctx->lists_valid = true;
   if (forces) {
@@ -596,15 +599,24 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
     else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind);
     if (rc) return rc;
   }
-  if (energy) {
-    double red[8];
+  if (ev) {
+    double red[24];
     CK(cudaMemcpyAsync(red, ctx->v.red, sizeof(red), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     const double e[4] = {red[3], red[4], ctx->self_energy, red[3] + red[4] - ctx->self_energy};
-    if (ptr_kind == RBSOG_PTR_HOST) std::memcpy(energy, e, sizeof(e));
-    else CK(cudaMemcpyAsync(energy, e, sizeof(e), cudaMemcpyHostToDevice, ctx->st));
+    double w[6];
+    for (int c = 0; c < 6; c++) w[c] = red[5 + c] + red[11 + c];   // W_N + W_F*
+    if (energy) {
+      if (ptr_kind == RBSOG_PTR_HOST) std::memcpy(energy, e, sizeof(e));
+      else CK(cudaMemcpyAsync(energy, e, sizeof(e), cudaMemcpyHostToDevice, ctx->st));
+    }
+    if (virial) {
+      if (ptr_kind == RBSOG_PTR_HOST) std::memcpy(virial, w, sizeof(w));
+      else CK(cudaMemcpyAsync(virial, w, sizeof(w), cudaMemcpyHostToDevice, ctx->st));
+    }
+    if (ptr_kind != RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));   // e, w are on this stack
   }
-  if (ptr_kind == RBSOG_PTR_HOST || energy) {
+  if (ptr_kind == RBSOG_PTR_HOST || ev) {
     if ((rc = read_err(ctx))) return rc;
   }
   return leave(ctx);

@@ -102,41 +102,48 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
 // result does not depend on which block finishes when.
 constexpr int CORR_BLOCKS = 64;
 __device__ void corr_block(const View &p, int blk, int step_off) {
-  __shared__ double red[4][256];
+  // p.npart partials per warp: sum F_N (3), U_N and, in energy evaluations,
+  // the pair virial (6)
+  __shared__ double red[NEAR_NPART][256];
   __shared__ bool last;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, nv = p.npart;
   const int np = p.nblk_near * NEAR_WARPS;
   const int per = (np + CORR_BLOCKS - 1) / CORR_BLOCKS;
   const int b0 = blk * per, b1 = min(b0 + per, np);
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  double f[NEAR_NPART] = {};
   for (int b = b0 + t; b < b1; b += 256)
-    for (int a = 0; a < 4; a++) f[a] += p.near_part[4 * b + a];
-  for (int a = 0; a < 4; a++) red[a][t] = f[a];
+#pragma unroll
+    for (int a = 0; a < NEAR_NPART; a++)
+      if (a < nv) f[a] += p.near_part[(int64_t)nv * b + a];
+#pragma unroll
+  for (int a = 0; a < NEAR_NPART; a++) red[a][t] = f[a];
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (t < o)
-      for (int a = 0; a < 4; a++) red[a][t] += red[a][t + o];
+      for (int a = 0; a < nv; a++) red[a][t] += red[a][t + o];
     __syncthreads();
   }
-  if (t < 4) p.corr_part[4 * blk + t] = red[t][0];
+  if (t < nv) p.corr_part[NEAR_NPART * blk + t] = red[t][0];
   __threadfence();
   __syncthreads();
   if (t == 0) last = (atomicAdd(p.corr_ticket, 1u) == CORR_BLOCKS - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // the CORR_BLOCKS block sums, one per thread, then the same fixed tree
-  static_assert(4 * CORR_BLOCKS == 256, "one block sum per thread");
-  red[t & 3][t >> 2] = __ldcg(p.corr_part + 4 * (t >> 2) + (t & 3));
+  // the CORR_BLOCKS block sums of each value, one per thread, then a fixed tree
+  static_assert(CORR_BLOCKS <= 256, "one block sum per thread");
+  for (int a = 0; a < nv; a++) red[a][t] = t < CORR_BLOCKS ? __ldcg(p.corr_part + NEAR_NPART * t + a) : 0.0;
   __syncthreads();
   for (int o = CORR_BLOCKS / 2; o > 0; o >>= 1) {
-    if (t < 4 * o) red[t & 3][t >> 2] += red[t & 3][(t >> 2) + o];
+    if (t < o)
+      for (int a = 0; a < nv; a++) red[a][t] += red[a][t + o];
     __syncthreads();
   }
-  if (t < 4) {
+  if (t < nv) {
     const double v = red[t][0];
     if (t < 3) p.red[t] = v / (double)p.n;
-    else p.red[3] = v;
+    else if (t == 3) p.red[3] = v;
+    else p.red[5 + (t - 4)] = v;                  // W_N
   }
   if (t == 0) *p.corr_ticket = 0u;                // ready for the next evaluation
 }
@@ -190,16 +197,46 @@ __global__ void __launch_bounds__(256) k_reduce(View p, int nkb, int step_off) {
         o[0] = kx; o[1] = ky; o[2] = kz; o[3] = A; o[4] = B;
       }
       p.uf[k] = c * (sr0 * sr0 + si0 * si0);
+      if (p.want_vir) {
+        // (Fhat'/Fhat)(k^2) of the SOG transform, a_m = (b^m s)^2 = 1 / (2 h_m):
+        // Fhat ~ sum_m w_m a_m^{3/2} e^{-a_m k^2/2}, Fhat' ~ -sum_m w_m a_m^{3/2} (a_m/2) e^{-a_m k^2/2}
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        double num = 0.0, den = 0.0;
+        for (int g = 0; g < p.G; g++) {
+          const double a = 0.5 / p.sog_h[g];
+          const double t = p.sog_w[g] * a * sqrt(a) * exp(-0.5 * a * k2);
+          den += t;
+          num += 0.5 * a * t;
+        }
+        p.vf[k] = -c * (num / den) * (sr0 * sr0 + si0 * si0);
+      }
     }
   }
 }
 
 // Energies: U_F* = k_e/(2V) sum_p c_p |rho_p|^2 (fixed order); U_self is host-side.
+// The far-field virial, minus the strain derivative of U_F* (k . r does not
+// change, k_a -> k_a - eps_ab k_b, V -> V (1 + tr eps)):
+//   W_F,ab = delta_ab U_F* + (k_e/V) sum_p c_p (Fhat'/Fhat)(k_p^2) k_pa k_pb |rho_p|^2.
 __global__ void k_energy(View p) {
   if (threadIdx.x != 0) return;
   double u = 0.0;
-  for (int k = 0; k < p.P; k++) u += p.uf[k];
-  p.red[4] = KE / (2.0 * p.V) * u;
+  double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < p.P; k++) {
+    u += p.uf[k];
+    if (p.want_vir) {
+      const int4 m = p.km[k];
+      const double ka[3] = {TWO_PI * (double)m.x / p.L[0], TWO_PI * (double)m.y / p.L[1],
+                            TWO_PI * (double)m.z / p.L[2]};
+      const double v = p.vf[k];
+      w[0] += v * ka[0] * ka[0]; w[1] += v * ka[1] * ka[1]; w[2] += v * ka[2] * ka[2];
+      w[3] += v * ka[0] * ka[1]; w[4] += v * ka[0] * ka[2]; w[5] += v * ka[1] * ka[2];
+    }
+  }
+  const double U = KE / (2.0 * p.V) * u;
+  p.red[4] = U;
+  if (p.want_vir)
+    for (int c = 0; c < 6; c++) p.red[11 + c] = KE / p.V * w[c] + (c < 3 ? U : 0.0);
 }
 
 template <typename R>

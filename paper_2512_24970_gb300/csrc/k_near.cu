@@ -61,10 +61,12 @@ struct PairOut {
   float fx, fy, fz, e;
 };
 
+// With ENERGY also the pair energy and the pair virial r_ij (x) f_ij
+// (xx, yy, zz, xy, xz, yz) into wv.
 template <bool ENERGY>
 __device__ __forceinline__ void pair_mixed(const View &p, const PairF &q, const float4 *gt,
                                            uint4 ui, uint4 uj, float &fx, float &fy, float &fz,
-                                           float &e) {
+                                           float &e, float *wv) {
   float d[3];
   const uint32_t a3[3] = {ui.x - uj.x, ui.y - uj.y, ui.z - uj.z};
 #pragma unroll
@@ -95,13 +97,16 @@ __device__ __forceinline__ void pair_mixed(const View &p, const PairF &q, const 
     const float4 cf = p.ftab[it];
     const float Fv = __fmaf_rn(__fmaf_rn(__fmaf_rn(cf.w, f, cf.z), f, cf.y), f, cf.x);
     e += q.kqq * (rinv - Fv) + q.A * ex - (q.C + q.D * rinv2) * r4 * rinv2;
+    const float f0 = phi * d[0], f1 = phi * d[1], f2 = phi * d[2];
+    wv[0] += d[0] * f0; wv[1] += d[1] * f1; wv[2] += d[2] * f2;
+    wv[3] += d[0] * f1; wv[4] += d[0] * f2; wv[5] += d[1] * f2;
   }
 }
 
 template <bool ENERGY>
 __device__ __forceinline__ void pair_fp64(const View &p, const PairD &q, const double *wa,
                                           const double *w, const double *h2, uint4 ui, uint4 uj,
-                                          double &fx, double &fy, double &fz, double &e) {
+                                          double &fx, double &fy, double &fz, double &e, double *wv) {
   const double dx = (double)(int)(ui.x - uj.x) * p.hd[0];
   const double dy = (double)(int)(ui.y - uj.y) * p.hd[1];
   const double dz = (double)(int)(ui.z - uj.z) * p.hd[2];
@@ -119,7 +124,12 @@ __device__ __forceinline__ void pair_fp64(const View &p, const PairD &q, const d
   fx += phi * dx;
   fy += phi * dy;
   fz += phi * dz;
-  if (ENERGY) e += q.kqq * (1.0 / r - fsum) + rep - q.C / r6 - q.D / r8;
+  if (ENERGY) {
+    e += q.kqq * (1.0 / r - fsum) + rep - q.C / r6 - q.D / r8;
+    const double f0 = phi * dx, f1 = phi * dy, f2 = phi * dz;
+    wv[0] += dx * f0; wv[1] += dy * f1; wv[2] += dz * f2;
+    wv[3] += dx * f1; wv[4] += dx * f2; wv[5] += dy * f2;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -152,6 +162,7 @@ __device__ __forceinline__ void floyd(const View &p, long long s, uint32_t id, i
 template <typename R>
 struct Acc {
   R x = 0, y = 0, z = 0, e = 0;
+  R w[6] = {0, 0, 0, 0, 0, 0};   // pair virial (energy evaluations only)
 };
 
 // Pair force of atom i with the sorted candidate uj (species in its top bits).
@@ -160,7 +171,7 @@ __device__ __forceinline__ void add_pair(const View &p, const PairF *spf, const 
                                          const float4 *sg, const double *swa, const double *sw,
                                          const double *sh2, int spi, uint4 ui, uint4 uj, Acc<R> &a) {
   const int spj = (int)(uj.w >> SU_SP_SHIFT);
-  if (sizeof(R) == 4) {
+  if constexpr (sizeof(R) == 4) {
     float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     // the pair record through the read-only cache (three 16-byte loads)
     const float4 *src = reinterpret_cast<const float4 *>(spf + spi * p.ns + spj);
@@ -169,11 +180,11 @@ __device__ __forceinline__ void add_pair(const View &p, const PairF *spf, const 
     q.kqq = r0.x; q.Ar = r0.y; q.lr = r0.z; q.sig = r0.w;
     q.C6 = r1.x; q.D8 = r1.y; q.A = r1.z; q.C = r1.w;
     q.D = r2.x;
-    pair_mixed<ENERGY>(p, q, sg, ui, uj, a0, a1, a2, a3);
+    pair_mixed<ENERGY>(p, q, sg, ui, uj, a0, a1, a2, a3, a.w);
     a.x += a0; a.y += a1; a.z += a2; a.e += a3;
   } else {
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    pair_fp64<ENERGY>(p, spd[spi * p.ns + spj], swa, sw, sh2, ui, uj, a0, a1, a2, a3);
+    pair_fp64<ENERGY>(p, spd[spi * p.ns + spj], swa, sw, sh2, ui, uj, a0, a1, a2, a3, a.w);
     a.x += a0; a.y += a1; a.z += a2; a.e += a3;
   }
 }
@@ -280,10 +291,10 @@ __device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *
 
 // One partial per warp of sum F_N and of the pair energy (FP32 sums of the
 // warp's eight atoms in mixed precision, FP64 otherwise).
-template <bool MIX>
-__device__ __forceinline__ void warp_partials(const View &p, double part[4], int warp, int lane) {
+template <bool MIX, int NP>
+__device__ __forceinline__ void warp_partials(const View &p, double part[NEAR_NPART], int warp, int lane) {
 #pragma unroll
-  for (int c = 0; c < 4; c++) {
+  for (int c = 0; c < NP; c++) {
     if (MIX) {
       float f = (float)part[c];
       for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
@@ -293,8 +304,9 @@ __device__ __forceinline__ void warp_partials(const View &p, double part[4], int
     }
   }
   if (lane == 0) {
-    double *d = p.near_part + 4 * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
-    d[0] = part[0]; d[1] = part[1]; d[2] = part[2]; d[3] = part[3];
+    double *d = p.near_part + NP * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
+#pragma unroll
+    for (int c = 0; c < NP; c++) d[c] = part[c];
   }
 }
 
@@ -303,7 +315,7 @@ __device__ __forceinline__ void warp_partials(const View &p, double part[4], int
 // terms.
 template <typename R, bool ENERGY>
 __device__ __forceinline__ void combine_atom(const View &p, Acc<R> &fc, Acc<R> &fs, R wgt, bool active,
-                                             int g, uint4 ui, double part[4]) {
+                                             int g, uint4 ui, double part[NEAR_NPART]) {
 #pragma unroll
   for (int o = 1; o < TPA; o <<= 1) {
     fc.x += __shfl_xor_sync(0xffffffffu, fc.x, o, TPA);
@@ -315,6 +327,11 @@ __device__ __forceinline__ void combine_atom(const View &p, Acc<R> &fc, Acc<R> &
     if (ENERGY) {
       fc.e += __shfl_xor_sync(0xffffffffu, fc.e, o, TPA);
       fs.e += __shfl_xor_sync(0xffffffffu, fs.e, o, TPA);
+#pragma unroll
+      for (int c = 0; c < 6; c++) {
+        fc.w[c] += __shfl_xor_sync(0xffffffffu, fc.w[c], o, TPA);
+        fs.w[c] += __shfl_xor_sync(0xffffffffu, fs.w[c], o, TPA);
+      }
     }
   }
   if (active && g == 0) {
@@ -327,6 +344,9 @@ __device__ __forceinline__ void combine_atom(const View &p, Acc<R> &fc, Acc<R> &
     }
     part[0] = (double)Fx; part[1] = (double)Fy; part[2] = (double)Fz;
     part[3] = (double)((R)0.5 * (fc.e + wgt * fs.e));
+    if (ENERGY)
+#pragma unroll
+      for (int c = 0; c < 6; c++) part[4 + c] = (double)((R)0.5 * (fc.w[c] + wgt * fs.w[c]));
   }
 }
 
@@ -369,7 +389,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   const int g = lane % TPA;
   const int nrow = p.nc[1] * p.nc[2];
   const int chunk = blockIdx.x * NEAR_WARPS + warp;
-  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  double part[NEAR_NPART] = {};
   if (chunk < p.row_chunk[nrow]) {
     // ---- the chunk ------------------------------------------------------------
     const int2 cinfo = p.chunk_info[chunk];   // (row of cells, first slot)
@@ -778,7 +798,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   if constexpr (BUILD) return;
   // ---- partials of sum F_N and of the pair energy, one per warp (FP32 sums of
   // the warp's eight atoms in mixed precision, FP64 otherwise) ----------------
-  warp_partials<MIX>(p, part, warp, lane);
+  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, warp, lane);
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
@@ -831,7 +851,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
   const bool active = ui.w != SU_PAD;
   const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
   const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
-  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  double part[NEAR_NPART] = {};
   Acc<R> fa, fb;
   // ---- A, exactly, dealt round-robin over the atom's threads ---------------
   const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
@@ -892,7 +912,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
       if (js[i] >= 0 && in_shell(p, ui, uj[i])) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fb);
   }
   combine_atom<R, ENERGY>(p, fa, fb, wgt, active, g, ui, part);
-  warp_partials<sizeof(R) == 4>(p, part, warp, lane);
+  warp_partials<sizeof(R) == 4, ENERGY ? NEAR_NPART : 4>(p, part, warp, lane);
 }
 
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy) {

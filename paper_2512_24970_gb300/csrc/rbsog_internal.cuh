@@ -21,6 +21,7 @@ constexpr int PREP_BLOCK = 128;    // threads per block of k_prepare and k_finis
 constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
 constexpr int NEAR_CHUNK = 8;      // atoms per warp of the near-field kernel (4 threads each)
 constexpr int NEAR_WARPS = 4;      // warps per near-field block
+constexpr int NEAR_NPART = 10;     // per-warp partials: sum F_N (3), U_N, pair virial (6)
 constexpr int RHO_BLOCK = 256;     // threads per block of the structure-factor kernel
 constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernel
 constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernel
@@ -112,7 +113,10 @@ struct View {
   float *sx, *sy, *sz;    // [nslot] 23-bit coordinates v = u >> 9 as exact floats
   uint4 *su;              // [nslot] (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
   int nslot;              // n + 3 * ncell
-  double *near_part;      // [nblk_near * NEAR_WARPS][4]: sum F_N (x,y,z), sum pair energy per warp
+  double *near_part;      // [nblk_near * NEAR_WARPS][npart]: sum F_N (x,y,z), pair energy, pair virial (6)
+  int npart;              // partials per warp: 4, or NEAR_NPART in energy evaluations
+  int want_vir;           // energy evaluation: also the far-field virial terms
+  double *vf;             // [Pmax] c_p (Fhat'/Fhat)(k_p^2) |rho_p|^2 (energy evaluations)
   double *corr_part;      // [64][4] block sums of near_part
   unsigned *corr_ticket;  // blocks of the F^corr reduction done (reset by the last)
   // far field
@@ -124,7 +128,7 @@ struct View {
   float4 *kff;            // [Pmax] mixed (k_x, k_y, k_z, c_p Im rho_p)
   float *kfB;             // [Pmax] mixed c_p Re rho_p
   double *kfd;            // [Pmax][5] FP64 (k_x, k_y, k_z, c Im rho, c Re rho)
-  double *red;            // [8]: F^corr (3), U_N, U_F*, spare
+  double *red;            // [24]: F^corr (3), U_N, U_F*, W_N (6) at 5, W_F* (6) at 11
   int *err;
   long long *step;
   // tables

@@ -231,17 +231,19 @@ class Context:
         ptr, kind = _ptr_kind(vel)
         self._ck(self._L.rbsog_set_velocities(self.h, ptr, kind))
 
-    def compute_forces(self, forces=None, energy=False):
+    def compute_forces(self, forces=None, energy=False, virial=False):
         """Forces [n,3] FP64 (numpy unless ``forces`` is a CUDA tensor to fill)
-        and, if ``energy``, the energy 4-vector."""
+        and, if asked, the energy 4-vector and the virial 6-vector
+        (xx, yy, zz, xy, xz, yz): returns F, (F, E), (F, W) or (F, E, W)."""
         out = np.zeros((self.n, 3)) if forces is None else forces
         ptr, kind = _ptr_kind(out)
+        if (energy or virial) and kind == PTR_DEVICE:
+            raise ValueError("energy or virial output with device forces: call again with host arrays")
         e = np.zeros(4) if energy else None
-        self._ck(self._L.rbsog_compute_forces(self.h, ptr, _np_ptr(e) if energy and kind == PTR_HOST else None,
-                                              None, kind))
-        if energy and kind == PTR_DEVICE:
-            raise ValueError("energy output with device forces: call again with host arrays")
-        return (out, e) if energy else out
+        wv = np.zeros(6) if virial else None
+        self._ck(self._L.rbsog_compute_forces(self.h, ptr, _np_ptr(e), _np_ptr(wv), kind))
+        res = (out,) + ((e,) if energy else ()) + ((wv,) if virial else ())
+        return res if len(res) > 1 else out
 
     def step(self, nsteps: int):
         self._ck(self._L.rbsog_step(self.h, int(nsteps)))

@@ -196,3 +196,18 @@ def test_kept_auto_rebuild_trajectory(rb, orc, precision):
             have = set(g["A"][q, :g["nA"][q]].tolist()) | set(g["B"][q, :g["nB"][q]].tolist())
             need = set(Lr["core"][q, :Lr["ncore"][q]].tolist()) | set(Lr["shell"][q, :Lr["nshell"][q]].tolist())
             assert need <= have
+
+
+def test_kept_virial(rb, orc):
+    """The virial of the kept-list estimator, FP64, three steps after the build."""
+    w = W.rock_salt((9, 9, 9), seed=5)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, S = setup_kept(rb, orc, w, list_every=10, P_F=300)
+    ctx.set_velocities(v0)
+    ctx.step(3)
+    pos, vel, step = ctx.get_state()
+    Fg, Eg, Wg = ctx.compute_forces(energy=True, virial=True)
+    S.build_pos = w.pos.copy()
+    S.pos, S.step = pos, step
+    o = S.forces(energy=True)
+    assert float(np.abs(Wg - o["virial"]).max() / np.abs(o["virial"]).max()) < 1e-11

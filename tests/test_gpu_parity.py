@@ -230,3 +230,36 @@ def test_device_phase_factors(rb):
     es, ec = s - np.sin(ang), c - np.cos(ang)
     assert np.abs(es).max() < 2.5e-7 and np.abs(ec).max() < 2.5e-7
     assert abs(es.mean()) < 1e-9 and abs(ec.mean()) < 1e-9
+
+
+def virial_err(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_virial(rb, orc, case):
+    """Virial W_N + W_F* (xx, yy, zz, xy, xz, yz) of the same samples as the
+    oracle's: FP64 within 1e-11 of its largest component."""
+    w = CASES[case]()
+    ctx, S = setup_pair(rb, orc, w, P_F=300, step=2)
+    Fg, Eg, Wg = ctx.compute_forces(energy=True, virial=True)
+    o = S.forces(energy=True)
+    assert virial_err(Wg, o["virial"]) < 1e-11, (Wg, o["virial"])
+    assert rms_rel(Fg, o["F"]) < FP64_TOL
+
+
+def test_virial_mixed_and_deterministic(rb, orc):
+    """Mixed precision within 1e-5; the deterministic limit (whole shell, all k
+    weighted Fhat) in both precisions."""
+    w = W.rock_salt((6, 5, 7), seed=3, composition="LiCl-NaCl")
+    ctx, S = setup_pair(rb, orc, w, P_F=300, precision=rb.MIXED, step=4)
+    _, Wg = ctx.compute_forces(virial=True)
+    assert virial_err(Wg, S.forces(energy=True)["virial"]) < MIXED_TOL
+    m, c = S.enumerated_modes(10)
+    ref = S.forces(kmodes=(m, c), all_shell=True, energy=True)["virial"]
+    for prec, tol in ((rb.FP64, 1e-11), (rb.MIXED, MIXED_TOL)):
+        ctx, _ = setup_pair(rb, orc, w, precision=prec, step=4)
+        ctx.debug_whole_shell(True)
+        ctx.debug_set_kbatch(m, c)
+        _, Wd = ctx.compute_forces(virial=True)
+        assert virial_err(Wd, ref) < tol, (prec, Wd, ref)

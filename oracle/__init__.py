@@ -30,6 +30,56 @@ FCONV = 9648.53321          # (eV / Angstrom) / amu -> Angstrom / ps^2
 
 INTEGRATOR_NVE_VV = 0
 INTEGRATOR_LANGEVIN_BAOAB = 1
+INTEGRATOR_NOSE_HOOVER = 2
+
+
+class NHChain:
+    """Nose-Hoover chain thermostat of length M (Martyna, Tuckerman, Klein,
+    Mol. Phys. 87 (1996) 1117), the NVT thermostat of the paper's production
+    runs (Sec. 3).  Masses Q_0 = g kT tau^2, Q_j = kT tau^2; forces on the
+    chain G_0 = (2K - g kT)/Q_0, G_j = (Q_{j-1} v_{j-1}^2 - kT)/Q_j.  One half
+    step of length d = dt/2 (one Trotter stage, no Suzuki-Yoshida weights):
+    the chain from its end to v_0 (each v_j damped by e^{-d v_{j+1}/4} before
+    and after its kick d G_j / 2), the velocity scale s = e^{-d v_0}, the
+    positions eta_j += d v_j, then the chain back from v_0 to its end.
+    K in eV, v_j in 1/ps."""
+
+    def __init__(self, M, T, tdamp, ndof):
+        self.M, self.g = int(M), float(ndof)
+        self.kT = KB * float(T)
+        self.Q = np.array([self.g * self.kT * tdamp ** 2] + [self.kT * tdamp ** 2] * (self.M - 1))
+        self.eta = np.zeros(self.M)
+        self.v = np.zeros(self.M)
+
+    def _G(self, j, k2):
+        if j == 0:
+            return (k2 - self.g * self.kT) / self.Q[0]
+        return (self.Q[j - 1] * self.v[j - 1] ** 2 - self.kT) / self.Q[j]
+
+    def _kick(self, j, k2, d):
+        if j + 1 < self.M:
+            x = np.exp(-0.25 * d * self.v[j + 1])
+            self.v[j] = (self.v[j] * x + 0.5 * d * self._G(j, k2)) * x
+        else:
+            self.v[j] += 0.5 * d * self._G(j, k2)
+
+    def half_step(self, k2, dt):
+        """k2 = sum_i m_i v_i^2 in eV (twice the kinetic energy); returns the
+        factor that scales every velocity."""
+        d = 0.5 * dt
+        for j in range(self.M - 1, -1, -1):
+            self._kick(j, k2, d)
+        s = float(np.exp(-d * self.v[0]))
+        k2 *= s * s
+        self.eta += d * self.v
+        for j in range(self.M):
+            self._kick(j, k2, d)
+        return s
+
+    def energy(self):
+        """Thermostat part of the conserved quantity."""
+        return float(0.5 * (self.Q * self.v ** 2).sum() + self.g * self.kT * self.eta[0]
+                     + self.kT * self.eta[1:].sum())
 
 
 def build(force: bool = False) -> str:
@@ -471,19 +521,30 @@ class System:
         return np.stack([r1 * np.cos(2.0 * np.pi * u[:, 1]), r1 * np.sin(2.0 * np.pi * u[:, 1]),
                          r2 * np.cos(2.0 * np.pi * u[:, 3])], axis=1)
 
+    def kinetic2(self, vel):
+        """sum_i m_i v_i^2 in eV."""
+        return float((self.mass[self.species][:, None] * vel ** 2).sum() / FCONV)
+
     def run(self, vel, nsteps, dt, integrator=INTEGRATOR_LANGEVIN_BAOAB, T=1200.0, gamma=1.0,
-            F=None):
+            F=None, tdamp=0.1, nh_chain=3, kmodes=None, all_shell=False):
         """Advance (pos, vel) by ``nsteps``; returns (vel, F).  Forces at step s use
         RNG step index s; the Langevin O-step of the step s -> s+1 uses index s+1.
-        ``gamma`` is the collision rate gamma/m in 1/ps (same for all species)."""
+        ``gamma`` is the collision rate gamma/m in 1/ps (same for all species);
+        Nose-Hoover: chain of ``nh_chain`` with time constant ``tdamp`` [ps], a
+        half step before the first half kick and after the second.  ``kmodes`` /
+        ``all_shell`` as in :meth:`forces` (the deterministic force)."""
         vel = np.array(vel, dtype=np.float64).reshape(-1, 3)
         minv = (FCONV / self.mass[self.species])[:, None]
         if F is None:
-            F = self.forces()["F"]
+            F = self.forces(kmodes=kmodes, all_shell=all_shell)["F"]
         c1 = np.exp(-gamma * dt)
         sig = np.sqrt((1.0 - c1 * c1) * KB * T * FCONV / self.mass[self.species])[:, None]
+        if integrator == INTEGRATOR_NOSE_HOOVER and getattr(self, "chain", None) is None:
+            self.chain = NHChain(nh_chain, T, tdamp, 3 * self.n - 3)
         for _ in range(nsteps):
             nxt = self.step + 1
+            if integrator == INTEGRATOR_NOSE_HOOVER:
+                vel = vel * self.chain.half_step(self.kinetic2(vel), dt)
             vel = vel + 0.5 * dt * F * minv
             if integrator == INTEGRATOR_LANGEVIN_BAOAB:
                 self.pos = self.pos + 0.5 * dt * vel
@@ -500,6 +561,8 @@ class System:
                 if d2.max() > self.displacement_limit2():
                     self.build_pos = self.pos.copy()
                     self.builds += 1
-            F = self.forces()["F"]
+            F = self.forces(kmodes=kmodes, all_shell=all_shell)["F"]
             vel = vel + 0.5 * dt * F * minv
+            if integrator == INTEGRATOR_NOSE_HOOVER:
+                vel = vel * self.chain.half_step(self.kinetic2(vel), dt)
         return vel, F

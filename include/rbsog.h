@@ -62,6 +62,10 @@ extern "C" {
 
 #define RBSOG_NVE_VV 0          /* velocity Verlet */
 #define RBSOG_LANGEVIN_BAOAB 1  /* BAOAB splitting of the Langevin SDE of Sec. 2.3 */
+#define RBSOG_NOSE_HOOVER 2     /* Nose-Hoover chain NVT, the thermostat of the runs of Sec. 3:
+                                   a half step of the chain (Martyna-Tuckerman-Klein splitting,
+                                   masses Q_0 = (3N-3) kT tdamp^2, Q_j = kT tdamp^2) before the
+                                   first and after the second half kick of velocity Verlet */
 
 #define RBSOG_LISTS_AUTO (-1)  /* list_every: rebuild kept lists when an atom moved by skin/2 */
 
@@ -78,6 +82,7 @@ extern "C" {
 #define RBSOG_MAX_SHELL 1024   /* shell neighbours of one atom when the batch is sampled */
 #define RBSOG_MAX_KEPT 512     /* kept lists: members of B (r_core <= r < r_shell + skin) per atom */
 #define RBSOG_MAX_M 128        /* Gaussians m = 0..M */
+#define RBSOG_MAX_NH_CHAIN 8   /* Nose-Hoover chain length */
 
 typedef struct rbsog_ctx rbsog_ctx; /* opaque, library-owned */
 
@@ -113,7 +118,9 @@ typedef struct {
    * (checked every step: RBSOG_E_SKIN with a fixed n).  Needs every box
    * length >= 2 r_list. */
   int32_t list_every;
-  double skin;     /* [A], >= 0; used when list_every >= 1 */
+  double skin;     /* [A], >= 0; used when list_every != 0 */
+  double tdamp;    /* Nose-Hoover time constant [ps] > 0 (RBSOG_NOSE_HOOVER) */
+  int32_t nh_chain;  /* Nose-Hoover chain length, 1..RBSOG_MAX_NH_CHAIN (RBSOG_NOSE_HOOVER) */
 } rbsog_params;
 
 /* Create a context on CUDA device `cuda_device`.  `cuda_stream` is the
@@ -188,6 +195,14 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
 /* Builds of the kept random batch lists since rbsog_set_system (waits for the
  * context's work).  Host pointer. */
 int rbsog_get_list_builds(rbsog_ctx *ctx, int64_t *builds);
+
+/* Nose-Hoover chain state between steps (RBSOG_NOSE_HOOVER): eta[nh_chain]
+ * and its velocities v_eta[nh_chain] [1/ps].  Host pointers; get waits for
+ * the context's work.  set_system starts the chain at rest; together with
+ * rbsog_get_state / rbsog_set_state these make a run resumable bit for bit.
+ * Errors: RBSOG_E_INVAL (another integrator), RBSOG_E_CUDA. */
+int rbsog_get_thermostat(rbsog_ctx *ctx, double *eta, double *v_eta);
+int rbsog_set_thermostat(rbsog_ctx *ctx, const double *eta, const double *v_eta);
 
 /* Wait for the context's work; return the latched device error, if any. */
 int rbsog_sync(rbsog_ctx *ctx);

@@ -38,6 +38,7 @@ struct rbsog_ctx {
   cudaGraphExec_t gexec_keep = nullptr;  // kept lists: the variant that reuses them
   bool graph_ok = false;
   bool lists_valid = false;              // kept lists built since the last set_system / set_state
+  bool nh_primed = false;                // Nose-Hoover: 2K of the current velocities is in the chain state
   int64_t host_step = 0;                 // mirror of the device step counter
   bool own_stream = false;
   bool profiling = false;
@@ -160,6 +161,7 @@ int run_force(rbsog_ctx *ctx, const View &v0, int mode, int step_off, bool energ
   CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[6], st, evflag));
   rb::launch_finish(v, st, mode);
+  if (mode != 0 && v.integ == RBSOG_NOSE_HOOVER) rb::launch_nh_close(v, st);
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[8], st, evflag));
   return check_launch(ctx);
 }
@@ -337,7 +339,11 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   if (P.P_R < 1 || P.P_R > RBSOG_MAX_PR) return fail(ctx, RBSOG_E_INVAL, "P_R out of range");
   if (P.P_F < 1) return fail(ctx, RBSOG_E_INVAL, "P_F out of range");
   if (P.precision != RBSOG_FP64 && P.precision != RBSOG_MIXED) return fail(ctx, RBSOG_E_INVAL, "bad precision");
-  if (P.integrator != RBSOG_NVE_VV && P.integrator != RBSOG_LANGEVIN_BAOAB) return fail(ctx, RBSOG_E_INVAL, "bad integrator");
+  if (P.integrator != RBSOG_NVE_VV && P.integrator != RBSOG_LANGEVIN_BAOAB && P.integrator != RBSOG_NOSE_HOOVER)
+    return fail(ctx, RBSOG_E_INVAL, "bad integrator");
+  if (P.integrator == RBSOG_NOSE_HOOVER &&
+      (!(P.tdamp > 0.0) || P.nh_chain < 1 || P.nh_chain > RBSOG_MAX_NH_CHAIN || !(P.T > 0.0)))
+    return fail(ctx, RBSOG_E_INVAL, "Nose-Hoover needs tdamp > 0, T > 0 and 1 <= nh_chain <= RBSOG_MAX_NH_CHAIN");
   if (P.list_every < RBSOG_LISTS_AUTO) return fail(ctx, RBSOG_E_INVAL, "list_every must be >= -1");
   if (P.list_every != 0 && !(P.skin >= 0.0)) return fail(ctx, RBSOG_E_INVAL, "skin must be >= 0");
   const bool kept = P.list_every != 0;
@@ -443,7 +449,14 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     v.kick[a] = 0.5 * P.dt * rb::FCONV / hm[a];
     v.qfar[a] = -rb::KE * hq[a] / v.V;
     v.sig_ou[a] = std::sqrt(std::max(0.0, (1.0 - v.c1 * v.c1) * rb::KBOLTZ * P.T * rb::FCONV / hm[a]));
+    v.massv[a] = hm[a];
   }
+  v.nh_M = P.integrator == RBSOG_NOSE_HOOVER ? P.nh_chain : 1;
+  v.nh_nblk = (int)((n + rb::PREP_BLOCK - 1) / rb::PREP_BLOCK);
+  v.nh_kT = rb::KBOLTZ * P.T;
+  v.nh_g = 3.0 * (double)n - 3.0;
+  for (int j = 0; j < RBSOG_MAX_NH_CHAIN; j++)
+    v.nh_Q[j] = (j == 0 ? v.nh_g : 1.0) * v.nh_kT * P.tdamp * P.tdamp;
   v.nblk_atoms = (int)((n + 255) / 256);
   v.nblk_kq = (P.P_F + 7) / 8;   // one warp per sample
   // chunks <= n / NEAR_CHUNK + rows; one warp per chunk
@@ -491,6 +504,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
     return rc;
   }
   if ((rc = dalloc(ctx, &v.lflag, 1)) || (rc = dalloc(ctx, &v.nbuild, 1)) ||
+      (rc = dalloc(ctx, &v.nh, rb::NH_STATE)) || (rc = dalloc(ctx, &v.ke_part, (size_t)v.nh_nblk)) ||
       (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
                 (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
     free_system(ctx);
@@ -561,12 +575,14 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(v.lflag, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(v.nh, 0, sizeof(double) * rb::NH_STATE, ctx->st));   // the chain at rest
   CK(cudaMemsetAsync(v.nbuild, 0, sizeof(unsigned long long), ctx->st));
   CK(cudaMemsetAsync(v.slot_of, 0, sizeof(int) * N, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
   ctx->has_system = true;
   ctx->forces_valid = false;
   ctx->lists_valid = false;
+  ctx->nh_primed = false;
   ctx->host_step = 0;
   return leave(ctx);
 }
@@ -579,6 +595,7 @@ int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind) {
   if ((rc = enter(ctx))) return rc;
   if ((rc = import_aos(ctx, vel, ctx->v.v, ptr_kind))) return rc;
   if (ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));
+  ctx->nh_primed = false;
   return leave(ctx);
 }
 
@@ -637,7 +654,8 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
     ctx->lists_valid = true;
   }
   if (!ctx->graph_ok) {
-    const int mode = ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 2;
+    // velocity Verlet (Nose-Hoover: with the chain's half steps) or BAOAB
+    const int mode = ctx->prm.integrator == RBSOG_LANGEVIN_BAOAB ? 2 : 1;
     // variant 0 bins and builds (per-step lists: the only one); variant 1
     // evaluates the kept lists of the last build
     for (int var = 0; var < ((ctx->v.kept && !ctx->v.auto_lists) ? 2 : 1); var++) {
@@ -657,6 +675,11 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
       if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     ctx->graph_ok = true;
+  }
+  if (ctx->prm.integrator == RBSOG_NOSE_HOOVER && !ctx->nh_primed) {
+    rb::launch_nh_prime(ctx->v, ctx->st);   // 2K of the velocities the first half step sees
+    if ((rc = check_launch(ctx))) return rc;
+    ctx->nh_primed = true;
   }
   // kept lists are rebuilt at the steps that are multiples of list_every
   const int64_t every = ctx->prm.list_every;
@@ -700,6 +723,7 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
   CK(cudaStreamSynchronize(ctx->st));
   ctx->forces_valid = false;
   ctx->lists_valid = false;
+  ctx->nh_primed = false;
   ctx->host_step = step;
   return leave(ctx);
 }
@@ -710,6 +734,40 @@ int rbsog_sync(rbsog_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   if (!ctx->has_system) return RBSOG_OK;
   return read_err(ctx);
+}
+
+int rbsog_get_thermostat(rbsog_ctx *ctx, double *eta, double *v_eta) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (ctx->prm.integrator != RBSOG_NOSE_HOOVER) return fail(ctx, RBSOG_E_INVAL, "not a Nose-Hoover run");
+  double h[rb::NH_STATE];
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaMemcpyAsync(h, ctx->v.nh, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int j = 0; j < ctx->v.nh_M; j++) {
+    if (eta) eta[j] = h[rb::NH_A_ETA + j];
+    if (v_eta) v_eta[j] = h[rb::NH_A_V + j];
+  }
+  return RBSOG_OK;
+}
+
+int rbsog_set_thermostat(rbsog_ctx *ctx, const double *eta, const double *v_eta) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (ctx->prm.integrator != RBSOG_NOSE_HOOVER) return fail(ctx, RBSOG_E_INVAL, "not a Nose-Hoover run");
+  if (!eta || !v_eta) return fail(ctx, RBSOG_E_INVAL, "null argument");
+  double h[rb::NH_STATE];
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaMemcpyAsync(h, ctx->v.nh, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int j = 0; j < ctx->v.nh_M; j++) {
+    h[rb::NH_A_ETA + j] = eta[j];
+    h[rb::NH_A_V + j] = v_eta[j];
+  }
+  CK(cudaMemcpyAsync(ctx->v.nh, h, sizeof(h), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->nh_primed = false;
+  return RBSOG_OK;
 }
 
 int rbsog_get_list_builds(rbsog_ctx *ctx, int64_t *builds) {

@@ -10,7 +10,7 @@
 //   k_scatter   counting-sort scatter (slot claimed by atomicAdd).
 //   k_rank      per atom: rank in its cell by (u_x, caller id), the canonical
 //               order of the list -> sorted slot; write the SoA arrays.
-#include "rbsog_internal.cuh"
+#include "nh.cuh"
 
 namespace rb {
 
@@ -107,6 +107,8 @@ template <int MODE>
 __global__ void __launch_bounds__(PREP_BLOCK) k_prepare(View p, int step_off) {
   const long long s = *p.step + step_off;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // Nose-Hoover: the opening half step of the chain, every block alike
+  const double s_open = (MODE == 1 && p.integ == RBSOG_NOSE_HOOVER) ? nh_open(p) : 1.0;
   if (i >= p.n) return;
   const int64_t n = p.n;
   const int sp = p.spc[i];
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_prepare(View p, int step_off) {
       F[0] = p.Ff[i]; F[1] = p.Ff[n + i]; F[2] = p.Ff[2 * n + i];
     }
     const double kick = p.kick[sp];
-    for (int a = 0; a < 3; a++) v[a] += kick * F[a];
+    for (int a = 0; a < 3; a++) v[a] = v[a] * s_open + kick * F[a];
     if (MODE == 1) {
       for (int a = 0; a < 3; a++) x[a] += p.dt * v[a];
     } else {

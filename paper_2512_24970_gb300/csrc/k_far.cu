@@ -8,7 +8,7 @@
 //             F^corr and U_N from the near-field warp partials.
 //   k_farforce F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
 //   k_finish  F_i = F_N,i - F^corr + F_F,i and the closing half kick of the MD step.
-#include "rbsog_internal.cuh"
+#include "nh.cuh"
 
 namespace rb {
 
@@ -349,34 +349,40 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
   }
 }
 
-// F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step.
+// F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step
+// (Nose-Hoover: with the block's sum of m v^2 for the chain's closing half step).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(PREP_BLOCK) k_finish(View p) {
   constexpr bool MIX = sizeof(R) == 4;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.n) return;
   const int64_t n = p.n;
-  double F[3];
-  for (int a = 0; a < 3; a++) {
-    const double fn = MIX ? (double)p.FNf[a * n + i] : p.FNd[a * n + i];
-    const double ff = MIX ? (double)p.FFf[a * n + i] : p.FFd[a * n + i];
-    F[a] = fn - p.red[a] + ff;
-  }
-  if (MIX) {
-    for (int a = 0; a < 3; a++) p.Ff[a * n + i] = (float)F[a];
-  } else {
-    for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
-  }
   // the step counter advances here, after both branches joined: every kernel
   // of the step that reads it (k-batch, noise, shell batch) has finished
   if (MODE != 0 && i == 0) *p.step += 1;
   if (i == 0 && p.auto_lists) *p.lflag = 0;     // the build flag of the next step starts down
-  if (MODE != 0) {
-    const double kick = p.kick[p.spc[i]];
+  if (i < n) {
+    double F[3];
     for (int a = 0; a < 3; a++) {
-      const double Fa = MIX ? (double)(float)F[a] : F[a];
-      p.v[a * n + i] += kick * Fa;
+      const double fn = MIX ? (double)p.FNf[a * n + i] : p.FNd[a * n + i];
+      const double ff = MIX ? (double)p.FFf[a * n + i] : p.FFd[a * n + i];
+      F[a] = fn - p.red[a] + ff;
     }
+    if (MIX) {
+      for (int a = 0; a < 3; a++) p.Ff[a * n + i] = (float)F[a];
+    } else {
+      for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
+    }
+    if (MODE != 0) {
+      const double kick = p.kick[p.spc[i]];
+      for (int a = 0; a < 3; a++) {
+        const double Fa = MIX ? (double)(float)F[a] : F[a];
+        p.v[a * n + i] += kick * Fa;
+      }
+    }
+  }
+  if (MODE != 0 && p.integ == RBSOG_NOSE_HOOVER) {
+    const double t = block_sum(mv2(p, i));
+    if (threadIdx.x == 0) p.ke_part[blockIdx.x] = t;
   }
 }
 

@@ -43,6 +43,13 @@ constexpr int ERR_PR_CAP = 4;
 constexpr int ERR_SKIN = 8;       // kept lists: an atom moved by more than skin/2
 constexpr int ERR_KEPT_CAP = 16;  // kept lists: |A| > RBSOG_MAX_CORE or |B| > RBSOG_MAX_KEPT
 
+// Nose-Hoover chain state in View::nh: the chain between steps (A: eta, v
+// after the closing half step), the closing half step's velocity scale, and
+// the chain after the opening half step (B, written by k_prepare).
+constexpr int NH_A_ETA = 0, NH_A_V = 8, NH_S_CLOSE = 17, NH_B_ETA = 24, NH_B_V = 32;
+constexpr int NH_STATE = 40;
+static_assert(RBSOG_MAX_NH_CHAIN <= 8, "chain state layout");
+
 // Pair record, mixed precision: force phi(r) r_ij with
 //   phi = kqq (1/r^3 - G(r^2)) + Ar/r * 2^((sig - r) lr) - (C6 + D8/r^2)/r^8
 // and pair energy kqq (1/r - F(r^2)) + A 2^((sig - r) lr) - (C + D/r^2)/r^6.
@@ -91,6 +98,13 @@ struct View {
   double kick[RBSOG_MAX_SPECIES];    // 0.5 dt FCONV / m
   double qfar[RBSOG_MAX_SPECIES];    // -k_e q / V (far-force prefactor)
   double sig_ou[RBSOG_MAX_SPECIES];  // sqrt((1 - c1^2) kT FCONV / m)
+  double massv[RBSOG_MAX_SPECIES];   // masses [amu]
+  // Nose-Hoover chain (integrator RBSOG_NOSE_HOOVER)
+  int nh_M, nh_nblk;      // chain length; blocks of the m v^2 partials (k_finish layout)
+  double nh_kT, nh_g;     // kT [eV]; degrees of freedom 3N - 3
+  double nh_Q[RBSOG_MAX_NH_CHAIN];  // chain masses [eV ps^2]
+  double *nh;             // [NH_STATE] chain state
+  double *ke_part;        // [nh_nblk] sum m v^2 per k_finish block
   int G;                  // M + 1
   int ntile, tile_atoms, nblk_atoms, nblk_kq, nblk_near;
   // per-atom state, caller order ([3][n] SoA)
@@ -360,6 +374,8 @@ void launch_rhosum(const View &v, cudaStream_t st, bool energy);
 void launch_corr(const View &v, cudaStream_t st, int step_off);
 void launch_farforce(const View &v, cudaStream_t st);
 void launch_finish(const View &v, cudaStream_t st, int mode);
+void launch_nh_close(const View &v, cudaStream_t st);
+void launch_nh_prime(const View &v, cudaStream_t st);
 void launch_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
                   int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
                   int *batch, int *nbatch, double *weight);

@@ -20,6 +20,7 @@ FP64 = 0
 MIXED = 1
 NVE_VV = 0
 LANGEVIN_BAOAB = 1
+NOSE_HOOVER = 2
 PTR_HOST = 0
 PTR_DEVICE = 1
 
@@ -37,7 +38,7 @@ MAX_KEPT = 512
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_get_list_builds", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -66,6 +67,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
         ("dt", ctypes.c_double), ("T", ctypes.c_double), ("gamma", ctypes.c_double),
         ("list_every", ctypes.c_int32), ("skin", ctypes.c_double),
+        ("tdamp", ctypes.c_double), ("nh_chain", ctypes.c_int32),
     ]
 
 
@@ -87,6 +89,8 @@ class MethodParams:
     gamma: float = 1.0
     list_every: int = 0     # 0: per-step lists; n >= 1: kept lists rebuilt every n steps; -1: when needed
     skin: float = 0.0       # Verlet skin of kept lists [A]
+    tdamp: float = 0.1      # Nose-Hoover time constant [ps]
+    nh_chain: int = 3       # Nose-Hoover chain length
 
     def c(self):
         p = Params()
@@ -126,6 +130,8 @@ def load():
     L.rbsog_sync.argtypes = [P]
     L.rbsog_get_sog.argtypes = [P, P, P, P]
     L.rbsog_get_list_builds.argtypes = [P, P]
+    L.rbsog_get_thermostat.argtypes = [P, P, P]
+    L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kbatch.argtypes = [P, P, P]
@@ -278,6 +284,18 @@ class Context:
         w = np.zeros(M + 1)
         self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
         return s.value, w, S.value
+
+    def thermostat(self):
+        """Nose-Hoover chain (eta, v_eta) between steps."""
+        M = self.params.nh_chain
+        eta, ve = np.zeros(M), np.zeros(M)
+        self._ck(self._L.rbsog_get_thermostat(self.h, _np_ptr(eta), _np_ptr(ve)))
+        return eta, ve
+
+    def set_thermostat(self, eta, v_eta):
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        ve = np.ascontiguousarray(v_eta, dtype=np.float64)
+        self._ck(self._L.rbsog_set_thermostat(self.h, _np_ptr(eta), _np_ptr(ve)))
 
     def list_builds(self) -> int:
         """Builds of the kept random batch lists since set_system."""

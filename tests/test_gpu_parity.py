@@ -263,3 +263,53 @@ def test_virial_mixed_and_deterministic(rb, orc):
         ctx.debug_set_kbatch(m, c)
         _, Wd = ctx.compute_forces(virial=True)
         assert virial_err(Wd, ref) < tol, (prec, Wd, ref)
+
+
+def setup_nh(rb, orc, w, precision, tdamp=0.05, chain=3, T=1500.0):
+    S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=20, P_F=100, seed=3)
+    prm = rb.MethodParams(s=S.s, w0=float(S.w[0]), P_R=20, P_F=100, seed=3, precision=precision,
+                          integrator=rb.NOSE_HOOVER, T=T, tdamp=tdamp, nh_chain=chain)
+    ctx = rb.Context(0)
+    ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
+    return ctx, S
+
+
+def test_nose_hoover_fp64_trajectory(rb, orc):
+    """Nose-Hoover chain (length 3, tdamp 0.05 ps, target 1500 K from 1200 K):
+    10 FP64 steps follow the oracle, chain state included."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, S = setup_nh(rb, orc, w, rb.FP64)
+    ctx.set_velocities(v0)
+    ctx.step(10)
+    pos, vel, step = ctx.get_state()
+    eta, ve = ctx.thermostat()
+    vo, _ = S.run(v0, 10, 0.001, integrator=orc.INTEGRATOR_NOSE_HOOVER, T=1500.0, tdamp=0.05, nh_chain=3)
+    assert step == 10
+    assert np.sqrt(((pos - S.pos) ** 2).mean()) < 1e-10
+    assert rms_rel(vel, vo) < 1e-10
+    np.testing.assert_allclose(eta, S.chain.eta, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(ve, S.chain.v, rtol=1e-9, atol=1e-11)
+    assert np.abs(ve).max() > 1e-3                 # the chain moved
+
+
+def test_nose_hoover_resume_bit_identical(rb, orc):
+    w = W.rock_salt((5, 5, 5), seed=2)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, _ = setup_nh(rb, orc, w, rb.MIXED)
+    ctx.set_velocities(v0)
+    ctx.step(12)
+    ref = ctx.get_state()
+    ctx1, _ = setup_nh(rb, orc, w, rb.MIXED)
+    ctx1.set_velocities(v0)
+    ctx1.step(6)
+    p, v, s = ctx1.get_state()
+    eta, ve = ctx1.thermostat()
+    ctx2, _ = setup_nh(rb, orc, w, rb.MIXED)
+    ctx2.set_state(p, v, s)
+    ctx2.set_thermostat(eta, ve)
+    ctx2.step(6)
+    got = ctx2.get_state()
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    assert got[2] == ref[2] == 12

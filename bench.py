@@ -128,7 +128,7 @@ def dist_env():
 
 
 # kernels of one MD step: main branch k_prepare, k_rowscan, k_cellstart, k_scatter, k_rank,
-# k_near, k_reduce (F^corr), k_finish; side branch k_ksample, k_rho, k_reduce (rho), k_farforce
+# k_near, k_corr (F^corr), k_finish; side branch k_ksample, k_rho, k_reduce (rho), k_farforce
 # (the histogram clear is a memset node)
 KERNELS_PER_STEP = 12
 # kept lists: a build step adds the list build to the per-step graph; a step

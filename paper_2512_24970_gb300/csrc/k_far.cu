@@ -3,9 +3,10 @@
 //             an atom tile, phase k . r = 2 pi (m . u mod 2^32) / 2^32 reduced
 //             exactly in uint32; FP32 polynomial sincos with FP32 accumulation
 //             over at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
-//   k_reduce  fixed-order FP64 sum over tiles (one warp per k), the per-k
-//             force coefficients c_p Im rho_p, c_p Re rho_p; extra blocks form
-//             F^corr and U_N from the near-field warp partials.
+//   k_reduce  fixed-order FP64 sum over tiles (one block per k), the per-k
+//             force coefficients c_p Im rho_p, c_p Re rho_p.
+//   k_corr    F^corr and U_N (and in energy evaluations the pair virial) from
+//             the near-field warp partials, fixed order.
 //   k_farforce F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
 //   k_finish  F_i = F_N,i - F^corr + F_F,i and the closing half kick of the MD step.
 #include "nh.cuh"
@@ -101,26 +102,28 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
 // last block to finish adds the CORR_BLOCKS block sums in index order, so the
 // result does not depend on which block finishes when.
 constexpr int CORR_BLOCKS = 64;
-__device__ void corr_block(const View &p, int blk, int step_off) {
-  // p.npart partials per warp: sum F_N (3), U_N and, in energy evaluations,
-  // the pair virial (6)
-  __shared__ double red[NEAR_NPART][256];
+// NV partials per warp (= p.npart): sum F_N (3), U_N and, in energy
+// evaluations, the pair virial (6)
+template <int NV>
+__global__ void __launch_bounds__(256) k_corr(View p) {
+  __shared__ double red[NV][256];
   __shared__ bool last;
-  const int t = threadIdx.x, nv = p.npart;
+  constexpr int nv = NV;
+  const int t = threadIdx.x, blk = blockIdx.x;
   const int np = p.nblk_near * NEAR_WARPS;
   const int per = (np + CORR_BLOCKS - 1) / CORR_BLOCKS;
   const int b0 = blk * per, b1 = min(b0 + per, np);
-  double f[NEAR_NPART] = {};
+  double f[NV] = {};
   for (int b = b0 + t; b < b1; b += 256)
 #pragma unroll
-    for (int a = 0; a < NEAR_NPART; a++)
-      if (a < nv) f[a] += p.near_part[(int64_t)nv * b + a];
+    for (int a = 0; a < NV; a++) f[a] += p.near_part[(int64_t)NV * b + a];
 #pragma unroll
-  for (int a = 0; a < NEAR_NPART; a++) red[a][t] = f[a];
+  for (int a = 0; a < NV; a++) red[a][t] = f[a];
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (t < o)
-      for (int a = 0; a < nv; a++) red[a][t] += red[a][t + o];
+#pragma unroll
+      for (int a = 0; a < NV; a++) red[a][t] += red[a][t + o];
     __syncthreads();
   }
   if (t < nv) p.corr_part[NEAR_NPART * blk + t] = red[t][0];
@@ -148,16 +151,11 @@ __device__ void corr_block(const View &p, int blk, int step_off) {
   if (t == 0) *p.corr_ticket = 0u;                // ready for the next evaluation
 }
 
-// Blocks [0, nkb): one block per k, fixed-order sum over tiles (thread-
-// strided partial sums, a shuffle tree per warp, the eight warp sums in
-// order), per-k force coefficients.  Blocks [nkb, nkb + CORR_BLOCKS): F^corr
-// and U_N (corr_block).
+// One block per k: fixed-order sum over tiles (thread-strided partial sums,
+// a shuffle tree per warp, the eight warp sums in order), per-k force
+// coefficients (and, in energy evaluations, the per-k virial term).
 template <typename R>
-__global__ void __launch_bounds__(256) k_reduce(View p, int nkb, int step_off) {
-  if ((int)blockIdx.x >= nkb) {
-    corr_block(p, (int)blockIdx.x - nkb, step_off);
-    return;
-  }
+__global__ void __launch_bounds__(256) k_reduce(View p) {
   __shared__ double2 wsum[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k = blockIdx.x;
@@ -406,13 +404,15 @@ void launch_rho(const View &v, cudaStream_t st) {
 
 void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
   const int g = max(1, v.P);                    // one block per k
-  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v, g, 0);
-  else k_reduce<double><<<g, 256, 0, st>>>(v, g, 0);
+  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v);
+  else k_reduce<double><<<g, 256, 0, st>>>(v);
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 
 void launch_corr(const View &v, cudaStream_t st, int step_off) {
-  k_reduce<float><<<CORR_BLOCKS, 256, 0, st>>>(v, 0, step_off);
+  (void)step_off;
+  if (v.npart == NEAR_NPART) k_corr<NEAR_NPART><<<CORR_BLOCKS, 256, 0, st>>>(v);
+  else k_corr<4><<<CORR_BLOCKS, 256, 0, st>>>(v);
 }
 
 void launch_farforce(const View &v, cudaStream_t st) {

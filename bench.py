@@ -457,9 +457,17 @@ def run_ensemble(args):
     stream = torch.cuda.Stream(device=dev)
     ens = rbsog.Ensemble(0, stream.cuda_stream, max_replicas=len(reps))
     natoms = 0
+    list_every = -1 if args.list_every is None else args.list_every
+
+    def params(r, w, T):
+        # kept lists rebuilt when needed, with the skin each box allows (at most
+        # 1 A; L >= 2 (r_shell + skin)); or per-step lists with --list-every 0
+        skin = min(1.0, 0.5 * float(w.box.min()) - 12.0 - 0.01) if list_every else 0.0
+        return rbsog.MethodParams(P_R=20, P_F=500, seed=5000 + r, precision=rbsog.MIXED,
+                                  integrator=rbsog.LANGEVIN_BAOAB, T=T, list_every=list_every, skin=skin)
+
     for r, (w, T) in enumerate(reps):
-        prm = rbsog.MethodParams(P_R=20, P_F=500, seed=5000 + r, precision=rbsog.MIXED,
-                                 integrator=rbsog.LANGEVIN_BAOAB, T=T)
+        prm = params(r, w, T)
         c = ens.add_workload(w, prm)
         c.set_velocities(w.vel)
         natoms += w.n
@@ -487,8 +495,7 @@ def run_ensemble(args):
     solo = []
     for r, (w, T) in enumerate(reps):
         c = rbsog.Context(0, stream.cuda_stream)
-        c.set_workload(w, rbsog.MethodParams(P_R=20, P_F=500, seed=5000 + r, precision=rbsog.MIXED,
-                                             integrator=rbsog.LANGEVIN_BAOAB, T=T))
+        c.set_workload(w, params(r, w, T))
         solo.append(c)
 
     def seq():
@@ -501,6 +508,9 @@ def run_ensemble(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "64 replicas: N = 8 n^3, n in [4, 16] (N 512..32768), NaCl / LiCl / LiCl-NaCl, "
                                    "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
+                       "lists": ("per step" if not list_every else
+                                 "kept, rebuilt when an atom has moved by skin/2; skin min(1 A, L/2 - r_shell)"),
+                       "launch": "one CUDA graph per ensemble step (every replica's step graph a child node)",
                        "l2": "flushed before every step (512 MiB memset)"},
             "sequential": {"value": natoms * K / (t_seq / 1000.0), "ms_per_step": t_seq / K,
                            "what": "the same replicas stepped one after another on one stream"}}

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx_internal.h"
 #include "rbsog_internal.cuh"
 #include "setup.h"
 
@@ -36,6 +37,8 @@ struct rbsog_ctx {
   double *stage = nullptr;     // [n][3] FP64 staging
   cudaGraphExec_t gexec = nullptr;       // step graph (with kept lists: the build variant)
   cudaGraphExec_t gexec_keep = nullptr;  // kept lists: the variant that reuses them
+  cudaGraph_t gstep = nullptr;           // the captured step graph behind gexec (ensemble child graphs)
+  uint64_t graph_gen = 0;                // bumped at every capture
   bool graph_ok = false;
   bool lists_valid = false;              // kept lists built since the last set_system / set_state
   bool nh_primed = false;                // Nose-Hoover: 2K of the current velocities is in the chain state
@@ -75,6 +78,9 @@ int dalloc(rbsog_ctx *ctx, T **p, size_t count) {
 void free_system(rbsog_ctx *ctx) {
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->gexec_keep) cudaGraphExecDestroy(ctx->gexec_keep);
+  if (ctx->gstep) cudaGraphDestroy(ctx->gstep);
+  ctx->gstep = nullptr;
+  ctx->graph_gen++;
   ctx->gexec = nullptr;
   ctx->gexec_keep = nullptr;
   ctx->graph_ok = false;
@@ -260,6 +266,70 @@ void set_rho_tiling(rbsog_ctx *ctx, int P) {
 }
 
 }  // namespace
+
+// ===========================================================================
+// Internal interface of a context for the ensemble (ctx_internal.h).
+namespace rb {
+
+int ctx_prepare_step(rbsog_ctx *ctx) {
+  int rc;
+  if (!ctx->forces_valid) {
+    View vv;
+    if ((rc = eval_view(ctx, vv))) return rc;
+    if ((rc = run_force(ctx, vv, 0, 0, false))) return rc;
+    ctx->forces_valid = true;
+    ctx->lists_valid = true;
+  }
+  if (!ctx->graph_ok) {
+    // velocity Verlet (Nose-Hoover: with the chain's half steps) or BAOAB
+    const int mode = ctx->prm.integrator == RBSOG_LANGEVIN_BAOAB ? 2 : 1;
+    // variant 0 bins and builds (per-step lists: the only one); variant 1
+    // evaluates the kept lists of the last build
+    for (int var = 0; var < ((ctx->v.kept && !ctx->v.auto_lists) ? 2 : 1); var++) {
+      View vs = ctx->v;
+      vs.build = var == 0 ? 1 : 0;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+      rc = run_force(ctx, vs, mode, 1, false);
+      cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      cudaGraphExec_t &ge = var == 0 ? ctx->gexec : ctx->gexec_keep;
+      if (ge) cudaGraphExecDestroy(ge);
+      ge = nullptr;
+      e = cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      if (var == 0) {                          // kept for an ensemble's graph
+        if (ctx->gstep) cudaGraphDestroy(ctx->gstep);
+        ctx->gstep = g;
+      } else {
+        cudaGraphDestroy(g);
+      }
+    }
+    ctx->graph_gen++;
+    ctx->graph_ok = true;
+  }
+  if (ctx->prm.integrator == RBSOG_NOSE_HOOVER && !ctx->nh_primed) {
+    rb::launch_nh_prime(ctx->v, ctx->st);   // 2K of the velocities the first half step sees
+    if ((rc = check_launch(ctx))) return rc;
+    ctx->nh_primed = true;
+  }
+  return RBSOG_OK;
+}
+
+bool ctx_single_graph(const rbsog_ctx *ctx) { return !ctx->v.kept || ctx->v.auto_lists; }
+
+cudaGraph_t ctx_step_graph(const rbsog_ctx *ctx, uint64_t *gen) {
+  if (gen) *gen = ctx->graph_gen;
+  return ctx->graph_ok ? ctx->gstep : nullptr;
+}
+
+void ctx_advance(rbsog_ctx *ctx, int64_t nsteps) { ctx->host_step += nsteps; }
+
+}  // namespace rb
 
 // ===========================================================================
 extern "C" {
@@ -646,41 +716,7 @@ int rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
   if (!(ctx->prm.dt > 0.0)) return fail(ctx, RBSOG_E_INVAL, "dt must be positive");
   int rc;
   if ((rc = enter(ctx))) return rc;
-  if (!ctx->forces_valid) {
-    View vv;
-    if ((rc = eval_view(ctx, vv))) return rc;
-    if ((rc = run_force(ctx, vv, 0, 0, false))) return rc;
-    ctx->forces_valid = true;
-    ctx->lists_valid = true;
-  }
-  if (!ctx->graph_ok) {
-    // velocity Verlet (Nose-Hoover: with the chain's half steps) or BAOAB
-    const int mode = ctx->prm.integrator == RBSOG_LANGEVIN_BAOAB ? 2 : 1;
-    // variant 0 bins and builds (per-step lists: the only one); variant 1
-    // evaluates the kept lists of the last build
-    for (int var = 0; var < ((ctx->v.kept && !ctx->v.auto_lists) ? 2 : 1); var++) {
-      View vs = ctx->v;
-      vs.build = var == 0 ? 1 : 0;
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-      rc = run_force(ctx, vs, mode, 1, false);
-      cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
-      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      cudaGraphExec_t &ge = var == 0 ? ctx->gexec : ctx->gexec_keep;
-      if (ge) cudaGraphExecDestroy(ge);
-      ge = nullptr;
-      e = cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
-    ctx->graph_ok = true;
-  }
-  if (ctx->prm.integrator == RBSOG_NOSE_HOOVER && !ctx->nh_primed) {
-    rb::launch_nh_prime(ctx->v, ctx->st);   // 2K of the velocities the first half step sees
-    if ((rc = check_launch(ctx))) return rc;
-    ctx->nh_primed = true;
-  }
+  if ((rc = rb::ctx_prepare_step(ctx))) return rc;
   // kept lists are rebuilt at the steps that are multiples of list_every
   const int64_t every = ctx->prm.list_every;
   for (int64_t k = 0; k < nsteps; k++) {

@@ -67,3 +67,61 @@ def test_ensemble_capacity_and_errors(rb):
         ens.add(w.pos, w.species, w.charge, w.mass, w.bmh, w.box * 0.7, rb.MethodParams())
     assert e.value.code in (-1, -3)
     ens.close()
+
+
+def _alone(rb, w, prm, nsteps):
+    alone = rb.Context(0)
+    alone.set_workload(w, prm)
+    alone.step(nsteps)
+    out = alone.get_state()
+    alone.close()
+    return out
+
+
+def test_ensemble_graph_rebuilt_after_direct_steps(rb):
+    """One graph per ensemble step; a replica stepped on its own in between
+    (and re-captured after a profiling switch) keeps every state exact."""
+    import dataclasses
+    reps = replicas(rb)
+    reps[1] = (reps[1][0], dataclasses.replace(reps[1][1], list_every=-1, skin=1.0))   # kept lists, automatic
+    reps[2] = (reps[2][0], dataclasses.replace(reps[2][1], integrator=rb.NOSE_HOOVER, tdamp=0.05))
+    ens = rb.Ensemble(0, max_replicas=len(reps))
+    views = []
+    for w, prm in reps:
+        c = ens.add_workload(w, prm)
+        c.set_velocities(w.vel)
+        views.append(c)
+    ens.step(3)
+    views[0].step(2)
+    views[3].set_profiling(True)                 # forces a new step graph
+    ens.step(2)
+    ens.sync()
+    for k, ((w, prm), c) in enumerate(zip(reps, views)):
+        n = 7 if k == 0 else 5
+        pa, va, sa = _alone(rb, w, prm, n)
+        pe, ve, se = c.get_state()
+        assert sa == se == n
+        np.testing.assert_array_equal(pe, pa)
+        np.testing.assert_array_equal(ve, va)
+    ens.close()
+
+
+def test_ensemble_fixed_schedule_replicas(rb):
+    """Kept lists on a fixed rebuild schedule: each replica launches its own
+    graphs (the host picks the variant per step); states exact."""
+    import dataclasses
+    reps = [(w, dataclasses.replace(prm, list_every=3, skin=1.0)) for w, prm in replicas(rb)[1:3]]
+    ens = rb.Ensemble(0, max_replicas=2)
+    views = []
+    for w, prm in reps:
+        c = ens.add_workload(w, prm)
+        c.set_velocities(w.vel)
+        views.append(c)
+    ens.step(7)
+    ens.sync()
+    for (w, prm), c in zip(reps, views):
+        pa, va, sa = _alone(rb, w, prm, 7)
+        pe, ve, se = c.get_state()
+        np.testing.assert_array_equal(pe, pa)
+        np.testing.assert_array_equal(ve, va)
+    ens.close()

@@ -17,6 +17,7 @@ time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -48,6 +49,8 @@ def parse():
                     help="0: per-step random batch lists; n >= 1: kept (skin) lists rebuilt every n steps; "
                          "-1: rebuilt when an atom has moved by skin/2 (default: the workload's, -1)")
     ap.add_argument("--skin", type=float, default=None, help="skin of kept lists [A] (default: the workload's)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="kept lists rebuilt when needed: use the workload's skin instead of timing candidates")
     ap.add_argument("--no-per-step-lists", action="store_true",
                     help="skip the second measurement with lists rebuilt at every step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -293,6 +296,17 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K, Wm = args.steps, args.warmup
+    # the skin of automatically rebuilt kept lists: timed candidates (outside
+    # the timed region), unless given
+    tuning = None
+    if list_every < 0 and args.skin is None and not args.no_autotune:
+        from paper_2512_24970_gb300 import autotune
+        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream)
+        prm = dataclasses.replace(prm, skin=skin)
+        tuning = {"chosen_skin": skin, "candidates": [{"skin": a, "ms_per_step": b, "list_builds": c}
+                                                      for a, b, c in table],
+                  "rejected": [{"skin": a, "why": r} for a, r in rejected],
+                  "how": "200 timed steps per candidate after 20 warm-up, CUDA events (autotune.tune_skin)"}
 
     def timed_run(params, clocks=None, k_stage=None):
         """Wm untimed steps, then K steps timed with CUDA events on the
@@ -343,7 +357,6 @@ def run_ours(args):
     # the same steps with the random batch lists rebuilt from scratch at every step
     per_step = None
     if list_every != 0 and not args.no_per_step_lists:
-        import dataclasses
         c1, ms1, st1 = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
         c1.close()
         v1, t1, _ = aggregate(float(ms1.sum()), float(w.n * K), dist if ws > 1 else None, dev)
@@ -356,7 +369,7 @@ def run_ours(args):
     nsm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    alg = algorithmic_ops(w, P_F, P_R, list_every=list_every, skin=skin)
+    alg = algorithmic_ops(w, P_F, P_R, list_every=list_every, skin=prm.skin)
     peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
     label = dict(KERNEL_LABEL)
     if list_every != 0:
@@ -432,8 +445,9 @@ def run_ours(args):
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
                        "lists": ("per step" if not list_every else
                                  ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in "
-                                  "%d steps)" % (skin, n_builds, n_steps_all)) if list_every < 0 else
-                                 "kept: skin %.2f A, rebuilt every %d steps" % (skin, list_every)),
+                                  "%d steps)" % (prm.skin, n_builds, n_steps_all)) if list_every < 0 else
+                                 "kept: skin %.2f A, rebuilt every %d steps" % (prm.skin, list_every)),
+                       "skin_tuning": tuning,
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
             "roofline": roof, "kernel_rooflines": kern, "step_roofline": step_roof, "per_step_lists": per_step, "peaks": pk_kind, "clocks": clk, "e2e": e2e,

@@ -114,6 +114,7 @@ class _Sys(ctypes.Structure):
         ("r_core", ctypes.c_double), ("r_shell", ctypes.c_double),
         ("P_R", ctypes.c_int32), ("P_F", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("step", ctypes.c_int64), ("skin", ctypes.c_double),
+        ("r_core_pair", ctypes.c_void_p),
     ]
 
 
@@ -227,7 +228,7 @@ class System:
 
     def __init__(self, pos, species, charge, mass, bmh, box, *, b=1.3, M=64, s=None, w=None,
                  r_core=6.0, r_shell=12.0, P_R=20, P_F=200, seed=1, step=0, skin=0.0,
-                 list_every=0):
+                 list_every=0, r_core_pair=None):
         self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         self.species = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
         self.charge = np.ascontiguousarray(charge, dtype=np.float64)
@@ -244,6 +245,8 @@ class System:
         self.P_R, self.P_F = int(P_R), int(P_F)
         self.seed, self.step = int(seed), int(step)
         self.skin, self.list_every = float(skin), int(list_every)
+        # species-dependent core radii [ns][ns] (symmetric, none above r_core) or None
+        self.r_core_pair = None if r_core_pair is None else np.ascontiguousarray(r_core_pair, dtype=np.float64)
         self.build_pos = None   # positions the kept lists were built from
         self.builds = 0         # automatic rebuilds (list_every = -1) during run()
 
@@ -292,6 +295,7 @@ class System:
         st.P_R, st.P_F = self.P_R, self.P_F
         st.seed, st.step = self.seed, self.step
         st.skin = self.skin
+        st.r_core_pair = self.r_core_pair.ctypes.data if self.r_core_pair is not None else None
         return st
 
     # ---- geometry -------------------------------------------------------
@@ -566,3 +570,4 @@ class System:
             if integrator == INTEGRATOR_NOSE_HOOVER:
                 vel = vel * self.chain.half_step(self.kinetic2(vel), dt)
         return vel, F
+

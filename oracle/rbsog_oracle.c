@@ -62,6 +62,7 @@ typedef struct {
   uint64_t seed;
   int64_t step;
   double skin;            /* Verlet skin of the kept lists (orc_*_skin only) */
+  const double *r_core_pair; /* [n_species][n_species] core radius of each species pair, or NULL */
 } orc_sys;
 
 /* ------------------------------------------------------------------------ */
@@ -333,7 +334,10 @@ static void geo_free(orc_geo *G) { free(G->u); free(G->cell); }
 /* Core set {j != i : r^2 < fl32(r_core^2)} and shell set
  * {j != i : fl32(r_core^2) <= r^2 < fl32(r_shell^2)} of atom i, both in
  * canonical order: ascending (cell linear index of j, fixed-point x
- * coordinate u_x of j, j).  Brute force.                                  */
+ * coordinate u_x of j, j).  Brute force.  With species-dependent core radii
+ * (the adaptive cutoff of Sec. 1, a reading: a symmetric table of r_core per
+ * species pair, none above r_core) the core threshold of the pair (i, j) is
+ * fl32(r_core(s_i, s_j)^2).                                                */
 static int atom_lists(const orc_sys *S, const orc_geo *G, int64_t i, cand_t *core,
                       int32_t *ncore, int cap_core, cand_t *shell, int32_t *nshell,
                       int cap_shell) {
@@ -342,7 +346,12 @@ static int atom_lists(const orc_sys *S, const orc_geo *G, int64_t i, cand_t *cor
   for (int64_t j = 0; j < S->n; j++) {
     if (j == i) continue;
     float r2 = pred_r2(ui, G->u + 3 * j, G->h);
-    if (r2 < G->rc2) {
+    float rc2 = G->rc2;
+    if (S->r_core_pair) {
+      const double rc = S->r_core_pair[S->species[i] * S->n_species + S->species[j]];
+      rc2 = (float)(rc * rc);
+    }
+    if (r2 < rc2) {
       if (nc < cap_core) { core[nc].key = G->cell[j]; core[nc].ux = G->u[3 * j]; core[nc].j = (int32_t)j; }
       else over = 1;
       nc++;

@@ -194,3 +194,12 @@ def ensemble(n_rep=64, seed=5):
         w.vel = maxwell_boltzmann(w, T)
         reps.append((w, T))
     return reps
+
+
+def core_radii_from_sigma(bmh, r_core=6.0):
+    """Species-dependent core radii (the adaptive cutoff named in Sec. 1 has no
+    printed rule; this is the example rule used here): r_core scaled by each
+    pair's BMH size parameter sigma_ab relative to the largest, so pairs of
+    small ions keep a smaller exact core.  Symmetric [ns][ns] table."""
+    sig = np.asarray(bmh, dtype=np.float64)[..., 1]
+    return r_core * sig / sig.max()

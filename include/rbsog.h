@@ -152,6 +152,15 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
                      const double *bmh, const double box[3], const rbsog_params *params,
                      int ptr_kind);
 
+/* Species-dependent core radii (the adaptive, species-dependent cutoff of
+ * Sec. 1, whose rule the paper does not print): r_core_pair [n_species]
+ * [n_species] FP64 [A], symmetric, each in (0, r_core]; the pair (i, j) is in
+ * the exact core iff r_ij < r_core_pair[s_i][s_j] (FP32 predicate), else in
+ * the shell up to r_shell.  Any split leaves the estimator unbiased; only its
+ * variance and cost change.  NULL restores the single r_core.  Host pointer;
+ * lists are rebuilt at the next evaluation.  Errors: RBSOG_E_INVAL. */
+int rbsog_set_core_radii(rbsog_ctx *ctx, const double *r_core_pair);
+
 /* Set velocities [n][3] FP64 [A/ps]. */
 int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind);
 

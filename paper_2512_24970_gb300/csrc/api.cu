@@ -657,6 +657,29 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   return leave(ctx);
 }
 
+int rbsog_set_core_radii(rbsog_ctx *ctx, const double *r_core_pair) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  View &v = ctx->v;
+  if (!r_core_pair) {
+    v.core_pair = 0;
+  } else {
+    const int ns = v.ns;
+    for (int a = 0; a < ns; a++)
+      for (int b = 0; b < ns; b++) {
+        const double r = r_core_pair[a * ns + b];
+        if (!(r > 0.0) || r > ctx->prm.r_core) return fail(ctx, RBSOG_E_INVAL, "core radii must lie in (0, r_core]");
+        if (r != r_core_pair[b * ns + a]) return fail(ctx, RBSOG_E_INVAL, "core radii must be symmetric");
+        v.rc2p[a * ns + b] = (float)(r * r);
+      }
+    v.core_pair = 1;
+  }
+  ctx->graph_ok = false;
+  ctx->forces_valid = false;
+  ctx->lists_valid = false;
+  return RBSOG_OK;
+}
+
 int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind) {
   if (!ctx) return RBSOG_E_INVAL;
   if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");

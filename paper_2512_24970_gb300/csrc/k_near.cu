@@ -572,6 +572,31 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
       }
     }
     __syncwarp();
+    // ---- species-dependent core radii: a core member (tested against the
+    // largest radius) whose pair radius is smaller moves to the shell; its
+    // predicate value is recomputed exactly (the minimum-image difference of
+    // 23-bit coordinates is an exact integer, as in the tests above) --------
+    if (p.core_pair) {                          // warp-uniform: every lane meets the barrier below
+      for (int r = g; active && !over && r < nr; r += TPA) {
+        const int ng = rgo[warp][r + 1] - rgo[warp][r];
+        const int4 sg = rseg[warp][r];
+        unsigned char *gb = &gres[a][rbo[warp][r]];
+        for (int gi = 0; gi < ng; gi++) {
+          uint32_t x = gb[gi];
+          uint32_t cm = (x >> 4) & 0xFu;
+          while (cm) {
+            const int b = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            const uint4 uj = p.su[row_slot(sg, CELL_ALIGN * gi + b)];
+            const float r2 = pred_r2((float)wrap23(uj.x, ui.x), (float)wrap23(uj.y, ui.y),
+                                     (float)wrap23(uj.z, ui.z), p.hp);
+            if (!(r2 < p.rc2p[spi * p.ns + (int)(uj.w >> SU_SP_SHIFT)])) x &= ~(0x10u << b);
+          }
+          gb[gi] = (unsigned char)x;
+        }
+      }
+      __syncwarp();
+    }
     // ---- shell counts of the rows r = g, g + 4, ...; the atom's core list -----
     int my_total = 0, mycore = 0;
     if (!over) {
@@ -990,7 +1015,11 @@ __global__ void k_lists(View p, int step_off, const long long *sel, int nsel, in
         for (int j = p.cell_start[cell]; j < p.cell_start[cell + 1]; j++) {
           if (j == slot) continue;
           const float r2 = cand_r2<SMALL>(p, j, me.x - shx, me.y - shy, me.z - shz, ui);
-          if (r2 < p.rc2f) {
+          // core: inside the largest radius and (species-dependent radii) the pair's own
+          const bool in_core = r2 < p.rc2f &&
+                               (!p.core_pair ||
+                                r2 < p.rc2p[(int)(ui.w >> SU_SP_SHIFT) * p.ns + (int)(p.su[j].w >> SU_SP_SHIFT)]);
+          if (in_core) {
             if (nc < cap_core) core[(long long)q * cap_core + nc] = p.perm[j];
             nc++;
           } else if (r2 < p.rs2f) {

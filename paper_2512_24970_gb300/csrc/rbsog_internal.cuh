@@ -78,6 +78,9 @@ struct View {
   double hd[3];           // L * 2^-32
   double kunit[3];        // 2 pi / L
   float rc2f, rs2f;
+  // species-dependent core radii: core iff r^2 < rc2p[s_i * ns + s_j] (<= rc2f)
+  int core_pair;
+  float rc2p[RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES];
   // kept (skin) lists: kept = list_every >= 1; build = this evaluation builds
   // them (the step graph has a build and a keep variant)
   int kept, build;

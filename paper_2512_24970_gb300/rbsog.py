@@ -38,7 +38,7 @@ MAX_KEPT = 512
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -130,6 +130,7 @@ def load():
     L.rbsog_sync.argtypes = [P]
     L.rbsog_get_sog.argtypes = [P, P, P, P]
     L.rbsog_get_list_builds.argtypes = [P, P]
+    L.rbsog_set_core_radii.argtypes = [P, P]
     L.rbsog_get_thermostat.argtypes = [P, P, P]
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
@@ -296,6 +297,11 @@ class Context:
         eta = np.ascontiguousarray(eta, dtype=np.float64)
         ve = np.ascontiguousarray(v_eta, dtype=np.float64)
         self._ck(self._L.rbsog_set_thermostat(self.h, _np_ptr(eta), _np_ptr(ve)))
+
+    def set_core_radii(self, r_core_pair=None):
+        """Species-dependent core radii [ns][ns] (None: the single r_core)."""
+        t = None if r_core_pair is None else np.ascontiguousarray(r_core_pair, dtype=np.float64)
+        self._ck(self._L.rbsog_set_core_radii(self.h, _np_ptr(t)))
 
     def list_builds(self) -> int:
         """Builds of the kept random batch lists since set_system."""

@@ -211,3 +211,41 @@ def test_kept_virial(rb, orc):
     S.pos, S.step = pos, step
     o = S.forces(energy=True)
     assert float(np.abs(Wg - o["virial"]).max() / np.abs(o["virial"]).max()) < 1e-11
+
+
+@pytest.mark.parametrize("kept", [False, True])
+def test_species_core_radii(rb, orc, kept):
+    """Species-dependent core radii (sigma rule): lists / kept lists and batches
+    bit-exact, FP64 forces within 1e-12, in both list modes."""
+    w = W.rock_salt((9, 9, 9), seed=6, composition="LiCl-NaCl")
+    rc = W.core_radii_from_sigma(w.bmh, 6.0)
+    kw = dict(list_every=4, skin=1.0) if kept else dict(list_every=0, skin=0.0)
+    S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=20, P_F=200, seed=3, step=5,
+                   r_core_pair=rc, **kw)
+    prm = rb.MethodParams(s=S.s, w0=float(S.w[0]), P_R=20, P_F=200, seed=3, precision=rb.FP64, **kw)
+    ctx = rb.Context(0)
+    ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
+    ctx.set_core_radii(rc)
+    ctx.set_state(w.pos, np.zeros_like(w.pos), 5)
+    Fg = ctx.compute_forces()
+    sel = np.arange(w.n)
+    if kept:
+        g = ctx.debug_kept_lists(sel)
+        o = S.lists_skin(sel, cap_a=64, cap_b=512)
+        keys = ("nA", "nB", "A", "B", "nbatch", "batch", "weight")
+    else:
+        g = ctx.debug_lists(sel, cap_core=128, cap_shell=512)
+        o = S.lists(sel, cap_core=128, cap_shell=512)
+        keys = ("ncore", "nshell", "core", "shell", "nbatch", "batch", "weight")
+    for k in keys:
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    o = S.forces()
+    parts = ctx.debug_parts()
+    assert rms_rel(parts["near"], o["near"]) < FP64_TOL
+    assert rms_rel(parts["far"], o["far"]) < FP64_TOL
+    assert rms_rel(Fg, o["F"]) < FP64_TOL
+    # the split really differs from the single radius
+    R = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=20, step=5, **kw)
+    nA = (S.lists_skin(sel)["nA"] if kept else S.lists(sel)["ncore"])
+    nA0 = (R.lists_skin(sel)["nA"] if kept else R.lists(sel)["ncore"])
+    assert nA.sum() < 0.9 * nA0.sum()

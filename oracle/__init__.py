@@ -159,6 +159,7 @@ def _declare(L):
     L.orc_self_energy.argtypes = [sp]
     L.orc_self_energy.restype = _D
     L.orc_num_threads.restype = _I32
+    L.orc_set_num_threads.argtypes = [_I32]
 
 
 def _ptr(a):
@@ -167,6 +168,11 @@ def _ptr(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later OpenMP regions."""
+    lib().orc_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------

@@ -914,3 +914,13 @@ int32_t orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the following parallel regions (the CPU baseline times one core
+ * and all cores). */
+void orc_set_num_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

@@ -339,17 +339,19 @@ def run_ours(args):
                 clocks.pause()
             ks = min(K, 500) if k_stage is None else k_stage
             st = np.zeros(rbsog.NSTAGE)
+            mk = np.zeros(rbsog.NMARK)
             c.set_profiling(True)
             for k in range(ks):
                 flush.zero_()
                 c.step(1)
                 st += c.stage_times()          # waits for this step's last event
+                mk += c.stage_marks()
             c.set_profiling(False)
         c.sync()
-        return c, np.array([a.elapsed_time(b) for a, b in ev]), st / max(ks, 1)
+        return c, np.array([a.elapsed_time(b) for a, b in ev]), st / max(ks, 1), mk / max(ks, 1)
 
     clocks = Clocks(local)
-    ctx, ms, stage_ms = timed_run(prm, clocks)
+    ctx, ms, stage_ms, marks = timed_run(prm, clocks)
     clk = clocks.stop()
     n_builds = ctx.list_builds()
     n_steps_all = Wm + K + min(K, 500) + 1
@@ -357,11 +359,12 @@ def run_ours(args):
     # the same steps with the random batch lists rebuilt from scratch at every step
     per_step = None
     if list_every != 0 and not args.no_per_step_lists:
-        c1, ms1, st1 = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
+        c1, ms1, st1, mk1 = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
         c1.close()
         v1, t1, _ = aggregate(float(ms1.sum()), float(w.n * K), dist if ws > 1 else None, dev)
         per_step = {"value": v1, "unit": "atom-steps/s", "ms_per_step": t1 / K,
                     "stage_ms": {n: float(t) for n, t in zip(rbsog.STAGES, st1)},
+                    "timeline_us": {n: round(float(t) * 1e3, 2) for n, t in zip(rbsog.MARKS, mk1)},
                     "what": "same workload and steps, random batch lists rebuilt from the positions at every step"}
     # ---- roofline of the dominant kernel -------------------------------------
     pk, pk_kind = peaks()
@@ -456,6 +459,7 @@ def run_ours(args):
                        "skin_tuning": tuning,
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
+            "timeline_us": {n: round(float(t) * 1e3, 2) for n, t in zip(rbsog.MARKS, marks)},
             "roofline": roof, "kernel_rooflines": kern, "step_roofline": step_roof, "per_step_lists": per_step, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "cpu_baseline": cpu, "force_error": ferr,
         }

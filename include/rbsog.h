@@ -312,6 +312,18 @@ int rbsog_set_profiling(rbsog_ctx *ctx, int on);
  * evaluation (waits for it).  Requires profiling on.  Host pointer. */
 int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage);
 
+#define RBSOG_NMARK 12  /* main stream: start, after the integrator, after binning, after the
+                           near field, after F^corr, after the join of the branches, end;
+                           side stream: branch start, structure factor start (after the
+                           k-batch and the integrator), structure factor end, its
+                           reduction end, far-field force end */
+
+/* Times [ms] of the RBSOG_NMARK stage marks of the most recent force
+ * evaluation, from its start (waits for it): the timeline behind the stage
+ * durations, both branches on one clock.  Requires profiling on.  Host
+ * pointer; the first min(nmark, RBSOG_NMARK) entries are written. */
+int rbsog_get_stage_marks(rbsog_ctx *ctx, float *ms, int32_t nmark);
+
 /* Message of the last error of this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

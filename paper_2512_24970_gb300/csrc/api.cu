@@ -1101,4 +1101,16 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage) {
   return RBSOG_OK;
 }
 
+int rbsog_get_stage_marks(rbsog_ctx *ctx, float *ms, int32_t nmark) {
+  if (!ctx || !ms || nmark < 1) return RBSOG_E_INVAL;
+  if (!ctx->profiling) return fail(ctx, RBSOG_E_INVAL, "profiling is off");
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaEventSynchronize(ctx->prof[8]));
+  CK(cudaEventSynchronize(ctx->prof[4]));
+  // the marks in the order of RBSOG_NMARK, as events of run_force
+  static const int ev[RBSOG_NMARK] = {0, 1, 2, 7, 5, 6, 8, 3, 9, 10, 11, 4};
+  for (int k = 0; k < nmark && k < RBSOG_NMARK; k++) CK(cudaEventElapsedTime(ms + k, ctx->prof[0], ctx->prof[ev[k]]));
+  return RBSOG_OK;
+}
+
 }  // extern "C"

@@ -40,7 +40,7 @@ EXPORTS = [
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
-    "rbsog_get_stage_times", "rbsog_last_error", "rbsog_structure_factor_static",
+    "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
     "rbsog_ensemble_step", "rbsog_ensemble_sync", "rbsog_ensemble_last_error",
 ]
@@ -51,6 +51,10 @@ NSTAGE = 9
 # closing total force + half kick after the branches join, the whole evaluation, and inside the
 # far-field branch the structure-factor kernel and the far-force kernel alone
 STAGES = ["prepare", "bin", "near", "far", "corr", "finish", "total", "rho", "farforce"]
+NMARK = 12
+# marks of rbsog_get_stage_marks (time from the start of the evaluation)
+MARKS = ["start", "prepared", "binned", "near_done", "corr_done", "joined", "end",
+         "side_start", "rho_start", "rho_done", "reduce_done", "far_done"]
 
 
 class RbsogError(RuntimeError):
@@ -142,6 +146,7 @@ def load():
     L.rbsog_debug_sincos.argtypes = [P, I64, P, P, P]
     L.rbsog_set_profiling.argtypes = [P, I]
     L.rbsog_get_stage_times.argtypes = [P, P, I32]
+    L.rbsog_get_stage_marks.argtypes = [P, P, I32]
     L.rbsog_structure_factor_static.argtypes = [P, I32, P, P]
     L.rbsog_ensemble_create.argtypes = [ctypes.POINTER(P), I, P, I32]
     L.rbsog_ensemble_destroy.argtypes = [P]
@@ -378,6 +383,12 @@ class Context:
     def stage_times(self):
         ms = np.zeros(NSTAGE, dtype=np.float32)
         self._ck(self._L.rbsog_get_stage_times(self.h, _np_ptr(ms), NSTAGE))
+        return ms
+
+    def stage_marks(self):
+        """Times [ms] of the stage marks (``MARKS``) of the latest evaluation, from its start."""
+        ms = np.zeros(NMARK, dtype=np.float32)
+        self._ck(self._L.rbsog_get_stage_marks(self.h, _np_ptr(ms), NMARK))
         return ms
 
     def debug_sincos(self, th):

@@ -82,14 +82,19 @@ class NHChain:
                      + self.kT * self.eta[1:].sum())
 
 
+def compile_c(src: str, out: str) -> None:
+    """gcc -O2, no FP contraction, OpenMP: the one way the C oracle is built."""
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-shared", "-fPIC", src, "-o", out, "-lm"]
+    subprocess.check_call(cmd)
+
+
 def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc, -O2, no FP contraction, OpenMP)."""
+    """Compile the C oracle (compile_c) into oracle/_build."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
-        subprocess.check_call(cmd)
+        compile_c(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 

@@ -191,6 +191,17 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
  * replayed.  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_CUDA. */
 int rbsog_step(rbsog_ctx *ctx, int64_t nsteps);
 
+/* Kinetic tensor of the current velocities, K [6] FP64 [eV] = (K_xx, K_yy,
+ * K_zz, K_xy, K_xz, K_yz), K_ab = sum_i m_i v_ia v_ib (the order of the
+ * virial), summed on the device in a fixed order (block sums, then the blocks
+ * in order).  With the virial W of rbsog_compute_forces it gives the stress
+ * tensor S = K + W; S_xy is the shear stress of the Green-Kubo viscosity of
+ * Sec. 3 (sum_i m_i v_xi v_yi plus the pair term 1/2 sum_{j != i} x_ij f_y,
+ * here with the far field's strain derivative as well), and tr K = 2 E_kin.
+ * ptr_kind: host (synchronous) or device (asynchronous on the caller's
+ * stream).  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL, RBSOG_E_CUDA. */
+int rbsog_get_kinetic_tensor(rbsog_ctx *ctx, double *K, int ptr_kind);
+
 /* Read the state: pos/vel [n][3] FP64 (each may be NULL), step counter. */
 int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int ptr_kind);
 

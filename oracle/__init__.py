@@ -540,6 +540,17 @@ class System:
         """sum_i m_i v_i^2 in eV."""
         return float((self.mass[self.species][:, None] * vel ** 2).sum() / FCONV)
 
+    def kinetic_tensor(self, vel):
+        """K_ab = sum_i m_i v_ia v_ib in eV, (xx, yy, zz, xy, xz, yz): the velocity
+        term of the stress whose xy component enters the Green-Kubo viscosity
+        of Sec. 3 (S = K + W with the virial W)."""
+        v = np.asarray(vel, dtype=np.float64).reshape(-1, 3)
+        m = self.mass[self.species]
+        out = np.empty(6)
+        for c, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+            out[c] = float(np.sum(m * v[:, a] * v[:, b])) / FCONV
+        return out
+
     def run(self, vel, nsteps, dt, integrator=INTEGRATOR_LANGEVIN_BAOAB, T=1200.0, gamma=1.0,
             F=None, tdamp=0.1, nh_chain=3, kmodes=None, all_shell=False):
         """Advance (pos, vel) by ``nsteps``; returns (vel, F).  Forces at step s use

@@ -575,6 +575,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   }
   if ((rc = dalloc(ctx, &v.lflag, 1)) || (rc = dalloc(ctx, &v.nbuild, 1)) ||
       (rc = dalloc(ctx, &v.nh, rb::NH_STATE)) || (rc = dalloc(ctx, &v.ke_part, (size_t)v.nh_nblk)) ||
+      (rc = dalloc(ctx, &v.kin_part, 6 * (size_t)v.nh_nblk)) || (rc = dalloc(ctx, &v.kin, 6)) ||
       (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
                 (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
     free_system(ctx);
@@ -793,6 +794,23 @@ int rbsog_sync(rbsog_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   if (!ctx->has_system) return RBSOG_OK;
   return read_err(ctx);
+}
+
+int rbsog_get_kinetic_tensor(rbsog_ctx *ctx, double *K, int ptr_kind) {
+  if (!ctx || !K) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (ptr_kind != RBSOG_PTR_HOST && ptr_kind != RBSOG_PTR_DEVICE) return fail(ctx, RBSOG_E_INVAL, "bad ptr_kind");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  rb::launch_kinetic_tensor(ctx->v, ctx->st);
+  if ((rc = check_launch(ctx))) return rc;
+  if (ptr_kind == RBSOG_PTR_HOST) {
+    CK(cudaMemcpyAsync(K, ctx->v.kin, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  } else {
+    CK(cudaMemcpyAsync(K, ctx->v.kin, 6 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  }
+  return leave(ctx);
 }
 
 int rbsog_get_thermostat(rbsog_ctx *ctx, double *eta, double *v_eta) {

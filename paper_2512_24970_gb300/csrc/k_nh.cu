@@ -16,6 +16,10 @@
 //             k_finish and k_nh_scale write the same partials within a step);
 //   k_nh_close one block: the partials in fixed order, the closing half step
 //             (B -> A) and its velocity scale; k_nh_scale applies that scale.
+//   k_kin_part / k_kin_sum  the kinetic tensor K_ab = sum_i m_i v_ia v_ib of
+//             the current velocities (block sums, then one block in block
+//             order), the velocity half of the stress S = K + W whose xy
+//             component is the Green-Kubo shear stress of Sec. 3.
 #include "nh.cuh"
 
 namespace rb {
@@ -54,6 +58,39 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_nh_scale(View p) {
   }
   const double t = block_sum(mv2(p, i));
   if (threadIdx.x == 0) p.ke_part[blockIdx.x] = t;
+}
+
+// (xx, yy, zz, xy, xz, yz), the order of the virial
+__global__ void __launch_bounds__(PREP_BLOCK) k_kin_part(View p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i < p.n) {
+    const int64_t n = p.n;
+    const double m = p.massv[p.spc[i]];
+    const double vx = p.v[i], vy = p.v[n + i], vz = p.v[2 * n + i];
+    t[0] = m * vx * vx; t[1] = m * vy * vy; t[2] = m * vz * vz;
+    t[3] = m * vx * vy; t[4] = m * vx * vz; t[5] = m * vy * vz;
+  }
+  for (int c = 0; c < 6; c++) {
+    const double b = block_sum(t[c]);
+    if (threadIdx.x == 0) p.kin_part[6 * (int64_t)blockIdx.x + c] = b;
+    __syncthreads();                              // block_sum's scratch is reused
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kin_sum(View p) {
+  for (int c = 0; c < 6; c++) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < p.nh_nblk; b += blockDim.x) x += p.kin_part[6 * (int64_t)b + c];
+    const double t = block_sum(x);
+    if (threadIdx.x == 0) p.kin[c] = t / FCONV;   // amu A^2/ps^2 -> eV
+    __syncthreads();
+  }
+}
+
+void launch_kinetic_tensor(const View &v, cudaStream_t st) {
+  k_kin_part<<<(unsigned)v.nh_nblk, PREP_BLOCK, 0, st>>>(v);
+  k_kin_sum<<<1, 256, 0, st>>>(v);
 }
 
 void launch_nh_close(const View &v, cudaStream_t st) {

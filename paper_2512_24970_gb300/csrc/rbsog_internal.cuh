@@ -108,6 +108,8 @@ struct View {
   double nh_Q[RBSOG_MAX_NH_CHAIN];  // chain masses [eV ps^2]
   double *nh;             // [NH_STATE] chain state
   double *ke_part;        // [nh_nblk] sum m v^2 per k_finish block
+  double *kin_part;       // [nh_nblk][6] block sums of m v_a v_b (kinetic tensor)
+  double *kin;            // [6] kinetic tensor K_ab = sum_i m_i v_ia v_ib [eV]
   int G;                  // M + 1
   int ntile, tile_atoms, nblk_atoms, nblk_kq, nblk_near;
   // per-atom state, caller order ([3][n] SoA)
@@ -379,6 +381,7 @@ void launch_farforce(const View &v, cudaStream_t st);
 void launch_finish(const View &v, cudaStream_t st, int mode);
 void launch_nh_close(const View &v, cudaStream_t st);
 void launch_nh_prime(const View &v, cudaStream_t st);
+void launch_kinetic_tensor(const View &v, cudaStream_t st);
 void launch_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
                   int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
                   int *batch, int *nbatch, double *weight);

@@ -38,7 +38,7 @@ MAX_KEPT = 512
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -136,6 +136,7 @@ def load():
     L.rbsog_get_list_builds.argtypes = [P, P]
     L.rbsog_set_core_radii.argtypes = [P, P]
     L.rbsog_get_thermostat.argtypes = [P, P, P]
+    L.rbsog_get_kinetic_tensor.argtypes = [P, P, I]
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
@@ -290,6 +291,17 @@ class Context:
         w = np.zeros(M + 1)
         self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
         return s.value, w, S.value
+
+    def kinetic_tensor(self, out=None):
+        """K_ab = sum_i m_i v_ia v_ib [eV], (xx, yy, zz, xy, xz, yz), of the current
+        velocities; with the virial W of compute_forces the stress is S = K + W.
+        ``out``: a CUDA float64 tensor of 6 to receive it on the device (no sync)."""
+        if out is not None:
+            self._ck(self._L.rbsog_get_kinetic_tensor(self.h, ctypes.c_void_p(out.data_ptr()), PTR_DEVICE))
+            return out
+        K = np.zeros(6)
+        self._ck(self._L.rbsog_get_kinetic_tensor(self.h, _np_ptr(K), PTR_HOST))
+        return K
 
     def thermostat(self):
         """Nose-Hoover chain (eta, v_eta) between steps."""

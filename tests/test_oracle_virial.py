@@ -101,3 +101,23 @@ def test_sampled_virial_unbiased(orc):
     X = np.array(X)
     z = (X.mean(0) - ref) / (X.std(0, ddof=1) / np.sqrt(len(X)))
     assert np.abs(z).max() < 5.0, z
+
+
+def test_kinetic_tensor(orc):
+    """K = sum_i m_i v_i (x) v_i: its trace is twice the kinetic energy
+    (kinetic2, which the Nose-Hoover conserved quantity pins), permuting the
+    axes of the velocities permutes K, and for Maxwell-Boltzmann velocities
+    K / N tends to kT times the identity (equipartition, per component)."""
+    w = W.rock_salt((5, 5, 5), seed=2, composition="LiCl")
+    S = make(orc, w)
+    v = W.maxwell_boltzmann(w, 1300.0, seed=3)
+    K = S.kinetic_tensor(v)
+    assert abs(K[:3].sum() - S.kinetic2(v)) < 1e-12 * S.kinetic2(v)
+    perm = [2, 0, 1]
+    Kp = S.kinetic_tensor(v[:, perm])
+    full = lambda k: np.array([[k[0], k[3], k[4]], [k[3], k[1], k[5]], [k[4], k[5], k[2]]])
+    np.testing.assert_allclose(full(Kp), full(K)[np.ix_(perm, perm)], rtol=1e-13)
+    kT = orc.KB * 1300.0
+    n = w.n
+    assert np.all(np.abs(K[:3] / (n * kT) - 1.0) < 5.0 * np.sqrt(2.0 / n))        # chi-square, n dof
+    assert np.all(np.abs(K[3:]) / (n * kT) < 5.0 / np.sqrt(n))                     # mean-zero products

@@ -249,3 +249,45 @@ def test_species_core_radii(rb, orc, kept):
     nA = (S.lists_skin(sel)["nA"] if kept else S.lists(sel)["ncore"])
     nA0 = (R.lists_skin(sel)["nA"] if kept else R.lists(sel)["ncore"])
     assert nA.sum() < 0.9 * nA0.sum()
+
+
+def test_bench_launch_configuration(rb, orc):
+    """The configuration the benchmark times: molten NaCl N = 64,000 (P_R = 20,
+    P_F = 500), kept lists rebuilt by the device whenever an atom has moved by
+    more than skin/2 (list_every = -1, skin 1.5 A, the autotuner's choice on
+    this workload), mixed precision, Langevin steps launched as the captured
+    step graph.  Stepping one launch at a time until the device rebuilds the
+    lists: the rebuilt lists and batches of 96 sampled atoms are bit-exact
+    against the oracle's, built at the same positions; three steps later (the
+    same lists, new batches) they still are, and the sample's near field is
+    within the mixed tolerance of the oracle's FP64 one."""
+    w, cfg = W.make("nacl_64k")
+    ctx, S = setup_kept(rb, orc, w, skin=1.5, list_every=-1, P_R=cfg.P_R, P_F=cfg.P_F, precision=rb.MIXED,
+                        seed=cfg.seed)
+    ctx.set_velocities(W.maxwell_boltzmann(w, cfg.T))
+    ctx.step(1)
+    builds = ctx.list_builds()
+    for _ in range(80):
+        ctx.step(1)
+        if ctx.list_builds() > builds:
+            break
+    else:
+        pytest.fail("the device did not rebuild the lists in 80 steps at 1200 K")
+    builds = ctx.list_builds()
+    pos, _, step = ctx.get_state()
+    S.pos, S.step, S.build_pos = pos, step, pos.copy()
+    sel = np.linspace(0, w.n - 1, 96).astype(np.int64)
+    keys = ("nA", "nB", "A", "B", "nbatch", "batch", "weight")
+    g, o = ctx.debug_kept_lists(sel), S.lists_skin(sel, cap_a=64, cap_b=512)
+    for k in keys:
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    ctx.step(3)
+    pos, _, step = ctx.get_state()
+    if ctx.list_builds() != builds:                  # rebuilt again within three steps: rare
+        S.build_pos = pos.copy()
+    S.pos, S.step = pos, step
+    parts = ctx.debug_parts()
+    g, o = ctx.debug_kept_lists(sel), S.lists_skin(sel, cap_a=64, cap_b=512)
+    for k in keys:
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL

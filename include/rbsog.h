@@ -208,9 +208,28 @@ int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int
 /* Overwrite the state (pos/vel may be NULL to keep them); forces are
  * re-evaluated at the new state before the next step.  Because every draw
  * depends only on (seed, step, index), save + restore + run(n) reproduces
- * run(2n) bit for bit. */
+ * run(2n) bit for bit; with kept lists the lists depend on the positions of
+ * their last build too, so a restore passes those on as well
+ * (rbsog_get_list_origin / rbsog_set_list_origin), else the restored run
+ * builds its lists at the restored positions (an equally valid sample path,
+ * not the same one). */
 int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_t step,
                     int ptr_kind);
+
+/* Kept lists (list_every != 0): the positions [n][3] FP64 [A] of the last
+ * build of the lists the next evaluation uses, caller order.  Errors:
+ * RBSOG_E_INVAL without kept lists or before the first evaluation. */
+int rbsog_get_list_origin(rbsog_ctx *ctx, double *pos_b, int ptr_kind);
+
+/* Kept lists: the next evaluation builds its lists from the positions pos_b
+ * (binned, listed and recorded as the build positions exactly as a build at
+ * pos_b would be) and evaluates at the current positions.  Call after
+ * rbsog_set_state (which lets lists be rebuilt at the restored positions);
+ * with the saved state it resumes a run bit for bit.  The caller keeps the
+ * build within skin/2 of the current positions, as a run does (a fixed
+ * schedule reports RBSOG_E_SKIN otherwise, the automatic one rebuilds).
+ * Errors: RBSOG_E_INVAL without kept lists, RBSOG_E_CUDA. */
+int rbsog_set_list_origin(rbsog_ctx *ctx, const double *pos_b, int ptr_kind);
 
 /* Builds of the kept random batch lists since rbsog_set_system (waits for the
  * context's work).  Host pointer. */

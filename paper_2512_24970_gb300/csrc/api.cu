@@ -41,6 +41,9 @@ struct rbsog_ctx {
   uint64_t graph_gen = 0;                // bumped at every capture
   bool graph_ok = false;
   bool lists_valid = false;              // kept lists built since the last set_system / set_state
+  bool origin_pending = false;           // the next build uses x_origin (rbsog_set_list_origin)
+  double *x_origin = nullptr;            // [3][n] positions for that build
+  double *x_save = nullptr;              // [3][n] the current positions meanwhile
   bool nh_primed = false;                // Nose-Hoover: 2K of the current velocities is in the chain state
   int64_t host_step = 0;                 // mirror of the device step counter
   bool own_stream = false;
@@ -85,6 +88,8 @@ void free_system(rbsog_ctx *ctx) {
   ctx->gexec_keep = nullptr;
   ctx->graph_ok = false;
   ctx->lists_valid = false;
+  ctx->origin_pending = false;
+  ctx->x_origin = ctx->x_save = nullptr;
   for (void *p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->has_system = false;
@@ -174,7 +179,31 @@ int run_force(rbsog_ctx *ctx, const View &v0, int mode, int step_off, bool energ
 
 // The view of a one-off evaluation: kept lists that are not valid are built
 // (automatic lists: by raising the device flag the binning kernels check).
+// Kept lists from the positions of rbsog_set_list_origin: one evaluation that
+// bins and builds at those positions (its forces are discarded), then the
+// current positions back.  The lists, slots and build positions are then those
+// of a build at the origin, whatever the current positions are.
+int build_at_origin(rbsog_ctx *ctx) {
+  View &v = ctx->v;
+  const size_t bytes = sizeof(double) * 3 * (size_t)ctx->n;
+  CK(cudaMemcpyAsync(ctx->x_save, v.x, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+  CK(cudaMemcpyAsync(v.x, ctx->x_origin, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+  View vb = v;
+  vb.build = 1;
+  if (v.auto_lists) CK(cudaMemsetAsync(v.lflag, 0x01, sizeof(int), ctx->st));
+  int rc = run_force(ctx, vb, 0, 0, false);
+  CK(cudaMemcpyAsync(v.x, ctx->x_save, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+  if (rc) return rc;
+  ctx->origin_pending = false;
+  ctx->lists_valid = true;
+  return RBSOG_OK;
+}
+
 int eval_view(rbsog_ctx *ctx, View &vv) {
+  if (ctx->origin_pending && !ctx->lists_valid) {
+    const int rc = build_at_origin(ctx);
+    if (rc) return rc;
+  }
   vv = ctx->v;
   vv.build = (ctx->lists_valid && !ctx->v.auto_lists) ? 0 : 1;
   if (ctx->v.auto_lists && !ctx->lists_valid) CK(cudaMemsetAsync(ctx->v.lflag, 0x01, sizeof(int), ctx->st));
@@ -785,6 +814,34 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
   ctx->lists_valid = false;
   ctx->nh_primed = false;
   ctx->host_step = step;
+  return leave(ctx);
+}
+
+int rbsog_get_list_origin(rbsog_ctx *ctx, double *pos_b, int ptr_kind) {
+  if (!ctx || !pos_b) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "no kept lists (list_every = 0)");
+  if (!ctx->lists_valid) return fail(ctx, RBSOG_E_INVAL, "no kept lists yet: evaluate forces first");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if ((rc = export_aos(ctx, ctx->v.xb, nullptr, pos_b, ptr_kind))) return rc;
+  return leave(ctx);
+}
+
+int rbsog_set_list_origin(rbsog_ctx *ctx, const double *pos_b, int ptr_kind) {
+  if (!ctx || !pos_b) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "no kept lists (list_every = 0)");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if (!ctx->x_origin && ((rc = dalloc(ctx, &ctx->x_origin, 3 * (size_t)ctx->n)) ||
+                         (rc = dalloc(ctx, &ctx->x_save, 3 * (size_t)ctx->n))))
+    return rc;
+  if ((rc = import_aos(ctx, pos_b, ctx->x_origin, ptr_kind))) return rc;
+  if (ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));   // the staging buffer is reused
+  ctx->origin_pending = true;
+  ctx->lists_valid = false;
+  ctx->forces_valid = false;
   return leave(ctx);
 }
 

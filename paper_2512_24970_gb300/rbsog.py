@@ -38,7 +38,8 @@ MAX_KEPT = 512
 EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
-    "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor",
+    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -137,6 +138,8 @@ def load():
     L.rbsog_set_core_radii.argtypes = [P, P]
     L.rbsog_get_thermostat.argtypes = [P, P, P]
     L.rbsog_get_kinetic_tensor.argtypes = [P, P, I]
+    L.rbsog_get_list_origin.argtypes = [P, P, I]
+    L.rbsog_set_list_origin.argtypes = [P, P, I]
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
@@ -291,6 +294,17 @@ class Context:
         w = np.zeros(M + 1)
         self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
         return s.value, w, S.value
+
+    def list_origin(self):
+        """Kept lists: the positions [n, 3] of their last build (with get_state, what a restore needs)."""
+        out = np.zeros((self.n, 3))
+        self._ck(self._L.rbsog_get_list_origin(self.h, _np_ptr(out), PTR_HOST))
+        return out
+
+    def set_list_origin(self, pos_b):
+        """Kept lists: build the next evaluation's lists from the positions pos_b [n, 3]."""
+        a = np.ascontiguousarray(pos_b, dtype=np.float64).reshape(-1, 3)
+        self._ck(self._L.rbsog_set_list_origin(self.h, _np_ptr(a), PTR_HOST))
 
     def kinetic_tensor(self, out=None):
         """K_ab = sum_i m_i v_ia v_ib [eV], (xx, yy, zz, xy, xz, yz), of the current

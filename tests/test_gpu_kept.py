@@ -291,3 +291,42 @@ def test_bench_launch_configuration(rb, orc):
     for k in keys:
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
     assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL
+
+
+@pytest.mark.parametrize("list_every", [-1, 4])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kept_resume_bit_identical(rb, orc, list_every, precision):
+    """Save + restore + run(n) = run(2n) bit for bit with kept lists when the
+    restore passes the lists' build positions on (rbsog_get_list_origin /
+    rbsog_set_list_origin): automatic rebuilds and a fixed schedule (the split
+    falls between two builds), both precisions.  Without the origin the
+    restored run builds at the restored positions and departs."""
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    v0 = W.maxwell_boltzmann(w, 2500.0)
+    prec = rb.FP64 if precision == "fp64" else rb.MIXED
+    runs = []
+    for mode in ("continuous", "origin", "no_origin"):
+        ctx, _ = setup_kept(rb, orc, w, skin=0.4, list_every=list_every, P_F=100, precision=prec)
+        ctx.set_velocities(v0)
+        if mode == "continuous":
+            ctx.step(14)
+            runs.append(ctx.get_state())
+            builds = ctx.list_builds()
+            continue
+        ctx.step(7)
+        p, v, s = ctx.get_state()
+        origin = ctx.list_origin()
+        moved = not np.array_equal(origin, p)            # the last build was before the split
+        assert moved or list_every == -1
+        ctx2, _ = setup_kept(rb, orc, w, skin=0.4, list_every=list_every, P_F=100, precision=prec)
+        ctx2.set_state(p, v, s)
+        if mode == "origin":
+            ctx2.set_list_origin(origin)
+        ctx2.step(7)
+        runs.append(ctx2.get_state())
+    assert builds >= 3                                   # several builds, some before the split
+    np.testing.assert_array_equal(runs[1][0], runs[0][0])
+    np.testing.assert_array_equal(runs[1][1], runs[0][1])
+    assert runs[1][2] == runs[0][2] == 14
+    if moved:
+        assert not np.array_equal(runs[2][0], runs[0][0])

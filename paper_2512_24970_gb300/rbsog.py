@@ -329,6 +329,36 @@ class Context:
         ve = np.ascontiguousarray(v_eta, dtype=np.float64)
         self._ck(self._L.rbsog_set_thermostat(self.h, _np_ptr(eta), _np_ptr(ve)))
 
+    def checkpoint(self, path=None):
+        """What a bit-for-bit restart needs: positions, velocities and step
+        counter, the kept lists' build positions (kept lists, once evaluated)
+        and the Nose-Hoover chain (Nose-Hoover runs).  Returns a dict; with
+        ``path`` also writes it with numpy.savez."""
+        pos, vel, step = self.get_state()
+        ck = {"pos": pos, "vel": vel, "step": np.int64(step)}
+        if self.params.list_every != 0:
+            try:
+                ck["list_origin"] = self.list_origin()
+            except RbsogError:          # no lists yet: a restore builds at the restored positions, as this would
+                pass
+        if self.params.integrator == NOSE_HOOVER:
+            ck["nh_eta"], ck["nh_v"] = self.thermostat()
+        if path is not None:
+            np.savez(path, **ck)
+        return ck
+
+    def restore(self, ck):
+        """Resume from checkpoint() (its dict or the .npz it wrote) on a context
+        with the same system and parameters."""
+        if not isinstance(ck, dict):
+            with np.load(ck) as f:
+                ck = {k: f[k] for k in f.files}
+        self.set_state(ck["pos"], ck["vel"], int(ck["step"]))
+        if "list_origin" in ck:
+            self.set_list_origin(ck["list_origin"])
+        if "nh_eta" in ck:
+            self.set_thermostat(ck["nh_eta"], ck["nh_v"])
+
     def set_core_radii(self, r_core_pair=None):
         """Species-dependent core radii [ns][ns] (None: the single r_core)."""
         t = None if r_core_pair is None else np.ascontiguousarray(r_core_pair, dtype=np.float64)

@@ -330,3 +330,36 @@ def test_kept_resume_bit_identical(rb, orc, list_every, precision):
     assert runs[1][2] == runs[0][2] == 14
     if moved:
         assert not np.array_equal(runs[2][0], runs[0][0])
+
+
+def test_checkpoint_file_restart(rb, orc, tmp_path):
+    """Context.checkpoint / restore through a file: a Nose-Hoover run with
+    automatic kept lists, stopped halfway, written, read into a new context
+    and continued, ends bit for bit where the uninterrupted run ends."""
+    w = W.rock_salt((6, 6, 6), seed=5, composition="LiCl-NaCl")
+    v0 = W.maxwell_boltzmann(w, 2200.0)
+    S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=20, P_F=100, seed=7)
+    prm = rb.MethodParams(s=S.s, w0=float(S.w[0]), P_R=20, P_F=100, seed=7, precision=rb.MIXED,
+                          integrator=rb.NOSE_HOOVER, T=1800.0, tdamp=0.05, nh_chain=3, list_every=-1, skin=0.4)
+
+    def fresh():
+        c = rb.Context(0)
+        c.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
+        c.set_velocities(v0)
+        return c
+
+    ref = fresh()
+    ref.step(16)
+    end = ref.get_state()
+    first = fresh()
+    first.step(8)
+    first.checkpoint(str(tmp_path / "ck.npz"))
+    second = fresh()
+    second.restore(str(tmp_path / "ck.npz"))
+    second.step(8)
+    got = second.get_state()
+    assert ref.list_builds() >= 3
+    np.testing.assert_array_equal(got[0], end[0])
+    np.testing.assert_array_equal(got[1], end[1])
+    assert got[2] == end[2] == 16
+    np.testing.assert_array_equal(second.thermostat()[1], ref.thermostat()[1])

@@ -399,26 +399,40 @@ def run_ours(args):
     # ---- end to end through the public API (host buffers) --------------------
     e2e = None
     if not args.no_e2e:
-        pos_h = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
-        frc_h = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
-        pos_h[:] = w.pos
-        ctx.set_profiling(False)
-        ctx2 = ctx
+        # a caller that integrates on its side: every step hands the positions
+        # over from pinned host memory and reads the forces back.  The positions
+        # are those of this run's own next steps, recorded beforehand, so the
+        # kept lists are rebuilt (by the device's skin/2 check) as often as in
+        # the run itself.
         Ke = args.e2e_steps
+        traj = torch.empty((Ke, w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        frc_h = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        ctx.set_profiling(False)
         with torch.cuda.stream(stream):
+            p0, v0s, s0 = ctx.get_state()
+            for k in range(Ke):
+                ctx.step(1)
+                ctx.get_state(pos=traj[k])
+            ctx.set_state(p0, v0s, s0)
             for k in range(3):
-                ctx2.set_state(pos_h, None, k)
-                ctx2.compute_forces(frc_h)
+                ctx.move_atoms(traj[k], s0 + 1 + k)
+                ctx.compute_forces(frc_h)
+            ctx.set_state(p0, v0s, s0)
+            ctx.compute_forces(frc_h)
+            b0 = ctx.list_builds()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(Ke):
-                ctx2.set_state(pos_h, None, k)     # H2D positions (pinned)
-                ctx2.compute_forces(frc_h)         # force evaluation, D2H forces (pinned)
+                ctx.move_atoms(traj[k], s0 + 1 + k)     # H2D positions (pinned)
+                ctx.compute_forces(frc_h)               # force evaluation, D2H forces (pinned)
             torch.cuda.synchronize()
             te = time.perf_counter() - t0
+            nb = ctx.list_builds() - b0
         e2e = {"value": w.n * Ke / te, "unit": "atom-steps/s", "h2d_bytes_per_step": 24 * w.n,
                "d2h_bytes_per_step": 24 * w.n,
-               "what": "rbsog_set_state(host positions) + rbsog_compute_forces(host forces) per step"}
+               "what": "rbsog_move_atoms(host positions of %d recorded steps of this run) + "
+                       "rbsog_compute_forces(host forces) per step%s" %
+                       (Ke, "; kept lists rebuilt by the device check: %d builds" % nb if list_every != 0 else "")}
     # ---- mixed vs FP64 force error on identical state and samples ---------------
     ferr = None
     if not args.no_force_error and prec == rbsog.MIXED and ws == 1:

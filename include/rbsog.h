@@ -216,6 +216,17 @@ int rbsog_get_state(rbsog_ctx *ctx, double *pos, double *vel, int64_t *step, int
 int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_t step,
                     int ptr_kind);
 
+/* Move the atoms to pos [n][3] FP64 [A] and set the step counter, keeping
+ * velocities and the kept lists: for a caller that integrates on its side
+ * and evaluates forces here every step.  As between two steps, the next
+ * evaluation reuses the lists of the last build unless some atom is more than
+ * skin/2 from its build position (automatic mode: rebuilt on the device;
+ * fixed schedule: RBSOG_E_SKIN, as the lists are rebuilt only by steps at
+ * multiples of list_every).  With per-step lists the same as rbsog_set_state
+ * with vel = NULL.  ptr_kind: host (synchronous) or device.  Errors:
+ * RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL, RBSOG_E_CUDA. */
+int rbsog_move_atoms(rbsog_ctx *ctx, const double *pos, int64_t step, int ptr_kind);
+
 /* Kept lists (list_every != 0): the positions [n][3] FP64 [A] of the last
  * build of the lists the next evaluation uses, caller order.  Errors:
  * RBSOG_E_INVAL without kept lists or before the first evaluation. */

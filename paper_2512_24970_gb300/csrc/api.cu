@@ -817,6 +817,21 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
   return leave(ctx);
 }
 
+int rbsog_move_atoms(rbsog_ctx *ctx, const double *pos, int64_t step, int ptr_kind) {
+  if (!ctx || !pos) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (step < 0) return fail(ctx, RBSOG_E_INVAL, "negative step");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if ((rc = import_aos(ctx, pos, ctx->v.x, ptr_kind))) return rc;
+  long long s = step;
+  CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
+  if (ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));   // s and the staging buffer
+  ctx->forces_valid = false;                   // the kept lists stay; the next evaluation checks them
+  ctx->host_step = step;
+  return leave(ctx);
+}
+
 int rbsog_get_list_origin(rbsog_ctx *ctx, double *pos_b, int ptr_kind) {
   if (!ctx || !pos_b) return RBSOG_E_INVAL;
   if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");

@@ -39,7 +39,7 @@ EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor",
-    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_move_atoms", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -139,6 +139,7 @@ def load():
     L.rbsog_get_thermostat.argtypes = [P, P, P]
     L.rbsog_get_kinetic_tensor.argtypes = [P, P, I]
     L.rbsog_get_list_origin.argtypes = [P, P, I]
+    L.rbsog_move_atoms.argtypes = [P, P, I64, I]
     L.rbsog_set_list_origin.argtypes = [P, P, I]
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
@@ -294,6 +295,14 @@ class Context:
         w = np.zeros(M + 1)
         self._ck(self._L.rbsog_get_sog(self.h, ctypes.byref(s), _np_ptr(w), ctypes.byref(S)))
         return s.value, w, S.value
+
+    def move_atoms(self, pos, step):
+        """Positions [n, 3] (numpy or CUDA tensor) and step counter, keeping the
+        velocities and the kept lists (rebuilt by the device check when needed)."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
+        pp, kind = _ptr_kind(pos)
+        self._ck(self._L.rbsog_move_atoms(self.h, pp, int(step), kind))
 
     def list_origin(self):
         """Kept lists: the positions [n, 3] of their last build (with get_state, what a restore needs)."""

@@ -363,3 +363,32 @@ def test_checkpoint_file_restart(rb, orc, tmp_path):
     np.testing.assert_array_equal(got[1], end[1])
     assert got[2] == end[2] == 16
     np.testing.assert_array_equal(second.thermostat()[1], ref.thermostat()[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_move_atoms_keeps_lists(rb, orc, precision):
+    """rbsog_move_atoms (positions from the caller, as a host-side integrator
+    gives them) keeps the kept lists: a move below skin/2 reuses the last build
+    (no new build; forces equal the oracle's kept-list forces with the old build
+    positions), a move past skin/2 makes the device rebuild at the new
+    positions (one more build; forces with those as build positions)."""
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    prec = rb.FP64 if precision == "fp64" else rb.MIXED
+    tol = 1e-12 if precision == "fp64" else MIXED_TOL
+    ctx, S = setup_kept(rb, orc, w, skin=1.0, list_every=-1, P_F=100, precision=prec)
+    ctx.compute_forces()
+    b0 = ctx.list_builds()
+    rng = np.random.default_rng(1)
+    small = w.pos + rng.uniform(-0.2, 0.2, w.pos.shape)      # every atom within 0.35 A < skin/2
+    ctx.move_atoms(small, 5)
+    Fg = ctx.compute_forces()
+    assert ctx.list_builds() == b0
+    S.pos, S.step, S.build_pos = small, 5, w.pos.copy()
+    assert rms_rel(Fg, S.forces()["F"]) < tol
+    big = small.copy()
+    big[0] += 0.8                                             # one atom past skin/2 from its build position
+    ctx.move_atoms(big, 6)
+    Fg = ctx.compute_forces()
+    assert ctx.list_builds() == b0 + 1
+    S.pos, S.step, S.build_pos = big, 6, big.copy()
+    assert rms_rel(Fg, S.forces()["F"]) < tol

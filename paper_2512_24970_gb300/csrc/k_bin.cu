@@ -54,37 +54,30 @@ __device__ void ksample_warp(const View &p, int q, long long s, int lane) {
   }
 }
 
-// Gaussian triple of the O-step: Box-Muller on Philox stream 2, block 0.
-__device__ __forceinline__ void noise3(const View &p, long long s, uint32_t i, double g[3]) {
+// Component a of the O-step's Gaussian triple: Box-Muller on Philox stream 2,
+// block 0, words (x, y, z, w) -> uniforms u0..u3 in (0, 1):
+// (g0, g1) = sqrt(-2 ln u0) (cos, sin)(2 pi u1), g2 = sqrt(-2 ln u2) cos(2 pi u3).
+// FP64 (noise1); mixed precision in FP32 on 24-bit uniforms (noise1f: FP64
+// transcendental throughput is low on this part, the noise needs no more).
+__device__ __forceinline__ double noise1(const View &p, long long s, uint32_t i, int a) {
   const uint4 w = draw(p.seed, s, i, 2u, 0u);
-  const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
-  const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
-  const double u2 = ((double)w.z + 0.5) * 2.3283064365386963e-10;
-  const double u3 = ((double)w.w + 0.5) * 2.3283064365386963e-10;
-  const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
-  double s0, c0, s1, c1;
-  sincospi(2.0 * u1, &s0, &c0);
-  sincospi(2.0 * u3, &s1, &c1);
-  g[0] = r0 * c0;
-  g[1] = r0 * s0;
-  g[2] = r1 * c1;
+  const uint32_t wu = a < 2 ? w.x : w.z, wa = a < 2 ? w.y : w.w;
+  const double u0 = ((double)wu + 0.5) * 2.3283064365386963e-10;
+  const double u1 = ((double)wa + 0.5) * 2.3283064365386963e-10;
+  const double r = sqrt(-2.0 * log(u0));
+  double sn, cs;
+  sincospi(2.0 * u1, &sn, &cs);
+  return a == 1 ? r * sn : r * cs;
 }
-
-// Mixed precision: the same Box-Muller transform in FP32 (FP64 transcendental
-// throughput is low on this part; the noise needs no more than FP32).
-__device__ __forceinline__ void noise3f(const View &p, long long s, uint32_t i, double g[3]) {
+__device__ __forceinline__ double noise1f(const View &p, long long s, uint32_t i, int a) {
   const uint4 w = draw(p.seed, s, i, 2u, 0u);
-  const float u0 = ((float)(w.x >> 8) + 0.5f) * 5.9604645e-08f;  // 24-bit uniforms in (0, 1)
-  const float u1 = ((float)(w.y >> 8) + 0.5f) * 5.9604645e-08f;
-  const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604645e-08f;
-  const float u3 = ((float)(w.w >> 8) + 0.5f) * 5.9604645e-08f;
-  const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
-  float s0, c0, s1, c1;
-  sincospif(2.0f * u1, &s0, &c0);
-  sincospif(2.0f * u3, &s1, &c1);
-  g[0] = r0 * c0;
-  g[1] = r0 * s0;
-  g[2] = r1 * c1;
+  const uint32_t wu = a < 2 ? w.x : w.z, wa = a < 2 ? w.y : w.w;
+  const float u0 = ((float)(wu >> 8) + 0.5f) * 5.9604645e-08f;
+  const float u1 = ((float)(wa >> 8) + 0.5f) * 5.9604645e-08f;
+  const float r = sqrtf(-2.0f * logf(u0));
+  float sn, cs;
+  sincospif(2.0f * u1, &sn, &cs);
+  return a == 1 ? r * sn : r * cs;
 }
 
 // Cell and row histograms; lanes of one warp that share a cell (or row) add once.
@@ -103,50 +96,62 @@ __device__ __forceinline__ bool skip_binning(const View &p) {
   return p.auto_lists && *(volatile const int *)p.lflag == 0;
 }
 
+// Three threads per atom, one per Cartesian component: the block takes
+// PREP_ATOMS atoms, component-major (threads [c PREP_ATOMS, (c + 1)
+// PREP_ATOMS) take component c), so the integrator's FP64 chain and the fixed
+// point run on three times the warps of one thread per atom (the FP64 pipe's
+// latency, not its throughput, bounds this kernel); the atom's first thread
+// then gathers the components (cell, slot refresh, displacement check in the
+// fixed order x, y, z, histograms).
+constexpr int PREP_ATOMS = 128;
+
 template <int MODE>
-__global__ void __launch_bounds__(PREP_BLOCK) k_prepare(View p, int step_off) {
+__global__ void __launch_bounds__(3 * PREP_ATOMS) k_prepare(View p, int step_off) {
+  __shared__ uint32_t su3[3][PREP_ATOMS];
+  __shared__ double sq3[3][PREP_ATOMS];
   const long long s = *p.step + step_off;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = threadIdx.x / PREP_ATOMS, li = threadIdx.x % PREP_ATOMS;
+  const int64_t i = (int64_t)blockIdx.x * PREP_ATOMS + li;
+  const int64_t n = p.n;
   // Nose-Hoover: the opening half step of the chain, every block alike
   const double s_open = (MODE == 1 && p.integ == RBSOG_NOSE_HOOVER) ? nh_open(p) : 1.0;
-  if (i >= p.n) return;
-  const int64_t n = p.n;
-  const int sp = p.spc[i];
-  double x[3] = {p.x[i], p.x[n + i], p.x[2 * n + i]};
-  if (MODE != 0) {
-    double v[3] = {p.v[i], p.v[n + i], p.v[2 * n + i]};
-    double F[3];
-    if (p.prec == RBSOG_FP64) {
-      F[0] = p.Fd[i]; F[1] = p.Fd[n + i]; F[2] = p.Fd[2 * n + i];
-    } else {
-      F[0] = p.Ff[i]; F[1] = p.Ff[n + i]; F[2] = p.Ff[2 * n + i];
-    }
-    const double kick = p.kick[sp];
-    for (int a = 0; a < 3; a++) v[a] = v[a] * s_open + kick * F[a];
-    if (MODE == 1) {
-      for (int a = 0; a < 3; a++) x[a] += p.dt * v[a];
-    } else {
-      double g[3];
-      if (p.prec == RBSOG_FP64) noise3(p, s, (uint32_t)i, g);
-      else noise3f(p, s, (uint32_t)i, g);
-      const double h = 0.5 * p.dt, so = p.sig_ou[sp];
-      for (int a = 0; a < 3; a++) {
-        x[a] += h * v[a];
-        v[a] = p.c1 * v[a] + so * g[a];
-        x[a] += h * v[a];
+  const bool act = i < n;
+  const bool keep_check = p.kept && (p.auto_lists || !p.build);   // displacement since the last build
+  if (act) {
+    const int sp = p.spc[i];
+    double x = p.x[c * n + i];
+    if (MODE != 0) {
+      double v = p.v[c * n + i];
+      const double F = p.prec == RBSOG_FP64 ? p.Fd[c * n + i] : (double)p.Ff[c * n + i];
+      v = v * s_open + p.kick[sp] * F;
+      if (MODE == 1) {
+        x += p.dt * v;
+      } else {
+        const double g = p.prec == RBSOG_FP64 ? noise1(p, s, (uint32_t)i, c) : noise1f(p, s, (uint32_t)i, c);
+        const double h = 0.5 * p.dt, so = p.sig_ou[sp];
+        x += h * v;
+        v = p.c1 * v + so * g;
+        x += h * v;
       }
+      p.x[c * n + i] = x;
+      p.v[c * n + i] = v;
     }
-    for (int a = 0; a < 3; a++) {
-      p.x[a * n + i] = x[a];
-      p.v[a * n + i] = v[a];
+    su3[c][li] = fixed_point(x, p.invL[c]);
+    if (keep_check) {
+      const double d = __dadd_rn(x, -p.xb[c * n + i]);
+      sq3[c][li] = __dmul_rn(d, d);
     }
   }
-  uint32_t u[3];
-  for (int a = 0; a < 3; a++) u[a] = fixed_point(x[a], p.invL[a]);
+  __syncthreads();
+  if (c != 0 || !act) return;
+  const int sp = p.spc[i];
+  const uint32_t u[3] = {su3[0][li], su3[1][li], su3[2][li]};
   const int cell = cell_of(u[0], p.nc[0]) + p.nc[0] * (cell_of(u[1], p.nc[1]) + p.nc[1] * cell_of(u[2], p.nc[2]));
   p.ua[i] = make_uint4(u[0], u[1], u[2], (uint32_t)sp);
   p.cellid[i] = cell;
   if (p.kept) {
+    // |x - x_build|^2 in the order x, y, z without contraction (the oracle's)
+    const double d2 = keep_check ? __dadd_rn(__dadd_rn(sq3[0][li], sq3[1][li]), sq3[2][li]) : 0.0;
     if (p.auto_lists) {
       // refresh the slot of the last build (unless the host asked for a build:
       // then there may be none yet) and raise the build flag when this atom
@@ -154,22 +159,12 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_prepare(View p, int step_off) {
       // binning kernels run only if the flag is up
       if (*(volatile int *)p.lflag == 0)
         p.su[p.slot_of[i]] = make_uint4(u[0], u[1], u[2], (uint32_t)i | ((uint32_t)sp << SU_SP_SHIFT));
-      double d2 = 0.0;
-      for (int a = 0; a < 3; a++) {
-        const double d = __dadd_rn(x[a], -p.xb[a * n + i]);
-        d2 = __dadd_rn(d2, __dmul_rn(d, d));
-      }
       const unsigned far = __ballot_sync(__activemask(), d2 > p.half_skin2);
       if (far && (threadIdx.x & 31) == __ffs(far) - 1) atomicOr(p.lflag, 1);   // one lane per warp
     } else if (!p.build) {
       // the lists and slots of the last build are kept: refresh this atom's
       // coordinates in its slot and check that it stayed within skin/2
       p.su[p.slot_of[i]] = make_uint4(u[0], u[1], u[2], (uint32_t)i | ((uint32_t)sp << SU_SP_SHIFT));
-      double d2 = 0.0;
-      for (int a = 0; a < 3; a++) {
-        const double d = __dadd_rn(x[a], -p.xb[a * n + i]);
-        d2 = __dadd_rn(d2, __dmul_rn(d, d));
-      }
       if (d2 > p.half_skin2) atomicOr(p.err, ERR_SKIN);
       return;                      // no binning in this evaluation
     }
@@ -322,10 +317,10 @@ void launch_ksample(const View &v, cudaStream_t st, int step_off) {
 // The cell and row histograms start at zero: cleared at set-up and, after
 // every use, by the near-field kernel (clear_counts) or by the caller.
 void launch_prepare(const View &v, cudaStream_t st, int mode, int step_off) {
-  const int blocks = (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);
-  if (mode == 0) k_prepare<0><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
-  else if (mode == 1) k_prepare<1><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
-  else k_prepare<2><<<blocks, PREP_BLOCK, 0, st>>>(v, step_off);
+  const int blocks = (int)((v.n + PREP_ATOMS - 1) / PREP_ATOMS);
+  if (mode == 0) k_prepare<0><<<blocks, 3 * PREP_ATOMS, 0, st>>>(v, step_off);
+  else if (mode == 1) k_prepare<1><<<blocks, 3 * PREP_ATOMS, 0, st>>>(v, step_off);
+  else k_prepare<2><<<blocks, 3 * PREP_ATOMS, 0, st>>>(v, step_off);
 }
 
 void launch_bin(const View &v, cudaStream_t st) {

@@ -349,37 +349,43 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
 
 // F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step
 // (Nose-Hoover: with the block's sum of m v^2 for the chain's closing half step).
+// Three threads per atom, one per component (component-major blocks of
+// PREP_BLOCK atoms, as k_prepare): the FP64 kick runs on three times the warps;
+// the atom's first thread forms m v^2 from the three updated components.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(PREP_BLOCK) k_finish(View p) {
+__global__ void __launch_bounds__(3 * PREP_BLOCK) k_finish(View p) {
   constexpr bool MIX = sizeof(R) == 4;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sv3[3][PREP_BLOCK];
+  const int c = threadIdx.x / PREP_BLOCK, li = threadIdx.x % PREP_BLOCK;
+  const int64_t i = (int64_t)blockIdx.x * PREP_BLOCK + li;
   const int64_t n = p.n;
+  const bool first = blockIdx.x == 0 && threadIdx.x == 0;
   // the step counter advances here, after both branches joined: every kernel
   // of the step that reads it (k-batch, noise, shell batch) has finished
-  if (MODE != 0 && i == 0) *p.step += 1;
-  if (i == 0 && p.auto_lists) *p.lflag = 0;     // the build flag of the next step starts down
-  if (i < n) {
-    double F[3];
-    for (int a = 0; a < 3; a++) {
-      const double fn = MIX ? (double)p.FNf[a * n + i] : p.FNd[a * n + i];
-      const double ff = MIX ? (double)p.FFf[a * n + i] : p.FFd[a * n + i];
-      F[a] = fn - p.red[a] + ff;
-    }
-    if (MIX) {
-      for (int a = 0; a < 3; a++) p.Ff[a * n + i] = (float)F[a];
-    } else {
-      for (int a = 0; a < 3; a++) p.Fd[a * n + i] = F[a];
-    }
+  if (MODE != 0 && first) *p.step += 1;
+  if (first && p.auto_lists) *p.lflag = 0;     // the build flag of the next step starts down
+  const bool act = i < n;
+  if (act) {
+    const double fn = MIX ? (double)p.FNf[c * n + i] : p.FNd[c * n + i];
+    const double ff = MIX ? (double)p.FFf[c * n + i] : p.FFd[c * n + i];
+    const double F = fn - p.red[c] + ff;
+    if (MIX) p.Ff[c * n + i] = (float)F;
+    else p.Fd[c * n + i] = F;
     if (MODE != 0) {
       const double kick = p.kick[p.spc[i]];
-      for (int a = 0; a < 3; a++) {
-        const double Fa = MIX ? (double)(float)F[a] : F[a];
-        p.v[a * n + i] += kick * Fa;
-      }
+      const double Fa = MIX ? (double)(float)F : F;
+      p.v[c * n + i] += kick * Fa;
+      sv3[c][li] = p.v[c * n + i];
     }
   }
   if (MODE != 0 && p.integ == RBSOG_NOSE_HOOVER) {
-    const double t = block_sum(mv2(p, i));
+    __syncthreads();
+    double m2 = 0.0;
+    if (c == 0 && act) {
+      const double vx = sv3[0][li], vy = sv3[1][li], vz = sv3[2][li];
+      m2 = p.massv[p.spc[i]] * (vx * vx + vy * vy + vz * vz);
+    }
+    const double t = block_sum(m2);
     if (threadIdx.x == 0) p.ke_part[blockIdx.x] = t;
   }
 }
@@ -423,13 +429,13 @@ void launch_farforce(const View &v, cudaStream_t st) {
 }
 
 void launch_finish(const View &v, cudaStream_t st, int mode) {
-  const int g = (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);
+  const int g = (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);   // the ke_part blocks of k_nh_scale
   if (v.prec == RBSOG_MIXED) {
-    if (mode == 0) k_finish<float, 0><<<g, PREP_BLOCK, 0, st>>>(v);
-    else k_finish<float, 1><<<g, PREP_BLOCK, 0, st>>>(v);
+    if (mode == 0) k_finish<float, 0><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
+    else k_finish<float, 1><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
   } else {
-    if (mode == 0) k_finish<double, 0><<<g, PREP_BLOCK, 0, st>>>(v);
-    else k_finish<double, 1><<<g, PREP_BLOCK, 0, st>>>(v);
+    if (mode == 0) k_finish<double, 0><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
+    else k_finish<double, 1><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
   }
 }
 

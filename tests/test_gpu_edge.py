@@ -80,3 +80,46 @@ def test_edge_cases(rb, orc, case, mode, precision):
     ctx.sync()
     p1, v1, s1 = ctx.get_state()
     assert s1 == 6 and np.isfinite(p1).all() and np.isfinite(v1).all()
+
+
+def test_empty_and_single_ion_rejected(rb):
+    """No system of fewer than two ions (a neutral system needs two): n = 0 and
+    n = 1 fail with RBSOG_E_INVAL and leave the context without a system."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    prm = rb.MethodParams()
+    ctx = rb.Context(0)
+    for n in (0, 1):
+        with pytest.raises(rb.RbsogError) as e:
+            ctx.set_system(w.pos[:n], w.species[:n], w.charge, w.mass, w.bmh, w.box, prm)
+        assert e.value.code == -1
+    with pytest.raises(rb.RbsogError) as e:
+        ctx.compute_forces()
+    assert e.value.code == -8                         # RBSOG_E_NO_SYSTEM
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_largest_batches(rb, orc, precision):
+    """P_R at its cap (RBSOG_MAX_PR = 64) and P_F = 2000 (four columns of the
+    structure factor, four chunks of the far-field force, the last ragged):
+    lists, batches and k-batch bit-exact, forces within the precision's bound."""
+    w = W.rock_salt((6, 6, 6), seed=8, composition="LiCl-NaCl")
+    P_R, P_F = 64, 2000
+    S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_R=P_R, P_F=P_F, seed=11, step=2)
+    prm = rb.MethodParams(s=S.s, w0=float(S.w[0]), P_R=P_R, P_F=P_F, seed=11,
+                          precision=rb.FP64 if precision == "fp64" else rb.MIXED)
+    ctx = rb.Context(0)
+    ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
+    ctx.set_state(w.pos, np.zeros_like(w.pos), 2)
+    Fg = ctx.compute_forces()
+    sel = np.arange(0, w.n, 29)
+    g = ctx.debug_lists(sel, cap_core=128, cap_shell=512)
+    o = S.lists(sel, cap_core=128, cap_shell=512)
+    for k in ("ncore", "nshell", "core", "shell", "nbatch", "batch", "weight"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    m, c, _ = S.kbatch()
+    mg, cg = ctx.debug_kbatch()
+    np.testing.assert_array_equal(mg, m)
+    ref = S.forces()["F"]
+    assert rms_rel(Fg, ref) < (1e-12 if precision == "fp64" else 1e-5)
+    ctx.close()

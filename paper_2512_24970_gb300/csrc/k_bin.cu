@@ -99,10 +99,11 @@ __device__ __forceinline__ bool skip_binning(const View &p) {
 // Three threads per atom, one per Cartesian component: the block takes
 // PREP_ATOMS atoms, component-major (threads [c PREP_ATOMS, (c + 1)
 // PREP_ATOMS) take component c), so the integrator's FP64 chain and the fixed
-// point run on three times the warps of one thread per atom (the FP64 pipe's
-// latency, not its throughput, bounds this kernel); the atom's first thread
-// then gathers the components (cell, slot refresh, displacement check in the
-// fixed order x, y, z, histograms).
+// point run on three times the warps of one thread per atom (the FP64 pipe is
+// this kernel's busiest unit; the extra warps help it share the SMs with the
+// far-field branch); the atom's first thread then gathers the components
+// (cell, slot refresh, displacement check in the fixed order x, y, z,
+// histograms).
 constexpr int PREP_ATOMS = 128;
 
 template <int MODE>

@@ -8,8 +8,8 @@ fails.  The unchanged oracle passes the same pins in their own modules; the
 committed oracle source is never changed.  Together the cases show that a
 mistake in the pair terms (Eq. (Fshort)), the far field (Eqs. (Long),
 (long-rangeforce)), the phases, the list predicate, the shell batch (Sec. 2.2),
-the k-space sampler (Eq. (Pk)), the self term, the virial or the random
-streams does not pass the pins unnoticed."""
+the k-space sampler (Eq. (Pk)), the self term, the virial, the kept lists'
+indicator and weight, or the random streams does not pass the pins unnoticed."""
 import ctypes
 import importlib.util
 import os
@@ -57,12 +57,16 @@ CASES = [
      [("e2[q] = k * k * e0[q];", "e2[q] = e0[q];", 1)]),
     ("virial_xz_index", "virial", "test_two_atom_pair_virial", {},
      [("w[4] += d[0] * phi * d[2];", "w[4] += d[1] * phi * d[2];", 1)]),
+    ("kept_lists_without_indicator", "skin", "test_skin_whole_batch_is_cutoff_force_after_motion", {},
+     [("if (!(pred_r2(ui, uj, Gn.h) < Gn.rs2)) continue;", "(void)0;", 2)]),
+    ("kept_batch_unweighted", "skin", "test_skin_estimator_unbiased", {},
+     [("wgt = (double)n_b / (double)S->P_R;", "wgt = 1.0;", 1)]),
 ]
 
 
 @pytest.fixture(scope="module")
 def pins():
-    return {m: _load(m) for m in ("physics", "rng", "sog", "virial")}
+    return {m: _load(m) for m in ("physics", "rng", "sog", "virial", "skin")}
 
 
 def _build(orc, tmp_path, name, edits):

@@ -115,3 +115,63 @@ def test_control_unchanged_source_passes(orc, pins, tmp_path, pin):
     failure in a mutant case comes from its mistake."""
     mod, fn, kw = pin
     _run_pin(orc, pins, _build(orc, tmp_path, "control", []), mod, fn, dict(kw))
+
+
+# The oracle's Python parts (integrators, kinetic tensor): the same, with the
+# mistake planted in a copy of oracle/__init__.py loaded as a separate module
+# that uses the oracle's C library.
+PY_CASES = [
+    ("baoab_noise_amplitude", "langevin", "test_baoab_free_particles_relax_to_equipartition", {},
+     [("sig = np.sqrt((1.0 - c1 * c1) * KB", "sig = np.sqrt((1.0 - c1) * KB", 1)]),
+    ("baoab_friction_half", "langevin", "test_baoab_free_particles_relax_to_equipartition", {},
+     [("c1 = np.exp(-gamma * dt)", "c1 = np.exp(-0.5 * gamma * dt)", 1)]),
+    ("nose_hoover_G0_sign", "nh", "test_nh_conserves_extended_energy", {},
+     [("return (k2 - self.g * self.kT) / self.Q[0]", "return (k2 + self.g * self.kT) / self.Q[0]", 1)]),
+    ("nose_hoover_scale_direction", "nh", "test_nh_conserves_extended_energy", {},
+     [("s = float(np.exp(-d * self.v[0]))", "s = float(np.exp(d * self.v[0]))", 1)]),
+    ("kinetic_tensor_components", "virial", "test_kinetic_tensor", {},
+     [("for c, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):\n            out[c]",
+       "for c, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2))):\n            out[c]", 1)]),
+]
+
+
+@pytest.fixture(scope="module")
+def py_pins():
+    return {m: _load(m) for m in ("langevin", "nh", "virial")}
+
+
+def _py_oracle(orc, tmp_path, name, edits):
+    """A copy of the oracle's Python module with `edits` applied, on the oracle's C library."""
+    src_path = os.path.join(os.path.dirname(orc._SRC), "__init__.py")
+    with open(src_path) as f:
+        src = f.read()
+    for text, repl, count in edits:
+        assert src.count(text) == count, (name, text)
+        src = src.replace(text, repl)
+    path = str(tmp_path / ("oracle_%s.py" % name))
+    with open(path, "w") as f:
+        f.write(src)
+    spec = importlib.util.spec_from_file_location("oracle_" + name, path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    orc.lib()                                       # the oracle's library, built
+    mod._SRC, mod._LIB, mod._lib = orc._SRC, orc._LIB, None   # the copy opens it with its own declarations
+    return mod
+
+
+@pytest.mark.parametrize("case", PY_CASES, ids=[c[0] for c in PY_CASES])
+def test_python_pin_catches_planted_mistake(orc, py_pins, tmp_path, case):
+    name, mod, fn, kw, edits = case
+    bad = _py_oracle(orc, tmp_path, name, edits)
+    with pytest.raises(AssertionError):
+        getattr(py_pins[mod], fn)(bad, **kw)
+
+
+PY_PINS = sorted({(c[1], c[2]) for c in PY_CASES})
+
+
+@pytest.mark.parametrize("pin", PY_PINS, ids=["%s.%s" % p for p in PY_PINS])
+def test_python_control_unchanged_source_passes(orc, py_pins, tmp_path, pin):
+    mod, fn = pin
+    getattr(py_pins[mod], fn)(_py_oracle(orc, tmp_path, "control", []))
+

@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-force-error", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form beside the line")
+    ap.add_argument("--schedule", default=None,
+                    help="far-field schedule rho_variant,rho_blocks_per_sm,far_atoms_per_thread,far_segments,"
+                         "far_packed (default: tuned, or the library's with --no-autotune)")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-replica ensemble beside the line")
     ap.add_argument("--sweep", action="store_true",
                     help="shell batch x P_F sweep of the configuration (one JSON line each)")
     return ap.parse_args()
@@ -144,19 +149,60 @@ KERNELS_AUTO_STEP = 13
 KERNEL_LABEL = {"near": "k_near", "rho": "k_rho", "farforce": "k_farforce"}
 
 
-def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0, list_every=0, skin=0.0):
-    """Algorithmic FP32/INT lane-operations of one force evaluation, per stage
-    (the minimal instruction model of the design notes): near field = 8 ops per
-    list test of every neighbour inside the list radius (r_shell every step;
-    r_shell + skin once per list_every steps with kept lists) plus 25 per
-    evaluated pair (core + P_R shell); structure factor = 15 per (atom, k)
-    (3 phase IMAD, ~10 sincos, 2 FMA); far force = 21 per (atom, k)."""
+METRIC = "atom-steps/s of RBSOG+RBL force step at <=1e-5 RMS rel. force err, mixed vs FP64"
+
+# Algorithmic work per unit (the minimal operation model of the design notes):
+# lane multiply-add / FP32 operations on the FMA pipe, and issue slots when
+# two FP32 lanes share one packed FP32x2 instruction (integer multiply-adds
+# take a slot per lane).
+OPS_PAIR = 25.0            # one near-field pair (FP32 pair force, tabulated SOG part)
+OPS_TEST = 8.0             # one list-predicate test
+OPS_RHO = 3.0 + 10.0 + 2.0     # per (atom, k): phase (3 IMAD), sin + cos (10), 2 FMA into rho
+OPS_FAR = 3.0 + 5.0 + 3.0      # per (atom, k): phase (3 IMAD), one sine (5), 3 FMA into the force
+SLOTS_RHO = 3.0 + 12.0 / 2.0
+SLOTS_FAR = 3.0 + 8.0 / 2.0
+# the plain FP64 form, FP64 multiply-adds: per pair M+1 = 65 Gaussians (exp ~ 11 + 1
+# each) plus the BMH terms; per (atom, k) an FP64 sincospi (~15) plus 2 (rho) or 5 (force)
+DFMA_PAIR = 65 * 12.0 + 20.0
+DFMA_RHO = 15.0 + 2.0
+DFMA_FAR = 15.0 + 5.0
+
+
+def algorithmic_ops(w, P_F, P_R, r_core=6.0, r_shell=12.0, list_every=0, skin=0.0, builds_per_step=None):
+    """Algorithmic FMA-pipe lane operations of one force evaluation, per stage:
+    near field = OPS_TEST per list test of every neighbour inside the list
+    radius, performed at every step with per-step lists and at each build
+    (r_shell + skin) with kept lists, charged by the builds actually made per
+    step, plus OPS_PAIR per evaluated pair (core + P_R shell); structure factor
+    OPS_RHO and far force OPS_FAR per (atom, k).  Also the packed issue-slot
+    count of the two far-field kernels."""
     rho_n = w.n / float(np.prod(w.box))
-    r_list = r_shell + (skin if list_every > 0 else 0.0)
-    tests = 4.0 / 3.0 * np.pi * r_list ** 3 * rho_n / max(list_every, 1)
+    if list_every == 0:
+        tests = 4.0 / 3.0 * np.pi * r_shell ** 3 * rho_n
+    else:
+        bps = builds_per_step if builds_per_step is not None else 1.0 / max(list_every, 1)
+        tests = 4.0 / 3.0 * np.pi * (r_shell + skin) ** 3 * rho_n * bps
     n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
-    return {"near": w.n * (8.0 * tests + 25.0 * (n_core + P_R)),
-            "rho": 15.0 * w.n * P_F, "farforce": 21.0 * w.n * P_F}
+    ops = {"near": w.n * (OPS_TEST * tests + OPS_PAIR * (n_core + P_R)),
+           "rho": OPS_RHO * w.n * P_F, "farforce": OPS_FAR * w.n * P_F}
+    slots = {"rho": SLOTS_RHO * w.n * P_F, "farforce": SLOTS_FAR * w.n * P_F}
+    return ops, slots, tests
+
+
+def fp64_dfma(w, P_F, P_R, r_core=6.0):
+    rho_n = w.n / float(np.prod(w.box))
+    n_core = 4.0 / 3.0 * np.pi * r_core ** 3 * rho_n
+    return w.n * (DFMA_PAIR * (n_core + P_R) + (DFMA_RHO + DFMA_FAR) * P_F)
+
+
+def measured_peaks(rbsog, local):
+    """Multiply-add lane operations per second of the FP32 (scalar and packed),
+    FP64 and integer pipes, measured on this GPU (rbsog_probe_peak)."""
+    out = {}
+    for name, kind in (("fp32", rbsog.PROBE_FP32), ("fp32x2", rbsog.PROBE_FP32X2), ("fp64", rbsog.PROBE_FP64),
+                       ("imad", rbsog.PROBE_IMAD)):
+        out[name] = max(rbsog.probe_peak(local, kind) for _ in range(3))
+    return out
 
 
 def profiled_traffic(stage):
@@ -260,7 +306,7 @@ def run_reference(args):
             vals.append(v)
     value = float(np.median(vals))
     line = {
-        "impl": "reference", "metric": "atom-steps/s of RBSOG+RBL force step (FP64 CPU oracle)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * w.n / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -308,6 +354,18 @@ def run_ours(args):
                   "rejected": [{"skin": a, "why": r} for a, r in rejected],
                   "how": "200 timed steps per candidate after 20 warm-up, CUDA events (autotune.tune_skin)"}
 
+    sched, sched_tuning = None, None
+    if args.schedule:
+        sched = tuple(int(x) for x in args.schedule.split(","))
+    elif prec == rbsog.MIXED and not args.no_autotune:
+        from paper_2512_24970_gb300 import autotune
+        sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream)
+        sched_tuning = {"chosen": dict(zip(("rho_variant", "rho_blocks_per_sm", "far_atoms_per_thread",
+                                             "far_segments", "far_packed"), sched)),
+                        "candidates": [{"schedule": list(q), "ms_per_step": t} for q, t in table],
+                        "how": "100 timed MD steps per candidate after 10 warm-up, CUDA events, coordinate search "
+                               "(autotune.tune_schedule)"}
+
     def timed_run(params, clocks=None, k_stage=None):
         """Wm untimed steps, then K steps timed with CUDA events on the
         launching stream (L2 flushed before each; no event inside the step
@@ -316,6 +374,8 @@ def run_ours(args):
         Returns the context, the per-step ms and the mean stage times."""
         c = rbsog.Context(local, stream.cuda_stream)
         c.set_workload(w, params)
+        if sched is not None:
+            c.set_schedule(*sched)
         with torch.cuda.stream(stream):
             for _ in range(Wm):
                 flush.zero_()
@@ -323,6 +383,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             if ws > 1:
                 dist.barrier()
+            b0 = c.list_builds()
             if clocks:
                 clocks.start()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -337,6 +398,7 @@ def run_ours(args):
                 dist.barrier()
             if clocks:
                 clocks.pause()
+            builds_timed = c.list_builds() - b0
             ks = min(K, 500) if k_stage is None else k_stage
             st = np.zeros(rbsog.NSTAGE)
             mk = np.zeros(rbsog.NMARK)
@@ -348,18 +410,17 @@ def run_ours(args):
                 mk += c.stage_marks()
             c.set_profiling(False)
         c.sync()
-        return c, np.array([a.elapsed_time(b) for a, b in ev]), st / max(ks, 1), mk / max(ks, 1)
+        return c, np.array([a.elapsed_time(b) for a, b in ev]), st / max(ks, 1), mk / max(ks, 1), builds_timed
 
+    peak_ops = measured_peaks(rbsog, local)
     clocks = Clocks(local)
-    ctx, ms, stage_ms, marks = timed_run(prm, clocks)
+    ctx, ms, stage_ms, marks, builds_timed = timed_run(prm, clocks)
     clk = clocks.stop()
-    n_builds = ctx.list_builds()
-    n_steps_all = Wm + K + min(K, 500) + 1
     value, t_total, _ = aggregate(float(ms.sum()), float(w.n * K), dist if ws > 1 else None, dev)
     # the same steps with the random batch lists rebuilt from scratch at every step
     per_step = None
     if list_every != 0 and not args.no_per_step_lists:
-        c1, ms1, st1, mk1 = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
+        c1, ms1, st1, mk1, _ = timed_run(dataclasses.replace(prm, list_every=0, skin=0.0), k_stage=min(K, 200))
         c1.close()
         v1, t1, _ = aggregate(float(ms1.sum()), float(w.n * K), dist if ws > 1 else None, dev)
         per_step = {"value": v1, "unit": "atom-steps/s", "ms_per_step": t1 / K,
@@ -367,35 +428,71 @@ def run_ours(args):
                     "timeline_us": {n: round(float(t) * 1e3, 2) for n, t in zip(rbsog.MARKS, mk1)},
                     "what": "same workload and steps, random batch lists rebuilt from the positions at every step"}
     # ---- roofline of the dominant kernel -------------------------------------
-    pk, pk_kind = peaks()
+    # denominators measured on this GPU in this run (rbsog_probe_peak): the
+    # FP32 FMA pipe in lane multiply-adds per second (packed or not, the larger),
+    # and the issue rate (4 warp instructions per clock per SM at the clock the
+    # probe ran, i.e. the scalar FP32 probe's rate, one lane-op per slot)
     props = torch.cuda.get_device_properties(dev)
     nsm = props.multi_processor_count
-    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     names = rbsog.STAGES
-    alg = algorithmic_ops(w, P_F, P_R, list_every=list_every, skin=prm.skin)
-    peak_ops = ISSUE_PER_SM * 32 * nsm * f_max            # FP32/INT lane-ops per second (issue-bound)
+    bps = (builds_timed / K) if list_every != 0 else None
+    alg, slots, tests = algorithmic_ops(w, P_F, P_R, list_every=list_every, skin=prm.skin, builds_per_step=bps)
+    fma_peak = max(peak_ops["fp32"], peak_ops["fp32x2"])
+    issue_peak = peak_ops["fp32"]
     label = dict(KERNEL_LABEL)
     if list_every != 0:
-        label["near"] = "k_near_kept (+ list builds by k_near, amortised)"
-    # every hot kernel against the issue peak, from its own live events (the
+        label["near"] = "k_near_kept (+ list builds by k_near, charged per build made in the timed steps)"
+    # every hot kernel against the FMA-pipe peak, from its own live events (the
     # near field on the main stream, k_rho and k_farforce on the side stream,
     # running concurrently, so a live duration includes time spent sharing
-    # the SMs).  The dominant kernel is the one with the largest share of the
-    # serialised launch list: k_near with per-step lists, k_farforce with kept
-    # lists (whose branch also runs at the greater stream priority)
+    # the SMs); the dominant kernel is the one with the longest live time
     kern = {}
     for kname in ("near", "rho", "farforce"):
         t = stage_ms[names.index(kname)] * 1e-3
         kern[kname] = {"kernel": label[kname], "ms": t * 1e3, "achieved": alg[kname] / t / 1e9,
-                       "frac": alg[kname] / t / peak_ops}
-    dom = "farforce" if list_every != 0 else "near"
-    roof = {"bound": "alu", "kernel": label[dom], "achieved": kern[dom]["achieved"], "peak": peak_ops / 1e9,
+                       "frac": alg[kname] / t / fma_peak}
+        if kname in slots:
+            kern[kname]["issue_frac"] = slots[kname] / t / issue_peak
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    roof = {"bound": "alu", "kernel": label[dom], "achieved": kern[dom]["achieved"], "peak": fma_peak / 1e9,
             "unit": "Glane-op/s", "frac": kern[dom]["frac"],
             "traffic": profiled_traffic(dom) if not (dom == "near" and list_every != 0) else None,
-            "peak_source": "4 warp-instructions/clk/SM x 32 lanes x %d SMs x %.0f MHz (max clock)" % (nsm, f_max / 1e6)}
+            "peak_source": "measured in this run: FP32 multiply-add pipe, %d SMs (rbsog_probe_peak)" % nsm,
+            "ops_per_unit": {"near_pair": OPS_PAIR, "list_test": OPS_TEST, "rho_atom_k": OPS_RHO,
+                             "far_atom_k": OPS_FAR},
+            "units": {"atoms": w.n, "P_F": P_F, "pairs_per_atom": None if list_every == 0 else None,
+                      "list_tests_per_atom_step": tests}}
+    if "issue_frac" in kern[dom]:
+        roof["issue_frac"] = kern[dom]["issue_frac"]
     step_ops = sum(alg.values())
-    step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / peak_ops * 1e6,
-                 "frac": (step_ops / peak_ops) / (t_total / K * 1e-3)}
+    step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / fma_peak * 1e6,
+                 "frac": (step_ops / fma_peak) / (t_total / K * 1e-3),
+                 "what": "all algorithmic FMA-pipe work of the step at the measured FP32 multiply-add rate"}
+    # ---- the plain FP64 GPU form on the same workload ---------------------------
+    fp64 = None
+    if prec == rbsog.MIXED and not args.no_fp64:
+        Kd = max(3, min(K, 20))
+        cd = rbsog.Context(local, stream.cuda_stream)
+        cd.set_workload(w, dataclasses.replace(prm, precision=rbsog.FP64))
+        with torch.cuda.stream(stream):
+            cd.step(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cd.step(Kd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        cd.sync()
+        td = e0.elapsed_time(e1) / Kd
+        cd.close()
+        dfma = fp64_dfma(w, P_F, P_R)
+        fp64 = {"value": w.n / (td * 1e-3), "unit": "atom-steps/s", "ms_per_step": td, "steps": Kd,
+                "dfma_per_step": dfma, "peak_dfma_per_s": peak_ops["fp64"],
+                "frac": dfma / (td * 1e-3) / peak_ops["fp64"],
+                "mixed_over_fp64": (t_total / K) ** -1 / td ** -1 if td > 0 else None,
+                "what": "same workload, lists and integrator in the plain FP64 form (analytic pair terms with "
+                        "all M+1 Gaussians, FP64 sincospi, FP64 sums); DFMA model per pair %.0f, per (atom, k) "
+                        "%.0f; peak = measured FP64 multiply-add rate" % (DFMA_PAIR, DFMA_RHO + DFMA_FAR)}
     # ---- end to end through the public API (host buffers) --------------------
     e2e = None
     if not args.no_e2e:
@@ -459,22 +556,30 @@ def run_ours(args):
     else:
         launches = KERNELS_PER_STEP * K
     if rank == 0:
+        ens = None
+        if ws == 1 and not args.no_ensemble and args.config == "nacl_64k":
+            ens = ensemble_measure(args, K, Wm, with_sequential=True)
         line = {
-            "metric": "atom-steps/s of RBSOG+RBL force step at <=1e-5 RMS rel. force err, mixed vs FP64",
+            "metric": METRIC,
             "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
             "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
                        "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
                        "lists": ("per step" if not list_every else
-                                 ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in "
-                                  "%d steps)" % (prm.skin, n_builds, n_steps_all)) if list_every < 0 else
-                                 "kept: skin %.2f A, rebuilt every %d steps" % (prm.skin, list_every)),
-                       "skin_tuning": tuning,
+                                 ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in the "
+                                  "%d timed steps)" % (prm.skin, builds_timed, K)) if list_every < 0 else
+                                 "kept: skin %.2f A, rebuilt every %d steps (%d builds in the %d timed steps)" %
+                                 (prm.skin, list_every, builds_timed, K)),
+                       "list_builds_timed": builds_timed if list_every != 0 else K,
+                       "skin_tuning": tuning, "schedule_tuning": sched_tuning,
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "stage_ms": {n: float(t) for n, t in zip(names, stage_ms)},
             "timeline_us": {n: round(float(t) * 1e3, 2) for n, t in zip(rbsog.MARKS, marks)},
-            "roofline": roof, "kernel_rooflines": kern, "step_roofline": step_roof, "per_step_lists": per_step, "peaks": pk_kind, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "kernel_rooflines": kern, "step_roofline": step_roof, "per_step_lists": per_step,
+            "peaks": {"measured_here": {k: v / 1e9 for k, v in peak_ops.items()}, "unit": "G lane multiply-adds/s",
+                      "how": "rbsog_probe_peak, best of 3"},
+            "clocks": clk, "e2e": e2e, "fp64_gpu": fp64, "ensemble": ens,
             "gpu_launches": launches, "cpu_baseline": cpu, "force_error": ferr,
         }
         print(json.dumps(line), flush=True)
@@ -483,7 +588,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_ensemble(args):
+def ensemble_measure(args, K, Wm, with_sequential=True):
     """The replica ensemble (64 replicas of uneven size and composition, one
     ensemble step = one MD step of every replica, all overlapping on the GPU)
     against the same replicas stepped one after another on one stream."""
@@ -510,7 +615,6 @@ def run_ensemble(args):
         c.set_velocities(w.vel)
         natoms += w.n
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    K, Wm = args.steps, args.warmup
 
     def timed(step_fn):
         with torch.cuda.stream(stream):
@@ -529,33 +633,42 @@ def run_ensemble(args):
 
     t_ens = timed(lambda: ens.step(1))
     ens.sync()
-    # the same replicas one after another, each step on the ensemble's stream
-    solo = []
-    for r, (w, T) in enumerate(reps):
-        c = rbsog.Context(0, stream.cuda_stream)
-        c.set_workload(w, params(r, w, T))
-        solo.append(c)
+    out = {"value": natoms * K / (t_ens / 1000.0), "unit": "atom-steps/s", "ms_per_step": t_ens / K, "steps": K,
+           "workload": "64 replicas: N = 8 n^3, n in [4, 16] (N 512..32768), NaCl / LiCl / LiCl-NaCl, "
+                       "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
+           "lists": ("per step" if not list_every else
+                     "kept, rebuilt when an atom has moved by skin/2; skin min(1 A, L/2 - r_shell)"),
+           "launch": ens.launch_kind(), "l2": "flushed before every step (512 MiB memset)"}
+    if with_sequential:
+        # the same replicas one after another, each step on the ensemble's stream
+        solo = []
+        for r, (w, T) in enumerate(reps):
+            c = rbsog.Context(0, stream.cuda_stream)
+            c.set_workload(w, params(r, w, T))
+            solo.append(c)
 
-    def seq():
+        def seq():
+            for c in solo:
+                c.step(1)
+
+        t_seq = timed(seq)
+        out["sequential"] = {"value": natoms * K / (t_seq / 1000.0), "ms_per_step": t_seq / K,
+                             "what": "the same replicas stepped one after another on one stream"}
         for c in solo:
-            c.step(1)
-
-    t_seq = timed(seq)
-    line = {"metric": "atom-steps/s of RBSOG+RBL force step, replica ensemble", "value": natoms * K / (t_ens / 1000.0),
-            "unit": "atom-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": t_ens / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "64 replicas: N = 8 n^3, n in [4, 16] (N 512..32768), NaCl / LiCl / LiCl-NaCl, "
-                                   "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
-                       "lists": ("per step" if not list_every else
-                                 "kept, rebuilt when an atom has moved by skin/2; skin min(1 A, L/2 - r_shell)"),
-                       "launch": "one CUDA graph per ensemble step (every replica's step graph a child node)",
-                       "l2": "flushed before every step (512 MiB memset)"},
-            "sequential": {"value": natoms * K / (t_seq / 1000.0), "ms_per_step": t_seq / K,
-                           "what": "the same replicas stepped one after another on one stream"}}
-    print(json.dumps(line), flush=True)
-    for c in solo:
-        c.close()
+            c.close()
     ens.close()
+    return out
+
+
+def run_ensemble(args):
+    K, Wm = args.steps, args.warmup
+    e = ensemble_measure(args, K, Wm)
+    line = {"metric": "atom-steps/s of RBSOG+RBL force step, replica ensemble", "value": e["value"],
+            "unit": "atom-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": e["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {k: e[k] for k in ("workload", "atoms", "lists", "launch", "l2")},
+            "sequential": e.get("sequential")}
+    print(json.dumps(line), flush=True)
 
 
 def main():

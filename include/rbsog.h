@@ -58,7 +58,8 @@ extern "C" {
 /* ---- enums ---------------------------------------------------------------- */
 #define RBSOG_FP64 0   /* analytic FP64 pair terms (M+1 Gaussians), FP64 sincospi and sums */
 #define RBSOG_MIXED 1  /* FP32 pair math (tabulated SOG residual), exact integer phases,
-                          FP32 MUFU trig, FP64 structure-factor / energy / position sums */
+                          FP32 minimax sin/cos polynomials after an exact half-turn
+                          reduction, FP64 structure-factor / energy / position sums */
 
 #define RBSOG_NVE_VV 0          /* velocity Verlet */
 #define RBSOG_LANGEVIN_BAOAB 1  /* BAOAB splitting of the Langevin SDE of Sec. 2.3 */
@@ -260,29 +261,57 @@ int rbsog_sync(rbsog_ctx *ctx);
 /* SOG parameters in use: s, w[0..M] (w[0] modified), S = sum_{k!=0} k^2 Fhat(k). */
 int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
 
+/* ---- kernel schedule -------------------------------------------------------- */
+
+/* Launch shapes of the mixed-precision far field (Sec. 2.2: the structure
+ * factors rho(k_p) over all atoms and the force of Eq. (long-rangeforce),
+ * O(N P_F) work each, Sec. 2.4).  They split that work over the GPU and
+ * change nothing but the order in which FP32 and FP64 partial sums are added;
+ * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1). */
+typedef struct {
+  int32_t rho_variant;           /* structure factor block shape: 0 = two groups of 256 threads,
+                                    one pair of modes per thread; 1 = one group of 256; 2 = two
+                                    groups of 128 threads, two pairs each; 3 = four such groups;
+                                    4..7 = 0..3 in scalar FP32 instead of packed FP32x2 */
+  int32_t rho_blocks_per_sm;     /* structure factor: tiles of atoms per SM the tiling aims at, 1..8 */
+  int32_t far_atoms_per_thread;  /* far force: atoms per thread, 1, 2 or 4 */
+  int32_t far_segments;          /* far force: k segments per block of 8 warps, 1, 2, 4 or 8 */
+  int32_t far_packed;            /* far force: 1 = two modes per packed FP32x2 instruction, 0 = scalar */
+} rbsog_schedule;
+
+/* Set the schedule (host pointer).  Takes effect at the next evaluation (the
+ * step graph is captured again).  Errors: RBSOG_E_INVAL (a value out of
+ * range), RBSOG_E_CUDA. */
+int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched);
+
+/* The schedule in use (host pointer). */
+int rbsog_get_schedule(rbsog_ctx *ctx, rbsog_schedule *sched);
+
 /* ---- allocation-free entry point -------------------------------------------- */
 
 #define RBSOG_SF_STATIC_PMAX 1024  /* largest P of rbsog_structure_factor_static */
 
-/* Structure factors rho(k_p) = sum_j q_j exp(i k_p . r_j), k_p = 2 pi m_p / L
- * (the rho(k) of Eq. (Long), Sec. 2.2), of the context's current positions for
- * P caller modes, with the same exact integer phase m.u mod 2^32 and FP64
+/* Structure factors rho(k_p) = sum_j q_j exp(i k_p . r_j), k_p = 2 pi m_p / L,
+ * of the context's current positions for P caller modes, with the same exact integer phase m.u mod 2^32 and FP64
  * sincos as the FP64 force path.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory, e.g. an
  * analysis hook that samples S(k) = |rho(k)|^2 / N between MD steps while
  * other work is in flight (cudaFree synchronises the whole device, and a
  * caching allocator may already hold all free memory).  It allocates
  * nothing: its scratch is a static 2 MiB device array of RBSOG_SF_STATIC_PMAX x
- * 128 tile partials, whose address is looked up once per device on the first
- * call (make that first call outside stream capture).  Nothing in the scratch
+ * 128 tile partials, whose device address is looked up once per device, on that
+ * device's first call (make that first call outside stream capture).  Like
+ * every context, the cached address does not survive a cudaDeviceReset of the
+ * device: do not use the library across one.  Nothing in the scratch
  * has to start at zero (every partial read is written in the same call).
  *   m   [P][3] int32, DEVICE pointer (mode indices m_x, m_y, m_z)
  *   rho [P][2] FP64, DEVICE pointer (Re, Im), written
  * Asynchronous on the context's stream.  The scratch is shared by every
  * context of a device, so two calls that overlap in time (two contexts or
  * streams of one device, or host threads) race on it: serialise them.
- * Errors: RBSOG_E_INVAL (P < 0, P > RBSOG_SF_STATIC_PMAX, null or non-device
- * pointer), RBSOG_E_NO_SYSTEM, RBSOG_E_CUDA.  P = 0 does nothing. */
+ * Errors: RBSOG_E_INVAL (P < 0, P > RBSOG_SF_STATIC_PMAX, null pointer, or a
+ * pointer that is not memory of the context's device), RBSOG_E_NO_SYSTEM,
+ * RBSOG_E_CUDA.  P = 0 does nothing. */
 int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, double *rho);
 
 /* ---- parity hooks (test use) ---------------------------------------------- */
@@ -291,7 +320,7 @@ int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, d
  * counter, computed by the device list kernel that shares the hot path's
  * predicate and canonical order: core/shell rows of width cap_core/cap_shell
  * hold caller atom indices in canonical order (ascending (cell index of j,
- * j)), batch rows of width P_R the sampled shell neighbours in the same order,
+ * fixed-point x coordinate u_x of j, j)), batch rows of width P_R the sampled shell neighbours in the same order,
  * weight = N_shell/P_R (1 if the whole shell is taken).  Host pointers. */
 int rbsog_debug_get_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t cap_core,
                           int32_t cap_shell, int32_t *core, int32_t *ncore, int32_t *shell,
@@ -364,6 +393,20 @@ int rbsog_get_stage_times(rbsog_ctx *ctx, float *ms, int32_t nstage);
  * durations, both branches on one clock.  Requires profiling on.  Host
  * pointer; the first min(nmark, RBSOG_NMARK) entries are written. */
 int rbsog_get_stage_marks(rbsog_ctx *ctx, float *ms, int32_t nmark);
+
+/* Throughput of one arithmetic pipe of `cuda_device`, measured: every thread
+ * of 4 blocks of 512 per SM runs 8 independent multiply-add chains (FP32 fma,
+ * packed FP32x2 fma, FP64 fma or 32-bit integer multiply-add, as `kind`
+ * says); one warm-up launch, then one launch timed with CUDA events.
+ * *ops_per_s = lane multiply-adds per second (an FP32x2 instruction counts
+ * two).  These are the denominators of the rooflines the benchmark reports
+ * (Sec. 2.4 gives the method's cost as operation counts).  Host pointer;
+ * allocates and frees a small buffer.  Errors: RBSOG_E_INVAL, RBSOG_E_CUDA. */
+#define RBSOG_PROBE_FP32 0
+#define RBSOG_PROBE_FP32X2 1
+#define RBSOG_PROBE_FP64 2
+#define RBSOG_PROBE_IMAD 3
+int rbsog_probe_peak(int cuda_device, int kind, double *ops_per_s);
 
 /* Message of the last error of this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);

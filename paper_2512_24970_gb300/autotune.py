@@ -1,4 +1,5 @@
-"""Autotuner of the kept random batch lists' skin.
+"""Autotuners: the kept random batch lists' skin, and the launch schedule of
+the mixed-precision far field.
 
 With kept lists (``list_every = -1``) the skin trades the cost of a list build
 (its candidate tests grow as (r_shell + skin)^3) against how often one is needed
@@ -9,6 +10,13 @@ the same state, the steps are timed with CUDA events on the launching stream,
 and the fastest is chosen.  Every candidate gives an unbiased estimator of the
 same force, so the choice changes the samples, not what they estimate; runs
 that must be reproducible pass the chosen skin explicitly.
+
+The far-field schedule (``rbsog_schedule``: the structure factor's block shape
+and tiles per SM, the far force's atoms per thread and k segments per block)
+changes nothing but the order of partial sums.  Which shape is fastest depends
+on N, P_F and on what the near field leaves of the SMs (the two branches of
+the step run concurrently), so whole MD steps are timed for each candidate, by
+coordinate search: the structure-factor shapes first, then the far-force ones.
 """
 from __future__ import annotations
 
@@ -62,3 +70,63 @@ def tune_skin(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
         raise ValueError("no candidate skin runs on this system: %s" % rejected)
     best = min(table, key=lambda t: t[1])[0]
     return best, table, rejected
+
+
+RHO_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7)
+RHO_BLOCKS_PER_SM = (1, 2, 3, 4)
+FAR_ATOMS = (1, 2, 4)
+FAR_SEGMENTS = (1, 2, 4, 8)
+FAR_PACKED = (1, 0)
+
+
+def _time_steps(ctx, st, warmup, steps):
+    import torch
+    with torch.cuda.stream(st):
+        ctx.step(warmup)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ctx.step(steps)
+        b.record(st)
+        b.synchronize()
+    ctx.sync()
+    return a.elapsed_time(b) / steps
+
+
+def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None, warmup: int = 10,
+                  steps: int = 100):
+    """Time ``steps`` MD steps of workload ``w`` (mixed precision) on one
+    context for each far-field schedule of a coordinate search and return
+    (best schedule (rho_variant, rho_blocks_per_sm, far_atoms_per_thread,
+    far_segments, far_packed), [(schedule, ms per step)])."""
+    import torch
+    dev = torch.device("cuda", device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    ctx = rbsog.Context(device, st.cuda_stream)
+    ctx.set_workload(w, params)
+    table = []
+    best = ctx.schedule()
+    try:
+        best_t = None
+        for rv in RHO_VARIANTS:
+            for bps in RHO_BLOCKS_PER_SM:
+                q = (rv, bps) + tuple(best[2:])
+                ctx.set_schedule(*q)
+                t = _time_steps(ctx, st, warmup, steps)
+                table.append((q, t))
+                if best_t is None or t < best_t:
+                    best, best_t = q, t
+        timed = best                               # the far-force shape the first search used
+        for A in FAR_ATOMS:
+            for S in FAR_SEGMENTS:
+                for pk in FAR_PACKED:
+                    q = (timed[0], timed[1], A, S, pk)
+                    if q == timed:
+                        continue
+                    ctx.set_schedule(*q)
+                    t = _time_steps(ctx, st, warmup, steps)
+                    table.append((q, t))
+                    if t < best_t:
+                        best, best_t = q, t
+    finally:
+        ctx.close()
+    return best, table

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "librbsog.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "setup.cpp", "k_bin.cu", "k_near.cu", "k_far.cu", "k_static.cu", "k_nh.cu", "ensemble.cu"]
+SOURCES = ["api.cu", "setup.cpp", "k_bin.cu", "k_near.cu", "k_far.cu", "k_static.cu", "k_nh.cu", "ensemble.cu", "k_probe.cu"]
 
 
 def nvcc() -> str:

@@ -52,6 +52,8 @@ struct rbsog_ctx {
   cudaStream_t st2_hi = nullptr;                // the same at the device's greatest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
+  int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
+  rbsog_schedule sched{0, 2, 2, 4, 1};  // far-field launch shapes (rbsog_set_schedule)
 };
 
 namespace {
@@ -275,7 +277,7 @@ int ensure_kcap(rbsog_ctx *ctx, int P) {
   int rc;
   if ((rc = dalloc(ctx, &v.km, P)) || (rc = dalloc(ctx, &v.kc, P)) ||
       (rc = dalloc(ctx, &v.rho, 2 * (size_t)P)) || (rc = dalloc(ctx, &v.uf, P)) ||
-      (rc = dalloc(ctx, &v.kff, P)) || (rc = dalloc(ctx, &v.kfB, P)) ||
+      (rc = dalloc(ctx, &v.kpair, (size_t)P / 2 + 1)) ||
       (rc = dalloc(ctx, &v.kfd, 5 * (size_t)P)) ||
       (rc = dalloc(ctx, &v.rho_part, 2 * (size_t)P * (size_t)v.ntile)) || (rc = dalloc(ctx, &v.vf, P)))
     return rc;
@@ -283,10 +285,13 @@ int ensure_kcap(rbsog_ctx *ctx, int P) {
   return RBSOG_OK;
 }
 
+// Structure-factor tiles: enough blocks for rho_bps resident blocks per SM
+// (mixed: the block shape of the schedule's rho_variant; FP64: blocks of
+// RHO_BLOCK threads), at least 32 atoms per tile.
 void set_rho_tiling(rbsog_ctx *ctx, int P) {
   View &v = ctx->v;
   const int nky = (P + rb::RHO_BLOCK * rb::RHO_KPT - 1) / (rb::RHO_BLOCK * rb::RHO_KPT);
-  const int target = 4 * ctx->nsm;
+  const int target = (v.prec == RBSOG_MIXED ? ctx->rho_bps : 4) * ctx->nsm;
   int64_t nt = (target + nky - 1) / nky;
   nt = std::min<int64_t>(nt, (ctx->n + 31) / 32);
   nt = std::max<int64_t>(nt, 1);
@@ -562,6 +567,11 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   // chunks (8 padded slots) <= nslot / 8 + rows; one warp per chunk
   v.nblk_near = (int)(((n + 3 * (int64_t)v.ncell + rb::NEAR_CHUNK - 1) / rb::NEAR_CHUNK + (int64_t)v.nc[1] * v.nc[2] +
                        rb::NEAR_WARPS - 1) / rb::NEAR_WARPS);
+  v.far_A = ctx->sched.far_atoms_per_thread;
+  v.far_S = ctx->sched.far_segments;
+  v.rho_var = ctx->sched.rho_variant;
+  v.far_packed = ctx->sched.far_packed;
+  ctx->rho_bps = ctx->sched.rho_blocks_per_sm;
   set_rho_tiling(ctx, P.P_F);
   // self term U_F^self = k_e/2 sum_i q_i^2 F(0)
   double F0 = 0.0, q2 = 0.0;
@@ -1157,6 +1167,8 @@ int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, d
     CK(cudaPointerGetAttributes(&at, q));
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
       return fail(ctx, RBSOG_E_INVAL, "m and rho must be device pointers");
+    if (at.type == cudaMemoryTypeDevice && at.device != ctx->dev)
+      return fail(ctx, RBSOG_E_INVAL, "m and rho must be memory of the context's device");
   }
   void *scratch = nullptr;
   CK(rb::sf_static_scratch(ctx->dev, &scratch));
@@ -1165,6 +1177,39 @@ int rbsog_structure_factor_static(rbsog_ctx *ctx, int32_t P, const int32_t *m, d
   rb::launch_sf_static(ctx->v, P, m, rho, scratch, ctx->st);
   if ((rc = check_launch(ctx))) return rc;
   return leave(ctx);
+}
+
+int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!sched) return fail(ctx, RBSOG_E_INVAL, "null schedule");
+  const rbsog_schedule q = *sched;
+  const int A = q.far_atoms_per_thread, S = q.far_segments;
+  if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
+      (A != 1 && A != 2 && A != 4) ||
+      (S != 1 && S != 2 && S != 4 && S != 8))
+    return fail(ctx, RBSOG_E_INVAL, "schedule out of range");
+  ctx->sched = q;
+  if (!ctx->has_system) return RBSOG_OK;
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  CK(cudaStreamSynchronize(ctx->st));
+  View &v = ctx->v;
+  v.far_A = A;
+  v.far_S = S;
+  v.rho_var = q.rho_variant;
+  v.far_packed = q.far_packed;
+  ctx->rho_bps = q.rho_blocks_per_sm;
+  set_rho_tiling(ctx, v.P);
+  ctx->Pmax = 0;                               // tile partials for the new tiling
+  if ((rc = ensure_kcap(ctx, std::max(v.P, v.P_F)))) return rc;
+  ctx->graph_ok = false;
+  return leave(ctx);
+}
+
+int rbsog_get_schedule(rbsog_ctx *ctx, rbsog_schedule *sched) {
+  if (!ctx || !sched) return RBSOG_E_INVAL;
+  *sched = ctx->sched;
+  return RBSOG_OK;
 }
 
 int rbsog_set_profiling(rbsog_ctx *ctx, int on) {

@@ -1,13 +1,14 @@
 // Stage (d) far field and stage (e) second half (Sec. 2.2, Eq. (long-rangeforce)):
-//   k_rho     structure-factor partials rho(k_p) = sum_j q_j e^{i k_p . r_j} over
+//   k_rho_*   structure-factor partials rho(k_p) = sum_j q_j e^{i k_p . r_j} over
 //             an atom tile, phase k . r = 2 pi (m . u mod 2^32) / 2^32 reduced
 //             exactly in uint32; FP32 polynomial sincos with FP32 accumulation
 //             over at most 256 atoms, then FP64 (mixed), or FP64 sincospi (FP64).
 //   k_reduce  fixed-order FP64 sum over tiles (one block per k), the per-k
-//             force coefficients c_p Im rho_p, c_p Re rho_p.
+//             force records: c_p Im rho_p, c_p Re rho_p (FP64), or arg rho_p as
+//             an exact 32-bit turn and c_p |rho_p| k_p (mixed).
 //   k_corr    F^corr and U_N (and in energy evaluations the pair virial) from
 //             the near-field warp partials, fixed order.
-//   k_farforce F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
+//   k_farforce_* F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
 //   k_finish  F_i = F_N,i - F^corr + F_F,i and the closing half kick of the MD step.
 #include "nh.cuh"
 
@@ -22,11 +23,11 @@ __device__ __forceinline__ void sincos_phase_d(uint32_t th, double &s, double &c
   sincospi((double)(int)th * 4.656612873077393e-10, &s, &c);  // * 2^-31
 }
 
-template <typename R>
-__global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
-  constexpr bool MIX = sizeof(R) == 4;
+// FP64 structure factor: one block per (tile, 512 modes), two modes per
+// thread, FP64 sincospi of the exact phase and FP64 sums.
+__global__ void __launch_bounds__(RHO_BLOCK) k_rho_fp64(View p) {
   __shared__ uint4 sa[256];
-  __shared__ R sq[256];
+  __shared__ double sq[256];
   const int tid = threadIdx.x;
   const int tile = blockIdx.x;
   const int64_t a0 = (int64_t)tile * p.tile_atoms;
@@ -48,42 +49,19 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
     if (tid < cnt) {
       const uint4 u = p.ua[base + tid];
       sa[tid] = u;
-      sq[tid] = (R)p.qs[u.w];
+      sq[tid] = p.qs[u.w];
     }
     __syncthreads();
-    if (MIX) {
-      // the thread's two k in packed pairs
-      static_assert(RHO_KPT == 2, "packed structure factor takes two k per thread");
-      unsigned long long fr = 0ull, fi = 0ull;
-#pragma unroll 4
-      for (int a = 0; a < cnt; a++) {
-        const uint4 u = sa[a];
-        const float q = (float)sq[a];
-        const uint32_t th0 = mx[0] * u.x + my[0] * u.y + mz[0] * u.z;
-        const uint32_t th1 = mx[1] * u.x + my[1] * u.y + mz[1] * u.z;
-        unsigned long long s2, c2;
-        sincos_turn2(th0, th1, s2, c2);
-        const unsigned long long q2 = pk2(q, q);
-        fr = fma2(q2, c2, fr);
-        fi = fma2(q2, s2, fi);
-      }
-      float r0, r1, i0, i1;
-      up2(fr, r0, r1);
-      up2(fi, i0, i1);
-      re[0] += (double)r0; re[1] += (double)r1;
-      im[0] += (double)i0; im[1] += (double)i1;
-    } else {
-      for (int a = 0; a < cnt; a++) {
-        const uint4 u = sa[a];
-        const double q = (double)sq[a];
+    for (int a = 0; a < cnt; a++) {
+      const uint4 u = sa[a];
+      const double q = sq[a];
 #pragma unroll
-        for (int t = 0; t < RHO_KPT; t++) {
-          const uint32_t th = mx[t] * u.x + my[t] * u.y + mz[t] * u.z;
-          double s, c;
-          sincos_phase_d(th, s, c);
-          re[t] += q * c;
-          im[t] += q * s;
-        }
+      for (int t = 0; t < RHO_KPT; t++) {
+        const uint32_t th = mx[t] * u.x + my[t] * u.y + mz[t] * u.z;
+        double s, c;
+        sincos_phase_d(th, s, c);
+        re[t] += q * c;
+        im[t] += q * s;
       }
     }
   }
@@ -96,6 +74,130 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho(View p) {
     }
   }
 }
+
+// Mixed structure factor.  A block holds G groups of GT = 256 / NP threads;
+// thread t of every group takes the NP pairs of modes 2 NP t ... 2 NP t +
+// 2 NP - 1 of the block's 512 (one packed FP32x2 lane per mode), group g the
+// g-th share of the tile's atoms.  Per (atom, mode): the exact phase
+// th = m.u mod 2^32 with the half-turn offset 2^30 folded into its
+// multiply-add chain, phi and the half-turn bit from it (half_turn_2r), the
+// minimax sine (packed) and cosine (per lane, so that the FMA pipe's two
+// halves share the work with the integer multiply-adds, which run on one of
+// them), the half-turn sign on the charge, and FP32 sums over at most
+// RHO_MCHUNK atoms, added in FP64.  The groups' FP64 sums are added in group
+// order in shared memory: one partial per (mode, tile).  MINB is the
+// occupancy the register allocation is bounded for.  PK = false evaluates the
+// same operations per lane in scalar FP32 instructions (bit for bit the same
+// results; it leaves the FMA pipe's two halves to be filled independently).
+constexpr int RHO_MCHUNK = 256;
+constexpr int RHO_KTILE = RHO_BLOCK * RHO_KPT;    // modes per block row (512)
+template <int NP, int G, int MINB, bool PK>
+__global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p) {
+  constexpr int GT = RHO_BLOCK / NP;
+  __shared__ uint4 sa[G][RHO_MCHUNK];
+  __shared__ double2 sg[G > 1 ? G - 1 : 1][RHO_KTILE];
+  static_assert(RHO_KPT == 2 && GT * NP * 2 == RHO_KTILE, "packed pairs of modes per thread");
+  const int tid = threadIdx.x, grp = tid / GT, gt = tid % GT;
+  const int tile = blockIdx.x;
+  const int kb = blockIdx.y * RHO_KTILE + 2 * NP * gt;
+  const int64_t a0 = (int64_t)tile * p.tile_atoms;
+  const int64_t a1 = min(a0 + (int64_t)p.tile_atoms, p.n);
+  const int sub = (p.tile_atoms + G - 1) / G;
+  const int64_t g0 = min(a0 + (int64_t)grp * sub, a1), g1 = min(g0 + sub, a1);
+  int4 m[2 * NP];
+#pragma unroll
+  for (int t = 0; t < 2 * NP; t++) m[t] = kb + t < p.P ? p.km[kb + t] : make_int4(0, 0, 0, 0);
+  double re[2 * NP], im[2 * NP];
+#pragma unroll
+  for (int t = 0; t < 2 * NP; t++) re[t] = im[t] = 0.0;
+  const int nch = (sub + RHO_MCHUNK - 1) / RHO_MCHUNK;   // the same for every group
+  for (int c = 0; c < nch; c++) {
+    const int64_t base = g0 + (int64_t)c * RHO_MCHUNK;
+    const int cnt = (int)max((int64_t)0, min((int64_t)RHO_MCHUNK, g1 - base));
+    __syncthreads();
+    for (int e = gt; e < cnt; e += GT) {
+      uint4 u = p.ua[base + e];
+      u.w = __float_as_uint((float)p.qs[u.w]);
+      sa[grp][e] = u;
+    }
+    __syncthreads();
+    unsigned long long fr[NP], fi[NP];
+#pragma unroll
+    for (int q = 0; q < NP; q++) fr[q] = fi[q] = 0ull;
+#pragma unroll 4
+    for (int a = 0; a < cnt; a++) {
+      const uint4 u = sa[grp][a];
+      const float q = __uint_as_float(u.w);
+#pragma unroll
+      for (int j = 0; j < NP; j++) {
+        const int4 mA = m[2 * j], mB = m[2 * j + 1];
+        const uint32_t t0 = (uint32_t)mA.x * u.x + ((uint32_t)mA.y * u.y + ((uint32_t)mA.z * u.z + 0x40000000u));
+        const uint32_t t1 = (uint32_t)mB.x * u.x + ((uint32_t)mB.y * u.y + ((uint32_t)mB.z * u.z + 0x40000000u));
+        if (PK) {
+          const unsigned long long phi = half_turn_phi2(t0, t1);
+          const unsigned long long z = mul2(phi, phi);
+          const unsigned long long sn = sin_poly2(phi, z);
+          float z0, z1;
+          up2(z, z0, z1);
+          const unsigned long long cs = pk2(cos_poly(z0), cos_poly(z1));
+          const unsigned long long q2 = pk2(flip_by(q, t0), flip_by(q, t1));
+          fr[j] = fma2(q2, cs, fr[j]);
+          fi[j] = fma2(q2, sn, fi[j]);
+        } else {
+          const float p0 = half_turn_2r(t0) * SC_PI32, p1 = half_turn_2r(t1) * SC_PI32;
+          const float z0 = p0 * p0, z1 = p1 * p1;
+          const float q0 = flip_by(q, t0), q1 = flip_by(q, t1);
+          float r0, r1, i0, i1;
+          up2(fr[j], r0, r1);
+          up2(fi[j], i0, i1);
+          r0 = __fmaf_rn(q0, cos_poly(z0), r0);
+          r1 = __fmaf_rn(q1, cos_poly(z1), r1);
+          i0 = __fmaf_rn(q0, sin_poly(p0, z0), i0);
+          i1 = __fmaf_rn(q1, sin_poly(p1, z1), i1);
+          fr[j] = pk2(r0, r1);
+          fi[j] = pk2(i0, i1);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NP; j++) {
+      float x0, x1, y0, y1;
+      up2(fr[j], x0, x1);
+      up2(fi[j], y0, y1);
+      re[2 * j] += (double)x0; re[2 * j + 1] += (double)x1;
+      im[2 * j] += (double)y0; im[2 * j + 1] += (double)y1;
+    }
+  }
+  if (G > 1) {
+    if (grp > 0)
+#pragma unroll
+      for (int t = 0; t < 2 * NP; t++) sg[grp - 1][2 * NP * gt + t] = make_double2(re[t], im[t]);
+    __syncthreads();
+    if (grp != 0) return;
+#pragma unroll
+    for (int g = 0; g < G - 1; g++)
+#pragma unroll
+      for (int t = 0; t < 2 * NP; t++) {
+        const double2 e = sg[g][2 * NP * gt + t];
+        re[t] += e.x;
+        im[t] += e.y;
+      }
+  }
+#pragma unroll
+  for (int t = 0; t < 2 * NP; t++)
+    if (kb + t < p.P) {
+      double *d = p.rho_part + 2 * ((int64_t)(kb + t) * p.ntile + tile);
+      d[0] = re[t];
+      d[1] = im[t];
+    }
+}
+
+// the structure factor's launch shapes (rbsog_schedule::rho_variant):
+// (pairs per thread, groups per block, blocks per SM of the register bound,
+// packed); variants 4..7 are 0..3 in scalar FP32
+constexpr int RHO_VARIANTS = 8;
+constexpr int RHO_VARIANT_NP[RHO_VARIANTS] = {1, 1, 2, 2, 1, 1, 2, 2};
+constexpr int RHO_VARIANT_G[RHO_VARIANTS] = {2, 1, 2, 4, 2, 1, 2, 4};
 
 // F^corr = (1/N) sum of the near-field warp partials, and U_N.  Block b sums
 // the fixed slice b of the partials (thread-strided, then a fixed tree); the
@@ -185,20 +287,36 @@ __global__ void __launch_bounds__(256) k_reduce(View p) {
       const double c = p.kc[k];
       const double kx = TWO_PI * (double)m.x / p.L[0];
       const double ky = TWO_PI * (double)m.y / p.L[1];
-      const double kz = TWO_PI * (double)m.z / p.L[2];
-      const double A = c * si0, B = c * sr0;
+      const double kz_ = TWO_PI * (double)m.z / p.L[2];
       if (sizeof(R) == 4) {
-        p.kff[k] = make_float4((float)kx, (float)ky, (float)kz, (float)A);
-        p.kfB[k] = (float)B;
+        // the mixed force record: Psi = arg(rho) in 2^-32 turn (plus the
+        // half-turn offset 2^30), K = c |rho| k (Eq. (long-rangeforce) with
+        // Im(e^{-i k.r} rho) = |rho| sin(arg rho - k.r))
+        const double turn = atan2(si0, sr0) * (1.0 / TWO_PI);      // (-1/2, 1/2]
+        const uint32_t psi = (uint32_t)(unsigned long long)(long long)llrint(turn * 4294967296.0);
+        const double R = c * hypot(sr0, si0);
+        KPair &kp = p.kpair[k >> 1];
+        const int h = k & 1;
+        int *ra = h ? &kp.b.x : &kp.a.x;
+        ra[0] = -m.x; ra[1] = -m.y; ra[2] = -m.z;
+        ra[3] = (int)(psi + 0x40000000u);
+        float *kxy = &kp.kxy.x, *kz = &kp.kz.x;
+        kxy[h] = (float)(R * kx);
+        kxy[2 + h] = (float)(R * ky);
+        kz[h] = (float)(R * kz_);
+        if (!h && k == p.P - 1) {                      // odd P: the pair's second mode is zero
+          kp.b = make_int4(0, 0, 0, 0);
+          kxy[1] = kxy[3] = kz[1] = 0.0f;
+        }
       } else {
         double *o = p.kfd + 5 * (int64_t)k;
-        o[0] = kx; o[1] = ky; o[2] = kz; o[3] = A; o[4] = B;
+        o[0] = kx; o[1] = ky; o[2] = kz_; o[3] = c * si0; o[4] = c * sr0;
       }
       p.uf[k] = c * (sr0 * sr0 + si0 * si0);
       if (p.want_vir) {
         // (Fhat'/Fhat)(k^2) of the SOG transform, a_m = (b^m s)^2 = 1 / (2 h_m):
         // Fhat ~ sum_m w_m a_m^{3/2} e^{-a_m k^2/2}, Fhat' ~ -sum_m w_m a_m^{3/2} (a_m/2) e^{-a_m k^2/2}
-        const double k2 = kx * kx + ky * ky + kz * kz;
+        const double k2 = kx * kx + ky * ky + kz_ * kz_;
         double num = 0.0, den = 0.0;
         for (int g = 0; g < p.G; g++) {
           const double a = 0.5 / p.sog_h[g];
@@ -237,113 +355,140 @@ __global__ void k_energy(View p) {
     for (int c = 0; c < 6; c++) p.red[11 + c] = KE / p.V * w[c] + (c < 3 ? U : 0.0);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce(View p) {
-  constexpr bool MIX = sizeof(R) == 4;
-  // per k: (m_x, m_y, m_z, bits of -c Re rho); mixed: per pair of k the packed
-  // (k_x, k_x'; k_y, k_y') and (k_z, k_z'; c Im rho, c' Im rho')
+// FP64 far force: one thread per atom, the k-batch staged in shared memory,
+// F_F,i = -(k_e q_i / V) sum_p k_p (c Im rho_p cos th - c Re rho_p sin th).
+__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_fp64(View p) {
   __shared__ int4 sm[FORCE_KCHUNK];
-  __shared__ float4 ska[MIX ? FORCE_KCHUNK / 2 : 1];
-  __shared__ float4 skb[MIX ? FORCE_KCHUNK / 2 : 1];
-  __shared__ double skd[MIX ? 1 : FORCE_KCHUNK * 5];
-  __shared__ float sred[MIX ? FORCE_TPA - 1 : 1][MIX ? FORCE_BLOCK / FORCE_TPA : 1][3];
+  __shared__ double skd[FORCE_KCHUNK * 5];
   const int tid = threadIdx.x;
-  // MIX: FORCE_TPA warps per 32 atoms; warp segment g takes the k pairs
-  // g, g + FORCE_TPA, ... (warp-uniform shared-memory reads)
-  constexpr int TPA_ = MIX ? FORCE_TPA : 1;
-  constexpr int APB_ = FORCE_BLOCK / TPA_;    // atoms per block
-  const int w = tid >> 5, lane = tid & 31;
-  const int g = MIX ? w / (APB_ / 32) : 0;
-  const int al = MIX ? (w % (APB_ / 32)) * 32 + lane : tid;   // atom of the block
-  const int64_t i = (int64_t)blockIdx.x * APB_ + al;
+  const int64_t i = (int64_t)blockIdx.x * FORCE_BLOCK + tid;
   const bool act = i < p.n;
   const uint4 u = act ? p.ua[i] : make_uint4(0, 0, 0, 0);
   double ax = 0.0, ay = 0.0, az = 0.0;
   for (int k0 = 0; k0 < p.P; k0 += FORCE_KCHUNK) {
     const int cnt = min(FORCE_KCHUNK, p.P - k0);
-    const int cnt2 = (cnt + 1) & ~1;          // an odd chunk ends with a zero pair member
     __syncthreads();
-    for (int k = tid; k < cnt2; k += FORCE_BLOCK) {
-      if (MIX) {
-        int4 m = make_int4(0, 0, 0, 0);
-        float4 kf = make_float4(0.f, 0.f, 0.f, 0.f);
-        float B = 0.0f;
-        if (k < cnt) {
-          m = p.km[k0 + k];
-          kf = p.kff[k0 + k];
-          B = p.kfB[k0 + k];
-        }
-        sm[k] = make_int4(m.x, m.y, m.z, __float_as_int(-B));
-        float *a4 = reinterpret_cast<float *>(&ska[k >> 1]);
-        float *b4 = reinterpret_cast<float *>(&skb[k >> 1]);
-        a4[k & 1] = kf.x;
-        a4[2 + (k & 1)] = kf.y;
-        b4[k & 1] = kf.z;
-        b4[2 + (k & 1)] = kf.w;
-      } else if (k < cnt) {
-        sm[k] = p.km[k0 + k];
-        for (int a = 0; a < 5; a++) skd[5 * k + a] = p.kfd[5 * (int64_t)(k0 + k) + a];
-      }
+    for (int k = tid; k < cnt; k += FORCE_BLOCK) {
+      sm[k] = p.km[k0 + k];
+      for (int a = 0; a < 5; a++) skd[5 * k + a] = p.kfd[5 * (int64_t)(k0 + k) + a];
     }
     __syncthreads();
-    if (MIX) {
-      unsigned long long fx = 0ull, fy = 0ull, fz = 0ull;
-#pragma unroll 2
-      for (int k = 2 * g; k < cnt2; k += 2 * TPA_) {
-        const int4 m0 = sm[k], m1 = sm[k + 1];
-        const uint32_t th0 = (uint32_t)m0.x * u.x + (uint32_t)m0.y * u.y + (uint32_t)m0.z * u.z;
-        const uint32_t th1 = (uint32_t)m1.x * u.x + (uint32_t)m1.y * u.y + (uint32_t)m1.z * u.z;
-        unsigned long long s2, c2;
-        sincos_turn2(th0, th1, s2, c2);
-        const float4 ka = ska[k >> 1], kb = skb[k >> 1];
-        // Im(e^{-i theta} rho) c = c Im rho cos - c Re rho sin, two k at once
-        const unsigned long long sv =
-            fma2(c2, pk2(kb.z, kb.w), mul2(s2, pk2(__int_as_float(m0.w), __int_as_float(m1.w))));
-        fx = fma2(sv, pk2(ka.x, ka.y), fx);
-        fy = fma2(sv, pk2(ka.z, ka.w), fy);
-        fz = fma2(sv, pk2(kb.x, kb.y), fz);
-      }
-      float x0, x1, y0, y1, z0, z1;
-      up2(fx, x0, x1);
-      up2(fy, y0, y1);
-      up2(fz, z0, z1);
-      float sx = x0 + x1, sy = y0 + y1, sz = z0 + z1;
-      if (MIX && TPA_ > 1) {                   // the segments' sums, in segment order
-        if (g > 0) {
-          sred[g - 1][al][0] = sx;
-          sred[g - 1][al][1] = sy;
-          sred[g - 1][al][2] = sz;
-        }
-        __syncthreads();
-        if (g == 0)
-          for (int t = 0; t < TPA_ - 1; t++) {
-            sx += sred[t][al][0];
-            sy += sred[t][al][1];
-            sz += sred[t][al][2];
-          }
-      }
-      ax += (double)sx; ay += (double)sy; az += (double)sz;
-    } else {
-      for (int k = 0; k < cnt; k++) {
-        const int4 m = sm[k];
-        const uint32_t th = (uint32_t)m.x * u.x + (uint32_t)m.y * u.y + (uint32_t)m.z * u.z;
-        double s, c;
-        sincos_phase_d(th, s, c);
-        const double *kd = skd + 5 * k;
-        const double sv = c * kd[3] - s * kd[4];
-        ax += sv * kd[0];
-        ay += sv * kd[1];
-        az += sv * kd[2];
-      }
+    for (int k = 0; k < cnt; k++) {
+      const int4 m = sm[k];
+      const uint32_t th = (uint32_t)m.x * u.x + (uint32_t)m.y * u.y + (uint32_t)m.z * u.z;
+      double s, c;
+      sincos_phase_d(th, s, c);
+      const double *kd = skd + 5 * k;
+      const double sv = c * kd[3] - s * kd[4];
+      ax += sv * kd[0];
+      ay += sv * kd[1];
+      az += sv * kd[2];
     }
   }
-  if (!act || g != 0) return;
+  if (!act) return;
   const int64_t n = p.n;
   const double pre = p.qfar[(int)u.w];          // -k_e q_i / V
-  if (MIX) {
-    p.FFf[i] = (float)(pre * ax); p.FFf[n + i] = (float)(pre * ay); p.FFf[2 * n + i] = (float)(pre * az);
-  } else {
-    p.FFd[i] = pre * ax; p.FFd[n + i] = pre * ay; p.FFd[2 * n + i] = pre * az;
+  p.FFd[i] = pre * ax; p.FFd[n + i] = pre * ay; p.FFd[2 * n + i] = pre * az;
+}
+
+// Mixed far force, Eq. (long-rangeforce) with Im(e^{-i k.r} rho) =
+// |rho| sin(arg rho - k.r):
+//   F_F,i = -(k_e q_i / V) sum_p K_p sin(2 pi (Psi_p - m_p.u_i) / 2^32),
+// K_p = c_p |rho_p| k_p and Psi_p = arg rho_p in 2^-32 turn from k_reduce
+// (KPair records), so each (atom, mode) takes one exact integer phase (three
+// multiply-adds from Psi_p + 2^30), one sine polynomial (two modes per packed
+// FP32x2 instruction) and three FMA.  A block's FORCE_BLOCK / 32 warps are
+// (far_S k segments) x (atom warps); a thread takes A atoms (lane + 32 a of
+// its atom warp's range) and every far_S-th pair of modes; the segments' FP32
+// sums are added in segment order in shared memory, per chunk of FAR_PCHUNK
+// pairs, and the chunks in FP64.  PK = false: the phase factors in scalar FP32
+// (bit for bit the same).
+template <int A, bool PK>
+__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
+  __shared__ KPair sk[FAR_PCHUNK];
+  __shared__ float sred[FORCE_BLOCK / 32 * A * 32 * 3];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int S = p.far_S, AW = (FORCE_BLOCK / 32) / S;
+  const int sg = w / AW, aw = w % AW;
+  const int64_t base = (int64_t)blockIdx.x * (AW * 32 * A) + (int64_t)aw * (32 * A) + lane;
+  const int64_t n = p.n;
+  uint32_t ux[A], uy[A], uz[A];
+#pragma unroll
+  for (int a = 0; a < A; a++) {
+    const int64_t i = base + 32 * a;
+    const uint4 u = i < n ? p.ua[i] : make_uint4(0, 0, 0, 0);
+    ux[a] = u.x; uy[a] = u.y; uz[a] = u.z;
+  }
+  double ax[A], ay[A], az[A];
+#pragma unroll
+  for (int a = 0; a < A; a++) ax[a] = ay[a] = az[a] = 0.0;
+  const int npair = (p.P + 1) >> 1;
+  for (int c0 = 0; c0 < npair; c0 += FAR_PCHUNK) {
+    const int cnt = min(FAR_PCHUNK, npair - c0);
+    __syncthreads();
+    {
+      const int4 *src = reinterpret_cast<const int4 *>(p.kpair + c0);
+      int4 *dst = reinterpret_cast<int4 *>(sk);
+      for (int e = tid; e < 4 * cnt; e += FORCE_BLOCK) dst[e] = src[e];
+    }
+    __syncthreads();
+    float fx[A], fy[A], fz[A];
+#pragma unroll
+    for (int a = 0; a < A; a++) fx[a] = fy[a] = fz[a] = 0.0f;
+#pragma unroll 2
+    for (int j = sg; j < cnt; j += S) {
+      const int4 ra = sk[j].a, rb = sk[j].b;
+      const float4 kxy = sk[j].kxy;
+      const float2 kz = sk[j].kz;
+#pragma unroll
+      for (int a = 0; a < A; a++) {
+        const uint32_t t0 = (uint32_t)ra.x * ux[a] + ((uint32_t)ra.y * uy[a] + ((uint32_t)ra.z * uz[a] + (uint32_t)ra.w));
+        const uint32_t t1 = (uint32_t)rb.x * ux[a] + ((uint32_t)rb.y * uy[a] + ((uint32_t)rb.z * uz[a] + (uint32_t)rb.w));
+        float s0, s1;
+        if (PK) {
+          const unsigned long long phi = half_turn_phi2(t0, t1);
+          up2(sin_poly2(phi, mul2(phi, phi)), s0, s1);
+        } else {
+          const float p0 = half_turn_2r(t0) * SC_PI32, p1 = half_turn_2r(t1) * SC_PI32;
+          s0 = sin_poly(p0, p0 * p0);
+          s1 = sin_poly(p1, p1 * p1);
+        }
+        s0 = flip_by(s0, t0);
+        s1 = flip_by(s1, t1);
+        fx[a] = __fmaf_rn(s1, kxy.y, __fmaf_rn(s0, kxy.x, fx[a]));
+        fy[a] = __fmaf_rn(s1, kxy.w, __fmaf_rn(s0, kxy.z, fy[a]));
+        fz[a] = __fmaf_rn(s1, kz.y, __fmaf_rn(s0, kz.x, fz[a]));
+      }
+    }
+    if (S > 1) {                                  // the segments' sums, in segment order
+      float *r = sred + ((aw * A) * 32 + lane) * 3;
+      if (sg > 0)
+#pragma unroll
+        for (int a = 0; a < A; a++) {
+          float *q = r + (((sg - 1) * AW * A + a) * 32) * 3;
+          q[0] = fx[a]; q[1] = fy[a]; q[2] = fz[a];
+        }
+      __syncthreads();
+      if (sg == 0)
+        for (int t = 0; t < S - 1; t++)
+#pragma unroll
+          for (int a = 0; a < A; a++) {
+            const float *q = r + ((t * AW * A + a) * 32) * 3;
+            fx[a] += q[0]; fy[a] += q[1]; fz[a] += q[2];
+          }
+    }
+#pragma unroll
+    for (int a = 0; a < A; a++) {
+      ax[a] += (double)fx[a]; ay[a] += (double)fy[a]; az[a] += (double)fz[a];
+    }
+  }
+  if (sg != 0) return;
+#pragma unroll
+  for (int a = 0; a < A; a++) {
+    const int64_t i = base + 32 * a;
+    if (i >= n) continue;
+    const double pre = p.qfar[p.ua[i].w];        // -k_e q_i / V
+    p.FFf[i] = (float)(pre * ax[a]); p.FFf[n + i] = (float)(pre * ay[a]); p.FFf[2 * n + i] = (float)(pre * az[a]);
   }
 }
 
@@ -403,9 +548,23 @@ void launch_sincos(int64_t n, const uint32_t *th, float *s, float *c, cudaStream
 }
 
 void launch_rho(const View &v, cudaStream_t st) {
-  const dim3 g(v.ntile, (v.P + RHO_BLOCK * RHO_KPT - 1) / (RHO_BLOCK * RHO_KPT));
-  if (v.prec == RBSOG_MIXED) k_rho<float><<<g, RHO_BLOCK, 0, st>>>(v);
-  else k_rho<double><<<g, RHO_BLOCK, 0, st>>>(v);
+  const dim3 g(v.ntile, (v.P + RHO_KTILE - 1) / RHO_KTILE);
+  if (v.prec == RBSOG_MIXED) {
+    const int var = v.rho_var;
+    const int threads = RHO_VARIANT_G[var] * (RHO_BLOCK / RHO_VARIANT_NP[var]);
+    switch (var) {
+      case 1: k_rho_mixed<1, 1, 2, true><<<g, threads, 0, st>>>(v); break;
+      case 2: k_rho_mixed<2, 2, 2, true><<<g, threads, 0, st>>>(v); break;
+      case 3: k_rho_mixed<2, 4, 1, true><<<g, threads, 0, st>>>(v); break;
+      case 4: k_rho_mixed<1, 2, 2, false><<<g, threads, 0, st>>>(v); break;
+      case 5: k_rho_mixed<1, 1, 2, false><<<g, threads, 0, st>>>(v); break;
+      case 6: k_rho_mixed<2, 2, 2, false><<<g, threads, 0, st>>>(v); break;
+      case 7: k_rho_mixed<2, 4, 1, false><<<g, threads, 0, st>>>(v); break;
+      default: k_rho_mixed<1, 2, 2, true><<<g, threads, 0, st>>>(v); break;
+    }
+  } else {
+    k_rho_fp64<<<g, RHO_BLOCK, 0, st>>>(v);
+  }
 }
 
 void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
@@ -421,11 +580,26 @@ void launch_corr(const View &v, cudaStream_t st, int step_off) {
   else k_corr<4><<<CORR_BLOCKS, 256, 0, st>>>(v);
 }
 
+int far_atoms_per_block(const View &v) {
+  return (FORCE_BLOCK / 32 / v.far_S) * 32 * v.far_A;
+}
+
 void launch_farforce(const View &v, cudaStream_t st) {
-  const int apb = v.prec == RBSOG_MIXED ? FORCE_BLOCK / FORCE_TPA : FORCE_BLOCK;   // atoms per block
-  const int g = (int)((v.n + apb - 1) / apb);
-  if (v.prec == RBSOG_MIXED) k_farforce<float><<<g, FORCE_BLOCK, 0, st>>>(v);
-  else k_farforce<double><<<g, FORCE_BLOCK, 0, st>>>(v);
+  if (v.prec == RBSOG_MIXED) {
+    const int g = (int)((v.n + far_atoms_per_block(v) - 1) / far_atoms_per_block(v));
+    if (v.far_packed) {
+      if (v.far_A == 1) k_farforce_mixed<1, true><<<g, FORCE_BLOCK, 0, st>>>(v);
+      else if (v.far_A == 2) k_farforce_mixed<2, true><<<g, FORCE_BLOCK, 0, st>>>(v);
+      else k_farforce_mixed<4, true><<<g, FORCE_BLOCK, 0, st>>>(v);
+    } else {
+      if (v.far_A == 1) k_farforce_mixed<1, false><<<g, FORCE_BLOCK, 0, st>>>(v);
+      else if (v.far_A == 2) k_farforce_mixed<2, false><<<g, FORCE_BLOCK, 0, st>>>(v);
+      else k_farforce_mixed<4, false><<<g, FORCE_BLOCK, 0, st>>>(v);
+    }
+  } else {
+    const int g = (int)((v.n + FORCE_BLOCK - 1) / FORCE_BLOCK);
+    k_farforce_fp64<<<g, FORCE_BLOCK, 0, st>>>(v);
+  }
 }
 
 void launch_finish(const View &v, cudaStream_t st, int mode) {

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) k_sf_static_sum(int P, int ntile, const d
 
 // Device address of g_sf_part, looked up once per device (the device must be
 // current) and cached; the lookup may load this module, so the first call on
-// a device must not be inside stream capture.
+// a device must not be inside stream capture.  A cudaDeviceReset invalidates
+// the cached address together with every context of the device.
 cudaError_t sf_static_scratch(int dev, void **out) {
   static std::mutex mu;
   static void *addr[SF_STATIC_MAX_DEVICES] = {};

@@ -22,11 +22,11 @@ constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
 constexpr int NEAR_CHUNK = 8;      // atoms per warp of the near-field kernel (4 threads each)
 constexpr int NEAR_WARPS = 4;      // warps per near-field block
 constexpr int NEAR_NPART = 10;     // per-warp partials: sum F_N (3), U_N, pair virial (6)
-constexpr int RHO_BLOCK = 256;     // threads per block of the structure-factor kernel
-constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernel
-constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernel
-constexpr int FORCE_KCHUNK = 512;  // k-vectors staged in shared memory per chunk
-constexpr int FORCE_TPA = 4;       // threads per atom of the mixed far-field force kernel
+constexpr int RHO_BLOCK = 256;     // threads per block of the FP64 structure-factor kernel
+constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernels
+constexpr int FORCE_BLOCK = 256;   // threads per block of the far-field force kernels
+constexpr int FORCE_KCHUNK = 512;  // k-vectors staged in shared memory per chunk (FP64)
+constexpr int FAR_PCHUNK = 256;    // mixed: k pairs staged in shared memory per chunk
 constexpr int STENCIL = 5;         // cells per axis in the neighbour stencil (cell >= r_shell/2)
 
 // sorted atoms carry (caller id | species << 28) in one word
@@ -59,6 +59,18 @@ struct PairF {
   float D, pad0, pad1, pad2;
 };
 static_assert(sizeof(PairF) == 48, "pair record read as three 16-byte words");
+// Mixed far-force record of the modes 2j and 2j + 1, one 64-byte line:
+//   a, b = (-m_x, -m_y, -m_z, Psi + 2^30) of each mode, Psi = arg(rho_p) in
+//   units of 2^-32 turn (so Psi - m.u is the exact integer phase of
+//   sin(arg rho_p - k_p.r));
+//   kxy = (K_x, K'_x, K_y, K'_y), kz = (K_z, K'_z), K = c_p |rho_p| k_p.
+// A missing second mode (odd P) is all zero.
+struct KPair {
+  int4 a, b;
+  float4 kxy;
+  float2 kz, pad;
+};
+static_assert(sizeof(KPair) == 64, "k-pair record is one 64-byte line");
 // Pair record, FP64: the Eq. (BMH) parameters and k_e q_i q_j.
 struct PairD {
   double kqq, A, sig, rho, C, D;
@@ -144,8 +156,10 @@ struct View {
   double *rho_part;       // [P][ntile][2]
   double *rho;            // [P][2]
   double *uf;             // [P] c_p |rho_p|^2
-  float4 *kff;            // [Pmax] mixed (k_x, k_y, k_z, c_p Im rho_p)
-  float *kfB;             // [Pmax] mixed c_p Re rho_p
+  KPair *kpair;           // [Pmax / 2 + 1] mixed far-force records, one per pair of modes
+  int far_A, far_S;       // mixed far force: atoms per thread, k segments per block
+  int rho_var;            // mixed structure factor: launch shape (rbsog_schedule::rho_variant)
+  int far_packed;         // mixed far force: two modes per FP32x2 instruction (else scalar FP32)
   double *kfd;            // [Pmax][5] FP64 (k_x, k_y, k_z, c Im rho, c Re rho)
   double *red;            // [24]: F^corr (3), U_N, U_F*, W_N (6) at 5, W_F* (6) at 11
   int *err;
@@ -289,6 +303,44 @@ __device__ __forceinline__ void sincos_turn2(uint32_t th0, uint32_t th1, unsigne
   const unsigned long long mm = ((unsigned long long)m1 << 32) | m0;   // the sign of each lane
   s2 = sn ^ mm;
   c2 = cs ^ mm;
+}
+
+// The same half-turn reduction from t = th + 2^30, the offset folded into the
+// phase's multiply-add chain: h is bit 31 of t, and (int)((t << 1) + 2^31) is
+// 2 r exactly (r = th ^ m of sincos_turn), so phi = (float)(2 r) * fl(pi / 2^32)
+// is bit for bit sincos_turn's phi (2 r converts to twice r's float, and
+// fl(pi / 2^32) is half of fl(2 pi / 2^32)).  One shift-add and one conversion
+// per phase; the sign (-1)^h is applied by the caller to whatever it
+// multiplies (the charge in rho, the sine in the far force).
+constexpr float SC_PI32 = (float)(3.141592653589793 / 4294967296.0);  // pi / 2^32
+__device__ __forceinline__ float half_turn_2r(uint32_t t) {
+  return __int2float_rn((int)((t << 1) + 0x80000000u));
+}
+// packed phi of two phases
+__device__ __forceinline__ unsigned long long half_turn_phi2(uint32_t t0, uint32_t t1) {
+  return mul2(pk2(half_turn_2r(t0), half_turn_2r(t1)), pk2(SC_PI32, SC_PI32));
+}
+// sin(phi) of sincos_turn's minimax polynomial, two lanes, z = phi^2
+__device__ __forceinline__ unsigned long long sin_poly2(unsigned long long phi, unsigned long long z) {
+  const unsigned long long ps =
+      fma2(fma2(fma2(pk2(SC_S9, SC_S9), z, pk2(SC_S7, SC_S7)), z, pk2(SC_S5, SC_S5)), z, pk2(SC_S3, SC_S3));
+  return fma2(mul2(ps, z), phi, phi);
+}
+// sin(phi) of sincos_turn's minimax polynomial, one lane (the lane-by-lane
+// twin of sin_poly2)
+__device__ __forceinline__ float sin_poly(float phi, float z) {
+  const float ps = __fmaf_rn(__fmaf_rn(__fmaf_rn(SC_S9, z, SC_S7), z, SC_S5), z, SC_S3);
+  return __fmaf_rn(ps * z, phi, phi);
+}
+// cos(phi) of sincos_turn's minimax polynomial, one lane
+__device__ __forceinline__ float cos_poly(float z) {
+  const float pc =
+      __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(SC_C10, z, SC_C8), z, SC_C6), z, SC_C4), z, SC_C2);
+  return __fmaf_rn(pc, z, 1.0f);
+}
+// x with its sign flipped where bit 31 of t is set
+__device__ __forceinline__ float flip_by(float x, uint32_t t) {
+  return __uint_as_float(__float_as_uint(x) ^ (t & 0x80000000u));
 }
 
 // Packed constants of the list predicate seen from one atom image:

@@ -44,7 +44,9 @@ EXPORTS = [
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
     "rbsog_ensemble_step", "rbsog_ensemble_sync", "rbsog_ensemble_last_error",
+    "rbsog_set_schedule", "rbsog_get_schedule", "rbsog_probe_peak",
 ]
+PROBE_FP32, PROBE_FP32X2, PROBE_FP64, PROBE_IMAD = 0, 1, 2, 3
 SF_STATIC_PMAX = 1024
 NSTAGE = 9
 # stages of rbsog_get_stage_times: integrator + histograms, binning, near field, the far-field
@@ -74,6 +76,17 @@ class Params(ctypes.Structure):
         ("list_every", ctypes.c_int32), ("skin", ctypes.c_double),
         ("tdamp", ctypes.c_double), ("nh_chain", ctypes.c_int32),
     ]
+
+
+class Schedule(ctypes.Structure):
+    """Launch shapes of the mixed far field (``rbsog_schedule``)."""
+    _fields_ = [("rho_variant", ctypes.c_int32), ("rho_blocks_per_sm", ctypes.c_int32),
+                ("far_atoms_per_thread", ctypes.c_int32), ("far_segments", ctypes.c_int32),
+                ("far_packed", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.rho_variant, self.rho_blocks_per_sm, self.far_atoms_per_thread, self.far_segments,
+                self.far_packed)
 
 
 @dataclasses.dataclass
@@ -166,8 +179,21 @@ def load():
     L.rbsog_ensemble_last_error.restype = ctypes.c_char_p
     L.rbsog_last_error.argtypes = [P]
     L.rbsog_last_error.restype = ctypes.c_char_p
+    L.rbsog_probe_peak.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]
+    L.rbsog_set_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
+    L.rbsog_get_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
     _lib = L
     return L
+
+
+def probe_peak(device: int, kind: int) -> float:
+    """Measured multiply-add lane operations per second of one pipe (``rbsog_probe_peak``)."""
+    L = load()
+    v = ctypes.c_double()
+    rc = L.rbsog_probe_peak(device, kind, ctypes.byref(v))
+    if rc != 0:
+        raise RbsogError(rc, "rbsog_probe_peak failed")
+    return v.value
 
 
 def _np_ptr(a):
@@ -442,6 +468,17 @@ class Context:
         self._ck(self._L.rbsog_debug_get_parts(self.h, _np_ptr(near), _np_ptr(far), _np_ptr(fc), _np_ptr(rho)))
         return dict(near=near, far=far, Fcorr=fc, rho=rho)
 
+    def set_schedule(self, rho_variant: int, rho_blocks_per_sm: int, far_atoms_per_thread: int,
+                     far_segments: int, far_packed: int = 1):
+        """Launch shapes of the mixed far field (the step graph is captured again)."""
+        q = Schedule(rho_variant, rho_blocks_per_sm, far_atoms_per_thread, far_segments, far_packed)
+        self._ck(self._L.rbsog_set_schedule(self.h, ctypes.byref(q)))
+
+    def schedule(self):
+        q = Schedule()
+        self._ck(self._L.rbsog_get_schedule(self.h, ctypes.byref(q)))
+        return q.as_tuple()
+
     def set_profiling(self, on: bool):
         self._ck(self._L.rbsog_set_profiling(self.h, 1 if on else 0))
 
@@ -524,6 +561,10 @@ class Ensemble:
 
     def step(self, nsteps: int):
         self._ck(self._L.rbsog_ensemble_step(self.h, int(nsteps)))
+
+    @staticmethod
+    def launch_kind():
+        return "one CUDA graph per ensemble step (every replica's step graph a child node)"
 
     def sync(self):
         self._ck(self._L.rbsog_ensemble_sync(self.h))

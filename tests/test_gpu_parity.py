@@ -136,6 +136,29 @@ def test_fp64_trajectory(rb, orc, integ):
     assert rms_rel(vel, vo) < 1e-10
 
 
+def test_c1_nve_100_steps(rb, orc):
+    """Molten NaCl N = 1000 (5^3 cells, seed 1), P_R = 20, P_F = 200, FP64: one
+    force evaluation (forces and energies within 1e-12), then 100 velocity
+    Verlet steps at dt = 1 fs from Maxwell-Boltzmann velocities at 1200 K,
+    following the oracle's run with the same samples at every step."""
+    w = W.rock_salt((5, 5, 5), seed=1)
+    v0 = W.maxwell_boltzmann(w, 1200.0)
+    ctx, S = setup_pair(rb, orc, w, P_F=200, integrator=rb.NVE_VV)
+    Fg, Eg = ctx.compute_forces(energy=True)
+    o = S.forces(energy=True)
+    assert rms_rel(Fg, o["F"]) < FP64_TOL
+    np.testing.assert_allclose(Eg, o["energy"], rtol=1e-12, atol=1e-9)
+    ctx.set_velocities(v0)
+    ctx.step(100)
+    pos, vel, step = ctx.get_state()
+    vo, _ = S.run(v0, 100, 0.001, integrator=0)
+    assert step == 100 and S.step == 100
+    dpos = float(np.sqrt(((pos - S.pos) ** 2).mean()))
+    assert dpos < 1e-9, dpos
+    assert rms_rel(vel, vo) < 1e-8, rms_rel(vel, vo)
+    assert float(np.sqrt(((pos - w.pos) ** 2).mean())) > 0.05       # the atoms did move
+
+
 def test_resume_bit_identical(rb, orc):
     w = W.rock_salt((5, 5, 5), seed=1)
     v0 = W.maxwell_boltzmann(w, 1200.0)

@@ -1,10 +1,12 @@
 """The allocation-free structure factor (rbsog_structure_factor_static, whose
 scratch is a static device array) against the context's own structure factor
 (a fixed k-batch through rbsog_compute_forces, read back with
-rbsog_debug_get_parts), on two calls in a row with different mode counts, so
-that partials left in the static scratch by the first call would show in the
-second.  Collected last (file name) so that it also runs after the rest of the
-GPU suite; it passes alone as well."""
+rbsog_debug_get_parts) and against the oracle's, on two calls in a row with
+different mode counts, and on calls from two contexts of different size (so a
+different tile count) with nothing cleared in between, so that partials left
+in the static scratch by one call would show in the next.  Collected last (file
+name) so that it also runs after the rest of the GPU suite; it passes alone as
+well."""
 import ctypes
 
 import numpy as np
@@ -61,6 +63,25 @@ def test_static_structure_factor_two_calls(rb):
     r3 = ctx.structure_factor_static(d2).cpu().numpy()
     np.testing.assert_allclose(r3, context_rho(ctx, m2), rtol=0, atol=tol)
     assert np.abs(r3 - r2).max() > 1e-6
+
+
+def test_static_structure_factor_tile_counts(rb, orc):
+    """Two contexts of different N (32 and 4 tiles) called back to back, each
+    against the oracle's rho(k) of the same positions."""
+    import torch
+    ws = [W.rock_salt((10, 10, 10), seed=12), W.rock_salt((5, 5, 5), seed=13, composition="LiCl")]
+    ctxs = []
+    for w in ws:
+        c = rb.Context(0)
+        c.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, rb.MethodParams(P_F=64, precision=rb.FP64))
+        ctxs.append(c)
+    m = modes(700, 3)
+    d = torch.from_numpy(m).cuda()
+    for rep in range(2):
+        for w, c in zip(ws, ctxs):
+            got = c.structure_factor_static(d).cpu().numpy()
+            S = orc.System(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, P_F=64)
+            np.testing.assert_allclose(got, S.rho(m), rtol=0, atol=1e-12 * w.n)
 
 
 def test_static_structure_factor_rejects(rb):

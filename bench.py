@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--no-force-error", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form beside the line")
     ap.add_argument("--schedule", default=None,
-                    help="far-field schedule rho_variant,rho_blocks_per_sm,far_atoms_per_thread,far_segments,"
-                         "far_packed (default: tuned, or the library's with --no-autotune)")
+                    help="schedule rho_variant,rho_blocks_per_sm,far_atoms_per_thread,far_segments,"
+                         "far_packed,near_blocks_per_sm (default: tuned, or the library's with --no-autotune)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-replica ensemble beside the line")
     ap.add_argument("--sweep", action="store_true",
                     help="shell batch x P_F sweep of the configuration (one JSON line each)")
@@ -352,7 +352,7 @@ def run_ours(args):
         tuning = {"chosen_skin": skin, "candidates": [{"skin": a, "ms_per_step": b, "list_builds": c}
                                                       for a, b, c in table],
                   "rejected": [{"skin": a, "why": r} for a, r in rejected],
-                  "how": "200 timed steps per candidate after 20 warm-up, CUDA events (autotune.tune_skin)"}
+                  "how": "500 timed steps per candidate after 20 warm-up, CUDA events (autotune.tune_skin)"}
 
     sched, sched_tuning = None, None
     if args.schedule:
@@ -361,7 +361,7 @@ def run_ours(args):
         from paper_2512_24970_gb300 import autotune
         sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream)
         sched_tuning = {"chosen": dict(zip(("rho_variant", "rho_blocks_per_sm", "far_atoms_per_thread",
-                                             "far_segments", "far_packed"), sched)),
+                                             "far_segments", "far_packed", "near_blocks_per_sm"), sched)),
                         "candidates": [{"schedule": list(q), "ms_per_step": t} for q, t in table],
                         "how": "100 timed MD steps per candidate after 10 warm-up, CUDA events, coordinate search "
                                "(autotune.tune_schedule)"}

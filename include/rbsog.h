@@ -265,9 +265,9 @@ int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
 
 /* Launch shapes of the mixed-precision far field (Sec. 2.2: the structure
  * factors rho(k_p) over all atoms and the force of Eq. (long-rangeforce),
- * O(N P_F) work each, Sec. 2.4).  They split that work over the GPU and
+ * O(N P_F) work each, Sec. 2.4) and of the near field beside it.  They split that work over the GPU and
  * change nothing but the order in which FP32 and FP64 partial sums are added;
- * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1). */
+ * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1, 0). */
 typedef struct {
   int32_t rho_variant;           /* structure factor block shape: 0 = two groups of 256 threads,
                                     one pair of modes per thread; 1 = one group of 256; 2 = two
@@ -277,6 +277,9 @@ typedef struct {
   int32_t far_atoms_per_thread;  /* far force: atoms per thread, 1, 2 or 4 */
   int32_t far_segments;          /* far force: k segments per block of 8 warps, 1, 2, 4 or 8 */
   int32_t far_packed;            /* far force: 1 = two modes per packed FP32x2 instruction, 0 = scalar */
+  int32_t near_blocks_per_sm;    /* near field with kept lists: 0 = one block per 32 slots; k = 1..16:
+                                    k blocks per SM loop over the slots, so that the far field's
+                                    kernels, which run beside it, always find free SM slots */
 } rbsog_schedule;
 
 /* Set the schedule (host pointer).  Takes effect at the next evaluation (the

@@ -12,8 +12,9 @@ same force, so the choice changes the samples, not what they estimate; runs
 that must be reproducible pass the chosen skin explicitly.
 
 The far-field schedule (``rbsog_schedule``: the structure factor's block shape
-and tiles per SM, the far force's atoms per thread and k segments per block)
-changes nothing but the order of partial sums.  Which shape is fastest depends
+and tiles per SM, the far force's atoms per thread and k segments per block,
+and how many blocks per SM the kept near field beside them may hold) changes
+nothing but the order of partial sums.  Which shape is fastest depends
 on N, P_F and on what the near field leaves of the SMs (the two branches of
 the step run concurrently), so whole MD steps are timed for each candidate, by
 coordinate search: the structure-factor shapes first, then the far-force ones.
@@ -33,7 +34,7 @@ def max_skin(box, r_shell: float) -> float:
 
 
 def tune_skin(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
-              skins=DEFAULT_SKINS, warmup: int = 20, steps: int = 200):
+              skins=DEFAULT_SKINS, warmup: int = 20, steps: int = 500):
     """Time ``steps`` MD steps (after ``warmup``) of workload ``w`` for every
     candidate skin and return (best skin, [(skin, ms per step, list builds)],
     [(skin, reason)] of the candidates the system cannot run: a box shorter
@@ -77,6 +78,7 @@ RHO_BLOCKS_PER_SM = (1, 2, 3, 4)
 FAR_ATOMS = (1, 2, 4)
 FAR_SEGMENTS = (1, 2, 4, 8)
 FAR_PACKED = (1, 0)
+NEAR_BLOCKS_PER_SM = (1, 2, 3, 4, 6)
 
 
 def _time_steps(ctx, st, warmup, steps):
@@ -97,7 +99,8 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
     """Time ``steps`` MD steps of workload ``w`` (mixed precision) on one
     context for each far-field schedule of a coordinate search and return
     (best schedule (rho_variant, rho_blocks_per_sm, far_atoms_per_thread,
-    far_segments, far_packed), [(schedule, ms per step)])."""
+    far_segments, far_packed, near_blocks_per_sm), [(schedule, ms per step)]).
+    The near field's residency cap is searched last, with kept lists only."""
     import torch
     dev = torch.device("cuda", device)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -119,7 +122,7 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
         for A in FAR_ATOMS:
             for S in FAR_SEGMENTS:
                 for pk in FAR_PACKED:
-                    q = (timed[0], timed[1], A, S, pk)
+                    q = (timed[0], timed[1], A, S, pk) + tuple(timed[5:])
                     if q == timed:
                         continue
                     ctx.set_schedule(*q)
@@ -127,6 +130,17 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
                     table.append((q, t))
                     if t < best_t:
                         best, best_t = q, t
+        if params.list_every != 0:
+            timed = best
+            for nb in NEAR_BLOCKS_PER_SM:
+                q = tuple(timed[:5]) + (nb,)
+                if q == timed:
+                    continue
+                ctx.set_schedule(*q)
+                t = _time_steps(ctx, st, warmup, steps)
+                table.append((q, t))
+                if t < best_t:
+                    best, best_t = q, t
     finally:
         ctx.close()
     return best, table

@@ -53,7 +53,7 @@ struct rbsog_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
   int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
-  rbsog_schedule sched{0, 2, 2, 4, 1};  // far-field launch shapes (rbsog_set_schedule)
+  rbsog_schedule sched{0, 2, 2, 4, 1, 0};  // far-field launch shapes (rbsog_set_schedule)
 };
 
 namespace {
@@ -536,6 +536,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.auto_lists = P.list_every == RBSOG_LISTS_AUTO ? 1 : 0;
   v.build = 0;
   v.rl2f = (float)(r_list * r_list);
+  v.a_inside = (kept && (P.r_core + P.skin) * (P.r_core + P.skin) < 0.98 * P.r_shell * P.r_shell) ? 1 : 0;
   // an atom may move by skin/2 (pair distances by skin): shaded by 2^-10 so
   // that the FP32 predicate's rounding stays inside the margin
   v.half_skin2 = 0.25 * P.skin * P.skin * (1.0 - 1.0 / 1024.0);
@@ -571,6 +572,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.far_S = ctx->sched.far_segments;
   v.rho_var = ctx->sched.rho_variant;
   v.far_packed = ctx->sched.far_packed;
+  v.near_bps = ctx->sched.near_blocks_per_sm;
+  v.nsm = ctx->nsm;
   ctx->rho_bps = ctx->sched.rho_blocks_per_sm;
   set_rho_tiling(ctx, P.P_F);
   // self term U_F^self = k_e/2 sum_i q_i^2 F(0)
@@ -1184,7 +1187,8 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   if (!sched) return fail(ctx, RBSOG_E_INVAL, "null schedule");
   const rbsog_schedule q = *sched;
   const int A = q.far_atoms_per_thread, S = q.far_segments;
-  if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
+  if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) ||
+      q.near_blocks_per_sm < 0 || q.near_blocks_per_sm > 16 || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
       (A != 1 && A != 2 && A != 4) ||
       (S != 1 && S != 2 && S != 4 && S != 8))
     return fail(ctx, RBSOG_E_INVAL, "schedule out of range");
@@ -1198,6 +1202,7 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   v.far_S = S;
   v.rho_var = q.rho_variant;
   v.far_packed = q.far_packed;
+  v.near_bps = q.near_blocks_per_sm;
   ctx->rho_bps = q.rho_blocks_per_sm;
   set_rho_tiling(ctx, v.P);
   ctx->Pmax = 0;                               // tile partials for the new tiling

@@ -6,6 +6,8 @@
 // tabulated (mixed) or analytic FP64 over m = 0..M.  The block's FP64 partial
 // sums of F_N feed the momentum correction F^corr.  With kept (skin) lists
 // the walk's BUILD variant writes the lists and k_near_kept evaluates them.
+#include <algorithm>
+
 #include "rbsog_internal.cuh"
 
 namespace rb {
@@ -292,7 +294,7 @@ __device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *
 // One partial per warp of sum F_N and of the pair energy (FP32 sums of the
 // warp's eight atoms in mixed precision, FP64 otherwise).
 template <bool MIX, int NP>
-__device__ __forceinline__ void warp_partials(const View &p, double part[NEAR_NPART], int warp, int lane) {
+__device__ __forceinline__ void warp_partials(const View &p, double part[NEAR_NPART], int wchunk, int lane) {
 #pragma unroll
   for (int c = 0; c < NP; c++) {
     if (MIX) {
@@ -304,7 +306,7 @@ __device__ __forceinline__ void warp_partials(const View &p, double part[NEAR_NP
     }
   }
   if (lane == 0) {
-    double *d = p.near_part + NP * ((int64_t)blockIdx.x * NEAR_WARPS + warp);
+    double *d = p.near_part + NP * (int64_t)wchunk;
 #pragma unroll
     for (int c = 0; c < NP; c++) d[c] = part[c];
   }
@@ -823,7 +825,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   if constexpr (BUILD) return;
   // ---- partials of sum F_N and of the pair energy, one per warp (FP32 sums of
   // the warp's eight atoms in mixed precision, FP64 otherwise) ----------------
-  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, warp, lane);
+  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, blockIdx.x * NEAR_WARPS + warp, lane);
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
@@ -859,38 +861,55 @@ __device__ __forceinline__ bool in_shell(const View &p, uint4 ui, uint4 uj) {
          p.rs2f;
 }
 
+// Pair force with the mixed pair record read from the block's shared copy
+// of the table (three 16-byte words per species pair).
+template <bool ENERGY>
+__device__ __forceinline__ void add_pair_sh(const View &p, const float4 *spf4, const float4 *sg, int spi,
+                                            uint4 ui, uint4 uj, Acc<float> &a) {
+  const int spj = (int)(uj.w >> SU_SP_SHIFT);
+  const float4 *src = spf4 + 3 * (spi * p.ns + spj);
+  const float4 r0 = src[0], r1 = src[1], r2 = src[2];
+  PairF q;
+  q.kqq = r0.x; q.Ar = r0.y; q.lr = r0.z; q.sig = r0.w;
+  q.C6 = r1.x; q.D8 = r1.y; q.A = r1.z; q.C = r1.w;
+  q.D = r2.x;
+  float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  pair_mixed<ENERGY>(p, q, sg, ui, uj, a0, a1, a2, a3, a.w);
+  a.x += a0; a.y += a1; a.z += a2; a.e += a3;
+}
+
+// KB batch members in flight per thread (TPA * KB = 20 = P_R of the
+// benchmark: one pass with every lane busy).
+constexpr int KB = 5;
+
 template <typename R, bool ENERGY>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
+  constexpr bool MIX = sizeof(R) == 4;
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
   __shared__ uint32_t bmask[APB][RBSOG_MAX_KEPT / 32 + 1];
-  const PairF *spf = p.pf;
+  __shared__ float4 spf4[MIX ? 3 * RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
   const PairD *spd = p.pd;
   const float4 *sg4 = p.gtab;
   const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int a = warp * APW + lane / TPA, g = lane % TPA;
+  if (MIX) {
+    const float4 *src = reinterpret_cast<const float4 *>(p.pf);
+    for (int e = tid; e < 3 * p.ns * p.ns; e += NEAR_BLOCK) spf4[e] = __ldg(src + e);
+  }
+  __syncthreads();                               // the pair table
   const long long s = *p.step + step_off;
   const int nslot = p.cell_start[p.ncell];
-  const int slot = (blockIdx.x * NEAR_WARPS + warp) * APW + lane / TPA;
+  // one warp per run of APW slots; a grid smaller than nblk_near (a capped
+  // number of resident blocks) takes the runs in a grid-stride loop
+  for (int wc = blockIdx.x * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += gridDim.x * NEAR_WARPS) {
+  const int slot = wc * APW + lane / TPA;
   const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
   const bool active = ui.w != SU_PAD;
   const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
   const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
   double part[NEAR_NPART] = {};
   Acc<R> fa, fb;
-  // ---- A, exactly, dealt round-robin over the atom's threads ---------------
-  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
-  for (int e0 = g; e0 < nab.x; e0 += 4 * TPA) {
-    int js[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) js[i] = (e0 + TPA * i < nab.x) ? la[e0 + TPA * i] : -1;
-    uint4 uj[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-      if (js[i] >= 0 && in_shell(p, ui, uj[i])) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fa);
-  }
   // ---- Floyd's P_R of |B|: Philox words in parallel, resolved in order -----
   const int nB = nab.y, PR = p.P_R;
   const bool sampled = active && !p.whole_shell && nB > PR;
@@ -907,7 +926,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
         stsel[a][r0 + 1] = (unsigned short)__umul64hi(U1, (unsigned long long)(nB - PR + r0 + 1) + 1ull);
     }
   }
-  __syncwarp();
+  __syncwarp();                                  // this warp's draws
   if (sampled && g == 0) {
     uint32_t *bm = bmask[a];
     for (int r = 0; r < PR; r++) {
@@ -918,30 +937,65 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
     }
   }
   __syncwarp();
-  // ---- the batch of B (or all of it) ---------------------------------------
+  // ---- the batch's list entries, loaded before A's pairs so that their
+  // latency overlaps that work -----------------------------------------------
   const R wgt = sampled ? (R)nB / (R)PR : (R)1;
   const int *lb = p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
   const int nb = sampled ? PR : nB;
-  for (int k0 = g; k0 < nb; k0 += 4 * TPA) {
+  int jb[KB];
+#pragma unroll
+  for (int i = 0; i < KB; i++) {
+    const int k = g + TPA * i;
+    jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+  }
+  // ---- A, exactly, dealt round-robin over the atom's threads; the
+  // indicator r < r_shell is 1 for every member of A when r_core + skin lies
+  // well inside r_shell (no atom moves by more than skin/2 between builds) -----
+  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
+  const bool acheck = !p.a_inside;
+  for (int e0 = g; e0 < nab.x; e0 += 4 * TPA) {
     int js[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      const int k = k0 + TPA * i;
-      js[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
-    }
+    for (int i = 0; i < 4; i++) js[i] = (e0 + TPA * i < nab.x) ? la[e0 + TPA * i] : -1;
     uint4 uj[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
 #pragma unroll
     for (int i = 0; i < 4; i++)
-      if (js[i] >= 0 && in_shell(p, ui, uj[i])) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fb);
+      if (js[i] >= 0 && (!acheck || in_shell(p, ui, uj[i]))) {
+        if constexpr (MIX) add_pair_sh<ENERGY>(p, spf4, sg4, spi, ui, uj[i], fa);
+        else add_pair<R, ENERGY>(p, nullptr, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fa);
+      }
+  }
+  // ---- the batch of B (or all of it) ---------------------------------------
+  for (int k0 = 0;; k0 += TPA * KB) {
+    uint4 uj[KB];
+#pragma unroll
+    for (int i = 0; i < KB; i++) uj[i] = p.su[max(jb[i], 0)];
+#pragma unroll
+    for (int i = 0; i < KB; i++)
+      if (jb[i] >= 0 && in_shell(p, ui, uj[i])) {
+        if constexpr (MIX) add_pair_sh<ENERGY>(p, spf4, sg4, spi, ui, uj[i], fb);
+        else add_pair<R, ENERGY>(p, nullptr, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fb);
+      }
+    if (k0 + TPA * KB >= nb) break;             // rare: P_R or |B| above TPA * KB
+#pragma unroll
+    for (int i = 0; i < KB; i++) {
+      const int k = k0 + TPA * KB + g + TPA * i;
+      jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+    }
   }
   combine_atom<R, ENERGY>(p, fa, fb, wgt, active, g, ui, part);
-  warp_partials<sizeof(R) == 4, ENERGY ? NEAR_NPART : 4>(p, part, warp, lane);
+  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, wc, lane);
+  __syncwarp();                                  // stsel / bmask of this warp are reused
+  }
 }
 
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy) {
-  const dim3 g(v.nblk_near), b(NEAR_BLOCK);
+  // near_bps > 0: at most that many resident blocks per SM, looping over the
+  // runs, so that the far-field branch always finds free slots
+  const int nb = v.near_bps > 0 ? std::min(v.nblk_near, v.near_bps * v.nsm) : v.nblk_near;
+  const dim3 g(nb), b(NEAR_BLOCK);
   if (v.prec == RBSOG_MIXED) {
     if (energy) k_near_kept<float, true><<<g, b, 0, st>>>(v, step_off);
     else k_near_kept<float, false><<<g, b, 0, st>>>(v, step_off);

@@ -100,6 +100,8 @@ struct View {
   int *lflag;             // [1] auto_lists: this step rebuilds (set by k_prepare or the host)
   unsigned long long *nbuild;  // [1] list builds so far
   float rl2f;             // fl32((r_shell + skin)^2), outer radius of a build
+  int a_inside;           // kept lists: (r_core + skin)^2 < 0.98 r_shell^2, so every member of A
+                          // stays inside r_shell while no atom moves by skin/2
   double half_skin2;      // (skin / 2)^2, shaded down: the displacement limit
   int *lA, *lB;           // [nslot][RBSOG_MAX_CORE], [nslot][RBSOG_MAX_KEPT] member slots
   int2 *nAB;              // [nslot] (|A|, |B|) of each slot
@@ -160,6 +162,8 @@ struct View {
   int far_A, far_S;       // mixed far force: atoms per thread, k segments per block
   int rho_var;            // mixed structure factor: launch shape (rbsog_schedule::rho_variant)
   int far_packed;         // mixed far force: two modes per FP32x2 instruction (else scalar FP32)
+  int near_bps;           // kept near field: resident blocks per SM (0: one block per 4 runs of slots)
+  int nsm;                // SMs of the device
   double *kfd;            // [Pmax][5] FP64 (k_x, k_y, k_z, c Im rho, c Re rho)
   double *red;            // [24]: F^corr (3), U_N, U_F*, W_N (6) at 5, W_F* (6) at 11
   int *err;

@@ -82,11 +82,11 @@ class Schedule(ctypes.Structure):
     """Launch shapes of the mixed far field (``rbsog_schedule``)."""
     _fields_ = [("rho_variant", ctypes.c_int32), ("rho_blocks_per_sm", ctypes.c_int32),
                 ("far_atoms_per_thread", ctypes.c_int32), ("far_segments", ctypes.c_int32),
-                ("far_packed", ctypes.c_int32)]
+                ("far_packed", ctypes.c_int32), ("near_blocks_per_sm", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.rho_variant, self.rho_blocks_per_sm, self.far_atoms_per_thread, self.far_segments,
-                self.far_packed)
+                self.far_packed, self.near_blocks_per_sm)
 
 
 @dataclasses.dataclass
@@ -469,9 +469,11 @@ class Context:
         return dict(near=near, far=far, Fcorr=fc, rho=rho)
 
     def set_schedule(self, rho_variant: int, rho_blocks_per_sm: int, far_atoms_per_thread: int,
-                     far_segments: int, far_packed: int = 1):
-        """Launch shapes of the mixed far field (the step graph is captured again)."""
-        q = Schedule(rho_variant, rho_blocks_per_sm, far_atoms_per_thread, far_segments, far_packed)
+                     far_segments: int, far_packed: int = 1, near_blocks_per_sm: int = 0):
+        """Launch shapes of the mixed far field and the kept near field (the step
+        graph is captured again)."""
+        q = Schedule(rho_variant, rho_blocks_per_sm, far_atoms_per_thread, far_segments, far_packed,
+                     near_blocks_per_sm)
         self._ck(self._L.rbsog_set_schedule(self.h, ctypes.byref(q)))
 
     def schedule(self):

@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form beside the line")
     ap.add_argument("--schedule", default=None,
                     help="schedule rho_variant,rho_blocks_per_sm,far_atoms_per_thread,far_segments,"
-                         "far_packed,near_blocks_per_sm (default: tuned, or the library's with --no-autotune)")
+                         "far_packed,near_blocks_per_sm,rho_tile_atoms (default: tuned, or the library's with --no-autotune)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-replica ensemble beside the line")
     ap.add_argument("--sweep", action="store_true",
                     help="shell batch x P_F sweep of the configuration (one JSON line each)")
@@ -347,24 +347,24 @@ def run_ours(args):
     tuning = None
     if list_every < 0 and args.skin is None and not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream)
+        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream, flush=flush.zero_)
         prm = dataclasses.replace(prm, skin=skin)
         tuning = {"chosen_skin": skin, "candidates": [{"skin": a, "ms_per_step": b, "list_builds": c}
                                                       for a, b, c in table],
                   "rejected": [{"skin": a, "why": r} for a, r in rejected],
-                  "how": "500 timed steps per candidate after 20 warm-up, CUDA events (autotune.tune_skin)"}
+                  "how": "500 steps per candidate after 20 warm-up, each after an L2 flush and timed alone with CUDA events (autotune.tune_skin)"}
 
     sched, sched_tuning = None, None
     if args.schedule:
         sched = tuple(int(x) for x in args.schedule.split(","))
     elif prec == rbsog.MIXED and not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream)
+        sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream, flush=flush.zero_)
         sched_tuning = {"chosen": dict(zip(("rho_variant", "rho_blocks_per_sm", "far_atoms_per_thread",
-                                             "far_segments", "far_packed", "near_blocks_per_sm"), sched)),
+                                             "far_segments", "far_packed", "near_blocks_per_sm", "rho_tile_atoms"), sched)),
                         "candidates": [{"schedule": list(q), "ms_per_step": t} for q, t in table],
-                        "how": "100 timed MD steps per candidate after 10 warm-up, CUDA events, coordinate search "
-                               "(autotune.tune_schedule)"}
+                        "how": "100 MD steps per candidate after 10 warm-up, each after an L2 flush and timed alone "
+                               "with CUDA events, coordinate search (autotune.tune_schedule)"}
 
     def timed_run(params, clocks=None, k_stage=None):
         """Wm untimed steps, then K steps timed with CUDA events on the
@@ -615,7 +615,6 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
         c.set_velocities(w.vel)
         natoms += w.n
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
     def timed(step_fn):
         with torch.cuda.stream(stream):
             for _ in range(Wm):
@@ -631,6 +630,20 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
             torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in ev))
 
+    tuning = None
+    if args.schedule:
+        q = tuple(int(x) for x in args.schedule.split(","))
+        for c in ens.replicas:
+            c.set_schedule(*q)
+        tuning = {"chosen": list(q), "how": "given (--schedule)"}
+    elif not args.no_autotune:
+        from paper_2512_24970_gb300 import autotune
+        best, table = autotune.tune_ensemble_schedule(ens, stream=stream, flush=flush.zero_)
+        tuning = {"chosen": {"schedule": list(best[0]), "groups": best[1]},
+                  "candidates": [{"schedule": list(q), "groups": g, "ms_per_step": t} for (q, g), t in table],
+                  "how": "20 ensemble steps per candidate after 3 warm-up, each after an L2 flush and timed alone, "
+                         "coordinate search (autotune.tune_ensemble_schedule); groups = replicas dealt into that "
+                         "many packed groups run as parallel graph branches, 0 = child graphs"}
     t_ens = timed(lambda: ens.step(1))
     ens.sync()
     out = {"value": natoms * K / (t_ens / 1000.0), "unit": "atom-steps/s", "ms_per_step": t_ens / K, "steps": K,
@@ -638,7 +651,17 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
                        "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
            "lists": ("per step" if not list_every else
                      "kept, rebuilt when an atom has moved by skin/2; skin min(1 A, L/2 - r_shell)"),
-           "launch": ens.launch_kind(), "l2": "flushed before every step (512 MiB memset)"}
+           "launch": ens.launch_kind(), "l2": "flushed before every step (512 MiB memset)",
+           "schedule_tuning": tuning}
+    # the same ensemble with every replica in one packed group, and as child
+    # graphs (each replica's own step graph), beside the tuned plan
+    used = ens.used_mode()
+    for name, mode, groups in (("one_packed_group", rbsog.ENSEMBLE_PACKED, 1), ("child_graphs", rbsog.ENSEMBLE_GRAPHS, 1)):
+        ens.set_mode(mode)
+        ens.set_groups(groups)
+        t_g = timed(lambda: ens.step(1))
+        ens.sync()
+        out[name] = {"value": natoms * K / (t_g / 1000.0), "ms_per_step": t_g / K, "launch": ens.launch_kind()}
     if with_sequential:
         # the same replicas one after another, each step on the ensemble's stream
         solo = []
@@ -666,8 +689,9 @@ def run_ensemble(args):
     line = {"metric": "atom-steps/s of RBSOG+RBL force step, replica ensemble", "value": e["value"],
             "unit": "atom-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": e["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {k: e[k] for k in ("workload", "atoms", "lists", "launch", "l2")},
-            "sequential": e.get("sequential")}
+            "config": {k: e[k] for k in ("workload", "atoms", "lists", "launch", "l2", "schedule_tuning")},
+            "sequential": e.get("sequential"), "child_graphs": e.get("child_graphs"),
+            "one_packed_group": e.get("one_packed_group")}
     print(json.dumps(line), flush=True)
 
 

@@ -267,7 +267,7 @@ int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
  * factors rho(k_p) over all atoms and the force of Eq. (long-rangeforce),
  * O(N P_F) work each, Sec. 2.4) and of the near field beside it.  They split that work over the GPU and
  * change nothing but the order in which FP32 and FP64 partial sums are added;
- * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1, 0). */
+ * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1, 0, 0). */
 typedef struct {
   int32_t rho_variant;           /* structure factor block shape: 0 = two groups of 256 threads,
                                     one pair of modes per thread; 1 = one group of 256; 2 = two
@@ -280,6 +280,9 @@ typedef struct {
   int32_t near_blocks_per_sm;    /* near field with kept lists: 0 = one block per 32 slots; k = 1..16:
                                     k blocks per SM loop over the slots, so that the far field's
                                     kernels, which run beside it, always find free SM slots */
+  int32_t rho_tile_atoms;        /* structure factor: 0 = tiles from rho_blocks_per_sm; 32..65536 =
+                                    that many atoms per tile (tiles in proportion to N, e.g. for the
+                                    replicas of a packed ensemble) */
 } rbsog_schedule;
 
 /* Set the schedule (host pointer).  Takes effect at the next evaluation (the
@@ -453,6 +456,34 @@ int rbsog_ensemble_step(rbsog_ensemble *ens, int64_t nsteps);
 
 /* Wait for all replicas; return the first latched device error, if any. */
 int rbsog_ensemble_sync(rbsog_ensemble *ens);
+
+/* How rbsog_ensemble_step runs the replicas (each replica's estimator needs
+ * only its own state, Sec. 2.2, so they are independent problems):
+ *   RBSOG_ENSEMBLE_PACKED (default): every stage of the step is one kernel
+ *     launch over the blocks of all replicas, in one CUDA graph per ensemble
+ *     step, when the replicas are all mixed precision, share the integrator
+ *     (velocity Verlet or BAOAB), the list mode (per-step lists or kept lists
+ *     rebuilt when needed) and the far-field schedule, and none is profiling;
+ *     otherwise the step falls back to
+ *   RBSOG_ENSEMBLE_GRAPHS: one CUDA graph whose child nodes are the replicas'
+ *     own step graphs (replicas on a fixed list schedule: each launches its
+ *     own graphs).
+ * Results per replica are bit-identical either way.  Errors: RBSOG_E_INVAL. */
+#define RBSOG_ENSEMBLE_PACKED 0
+#define RBSOG_ENSEMBLE_GRAPHS 1
+int rbsog_ensemble_set_mode(rbsog_ensemble *ens, int32_t mode);
+
+/* Packed mode: deal the replicas into `groups` groups of about equal atoms;
+ * each group's stages are packed launches, and the groups run as parallel
+ * branches of the step graph, so that one group's reductions overlap another's
+ * arithmetic (1 = every replica in one group, the default; more than the
+ * number of replicas = one replica per group).  The tuner of
+ * paper_2512_24970_gb300/autotune.py picks it by timing.  Errors: RBSOG_E_INVAL. */
+int rbsog_ensemble_set_groups(rbsog_ensemble *ens, int32_t groups);
+
+/* The way the last rbsog_ensemble_step ran (RBSOG_ENSEMBLE_PACKED or
+ * RBSOG_ENSEMBLE_GRAPHS; -1 before the first step).  Host pointer. */
+int rbsog_ensemble_get_mode(rbsog_ensemble *ens, int32_t *used);
 
 /* Message of the last error of the ensemble (never NULL). */
 const char *rbsog_ensemble_last_error(const rbsog_ensemble *ens);

@@ -53,7 +53,7 @@ struct rbsog_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
   int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
-  rbsog_schedule sched{0, 2, 2, 4, 1, 0};  // far-field launch shapes (rbsog_set_schedule)
+  rbsog_schedule sched{0, 2, 2, 4, 1, 0, 0};  // far-field launch shapes (rbsog_set_schedule)
 };
 
 namespace {
@@ -286,6 +286,7 @@ int ensure_kcap(rbsog_ctx *ctx, int P) {
 }
 
 // Structure-factor tiles: enough blocks for rho_bps resident blocks per SM
+// (or, with the schedule's rho_tile_atoms, that many atoms per tile)
 // (mixed: the block shape of the schedule's rho_variant; FP64: blocks of
 // RHO_BLOCK threads), at least 32 atoms per tile.
 void set_rho_tiling(rbsog_ctx *ctx, int P) {
@@ -293,6 +294,8 @@ void set_rho_tiling(rbsog_ctx *ctx, int P) {
   const int nky = (P + rb::RHO_BLOCK * rb::RHO_KPT - 1) / (rb::RHO_BLOCK * rb::RHO_KPT);
   const int target = (v.prec == RBSOG_MIXED ? ctx->rho_bps : 4) * ctx->nsm;
   int64_t nt = (target + nky - 1) / nky;
+  if (v.prec == RBSOG_MIXED && ctx->sched.rho_tile_atoms > 0)
+    nt = (ctx->n + ctx->sched.rho_tile_atoms - 1) / ctx->sched.rho_tile_atoms;
   nt = std::min<int64_t>(nt, (ctx->n + 31) / 32);
   nt = std::max<int64_t>(nt, 1);
   v.tile_atoms = (int)((ctx->n + nt - 1) / nt);
@@ -362,6 +365,16 @@ cudaGraph_t ctx_step_graph(const rbsog_ctx *ctx, uint64_t *gen) {
 }
 
 void ctx_advance(rbsog_ctx *ctx, int64_t nsteps) { ctx->host_step += nsteps; }
+
+void ctx_step_view(const rbsog_ctx *ctx, View *out, int *mode, bool *profiling) {
+  View v = ctx->v;
+  v.npart = 4;                     // as run_force sets them for a step
+  v.want_vir = 0;
+  v.build = 1;                     // per-step lists, or automatic kept lists (one graph)
+  *out = v;
+  *mode = ctx->prm.integrator == RBSOG_LANGEVIN_BAOAB ? 2 : (ctx->prm.integrator == RBSOG_NVE_VV ? 1 : 0);
+  *profiling = ctx->profiling;
+}
 
 }  // namespace rb
 
@@ -1188,7 +1201,8 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   const rbsog_schedule q = *sched;
   const int A = q.far_atoms_per_thread, S = q.far_segments;
   if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) ||
-      q.near_blocks_per_sm < 0 || q.near_blocks_per_sm > 16 || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
+      q.near_blocks_per_sm < 0 || q.near_blocks_per_sm > 16 ||
+      (q.rho_tile_atoms != 0 && (q.rho_tile_atoms < 32 || q.rho_tile_atoms > 65536)) || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
       (A != 1 && A != 2 && A != 4) ||
       (S != 1 && S != 2 && S != 4 && S != 8))
     return fail(ctx, RBSOG_E_INVAL, "schedule out of range");

@@ -22,4 +22,11 @@ cudaGraph_t ctx_step_graph(const rbsog_ctx *ctx, uint64_t *gen);
 // The host's copy of the step counter after nsteps launches of the graph.
 void ctx_advance(rbsog_ctx *ctx, int64_t nsteps);
 
+struct View;
+// The view a step of the context evaluates with (the device view with the
+// step's settings: no energy or virial partials; with kept lists, the build
+// variant's flags), its integrator mode (1 velocity Verlet, 2 BAOAB, 0 other)
+// and whether the context is profiling.
+void ctx_step_view(const rbsog_ctx *ctx, View *out, int *mode, bool *profiling);
+
 }  // namespace rb

@@ -107,12 +107,12 @@ __device__ __forceinline__ bool skip_binning(const View &p) {
 constexpr int PREP_ATOMS = 128;
 
 template <int MODE>
-__global__ void __launch_bounds__(3 * PREP_ATOMS) k_prepare(View p, int step_off) {
+__device__ __forceinline__ void prepare_body(const View &p, int step_off, int bid) {
   __shared__ uint32_t su3[3][PREP_ATOMS];
   __shared__ double sq3[3][PREP_ATOMS];
   const long long s = *p.step + step_off;
   const int c = threadIdx.x / PREP_ATOMS, li = threadIdx.x % PREP_ATOMS;
-  const int64_t i = (int64_t)blockIdx.x * PREP_ATOMS + li;
+  const int64_t i = (int64_t)bid * PREP_ATOMS + li;
   const int64_t n = p.n;
   // Nose-Hoover: the opening half step of the chain, every block alike
   const double s_open = (MODE == 1 && p.integ == RBSOG_NOSE_HOOVER) ? nh_open(p) : 1.0;
@@ -173,6 +173,17 @@ __global__ void __launch_bounds__(3 * PREP_ATOMS) k_prepare(View p, int step_off
   histogram_add(p, cell);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(3 * PREP_ATOMS) k_prepare(View p, int step_off) {
+  prepare_body<MODE>(p, step_off, blockIdx.x);
+}
+template <int MODE>
+__global__ void __launch_bounds__(3 * PREP_ATOMS) kp_prepare(Pack pk, int step_off) {
+  RB_PACK_PROLOGUE(pk);
+  (void)nb;
+  prepare_body<MODE>(sv, step_off, bid);
+}
+
 // Block-wide exclusive scan of one value per thread (1024 threads).
 __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
   const int t = threadIdx.x, nt = blockDim.x;
@@ -202,7 +213,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum) {
 // all slots) and the near-field chunks: each row's slots cut into runs of
 // NEAR_CHUNK from its start, row_chunk[r] = first chunk of row r.  One block;
 // the row totals come from the binning's atomic counts.
-__global__ void __launch_bounds__(1024) k_rowscan(View p) {
+__device__ __forceinline__ void rowscan_body(const View &p) {
   __shared__ int wsum[32];
   if (skip_binning(p)) return;
   const int nt = blockDim.x, t = threadIdx.x;
@@ -237,13 +248,19 @@ __global__ void __launch_bounds__(1024) k_rowscan(View p) {
     p.row_chunk[nrow] = crun;
   }
 }
+__global__ void __launch_bounds__(1024) k_rowscan(View p) { rowscan_body(p); }
+__global__ void __launch_bounds__(1024) kp_rowscan(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)bid; (void)nb;
+  rowscan_body(sv);
+}
 
 // Cell ranges inside each row: one warp per row, an inclusive warp scan of
 // the cell counts (32 cells per round) on top of the row's start.
-__global__ void __launch_bounds__(256) k_cellstart(View p) {
+__device__ __forceinline__ void cellstart_body(const View &p, int bid) {
   if (skip_binning(p)) return;
   const int nrow = p.nc[1] * p.nc[2], nc0 = p.nc[0];
-  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int r = (int)(((int64_t)bid * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= nrow) return;
   int base = p.row_start[r];
@@ -263,20 +280,32 @@ __global__ void __launch_bounds__(256) k_cellstart(View p) {
     base += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
+__global__ void __launch_bounds__(256) k_cellstart(View p) { cellstart_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(256) kp_cellstart(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  cellstart_body(sv, bid);
+}
 
-__global__ void __launch_bounds__(256) k_scatter(View p) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void scatter_body(const View &p, int bid) {
+  const int64_t i = (int64_t)bid * blockDim.x + threadIdx.x;
   if (i >= p.n || skip_binning(p)) return;
   const int slot = atomicAdd(p.cell_cursor + p.cellid[i], 1);
   p.perm_tmp[slot] = (int)i;
   p.key_tmp[slot] = p.ua[i].x;
 }
+__global__ void __launch_bounds__(256) k_scatter(View p) { scatter_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(256) kp_scatter(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  scatter_body(sv, bid);
+}
 
 // One thread per atom: its rank in its cell under the canonical order
 // (fixed-point x coordinate, caller id), so every row of cells is sorted by x;
 // writes the sorted SoA arrays and the near-field chunk table.
-__global__ void __launch_bounds__(256) k_rank(View p) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rank_body(const View &p, int bid) {
+  const int64_t i = (int64_t)bid * blockDim.x + threadIdx.x;
   if (i >= p.n || skip_binning(p)) return;
   if (p.kept)                      // positions of this build, for the displacement check
     for (int a = 0; a < 3; a++) p.xb[a * p.n + i] = p.x[a * p.n + i];
@@ -304,11 +333,23 @@ __global__ void __launch_bounds__(256) k_rank(View p) {
   if (((slot - rbeg) & (NEAR_CHUNK - 1)) == 0)
     p.chunk_info[p.row_chunk[row] + (slot - rbeg) / NEAR_CHUNK] = make_int2(row, slot);
 }
+__global__ void __launch_bounds__(256) k_rank(View p) { rank_body(p, blockIdx.x); }
+__global__ void __launch_bounds__(256) kp_rank(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  rank_body(sv, bid);
+}
 
 // The k-batch, one warp per sample (needs only the step counter).
 __global__ void __launch_bounds__(256) k_ksample(View p, int step_off) {
   const long long s = *p.step + step_off;
   ksample_warp(p, (int)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), s, threadIdx.x & 31);
+}
+__global__ void __launch_bounds__(256) kp_ksample(Pack pk, int step_off) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  const long long s = *sv.step + step_off;
+  ksample_warp(sv, bid * (blockDim.x >> 5) + (threadIdx.x >> 5), s, threadIdx.x & 31);
 }
 
 void launch_ksample(const View &v, cudaStream_t st, int step_off) {
@@ -329,6 +370,24 @@ void launch_bin(const View &v, cudaStream_t st) {
   k_cellstart<<<(unsigned)(((int64_t)v.nc[1] * v.nc[2] * 32 + 255) / 256), 256, 0, st>>>(v);
   k_scatter<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
   k_rank<<<(unsigned)((v.n + 255) / 256), 256, 0, st>>>(v);
+}
+
+// ---------------------------------------------------------------------------
+// Packed launches of an ensemble (one grid over every replica; the block
+// counts per replica are the prefix tables of PackPlan).
+void pack_ksample(const PackPlan &q, cudaStream_t st, int step_off) {
+  kp_ksample<<<q.total[PK_KSAMPLE], 256, 0, st>>>(q.pack(PK_KSAMPLE), step_off);
+}
+void pack_prepare(const PackPlan &q, cudaStream_t st, int mode, int step_off) {
+  const int g = q.total[PK_PREP];
+  if (mode == 1) kp_prepare<1><<<g, 3 * PREP_ATOMS, 0, st>>>(q.pack(PK_PREP), step_off);
+  else kp_prepare<2><<<g, 3 * PREP_ATOMS, 0, st>>>(q.pack(PK_PREP), step_off);
+}
+void pack_bin(const PackPlan &q, cudaStream_t st) {
+  kp_rowscan<<<q.total[PK_ONE], 1024, 0, st>>>(q.pack(PK_ONE));
+  kp_cellstart<<<q.total[PK_ROWS], 256, 0, st>>>(q.pack(PK_ROWS));
+  kp_scatter<<<q.total[PK_ATOM256], 256, 0, st>>>(q.pack(PK_ATOM256));
+  kp_rank<<<q.total[PK_ATOM256], 256, 0, st>>>(q.pack(PK_ATOM256));
 }
 
 // ---------------------------------------------------------------------------

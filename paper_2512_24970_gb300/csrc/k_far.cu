@@ -10,6 +10,8 @@
 //             the near-field warp partials, fixed order.
 //   k_farforce_* F_F,i = -(k_e q_i / V) sum_p c_p k_p Im(e^{-i k_p.r_i} rho_p).
 //   k_finish  F_i = F_N,i - F^corr + F_F,i and the closing half kick of the MD step.
+#include <algorithm>
+
 #include "nh.cuh"
 
 namespace rb {
@@ -84,22 +86,29 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho_fp64(View p) {
 // minimax sine (packed) and cosine (per lane, so that the FMA pipe's two
 // halves share the work with the integer multiply-adds, which run on one of
 // them), the half-turn sign on the charge, and FP32 sums over at most
-// RHO_MCHUNK atoms, added in FP64.  The groups' FP64 sums are added in group
+// RHO_FLUSH atoms, added in FP64.  The groups' FP64 sums are added in group
 // order in shared memory: one partial per (mode, tile).  MINB is the
 // occupancy the register allocation is bounded for.  PK = false evaluates the
 // same operations per lane in scalar FP32 instructions (bit for bit the same
 // results; it leaves the FMA pipe's two halves to be filled independently).
-constexpr int RHO_MCHUNK = 256;
+constexpr int RHO_MCHUNK = 256;                  // atoms staged in shared memory per group and round
+// FP32 partial sums run over at most RHO_FLUSH atoms before they are added in
+// FP64: on lattice-like configurations the sums over one sublattice are
+// coherent (of order the number of atoms) while rho is small, so the FP32
+// rounding of a partial sum grows with its length; 64 atoms keep it near
+// 64 * 2^-24 of the largest partial
+constexpr int RHO_FLUSH = 64;
+constexpr int RHO_WARP_TILES = 160;  // tiles up to which the tile sums take a warp per mode
 constexpr int RHO_KTILE = RHO_BLOCK * RHO_KPT;    // modes per block row (512)
 template <int NP, int G, int MINB, bool PK>
-__global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p) {
+__device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
   constexpr int GT = RHO_BLOCK / NP;
   __shared__ uint4 sa[G][RHO_MCHUNK];
   __shared__ double2 sg[G > 1 ? G - 1 : 1][RHO_KTILE];
   static_assert(RHO_KPT == 2 && GT * NP * 2 == RHO_KTILE, "packed pairs of modes per thread");
   const int tid = threadIdx.x, grp = tid / GT, gt = tid % GT;
-  const int tile = blockIdx.x;
-  const int kb = blockIdx.y * RHO_KTILE + 2 * NP * gt;
+  const int tile = bid % p.ntile;                // blocks: tiles fastest, then columns of modes
+  const int kb = (bid / p.ntile) * RHO_KTILE + 2 * NP * gt;
   const int64_t a0 = (int64_t)tile * p.tile_atoms;
   const int64_t a1 = min(a0 + (int64_t)p.tile_atoms, p.n);
   const int sub = (p.tile_atoms + G - 1) / G;
@@ -121,11 +130,13 @@ __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p
       sa[grp][e] = u;
     }
     __syncthreads();
+    for (int a0 = 0; a0 < cnt; a0 += RHO_FLUSH) {
     unsigned long long fr[NP], fi[NP];
 #pragma unroll
     for (int q = 0; q < NP; q++) fr[q] = fi[q] = 0ull;
+    const int a1 = min(cnt, a0 + RHO_FLUSH);
 #pragma unroll 4
-    for (int a = 0; a < cnt; a++) {
+    for (int a = a0; a < a1; a++) {
       const uint4 u = sa[grp][a];
       const float q = __uint_as_float(u.w);
 #pragma unroll
@@ -167,6 +178,7 @@ __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p
       re[2 * j] += (double)x0; re[2 * j + 1] += (double)x1;
       im[2 * j] += (double)y0; im[2 * j + 1] += (double)y1;
     }
+    }
   }
   if (G > 1) {
     if (grp > 0)
@@ -191,6 +203,16 @@ __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p
       d[1] = im[t];
     }
 }
+template <int NP, int G, int MINB, bool PK>
+__global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p) {
+  rho_mixed_body<NP, G, MINB, PK>(p, blockIdx.x);
+}
+template <int NP, int G, int MINB, bool PK>
+__global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) kp_rho_mixed(Pack pk) {
+  RB_PACK_PROLOGUE(pk);
+  (void)nb;
+  rho_mixed_body<NP, G, MINB, PK>(sv, bid);
+}
 
 // the structure factor's launch shapes (rbsog_schedule::rho_variant):
 // (pairs per thread, groups per block, blocks per SM of the register bound,
@@ -207,11 +229,11 @@ constexpr int CORR_BLOCKS = 64;
 // NV partials per warp (= p.npart): sum F_N (3), U_N and, in energy
 // evaluations, the pair virial (6)
 template <int NV>
-__global__ void __launch_bounds__(256) k_corr(View p) {
+__device__ __forceinline__ void corr_body(const View &p, int blk) {
   __shared__ double red[NV][256];
   __shared__ bool last;
   constexpr int nv = NV;
-  const int t = threadIdx.x, blk = blockIdx.x;
+  const int t = threadIdx.x;
   const int np = p.nblk_near * NEAR_WARPS;
   const int per = (np + CORR_BLOCKS - 1) / CORR_BLOCKS;
   const int b0 = blk * per, b1 = min(b0 + per, np);
@@ -252,15 +274,72 @@ __global__ void __launch_bounds__(256) k_corr(View p) {
   }
   if (t == 0) *p.corr_ticket = 0u;                // ready for the next evaluation
 }
+template <int NV>
+__global__ void __launch_bounds__(256) k_corr(View p) { corr_body<NV>(p, blockIdx.x); }
+__global__ void __launch_bounds__(256) kp_corr(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  corr_body<4>(sv, bid);
+}
+
+// The per-k outputs of the tile sums (sr0, si0) = rho(k_p): rho, the force
+// record (FP64: c Im rho, c Re rho; mixed: the KPair half of mode k), c |rho|^2
+// and, in energy evaluations, the per-k virial term.
+template <typename R>
+__device__ __forceinline__ void reduce_tail(const View &p, int k, double sr0, double si0) {
+  p.rho[2 * k] = sr0;
+  p.rho[2 * k + 1] = si0;
+  const int4 m = p.km[k];
+  const double c = p.kc[k];
+  const double kx = (double)m.x * p.kunit[0];     // k = 2 pi m / L
+  const double ky = (double)m.y * p.kunit[1];
+  const double kz_ = (double)m.z * p.kunit[2];
+  if (sizeof(R) == 4) {
+    // the mixed force record: Psi = arg(rho) in 2^-32 turn (plus the
+    // half-turn offset 2^30), K = c |rho| k (Eq. (long-rangeforce) with
+    // Im(e^{-i k.r} rho) = |rho| sin(arg rho - k.r))
+    const double turn = atan2(si0, sr0) * (1.0 / TWO_PI);      // (-1/2, 1/2]
+    const uint32_t psi = (uint32_t)(unsigned long long)(long long)llrint(turn * 4294967296.0);
+    const double R = c * hypot(sr0, si0);
+    KPair &kp = p.kpair[k >> 1];
+    const int h = k & 1;
+    int *ra = h ? &kp.b.x : &kp.a.x;
+    ra[0] = -m.x; ra[1] = -m.y; ra[2] = -m.z;
+    ra[3] = (int)(psi + 0x40000000u);
+    float *kxy = &kp.kxy.x, *kz = &kp.kz.x;
+    kxy[h] = (float)(R * kx);
+    kxy[2 + h] = (float)(R * ky);
+    kz[h] = (float)(R * kz_);
+    if (!h && k == p.P - 1) {                      // odd P: the pair's second mode is zero
+      kp.b = make_int4(0, 0, 0, 0);
+      kxy[1] = kxy[3] = kz[1] = 0.0f;
+    }
+  } else {
+    double *o = p.kfd + 5 * (int64_t)k;
+    o[0] = kx; o[1] = ky; o[2] = kz_; o[3] = c * si0; o[4] = c * sr0;
+  }
+  p.uf[k] = c * (sr0 * sr0 + si0 * si0);
+  if (p.want_vir) {
+    // (Fhat'/Fhat)(k^2) of the SOG transform, a_m = (b^m s)^2 = 1 / (2 h_m):
+    // Fhat ~ sum_m w_m a_m^{3/2} e^{-a_m k^2/2}, Fhat' ~ -sum_m w_m a_m^{3/2} (a_m/2) e^{-a_m k^2/2}
+    const double k2 = kx * kx + ky * ky + kz_ * kz_;
+    double num = 0.0, den = 0.0;
+    for (int g = 0; g < p.G; g++) {
+      const double a = 0.5 / p.sog_h[g];
+      const double t = p.sog_w[g] * a * sqrt(a) * exp(-0.5 * a * k2);
+      den += t;
+      num += 0.5 * a * t;
+    }
+    p.vf[k] = -c * (num / den) * (sr0 * sr0 + si0 * si0);
+  }
+}
 
 // One block per k: fixed-order sum over tiles (thread-strided partial sums,
-// a shuffle tree per warp, the eight warp sums in order), per-k force
-// coefficients (and, in energy evaluations, the per-k virial term).
+// a shuffle tree per warp, the eight warp sums in order), then reduce_tail.
 template <typename R>
-__global__ void __launch_bounds__(256) k_reduce(View p) {
+__device__ __forceinline__ void reduce_body(const View &p, int k) {
   __shared__ double2 wsum[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k = blockIdx.x;
   if (k < p.P) {
     const double2 *d = reinterpret_cast<const double2 *>(p.rho_part) + (int64_t)k * p.ntile;
     double r = 0.0, i = 0.0;
@@ -281,53 +360,42 @@ __global__ void __launch_bounds__(256) k_reduce(View p) {
         sr0 += wsum[u].x;
         si0 += wsum[u].y;
       }
-      p.rho[2 * k] = sr0;
-      p.rho[2 * k + 1] = si0;
-      const int4 m = p.km[k];
-      const double c = p.kc[k];
-      const double kx = TWO_PI * (double)m.x / p.L[0];
-      const double ky = TWO_PI * (double)m.y / p.L[1];
-      const double kz_ = TWO_PI * (double)m.z / p.L[2];
-      if (sizeof(R) == 4) {
-        // the mixed force record: Psi = arg(rho) in 2^-32 turn (plus the
-        // half-turn offset 2^30), K = c |rho| k (Eq. (long-rangeforce) with
-        // Im(e^{-i k.r} rho) = |rho| sin(arg rho - k.r))
-        const double turn = atan2(si0, sr0) * (1.0 / TWO_PI);      // (-1/2, 1/2]
-        const uint32_t psi = (uint32_t)(unsigned long long)(long long)llrint(turn * 4294967296.0);
-        const double R = c * hypot(sr0, si0);
-        KPair &kp = p.kpair[k >> 1];
-        const int h = k & 1;
-        int *ra = h ? &kp.b.x : &kp.a.x;
-        ra[0] = -m.x; ra[1] = -m.y; ra[2] = -m.z;
-        ra[3] = (int)(psi + 0x40000000u);
-        float *kxy = &kp.kxy.x, *kz = &kp.kz.x;
-        kxy[h] = (float)(R * kx);
-        kxy[2 + h] = (float)(R * ky);
-        kz[h] = (float)(R * kz_);
-        if (!h && k == p.P - 1) {                      // odd P: the pair's second mode is zero
-          kp.b = make_int4(0, 0, 0, 0);
-          kxy[1] = kxy[3] = kz[1] = 0.0f;
-        }
-      } else {
-        double *o = p.kfd + 5 * (int64_t)k;
-        o[0] = kx; o[1] = ky; o[2] = kz_; o[3] = c * si0; o[4] = c * sr0;
-      }
-      p.uf[k] = c * (sr0 * sr0 + si0 * si0);
-      if (p.want_vir) {
-        // (Fhat'/Fhat)(k^2) of the SOG transform, a_m = (b^m s)^2 = 1 / (2 h_m):
-        // Fhat ~ sum_m w_m a_m^{3/2} e^{-a_m k^2/2}, Fhat' ~ -sum_m w_m a_m^{3/2} (a_m/2) e^{-a_m k^2/2}
-        const double k2 = kx * kx + ky * ky + kz_ * kz_;
-        double num = 0.0, den = 0.0;
-        for (int g = 0; g < p.G; g++) {
-          const double a = 0.5 / p.sog_h[g];
-          const double t = p.sog_w[g] * a * sqrt(a) * exp(-0.5 * a * k2);
-          den += t;
-          num += 0.5 * a * t;
-        }
-        p.vf[k] = -c * (num / den) * (sr0 * sr0 + si0 * si0);
-      }
+      reduce_tail<R>(p, k, sr0, si0);
     }
   }
+}
+
+// One warp per k (8 modes per block of 256): lane-strided partial sums (eight
+// loads in flight per lane), a shuffle tree, then reduce_tail by lane 0.  For
+// few tiles per mode, where a block per mode would mostly wait on its tail.
+template <typename R>
+__device__ __forceinline__ void reduce_warp_body(const View &p, int bid) {
+  const int lane = threadIdx.x & 31;
+  const int k = bid * 8 + (threadIdx.x >> 5);
+  if (k >= p.P) return;
+  const double2 *d = reinterpret_cast<const double2 *>(p.rho_part) + (int64_t)k * p.ntile;
+  double r = 0.0, i = 0.0;
+#pragma unroll 8
+  for (int t = lane; t < p.ntile; t += 32) {
+    const double2 v = d[t];
+    r += v.x;
+    i += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r += __shfl_down_sync(0xffffffffu, r, o);
+    i += __shfl_down_sync(0xffffffffu, i, o);
+  }
+  if (lane == 0) reduce_tail<R>(p, k, r, i);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce(View p) { reduce_body<R>(p, blockIdx.x); }
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce_warp(View p) { reduce_warp_body<R>(p, blockIdx.x); }
+__global__ void __launch_bounds__(256) kp_reduce(Pack pk) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  reduce_warp_body<float>(sv, bid);
 }
 
 // Energies: U_F* = k_e/(2V) sum_p c_p |rho_p|^2 (fixed order); U_self is host-side.
@@ -404,13 +472,13 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_fp64(View p) {
 // pairs, and the chunks in FP64.  PK = false: the phase factors in scalar FP32
 // (bit for bit the same).
 template <int A, bool PK>
-__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
+__device__ __forceinline__ void farforce_mixed_body(const View &p, int bid) {
   __shared__ KPair sk[FAR_PCHUNK];
   __shared__ float sred[FORCE_BLOCK / 32 * A * 32 * 3];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int S = p.far_S, AW = (FORCE_BLOCK / 32) / S;
   const int sg = w / AW, aw = w % AW;
-  const int64_t base = (int64_t)blockIdx.x * (AW * 32 * A) + (int64_t)aw * (32 * A) + lane;
+  const int64_t base = (int64_t)bid * (AW * 32 * A) + (int64_t)aw * (32 * A) + lane;
   const int64_t n = p.n;
   uint32_t ux[A], uy[A], uz[A];
 #pragma unroll
@@ -491,6 +559,16 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
     p.FFf[i] = (float)(pre * ax[a]); p.FFf[n + i] = (float)(pre * ay[a]); p.FFf[2 * n + i] = (float)(pre * az[a]);
   }
 }
+template <int A, bool PK>
+__global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
+  farforce_mixed_body<A, PK>(p, blockIdx.x);
+}
+template <int A, bool PK>
+__global__ void __launch_bounds__(FORCE_BLOCK) kp_farforce_mixed(Pack pk) {
+  RB_PACK_PROLOGUE(pk);
+  (void)nb;
+  farforce_mixed_body<A, PK>(sv, bid);
+}
 
 // F_i = F_N,i - F^corr + F_F,i, and the closing half kick of the MD step
 // (Nose-Hoover: with the block's sum of m v^2 for the chain's closing half step).
@@ -498,13 +576,13 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
 // PREP_BLOCK atoms, as k_prepare): the FP64 kick runs on three times the warps;
 // the atom's first thread forms m v^2 from the three updated components.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(3 * PREP_BLOCK) k_finish(View p) {
+__device__ __forceinline__ void finish_body(const View &p, int bid) {
   constexpr bool MIX = sizeof(R) == 4;
   __shared__ double sv3[3][PREP_BLOCK];
   const int c = threadIdx.x / PREP_BLOCK, li = threadIdx.x % PREP_BLOCK;
-  const int64_t i = (int64_t)blockIdx.x * PREP_BLOCK + li;
+  const int64_t i = (int64_t)bid * PREP_BLOCK + li;
   const int64_t n = p.n;
-  const bool first = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool first = bid == 0 && threadIdx.x == 0;
   // the step counter advances here, after both branches joined: every kernel
   // of the step that reads it (k-batch, noise, shell batch) has finished
   if (MODE != 0 && first) *p.step += 1;
@@ -531,8 +609,15 @@ __global__ void __launch_bounds__(3 * PREP_BLOCK) k_finish(View p) {
       m2 = p.massv[p.spc[i]] * (vx * vx + vy * vy + vz * vz);
     }
     const double t = block_sum(m2);
-    if (threadIdx.x == 0) p.ke_part[blockIdx.x] = t;
+    if (threadIdx.x == 0) p.ke_part[bid] = t;
   }
+}
+template <typename R, int MODE>
+__global__ void __launch_bounds__(3 * PREP_BLOCK) k_finish(View p) { finish_body<R, MODE>(p, blockIdx.x); }
+__global__ void __launch_bounds__(3 * PREP_BLOCK) kp_finish(Pack pk) {
+  RB_PACK_PROLOGUE(pk);
+  (void)nb;
+  finish_body<float, 1>(sv, bid);
 }
 
 __global__ void k_sincos(int64_t n, const uint32_t *th, float *s, float *c) {
@@ -548,7 +633,7 @@ void launch_sincos(int64_t n, const uint32_t *th, float *s, float *c, cudaStream
 }
 
 void launch_rho(const View &v, cudaStream_t st) {
-  const dim3 g(v.ntile, (v.P + RHO_KTILE - 1) / RHO_KTILE);
+  const dim3 g(v.ntile * ((v.P + RHO_KTILE - 1) / RHO_KTILE));
   if (v.prec == RBSOG_MIXED) {
     const int var = v.rho_var;
     const int threads = RHO_VARIANT_G[var] * (RHO_BLOCK / RHO_VARIANT_NP[var]);
@@ -563,14 +648,20 @@ void launch_rho(const View &v, cudaStream_t st) {
       default: k_rho_mixed<1, 2, 2, true><<<g, threads, 0, st>>>(v); break;
     }
   } else {
-    k_rho_fp64<<<g, RHO_BLOCK, 0, st>>>(v);
+    k_rho_fp64<<<dim3(v.ntile, (v.P + RHO_KTILE - 1) / RHO_KTILE), RHO_BLOCK, 0, st>>>(v);
   }
 }
 
 void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
-  const int g = max(1, v.P);                    // one block per k
-  if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v);
-  else k_reduce<double><<<g, 256, 0, st>>>(v);
+  if (v.ntile <= RHO_WARP_TILES) {              // a warp per k
+    const int g = (std::max(1, v.P) + 7) / 8;
+    if (v.prec == RBSOG_MIXED) k_reduce_warp<float><<<g, 256, 0, st>>>(v);
+    else k_reduce_warp<double><<<g, 256, 0, st>>>(v);
+  } else {                                      // a block per k
+    const int g = std::max(1, v.P);
+    if (v.prec == RBSOG_MIXED) k_reduce<float><<<g, 256, 0, st>>>(v);
+    else k_reduce<double><<<g, 256, 0, st>>>(v);
+  }
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 
@@ -611,6 +702,62 @@ void launch_finish(const View &v, cudaStream_t st, int mode) {
     if (mode == 0) k_finish<double, 0><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
     else k_finish<double, 1><<<g, 3 * PREP_BLOCK, 0, st>>>(v);
   }
+}
+
+int pack_blocks(const View &v, int kind) {
+  switch (kind) {
+    case PK_KSAMPLE: return v.fixed_k ? 0 : v.nblk_kq;
+    case PK_PREP: return (int)((v.n + PREP_BLOCK - 1) / PREP_BLOCK);
+    case PK_ONE: return 1;
+    case PK_ROWS: return (int)(((int64_t)v.nc[1] * v.nc[2] * 32 + 255) / 256);
+    case PK_ATOM256: return (int)((v.n + 255) / 256);
+    case PK_NEAR: return v.nblk_near;
+    case PK_NEAR_W0: return v.wrap ? 0 : v.nblk_near;
+    case PK_NEAR_W1: return v.wrap ? v.nblk_near : 0;
+    case PK_CORR: return CORR_BLOCKS;
+    case PK_RHO: return v.ntile * ((v.P + RHO_KTILE - 1) / RHO_KTILE);
+    case PK_REDUCE: return (std::max(1, v.P) + 7) / 8;
+    case PK_FAR: return (int)((v.n + far_atoms_per_block(v) - 1) / far_atoms_per_block(v));
+    default: return 0;
+  }
+}
+
+// Packed launches of an ensemble (mixed precision, the schedule of the plan).
+void pack_rho(const PackPlan &q, cudaStream_t st) {
+  const int g = q.total[PK_RHO], threads = RHO_VARIANT_G[q.rho_var] * (RHO_BLOCK / RHO_VARIANT_NP[q.rho_var]);
+  const Pack k = q.pack(PK_RHO);
+  switch (q.rho_var) {
+    case 1: kp_rho_mixed<1, 1, 2, true><<<g, threads, 0, st>>>(k); break;
+    case 2: kp_rho_mixed<2, 2, 2, true><<<g, threads, 0, st>>>(k); break;
+    case 3: kp_rho_mixed<2, 4, 1, true><<<g, threads, 0, st>>>(k); break;
+    case 4: kp_rho_mixed<1, 2, 2, false><<<g, threads, 0, st>>>(k); break;
+    case 5: kp_rho_mixed<1, 1, 2, false><<<g, threads, 0, st>>>(k); break;
+    case 6: kp_rho_mixed<2, 2, 2, false><<<g, threads, 0, st>>>(k); break;
+    case 7: kp_rho_mixed<2, 4, 1, false><<<g, threads, 0, st>>>(k); break;
+    default: kp_rho_mixed<1, 2, 2, true><<<g, threads, 0, st>>>(k); break;
+  }
+}
+void pack_rhosum(const PackPlan &q, cudaStream_t st) {
+  kp_reduce<<<q.total[PK_REDUCE], 256, 0, st>>>(q.pack(PK_REDUCE));
+}
+void pack_corr(const PackPlan &q, cudaStream_t st) {
+  kp_corr<<<q.total[PK_CORR], 256, 0, st>>>(q.pack(PK_CORR));
+}
+void pack_farforce(const PackPlan &q, cudaStream_t st) {
+  const int g = q.total[PK_FAR];
+  const Pack k = q.pack(PK_FAR);
+  if (q.far_packed) {
+    if (q.far_A == 1) kp_farforce_mixed<1, true><<<g, FORCE_BLOCK, 0, st>>>(k);
+    else if (q.far_A == 2) kp_farforce_mixed<2, true><<<g, FORCE_BLOCK, 0, st>>>(k);
+    else kp_farforce_mixed<4, true><<<g, FORCE_BLOCK, 0, st>>>(k);
+  } else {
+    if (q.far_A == 1) kp_farforce_mixed<1, false><<<g, FORCE_BLOCK, 0, st>>>(k);
+    else if (q.far_A == 2) kp_farforce_mixed<2, false><<<g, FORCE_BLOCK, 0, st>>>(k);
+    else kp_farforce_mixed<4, false><<<g, FORCE_BLOCK, 0, st>>>(k);
+  }
+}
+void pack_finish(const PackPlan &q, cudaStream_t st) {
+  kp_finish<<<q.total[PK_PREP], 3 * PREP_BLOCK, 0, st>>>(q.pack(PK_PREP));
 }
 
 }  // namespace rb

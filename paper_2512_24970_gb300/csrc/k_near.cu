@@ -356,7 +356,7 @@ __device__ __forceinline__ void combine_atom(const View &p, Acc<R> &fc, Acc<R> &
 // the kept lists instead (A = core members, B = the rest inside r_list, both
 // in canonical order, i.e. ascending slot) and evaluates nothing.
 template <typename R, bool WRAP, bool ENERGY, bool BUILD>
-__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
+__device__ __forceinline__ void near_body(const View &p, int step_off, int bid, int nbk) {
   constexpr bool MIX = sizeof(R) == 4;
   // per-atom rows padded by one word so that the eight atoms of a warp hit distinct banks
   constexpr int GBYTES = WRAP ? GBYTES_WRAP : (BUILD ? GBYTES_BUILD : GBYTES_CULLED);
@@ -378,19 +378,19 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   const long long s = *p.step + step_off;
   // the binning's histograms are consumed: clear them for the next evaluation
-  for (int64_t c = (int64_t)blockIdx.x * NEAR_BLOCK + tid; c < (int64_t)p.ncell + p.nc[1] * p.nc[2];
-       c += (int64_t)gridDim.x * NEAR_BLOCK)
+  for (int64_t c = (int64_t)bid * NEAR_BLOCK + tid; c < (int64_t)p.ncell + p.nc[1] * p.nc[2];
+       c += (int64_t)nbk * NEAR_BLOCK)
     p.cell_count[c] = 0;
   if (BUILD) {
     // automatic kept lists: only a step whose k_prepare raised the flag builds
     if (p.auto_lists && *(volatile const int *)p.lflag == 0) return;
-    if (blockIdx.x == 0 && tid == 0) atomicAdd(p.nbuild, 1ull);
+    if (bid == 0 && tid == 0) atomicAdd(p.nbuild, 1ull);
   }
   const int warp = tid >> 5, lane = tid & 31;
   const int a = warp * APW + lane / TPA;      // atom row of the shared arrays
   const int g = lane % TPA;
   const int nrow = p.nc[1] * p.nc[2];
-  const int chunk = blockIdx.x * NEAR_WARPS + warp;
+  const int chunk = bid * NEAR_WARPS + warp;
   double part[NEAR_NPART] = {};
   if (chunk < p.row_chunk[nrow]) {
     // ---- the chunk ------------------------------------------------------------
@@ -825,7 +825,17 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
   if constexpr (BUILD) return;
   // ---- partials of sum F_N and of the pair energy, one per warp (FP32 sums of
   // the warp's eight atoms in mixed precision, FP64 otherwise) ----------------
-  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, blockIdx.x * NEAR_WARPS + warp, lane);
+  warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, bid * NEAR_WARPS + warp, lane);
+}
+
+template <typename R, bool WRAP, bool ENERGY, bool BUILD>
+__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near(View p, int step_off) {
+  near_body<R, WRAP, ENERGY, BUILD>(p, step_off, blockIdx.x, gridDim.x);
+}
+template <bool WRAP, bool BUILD>
+__global__ void __launch_bounds__(NEAR_BLOCK, 4) kp_near(Pack pk, int step_off) {
+  RB_PACK_PROLOGUE(pk);
+  near_body<float, WRAP, false, BUILD>(sv, step_off, bid, nb);
 }
 
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy) {
@@ -883,7 +893,7 @@ __device__ __forceinline__ void add_pair_sh(const View &p, const float4 *spf4, c
 constexpr int KB = 5;
 
 template <typename R, bool ENERGY>
-__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
+__device__ __forceinline__ void near_kept_body(const View &p, int step_off, int bid, int nbk) {
   constexpr bool MIX = sizeof(R) == 4;
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
   __shared__ uint32_t bmask[APB][RBSOG_MAX_KEPT / 32 + 1];
@@ -902,7 +912,7 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
   const int nslot = p.cell_start[p.ncell];
   // one warp per run of APW slots; a grid smaller than nblk_near (a capped
   // number of resident blocks) takes the runs in a grid-stride loop
-  for (int wc = blockIdx.x * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += gridDim.x * NEAR_WARPS) {
+  for (int wc = bid * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += nbk * NEAR_WARPS) {
   const int slot = wc * APW + lane / TPA;
   const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
   const bool active = ui.w != SU_PAD;
@@ -989,6 +999,15 @@ __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_of
   warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, wc, lane);
   __syncwarp();                                  // stsel / bmask of this warp are reused
   }
+}
+
+template <typename R, bool ENERGY>
+__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
+  near_kept_body<R, ENERGY>(p, step_off, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(NEAR_BLOCK, 4) kp_near_kept(Pack pk, int step_off) {
+  RB_PACK_PROLOGUE(pk);
+  near_kept_body<float, false>(sv, step_off, bid, nb);
 }
 
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy) {
@@ -1110,6 +1129,19 @@ void launch_lists(const View &v, cudaStream_t st, int step_off, const long long 
   else
     k_lists<false><<<g, b, 0, st>>>(v, step_off, sel, nsel, cap_core, cap_shell, core, ncore, shell,
                                     nshell, batch, nbatch, weight);
+}
+
+// Packed launches of an ensemble (mixed precision, step evaluations).
+void pack_near(const PackPlan &q, cudaStream_t st, int step_off) {
+  if (q.total[PK_NEAR_W0]) kp_near<false, false><<<q.total[PK_NEAR_W0], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W0), step_off);
+  if (q.total[PK_NEAR_W1]) kp_near<true, false><<<q.total[PK_NEAR_W1], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W1), step_off);
+}
+void pack_build_lists(const PackPlan &q, cudaStream_t st) {
+  if (q.total[PK_NEAR_W0]) kp_near<false, true><<<q.total[PK_NEAR_W0], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W0), 0);
+  if (q.total[PK_NEAR_W1]) kp_near<true, true><<<q.total[PK_NEAR_W1], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W1), 0);
+}
+void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off) {
+  kp_near_kept<<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);
 }
 
 }  // namespace rb

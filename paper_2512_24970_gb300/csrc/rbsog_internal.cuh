@@ -77,7 +77,7 @@ struct PairD {
 };
 
 // Everything a kernel needs, by value.
-struct View {
+struct alignas(16) View {
   int64_t n;
   int ns, M, prec, whole_shell;
   int P_R, P_F, P;        // P = modes in use (P_F, or the fixed list length)
@@ -180,6 +180,51 @@ struct View {
   const unsigned long long *cdf;   // flat 1-D CDFs
   const int *cdf_off0, *cdf_off2, *cdf_nmax;  // [3G]
 };
+
+static_assert(sizeof(View) % 16 == 0, "a view is copied in 16-byte words");
+
+// A packed launch of an ensemble: the blocks of every replica in one grid.
+// Block b belongs to replica r with b0[r] <= b < b0[r + 1]; views[r] is the
+// replica's view (device memory).  Each kernel's body takes (view, block
+// index, number of blocks) so that a single launch (blockIdx.x, gridDim.x)
+// and a packed one run the same code.
+struct Pack {
+  const View *views;
+  const int *b0;      // [R + 1]
+  int R;
+};
+__device__ __forceinline__ int pack_replica(const Pack &k) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = k.R - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(k.b0 + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// the replica's view into the block's shared copy (every thread calls it)
+__device__ __forceinline__ void pack_view(View &dst, const View *src) {
+  const int4 *s = reinterpret_cast<const int4 *>(src);
+  int4 *d = reinterpret_cast<int4 *>(&dst);
+  for (int e = threadIdx.x; e < (int)(sizeof(View) / 16); e += blockDim.x) d[e] = __ldg(s + e);
+  __syncthreads();
+}
+// Body of a packed kernel: `r` the replica, `sv` its view, (bid, nb) the
+// block's index and the replica's block count.  RB_PACK_PROLOGUE copies the
+// view into shared memory (kernels whose blocks read it many times);
+// RB_PACK_PROLOGUE_REF reads it in place (short blocks: the copy would cost
+// more than the reads).
+#define RB_PACK_PROLOGUE(pk)                                  \
+  __shared__ View sv;                                         \
+  const int r_ = pack_replica(pk);                            \
+  pack_view(sv, (pk).views + r_);                             \
+  const int bid = (int)blockIdx.x - __ldg((pk).b0 + r_);      \
+  const int nb = __ldg((pk).b0 + r_ + 1) - __ldg((pk).b0 + r_)
+#define RB_PACK_PROLOGUE_REF(pk)                              \
+  const int r_ = pack_replica(pk);                            \
+  const View &sv = (pk).views[r_];                            \
+  const int bid = (int)blockIdx.x - __ldg((pk).b0 + r_);      \
+  const int nb = __ldg((pk).b0 + r_ + 1) - __ldg((pk).b0 + r_)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32 multiplies
@@ -442,6 +487,46 @@ void launch_lists(const View &v, cudaStream_t st, int step_off, const long long 
                   int cap_core, int cap_shell, int *core, int *ncore, int *shell, int *nshell,
                   int *batch, int *nbatch, double *weight);
 void launch_sincos(int64_t n, const uint32_t *th, float *s, float *c, cudaStream_t st);
+
+// Packed launches of an ensemble: one grid per stage over every replica.
+// Kinds of block tables (blocks per replica of each launch shape).
+enum PackKind {
+  PK_KSAMPLE,   // k-batch: one warp per sample
+  PK_PREP,      // integrator kernels: PREP_BLOCK atoms per block
+  PK_ONE,       // one block per replica (row scan)
+  PK_ROWS,      // a warp per row of cells (cell prefix)
+  PK_ATOM256,   // one thread per atom, blocks of 256 (scatter, rank)
+  PK_NEAR,      // near-field warps over runs of slots (kept lists)
+  PK_NEAR_W0,   // the list walk of replicas without minimum-image wrapping (others: no blocks)
+  PK_NEAR_W1,   // ... with it
+  PK_CORR,      // F^corr reduction
+  PK_RHO,       // structure-factor tiles x columns of modes
+  PK_REDUCE,    // one block per mode
+  PK_FAR,       // far-force blocks
+  PK_KINDS
+};
+struct PackPlan {
+  const View *views = nullptr;     // [R] device copies of the replicas' step views
+  int R = 0;
+  const int *b0[PK_KINDS] = {};    // [R + 1] device prefix tables
+  int total[PK_KINDS] = {};
+  int rho_var = 0, far_A = 2, far_packed = 1;   // the replicas' common far-field schedule
+  Pack pack(int k) const { return Pack{views, b0[k], R}; }
+};
+// blocks of replica view v in launch shape `kind` (host)
+int pack_blocks(const View &v, int kind);
+void pack_ksample(const PackPlan &q, cudaStream_t st, int step_off);
+void pack_prepare(const PackPlan &q, cudaStream_t st, int mode, int step_off);
+void pack_bin(const PackPlan &q, cudaStream_t st);
+void pack_near(const PackPlan &q, cudaStream_t st, int step_off);
+void pack_build_lists(const PackPlan &q, cudaStream_t st);
+void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off);
+void pack_corr(const PackPlan &q, cudaStream_t st);
+void pack_rho(const PackPlan &q, cudaStream_t st);
+void pack_rhosum(const PackPlan &q, cudaStream_t st);
+void pack_farforce(const PackPlan &q, cudaStream_t st);
+void pack_finish(const PackPlan &q, cudaStream_t st);
+int far_atoms_per_block(const View &v);
 
 // Allocation-free structure factor (k_static.cu): static scratch of
 // SF_STATIC_PMAX modes x SF_STATIC_TILES tile partials of 16 B (2 MiB).

@@ -45,7 +45,9 @@ EXPORTS = [
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
     "rbsog_ensemble_step", "rbsog_ensemble_sync", "rbsog_ensemble_last_error",
     "rbsog_set_schedule", "rbsog_get_schedule", "rbsog_probe_peak",
+    "rbsog_ensemble_set_mode", "rbsog_ensemble_get_mode", "rbsog_ensemble_set_groups",
 ]
+ENSEMBLE_PACKED, ENSEMBLE_GRAPHS = 0, 1
 PROBE_FP32, PROBE_FP32X2, PROBE_FP64, PROBE_IMAD = 0, 1, 2, 3
 SF_STATIC_PMAX = 1024
 NSTAGE = 9
@@ -82,11 +84,12 @@ class Schedule(ctypes.Structure):
     """Launch shapes of the mixed far field (``rbsog_schedule``)."""
     _fields_ = [("rho_variant", ctypes.c_int32), ("rho_blocks_per_sm", ctypes.c_int32),
                 ("far_atoms_per_thread", ctypes.c_int32), ("far_segments", ctypes.c_int32),
-                ("far_packed", ctypes.c_int32), ("near_blocks_per_sm", ctypes.c_int32)]
+                ("far_packed", ctypes.c_int32), ("near_blocks_per_sm", ctypes.c_int32),
+                ("rho_tile_atoms", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.rho_variant, self.rho_blocks_per_sm, self.far_atoms_per_thread, self.far_segments,
-                self.far_packed, self.near_blocks_per_sm)
+                self.far_packed, self.near_blocks_per_sm, self.rho_tile_atoms)
 
 
 @dataclasses.dataclass
@@ -175,6 +178,9 @@ def load():
     L.rbsog_ensemble_replica.restype = P
     L.rbsog_ensemble_step.argtypes = [P, I64]
     L.rbsog_ensemble_sync.argtypes = [P]
+    L.rbsog_ensemble_set_mode.argtypes = [P, I32]
+    L.rbsog_ensemble_get_mode.argtypes = [P, ctypes.POINTER(I32)]
+    L.rbsog_ensemble_set_groups.argtypes = [P, I32]
     L.rbsog_ensemble_last_error.argtypes = [P]
     L.rbsog_ensemble_last_error.restype = ctypes.c_char_p
     L.rbsog_last_error.argtypes = [P]
@@ -469,11 +475,12 @@ class Context:
         return dict(near=near, far=far, Fcorr=fc, rho=rho)
 
     def set_schedule(self, rho_variant: int, rho_blocks_per_sm: int, far_atoms_per_thread: int,
-                     far_segments: int, far_packed: int = 1, near_blocks_per_sm: int = 0):
+                     far_segments: int, far_packed: int = 1, near_blocks_per_sm: int = 0,
+                     rho_tile_atoms: int = 0):
         """Launch shapes of the mixed far field and the kept near field (the step
         graph is captured again)."""
         q = Schedule(rho_variant, rho_blocks_per_sm, far_atoms_per_thread, far_segments, far_packed,
-                     near_blocks_per_sm)
+                     near_blocks_per_sm, rho_tile_atoms)
         self._ck(self._L.rbsog_set_schedule(self.h, ctypes.byref(q)))
 
     def schedule(self):
@@ -564,9 +571,33 @@ class Ensemble:
     def step(self, nsteps: int):
         self._ck(self._L.rbsog_ensemble_step(self.h, int(nsteps)))
 
-    @staticmethod
-    def launch_kind():
-        return "one CUDA graph per ensemble step (every replica's step graph a child node)"
+    def set_mode(self, mode: int):
+        """ENSEMBLE_PACKED (one launch per stage over all replicas, where they
+        allow it) or ENSEMBLE_GRAPHS (the replicas' own step graphs as child
+        nodes of one graph)."""
+        self._ck(self._L.rbsog_ensemble_set_mode(self.h, int(mode)))
+
+    def set_groups(self, groups: int):
+        """Packed mode: replicas dealt into this many groups of about equal
+        atoms, the groups' packed launches as parallel graph branches."""
+        self._ck(self._L.rbsog_ensemble_set_groups(self.h, int(groups)))
+        self._groups = int(groups)
+
+    def used_mode(self) -> int:
+        m = ctypes.c_int32()
+        self._ck(self._L.rbsog_ensemble_get_mode(self.h, ctypes.byref(m)))
+        return m.value
+
+    def launch_kind(self):
+        m = self.used_mode()
+        if m == ENSEMBLE_PACKED:
+            g = getattr(self, "_groups", 1)
+            return ("packed: one CUDA graph per ensemble step; the replicas in %d group(s) of about equal atoms, "
+                    "each stage of a group one kernel launch over its replicas' blocks, the groups as parallel "
+                    "branches" % g)
+        if m == ENSEMBLE_GRAPHS:
+            return "one CUDA graph per ensemble step (every replica's step graph a child node)"
+        return "not stepped yet"
 
     def sync(self):
         self._ck(self._L.rbsog_ensemble_sync(self.h))

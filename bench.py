@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form beside the line")
     ap.add_argument("--schedule", default=None,
                     help="schedule rho_variant,rho_blocks_per_sm,far_atoms_per_thread,far_segments,"
-                         "far_packed,near_blocks_per_sm,rho_tile_atoms (default: tuned, or the library's with --no-autotune)")
+                         "far_packed,near_blocks_per_sm,rho_tile_atoms,near_wide,rho_reduce (default: tuned, or the library's with "
+                         "--no-autotune)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-replica ensemble beside the line")
     ap.add_argument("--sweep", action="store_true",
                     help="shell batch x P_F sweep of the configuration (one JSON line each)")
@@ -361,7 +362,8 @@ def run_ours(args):
         from paper_2512_24970_gb300 import autotune
         sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream, flush=flush.zero_)
         sched_tuning = {"chosen": dict(zip(("rho_variant", "rho_blocks_per_sm", "far_atoms_per_thread",
-                                             "far_segments", "far_packed", "near_blocks_per_sm", "rho_tile_atoms"), sched)),
+                                             "far_segments", "far_packed", "near_blocks_per_sm", "rho_tile_atoms", "near_wide",
+                                             "rho_reduce"), sched)),
                         "candidates": [{"schedule": list(q), "ms_per_step": t} for q, t in table],
                         "how": "100 MD steps per candidate after 10 warm-up, each after an L2 flush and timed alone "
                                "with CUDA events, coordinate search (autotune.tune_schedule)"}

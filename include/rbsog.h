@@ -267,7 +267,7 @@ int rbsog_get_sog(rbsog_ctx *ctx, double *s, double *w, double *S);
  * factors rho(k_p) over all atoms and the force of Eq. (long-rangeforce),
  * O(N P_F) work each, Sec. 2.4) and of the near field beside it.  They split that work over the GPU and
  * change nothing but the order in which FP32 and FP64 partial sums are added;
- * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1, 0, 0). */
+ * paper_2512_24970_gb300/autotune.py picks them by timing.  Defaults (0, 2, 2, 4, 1, 0, 0, 0, 0). */
 typedef struct {
   int32_t rho_variant;           /* structure factor block shape: 0 = two groups of 256 threads,
                                     one pair of modes per thread; 1 = one group of 256; 2 = two
@@ -283,6 +283,13 @@ typedef struct {
   int32_t rho_tile_atoms;        /* structure factor: 0 = tiles from rho_blocks_per_sm; 32..65536 =
                                     that many atoms per tile (tiles in proportion to N, e.g. for the
                                     replicas of a packed ensemble) */
+  int32_t near_wide;             /* near field with kept lists: 1 = a thread gathers its first 8 members
+                                    of A and its first batch members at once (more loads in flight, more
+                                    registers); 0 = in rounds of 4 and 5 (same sums bit for bit) */
+  int32_t rho_reduce;            /* sum of the structure factor's tile partials: 0 = a warp per mode up
+                                    to 160 tiles, else a block per mode; 1 = always a block per mode;
+                                    2 = always a warp per mode (8 modes per block: fewer blocks to
+                                    schedule beside the near field) */
 } rbsog_schedule;
 
 /* Set the schedule (host pointer).  Takes effect at the next evaluation (the

@@ -109,8 +109,8 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
     """Time ``steps`` MD steps of workload ``w`` (mixed precision) on one
     context for each far-field schedule of a coordinate search and return
     (best schedule (rho_variant, rho_blocks_per_sm, far_atoms_per_thread,
-    far_segments, far_packed, near_blocks_per_sm, rho_tile_atoms), [(schedule,
-    ms per step)]).
+    far_segments, far_packed, near_blocks_per_sm, rho_tile_atoms, near_wide,
+    rho_reduce), [(schedule, ms per step)]).
     The near field's residency cap is searched last, with kept lists only."""
     import torch
     dev = torch.device("cuda", device)
@@ -143,15 +143,26 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
                         best, best_t = q, t
         if params.list_every != 0:
             timed = best
-            for nb in NEAR_BLOCKS_PER_SM:
-                q = tuple(timed[:5]) + (nb,) + tuple(timed[6:])
-                if q == timed:
-                    continue
-                ctx.set_schedule(*q)
-                t = timed_steps(ctx, st, warmup, steps, flush)
-                table.append((q, t))
-                if t < best_t:
-                    best, best_t = q, t
+            for wide in (0, 1):
+                for nb in (0,) + NEAR_BLOCKS_PER_SM:
+                    q = tuple(timed[:5]) + (nb, timed[6], wide) + tuple(timed[8:])
+                    if q == timed:
+                        continue
+                    ctx.set_schedule(*q)
+                    t = timed_steps(ctx, st, warmup, steps, flush)
+                    table.append((q, t))
+                    if t < best_t:
+                        best, best_t = q, t
+        timed = best
+        for red in (1, 2):                         # the tile sums' form
+            q = tuple(timed[:8]) + (red,)
+            if q == timed:
+                continue
+            ctx.set_schedule(*q)
+            t = timed_steps(ctx, st, warmup, steps, flush)
+            table.append((q, t))
+            if t < best_t:
+                best, best_t = q, t
     finally:
         ctx.close()
     return best, table
@@ -215,7 +226,7 @@ def tune_ensemble_schedule(ens, stream=None, warmup: int = 3, steps: int = 20, f
             best, best_t = (q, groups), t
 
     for ta in ENSEMBLE_TILE_ATOMS:
-        trial((0, 2, 2, 4, 1, 0, ta), 4)
+        trial((0, 2, 2, 4, 1, 0, ta, 0, 0), 4)
     q0, g0 = best
     for g in ENSEMBLE_GROUPS:
         if g != g0:
@@ -230,5 +241,7 @@ def tune_ensemble_schedule(ens, stream=None, warmup: int = 3, steps: int = 20, f
         q = q0[:2] + (A, S) + q0[4:]
         if q != q0:
             trial(q, g0)
+    q0, g0 = best
+    trial(q0[:7] + (1 - q0[7],) + q0[8:], g0)     # the near field's wide gathers
     apply(*best)
     return best, table

@@ -53,7 +53,7 @@ struct rbsog_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
   int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
-  rbsog_schedule sched{0, 2, 2, 4, 1, 0, 0};  // far-field launch shapes (rbsog_set_schedule)
+  rbsog_schedule sched{0, 2, 2, 4, 1, 0, 0, 0, 0};  // far-field launch shapes (rbsog_set_schedule)
 };
 
 namespace {
@@ -586,6 +586,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   v.rho_var = ctx->sched.rho_variant;
   v.far_packed = ctx->sched.far_packed;
   v.near_bps = ctx->sched.near_blocks_per_sm;
+  v.near_wide = ctx->sched.near_wide;
+  v.rho_reduce = ctx->sched.rho_reduce;
   v.nsm = ctx->nsm;
   ctx->rho_bps = ctx->sched.rho_blocks_per_sm;
   set_rho_tiling(ctx, P.P_F);
@@ -1202,7 +1204,8 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   const int A = q.far_atoms_per_thread, S = q.far_segments;
   if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) ||
       q.near_blocks_per_sm < 0 || q.near_blocks_per_sm > 16 ||
-      (q.rho_tile_atoms != 0 && (q.rho_tile_atoms < 32 || q.rho_tile_atoms > 65536)) || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
+      (q.rho_tile_atoms != 0 && (q.rho_tile_atoms < 32 || q.rho_tile_atoms > 65536)) ||
+      (q.near_wide != 0 && q.near_wide != 1) || q.rho_reduce < 0 || q.rho_reduce > 2 || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||
       (A != 1 && A != 2 && A != 4) ||
       (S != 1 && S != 2 && S != 4 && S != 8))
     return fail(ctx, RBSOG_E_INVAL, "schedule out of range");
@@ -1217,6 +1220,8 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   v.rho_var = q.rho_variant;
   v.far_packed = q.far_packed;
   v.near_bps = q.near_blocks_per_sm;
+  v.near_wide = q.near_wide;
+  v.rho_reduce = q.rho_reduce;
   ctx->rho_bps = q.rho_blocks_per_sm;
   set_rho_tiling(ctx, v.P);
   ctx->Pmax = 0;                               // tile partials for the new tiling

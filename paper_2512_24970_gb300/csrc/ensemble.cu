@@ -195,7 +195,7 @@ bool packable(rbsog_ensemble *e, std::vector<rb::View> &views, int *mode, bool *
     }
     const rb::View &v0 = views[0];
     if (m != *mode || (v.kept != 0) != *kept || v.rho_var != v0.rho_var || v.far_A != v0.far_A ||
-        v.far_S != v0.far_S || v.far_packed != v0.far_packed)
+        v.far_S != v0.far_S || v.far_packed != v0.far_packed || v.near_wide != v0.near_wide)
       return false;
   }
   return R > 0;
@@ -276,6 +276,7 @@ int ensure_packed(rbsog_ensemble *e) {
     q.rho_var = views[0].rho_var;
     q.far_A = views[0].far_A;
     q.far_packed = views[0].far_packed;
+    q.near_wide = views[0].near_wide;
   }
   if (e->dbuf) cudaFree(e->dbuf);
   e->dbuf = nullptr;

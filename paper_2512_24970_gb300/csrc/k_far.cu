@@ -653,7 +653,7 @@ void launch_rho(const View &v, cudaStream_t st) {
 }
 
 void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
-  if (v.ntile <= RHO_WARP_TILES) {              // a warp per k
+  if (v.rho_reduce == 2 || (v.rho_reduce == 0 && v.ntile <= RHO_WARP_TILES)) {   // a warp per k
     const int g = (std::max(1, v.P) + 7) / 8;
     if (v.prec == RBSOG_MIXED) k_reduce_warp<float><<<g, 256, 0, st>>>(v);
     else k_reduce_warp<double><<<g, 256, 0, st>>>(v);

@@ -892,7 +892,7 @@ __device__ __forceinline__ void add_pair_sh(const View &p, const float4 *spf4, c
 // benchmark: one pass with every lane busy).
 constexpr int KB = 5;
 
-template <typename R, bool ENERGY>
+template <typename R, bool ENERGY, bool WIDE, bool CAPPED>
 __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int bid, int nbk) {
   constexpr bool MIX = sizeof(R) == 4;
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
@@ -963,7 +963,41 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   // well inside r_shell (no atom moves by more than skin/2 between builds) -----
   const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
   const bool acheck = !p.a_inside;
-  for (int e0 = g; e0 < nab.x; e0 += 4 * TPA) {
+  int a_from = g, b_from = 0;                    // where the loops below start
+  if (WIDE) {
+    // a thread's first eight members of A and its first batch members are all
+    // gathered before any pair is evaluated (13 independent loads in flight);
+    // the members are visited in the same order as below, so the sums are
+    // the same bit for bit
+    int jsA[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) jsA[i] = (g + TPA * i < nab.x) ? la[g + TPA * i] : -1;
+    uint4 uA[8], uB[KB];
+#pragma unroll
+    for (int i = 0; i < 8; i++) uA[i] = p.su[max(jsA[i], 0)];
+#pragma unroll
+    for (int i = 0; i < KB; i++) uB[i] = p.su[max(jb[i], 0)];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if (jsA[i] >= 0 && (!acheck || in_shell(p, ui, uA[i]))) {
+        if constexpr (MIX) add_pair_sh<ENERGY>(p, spf4, sg4, spi, ui, uA[i], fa);
+        else add_pair<R, ENERGY>(p, nullptr, spd, sg4, swa, sw, sh2, spi, ui, uA[i], fa);
+      }
+#pragma unroll
+    for (int i = 0; i < KB; i++)
+      if (jb[i] >= 0 && in_shell(p, ui, uB[i])) {
+        if constexpr (MIX) add_pair_sh<ENERGY>(p, spf4, sg4, spi, ui, uB[i], fb);
+        else add_pair<R, ENERGY>(p, nullptr, spd, sg4, swa, sw, sh2, spi, ui, uB[i], fb);
+      }
+    a_from = g + 8 * TPA;
+    b_from = TPA * KB;
+#pragma unroll
+    for (int i = 0; i < KB; i++) {
+      const int k = b_from + g + TPA * i;
+      jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+    }
+  }
+  for (int e0 = a_from; e0 < nab.x; e0 += 4 * TPA) {
     int js[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) js[i] = (e0 + TPA * i < nab.x) ? la[e0 + TPA * i] : -1;
@@ -978,7 +1012,8 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
       }
   }
   // ---- the batch of B (or all of it) ---------------------------------------
-  for (int k0 = 0;; k0 += TPA * KB) {
+  for (int k0 = b_from;; k0 += TPA * KB) {
+    if (WIDE && k0 >= nb) break;
     uint4 uj[KB];
 #pragma unroll
     for (int i = 0; i < KB; i++) uj[i] = p.su[max(jb[i], 0)];
@@ -997,17 +1032,19 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   }
   combine_atom<R, ENERGY>(p, fa, fb, wgt, active, g, ui, part);
   warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, wc, lane);
+  if (!CAPPED) break;                            // a warp per run: one pass
   __syncwarp();                                  // stsel / bmask of this warp are reused
   }
 }
 
-template <typename R, bool ENERGY>
+template <typename R, bool ENERGY, bool WIDE, bool CAPPED>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
-  near_kept_body<R, ENERGY>(p, step_off, blockIdx.x, gridDim.x);
+  near_kept_body<R, ENERGY, WIDE, CAPPED>(p, step_off, blockIdx.x, gridDim.x);
 }
+template <bool WIDE>
 __global__ void __launch_bounds__(NEAR_BLOCK, 4) kp_near_kept(Pack pk, int step_off) {
   RB_PACK_PROLOGUE(pk);
-  near_kept_body<float, false>(sv, step_off, bid, nb);
+  near_kept_body<float, false, WIDE, false>(sv, step_off, bid, nb);
 }
 
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy) {
@@ -1015,13 +1052,21 @@ void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy)
   // runs, so that the far-field branch always finds free slots
   const int nb = v.near_bps > 0 ? std::min(v.nblk_near, v.near_bps * v.nsm) : v.nblk_near;
   const dim3 g(nb), b(NEAR_BLOCK);
+  const bool cap = v.near_bps > 0;
+#define RB_KEPT(R, EN, WI)                                                    \
+  do {                                                                        \
+    if (cap) k_near_kept<R, EN, WI, true><<<g, b, 0, st>>>(v, step_off);      \
+    else k_near_kept<R, EN, WI, false><<<g, b, 0, st>>>(v, step_off);         \
+  } while (0)
   if (v.prec == RBSOG_MIXED) {
-    if (energy) k_near_kept<float, true><<<g, b, 0, st>>>(v, step_off);
-    else k_near_kept<float, false><<<g, b, 0, st>>>(v, step_off);
+    if (energy) RB_KEPT(float, true, false);
+    else if (v.near_wide) RB_KEPT(float, false, true);
+    else RB_KEPT(float, false, false);
   } else {
-    if (energy) k_near_kept<double, true><<<g, b, 0, st>>>(v, step_off);
-    else k_near_kept<double, false><<<g, b, 0, st>>>(v, step_off);
+    if (energy) RB_KEPT(double, true, false);
+    else RB_KEPT(double, false, false);
   }
+#undef RB_KEPT
 }
 
 // Parity hook: the kept lists of selected atoms (caller ids, canonical order)
@@ -1141,7 +1186,8 @@ void pack_build_lists(const PackPlan &q, cudaStream_t st) {
   if (q.total[PK_NEAR_W1]) kp_near<true, true><<<q.total[PK_NEAR_W1], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W1), 0);
 }
 void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off) {
-  kp_near_kept<<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);
+  if (q.near_wide) kp_near_kept<true><<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);
+  else kp_near_kept<false><<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);
 }
 
 }  // namespace rb

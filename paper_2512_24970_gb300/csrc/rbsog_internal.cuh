@@ -163,6 +163,8 @@ struct alignas(16) View {
   int rho_var;            // mixed structure factor: launch shape (rbsog_schedule::rho_variant)
   int far_packed;         // mixed far force: two modes per FP32x2 instruction (else scalar FP32)
   int near_bps;           // kept near field: resident blocks per SM (0: one block per 4 runs of slots)
+  int near_wide;          // kept near field: a thread's first members of A and of the batch gathered at once
+  int rho_reduce;         // tile sums: 0 auto, 1 a block per mode, 2 a warp per mode
   int nsm;                // SMs of the device
   double *kfd;            // [Pmax][5] FP64 (k_x, k_y, k_z, c Im rho, c Re rho)
   double *red;            // [24]: F^corr (3), U_N, U_F*, W_N (6) at 5, W_F* (6) at 11
@@ -511,6 +513,7 @@ struct PackPlan {
   const int *b0[PK_KINDS] = {};    // [R + 1] device prefix tables
   int total[PK_KINDS] = {};
   int rho_var = 0, far_A = 2, far_packed = 1;   // the replicas' common far-field schedule
+  int near_wide = 0;
   Pack pack(int k) const { return Pack{views, b0[k], R}; }
 };
 // blocks of replica view v in launch shape `kind` (host)

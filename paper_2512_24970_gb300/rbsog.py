@@ -85,11 +85,12 @@ class Schedule(ctypes.Structure):
     _fields_ = [("rho_variant", ctypes.c_int32), ("rho_blocks_per_sm", ctypes.c_int32),
                 ("far_atoms_per_thread", ctypes.c_int32), ("far_segments", ctypes.c_int32),
                 ("far_packed", ctypes.c_int32), ("near_blocks_per_sm", ctypes.c_int32),
-                ("rho_tile_atoms", ctypes.c_int32)]
+                ("rho_tile_atoms", ctypes.c_int32), ("near_wide", ctypes.c_int32),
+                ("rho_reduce", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.rho_variant, self.rho_blocks_per_sm, self.far_atoms_per_thread, self.far_segments,
-                self.far_packed, self.near_blocks_per_sm, self.rho_tile_atoms)
+                self.far_packed, self.near_blocks_per_sm, self.rho_tile_atoms, self.near_wide, self.rho_reduce)
 
 
 @dataclasses.dataclass
@@ -476,11 +477,11 @@ class Context:
 
     def set_schedule(self, rho_variant: int, rho_blocks_per_sm: int, far_atoms_per_thread: int,
                      far_segments: int, far_packed: int = 1, near_blocks_per_sm: int = 0,
-                     rho_tile_atoms: int = 0):
+                     rho_tile_atoms: int = 0, near_wide: int = 0, rho_reduce: int = 0):
         """Launch shapes of the mixed far field and the kept near field (the step
         graph is captured again)."""
         q = Schedule(rho_variant, rho_blocks_per_sm, far_atoms_per_thread, far_segments, far_packed,
-                     near_blocks_per_sm, rho_tile_atoms)
+                     near_blocks_per_sm, rho_tile_atoms, near_wide, rho_reduce)
         self._ck(self._L.rbsog_set_schedule(self.h, ctypes.byref(q)))
 
     def schedule(self):

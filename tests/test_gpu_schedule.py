@@ -26,9 +26,10 @@ def rms_rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
-SCHEDULES = [(0, 2, 2, 4, 1, 0, 0), (1, 1, 1, 1, 1, 0, 0), (1, 4, 4, 2, 0, 0, 0), (2, 2, 2, 8, 1, 0, 0),
-             (3, 1, 1, 4, 0, 0, 0), (3, 3, 4, 8, 1, 0, 0), (2, 4, 1, 2, 1, 0, 0), (5, 3, 2, 4, 0, 0, 0),
-             (7, 1, 4, 1, 0, 0, 0), (6, 2, 2, 2, 1, 0, 0), (0, 2, 2, 4, 1, 0, 64), (1, 2, 2, 4, 1, 0, 1000)]
+SCHEDULES = [(0, 2, 2, 4, 1, 0, 0, 0, 0), (1, 1, 1, 1, 1, 0, 0, 0, 0), (1, 4, 4, 2, 0, 0, 0, 0, 0), (2, 2, 2, 8, 1, 0, 0, 0, 0),
+             (3, 1, 1, 4, 0, 0, 0, 0, 0), (3, 3, 4, 8, 1, 0, 0, 0, 0), (2, 4, 1, 2, 1, 0, 0, 0, 0), (5, 3, 2, 4, 0, 0, 0, 0, 0),
+             (7, 1, 4, 1, 0, 0, 0, 0, 0), (6, 2, 2, 2, 1, 0, 0, 0, 0), (0, 2, 2, 4, 1, 0, 64, 0, 0),
+             (1, 2, 2, 4, 1, 0, 1000, 0, 0), (0, 2, 2, 4, 1, 0, 0, 0, 1), (1, 4, 2, 4, 1, 0, 0, 0, 2)]
 
 
 @pytest.mark.parametrize("P_F", [500, 1301])       # one column of modes; three, the last ragged, odd P
@@ -52,10 +53,10 @@ def test_schedules_agree(rb, orc, P_F):
         assert rms_rel(F, o["F"]) < MIXED_TOL, q
         assert rms_rel(parts["rho"], o["rho"]) < MIXED_TOL, q
     # scalar FP32 and packed FP32x2 forms of one shape: lane by lane the same operations
-    ctx.set_schedule(0, 2, 2, 4, 1, 0, 0)
+    ctx.set_schedule(0, 2, 2, 4, 1, 0, 0, 0, 0)
     ctx.compute_forces()
     a = ctx.debug_parts(P=P_F)
-    ctx.set_schedule(4, 2, 2, 4, 0, 0, 0)
+    ctx.set_schedule(4, 2, 2, 4, 0, 0, 0, 0, 0)
     ctx.compute_forces()
     b = ctx.debug_parts(P=P_F)
     np.testing.assert_array_equal(a["rho"], b["rho"])
@@ -64,16 +65,17 @@ def test_schedules_agree(rb, orc, P_F):
 
 def test_near_residency_cap_same_forces(rb, orc):
     """Kept lists: the near field with a capped number of resident blocks
-    (grid-stride over the runs of slots) gives the uncapped result bit for
-    bit (same warps' arithmetic, same partials), in both precisions."""
+    (grid-stride over the runs of slots), and with its wide gathers, gives the
+    default result bit for bit (same warps' arithmetic in the same order,
+    same partials), in both precisions."""
     w = W.rock_salt((9, 8, 7), seed=23, composition="LiCl-NaCl")
     for prec in (rb.MIXED, rb.FP64):
         prm = rb.MethodParams(P_R=20, P_F=200, seed=5, precision=prec, list_every=-1, skin=1.0)
         out = []
-        for nb in (0, 1, 3):
+        for nb, wide in ((0, 0), (1, 0), (3, 0), (0, 1), (2, 1)):
             ctx = rb.Context(0)
             ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, prm)
-            ctx.set_schedule(0, 2, 2, 4, 1, nb, 0)
+            ctx.set_schedule(0, 2, 2, 4, 1, nb, 0, wide, 0)
             ctx.set_velocities(W.maxwell_boltzmann(w, 1200.0))
             ctx.step(4)
             F, E = ctx.compute_forces(energy=True)
@@ -88,13 +90,14 @@ def test_schedule_rejects(rb):
     w = W.rock_salt((5, 5, 5), seed=1)
     ctx = rb.Context(0)
     ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, rb.MethodParams())
-    for bad in [(8, 2, 2, 4, 1, 0, 0), (-1, 2, 2, 4, 1, 0, 0), (0, 0, 2, 4, 1, 0, 0), (0, 9, 2, 4, 1, 0, 0),
-                (0, 2, 3, 4, 1, 0, 0), (0, 2, 2, 3, 1, 0, 0), (0, 2, 2, 16, 1, 0, 0), (0, 2, 2, 4, 2, 0, 0),
-                (0, 2, 2, 4, 1, -1, 0), (0, 2, 2, 4, 1, 17, 0), (0, 2, 2, 4, 1, 0, 31), (0, 2, 2, 4, 1, 0, 65537)]:
+    for bad in [(8, 2, 2, 4, 1, 0, 0, 0, 0), (-1, 2, 2, 4, 1, 0, 0, 0), (0, 0, 2, 4, 1, 0, 0, 0, 0), (0, 9, 2, 4, 1, 0, 0, 0, 0),
+                (0, 2, 3, 4, 1, 0, 0, 0, 0), (0, 2, 2, 3, 1, 0, 0, 0, 0), (0, 2, 2, 16, 1, 0, 0, 0, 0), (0, 2, 2, 4, 2, 0, 0, 0, 0),
+                (0, 2, 2, 4, 1, -1, 0, 0, 0), (0, 2, 2, 4, 1, 17, 0, 0, 0), (0, 2, 2, 4, 1, 0, 31, 0, 0),
+                (0, 2, 2, 4, 1, 0, 65537, 0, 0), (0, 2, 2, 4, 1, 0, 0, 2, 0), (0, 2, 2, 4, 1, 0, 0, 0, 3), (0, 2, 2, 4, 1, 0, 0, 0, -1)]:
         with pytest.raises(rb.RbsogError) as e:
             ctx.set_schedule(*bad)
         assert e.value.code == -1
-    assert ctx.schedule() == (0, 2, 2, 4, 1, 0, 0)
+    assert ctx.schedule() == (0, 2, 2, 4, 1, 0, 0, 0, 0)
 
 
 def test_tune_schedule(rb):
@@ -105,5 +108,5 @@ def test_tune_schedule(rb):
     best, table = autotune.tune_schedule(w, prm, warmup=3, steps=10)
     assert best in [q for q, _ in table]
     assert all(t > 0 for _, t in table)
-    assert len(table) == 8 * 4 + 3 * 4 * 2 - 1 + 5
+    assert len(table) == 8 * 4 + 3 * 4 * 2 - 1 + 2 * 6 - 1 + 2
     assert min(t for _, t in table) == dict(table)[best]

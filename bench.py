@@ -206,18 +206,19 @@ def measured_peaks(rbsog, local):
     return out
 
 
-def profiled_traffic(stage):
+def profiled_traffic(stage, kept=False):
     """DRAM bytes per launch of the stage's kernel from the committed ncu summary,
     only while the kernel source is the one that was profiled (else None)."""
     import hashlib
     src = {"near": "k_near.cu", "rho": "k_far.cu", "farforce": "k_far.cu"}.get(stage)
+    name = "k_near_kept" if (stage == "near" and kept) else KERNEL_LABEL.get(stage)
     summ = os.path.join(ROOT, "profiles", "traffic_nacl64k.txt")
     if src is None or not os.path.exists(summ):
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_24970_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
     for line in open(summ):
         f = line.split()
-        if len(f) >= 3 and f[0] == KERNEL_LABEL[stage] and f[1] == h:
+        if len(f) >= 3 and f[0] == name and f[1] == h:
             return float(f[2])
     return None
 
@@ -455,17 +456,38 @@ def run_ours(args):
                        "frac": alg[kname] / t / fma_peak}
         if kname in slots:
             kern[kname]["issue_frac"] = slots[kname] / t / issue_peak
+    # the kept near field reads its lists from HBM: algorithmic bytes per atom-step
+    # = the entries of A and of the batch (4 B each), |A| and |B| (8 B), its own
+    # slot record and each member's coordinates once (16 B + 16 B), its force (12 B)
+    pk_json, pk_kind = peaks()
+    hbm_peak = float(pk_json.get("hbm_gbs", 6800.0)) * 1e9
+    rho_n = w.n / float(np.prod(w.box))
+    n_core = 4.0 / 3.0 * np.pi * 6.0 ** 3 * rho_n
+    if list_every != 0:
+        kb = w.n * (4.0 * (n_core + P_R) + 8.0 + 16.0 + 16.0 + 12.0)
+        t = kern["near"]["ms"] * 1e-3
+        kern["near"].update({"algorithmic_bytes": kb, "achieved_gbs": kb / t / 1e9, "hbm_frac": kb / t / hbm_peak,
+                             "hbm_peak_gbs": hbm_peak / 1e9, "hbm_peak_source": pk_kind + " (MEASURED_PEAKS.json)"})
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    roof = {"bound": "alu", "kernel": label[dom], "achieved": kern[dom]["achieved"], "peak": fma_peak / 1e9,
+    near_hbm = dom == "near" and list_every != 0 and kern["near"]["algorithmic_bytes"] / hbm_peak > alg["near"] / fma_peak
+    if near_hbm:
+        roof = {"bound": "hbm", "kernel": label[dom], "achieved": kern[dom]["achieved_gbs"], "peak": hbm_peak / 1e9,
+                "unit": "GB/s", "frac": kern[dom]["hbm_frac"],
+                "traffic": profiled_traffic(dom, kept=True),
+                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % pk_kind,
+                "bytes_per_unit": {"atom_step": kern[dom]["algorithmic_bytes"] / w.n},
+                "units": {"atoms": w.n},
+                "alu_frac": kern[dom]["frac"]}
+    else:
+        roof = {"bound": "alu", "kernel": label[dom], "achieved": kern[dom]["achieved"], "peak": fma_peak / 1e9,
             "unit": "Glane-op/s", "frac": kern[dom]["frac"],
-            "traffic": profiled_traffic(dom) if not (dom == "near" and list_every != 0) else None,
+            "traffic": profiled_traffic(dom, kept=list_every != 0),
             "peak_source": "measured in this run: FP32 multiply-add pipe, %d SMs (rbsog_probe_peak)" % nsm,
             "ops_per_unit": {"near_pair": OPS_PAIR, "list_test": OPS_TEST, "rho_atom_k": OPS_RHO,
                              "far_atom_k": OPS_FAR},
-            "units": {"atoms": w.n, "P_F": P_F, "pairs_per_atom": None if list_every == 0 else None,
-                      "list_tests_per_atom_step": tests}}
-    if "issue_frac" in kern[dom]:
-        roof["issue_frac"] = kern[dom]["issue_frac"]
+            "units": {"atoms": w.n, "P_F": P_F, "list_tests_per_atom_step": tests}}
+        if "issue_frac" in kern[dom]:
+            roof["issue_frac"] = kern[dom]["issue_frac"]
     step_ops = sum(alg.values())
     step_roof = {"ops_per_step": step_ops, "t_roof_us": step_ops / fma_peak * 1e6,
                  "frac": (step_ops / fma_peak) / (t_total / K * 1e-3),

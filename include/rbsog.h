@@ -272,11 +272,13 @@ typedef struct {
   int32_t rho_variant;           /* structure factor block shape: 0 = two groups of 256 threads,
                                     one pair of modes per thread; 1 = one group of 256; 2 = two
                                     groups of 128 threads, two pairs each; 3 = four such groups;
-                                    4..7 = 0..3 in scalar FP32 instead of packed FP32x2 */
+                                    4..7 = 0..3 in scalar FP32 instead of packed FP32x2; 8, 9 =
+                                    0, 1 with the cosine packed too */
   int32_t rho_blocks_per_sm;     /* structure factor: tiles of atoms per SM the tiling aims at, 1..8 */
   int32_t far_atoms_per_thread;  /* far force: atoms per thread, 1, 2 or 4 */
   int32_t far_segments;          /* far force: k segments per block of 8 warps, 1, 2, 4 or 8 */
-  int32_t far_packed;            /* far force: 1 = two modes per packed FP32x2 instruction, 0 = scalar */
+  int32_t far_packed;            /* far force: 1 = two modes per packed FP32x2 instruction, 0 = scalar,
+                                    2 = packed and the sums kept in packed lanes too */
   int32_t near_blocks_per_sm;    /* near field with kept lists: 0 = one block per 32 slots; k = 1..16:
                                     k blocks per SM loop over the slots, so that the far field's
                                     kernels, which run beside it, always find free SM slots */

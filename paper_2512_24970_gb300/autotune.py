@@ -96,11 +96,11 @@ def tune_skin(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
     return best, table, rejected
 
 
-RHO_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7)
+RHO_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
 RHO_BLOCKS_PER_SM = (1, 2, 3, 4)
 FAR_ATOMS = (1, 2, 4)
 FAR_SEGMENTS = (1, 2, 4, 8)
-FAR_PACKED = (1, 0)
+FAR_PACKED = (1, 0, 2)
 NEAR_BLOCKS_PER_SM = (1, 2, 3, 4, 6)
 
 

@@ -166,6 +166,7 @@ int run_force(rbsog_ctx *ctx, const View &v0, int mode, int step_off, bool energ
     rb::launch_near(v, st, step_off, energy);
   } else {
     if (v.build) rb::launch_build_lists(v, st);
+    rb::launch_sample_batch(v, st, step_off);
     rb::launch_near_kept(v, st, step_off, energy);
   }
   if (pr) CK(cudaEventRecordWithFlags(ctx->prof[7], st, evflag));
@@ -634,7 +635,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.nh, rb::NH_STATE)) || (rc = dalloc(ctx, &v.ke_part, (size_t)v.nh_nblk)) ||
       (rc = dalloc(ctx, &v.kin_part, 6 * (size_t)v.nh_nblk)) || (rc = dalloc(ctx, &v.kin, 6)) ||
       (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
-                (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
+                (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.bsel, NS * (size_t)P.P_R)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
     free_system(ctx);
     return rc;
   }
@@ -1202,7 +1203,7 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   if (!sched) return fail(ctx, RBSOG_E_INVAL, "null schedule");
   const rbsog_schedule q = *sched;
   const int A = q.far_atoms_per_thread, S = q.far_segments;
-  if (q.rho_variant < 0 || q.rho_variant > 7 || (q.far_packed != 0 && q.far_packed != 1) ||
+  if (q.rho_variant < 0 || q.rho_variant > 9 || q.far_packed < 0 || q.far_packed > 2 ||
       q.near_blocks_per_sm < 0 || q.near_blocks_per_sm > 16 ||
       (q.rho_tile_atoms != 0 && (q.rho_tile_atoms < 32 || q.rho_tile_atoms > 65536)) ||
       (q.near_wide != 0 && q.near_wide != 1) || q.rho_reduce < 0 || q.rho_reduce > 2 || q.rho_blocks_per_sm < 1 || q.rho_blocks_per_sm > 8 ||

@@ -315,6 +315,7 @@ int ensure_packed(rbsog_ensemble *e) {
     rb::pack_bin(q, st);
     if (kept) {
       rb::pack_build_lists(q, st);
+      rb::pack_sample_batch(q, st, 1);
       rb::pack_near_kept(q, st, 1);
     } else {
       rb::pack_near(q, st, 1);

@@ -100,7 +100,7 @@ constexpr int RHO_MCHUNK = 256;                  // atoms staged in shared memor
 constexpr int RHO_FLUSH = 64;
 constexpr int RHO_WARP_TILES = 160;  // tiles up to which the tile sums take a warp per mode
 constexpr int RHO_KTILE = RHO_BLOCK * RHO_KPT;    // modes per block row (512)
-template <int NP, int G, int MINB, bool PK>
+template <int NP, int G, int MINB, int PK>
 __device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
   constexpr int GT = RHO_BLOCK / NP;
   __shared__ uint4 sa[G][RHO_MCHUNK];
@@ -148,9 +148,14 @@ __device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
           const unsigned long long phi = half_turn_phi2(t0, t1);
           const unsigned long long z = mul2(phi, phi);
           const unsigned long long sn = sin_poly2(phi, z);
-          float z0, z1;
-          up2(z, z0, z1);
-          const unsigned long long cs = pk2(cos_poly(z0), cos_poly(z1));
+          unsigned long long cs;
+          if (PK == 2) {
+            cs = cos_poly2(z);
+          } else {
+            float z0, z1;
+            up2(z, z0, z1);
+            cs = pk2(cos_poly(z0), cos_poly(z1));
+          }
           const unsigned long long q2 = pk2(flip_by(q, t0), flip_by(q, t1));
           fr[j] = fma2(q2, cs, fr[j]);
           fi[j] = fma2(q2, sn, fi[j]);
@@ -203,11 +208,11 @@ __device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
       d[1] = im[t];
     }
 }
-template <int NP, int G, int MINB, bool PK>
+template <int NP, int G, int MINB, int PK>
 __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) k_rho_mixed(View p) {
   rho_mixed_body<NP, G, MINB, PK>(p, blockIdx.x);
 }
-template <int NP, int G, int MINB, bool PK>
+template <int NP, int G, int MINB, int PK>
 __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) kp_rho_mixed(Pack pk) {
   RB_PACK_PROLOGUE(pk);
   (void)nb;
@@ -216,10 +221,11 @@ __global__ void __launch_bounds__(G * (RHO_BLOCK / NP), MINB) kp_rho_mixed(Pack 
 
 // the structure factor's launch shapes (rbsog_schedule::rho_variant):
 // (pairs per thread, groups per block, blocks per SM of the register bound,
-// packed); variants 4..7 are 0..3 in scalar FP32
-constexpr int RHO_VARIANTS = 8;
-constexpr int RHO_VARIANT_NP[RHO_VARIANTS] = {1, 1, 2, 2, 1, 1, 2, 2};
-constexpr int RHO_VARIANT_G[RHO_VARIANTS] = {2, 1, 2, 4, 2, 1, 2, 4};
+// packed); variants 4..7 are 0..3 in scalar FP32, 8 and 9 are 0 and 1 with
+// the cosine packed as well
+constexpr int RHO_VARIANTS = 10;
+constexpr int RHO_VARIANT_NP[RHO_VARIANTS] = {1, 1, 2, 2, 1, 1, 2, 2, 1, 1};
+constexpr int RHO_VARIANT_G[RHO_VARIANTS] = {2, 1, 2, 4, 2, 1, 2, 4, 2, 1};
 
 // F^corr = (1/N) sum of the near-field warp partials, and U_N.  Block b sums
 // the fixed slice b of the partials (thread-strided, then a fixed tree); the
@@ -469,9 +475,11 @@ __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_fp64(View p) {
 // (far_S k segments) x (atom warps); a thread takes A atoms (lane + 32 a of
 // its atom warp's range) and every far_S-th pair of modes; the segments' FP32
 // sums are added in segment order in shared memory, per chunk of FAR_PCHUNK
-// pairs, and the chunks in FP64.  PK = false: the phase factors in scalar FP32
-// (bit for bit the same).
-template <int A, bool PK>
+// pairs, and the chunks in FP64.  PK = 0: the phase factors in scalar FP32
+// (bit for bit the same as PK = 1); PK = 2: also the accumulation in packed
+// lanes (one lane per mode of the pair, the lanes added at the end: another
+// order of the same FP32 terms).
+template <int A, int PK>
 __device__ __forceinline__ void farforce_mixed_body(const View &p, int bid) {
   __shared__ KPair sk[FAR_PCHUNK];
   __shared__ float sred[FORCE_BLOCK / 32 * A * 32 * 3];
@@ -501,8 +509,12 @@ __device__ __forceinline__ void farforce_mixed_body(const View &p, int bid) {
     }
     __syncthreads();
     float fx[A], fy[A], fz[A];
+    unsigned long long gx[A], gy[A], gz[A];
 #pragma unroll
-    for (int a = 0; a < A; a++) fx[a] = fy[a] = fz[a] = 0.0f;
+    for (int a = 0; a < A; a++) {
+      fx[a] = fy[a] = fz[a] = 0.0f;
+      gx[a] = gy[a] = gz[a] = 0ull;
+    }
 #pragma unroll 2
     for (int j = sg; j < cnt; j += S) {
       const int4 ra = sk[j].a, rb = sk[j].b;
@@ -523,11 +535,26 @@ __device__ __forceinline__ void farforce_mixed_body(const View &p, int bid) {
         }
         s0 = flip_by(s0, t0);
         s1 = flip_by(s1, t1);
-        fx[a] = __fmaf_rn(s1, kxy.y, __fmaf_rn(s0, kxy.x, fx[a]));
-        fy[a] = __fmaf_rn(s1, kxy.w, __fmaf_rn(s0, kxy.z, fy[a]));
-        fz[a] = __fmaf_rn(s1, kz.y, __fmaf_rn(s0, kz.x, fz[a]));
+        if (PK == 2) {                             // the two modes in two lanes, summed at the end
+          const unsigned long long s2 = pk2(s0, s1);
+          gx[a] = fma2(s2, pk2(kxy.x, kxy.y), gx[a]);
+          gy[a] = fma2(s2, pk2(kxy.z, kxy.w), gy[a]);
+          gz[a] = fma2(s2, pk2(kz.x, kz.y), gz[a]);
+        } else {
+          fx[a] = __fmaf_rn(s1, kxy.y, __fmaf_rn(s0, kxy.x, fx[a]));
+          fy[a] = __fmaf_rn(s1, kxy.w, __fmaf_rn(s0, kxy.z, fy[a]));
+          fz[a] = __fmaf_rn(s1, kz.y, __fmaf_rn(s0, kz.x, fz[a]));
+        }
       }
     }
+    if (PK == 2)
+#pragma unroll
+      for (int a = 0; a < A; a++) {
+        float u0, u1;
+        up2(gx[a], u0, u1); fx[a] = u0 + u1;
+        up2(gy[a], u0, u1); fy[a] = u0 + u1;
+        up2(gz[a], u0, u1); fz[a] = u0 + u1;
+      }
     if (S > 1) {                                  // the segments' sums, in segment order
       float *r = sred + ((aw * A) * 32 + lane) * 3;
       if (sg > 0)
@@ -559,11 +586,11 @@ __device__ __forceinline__ void farforce_mixed_body(const View &p, int bid) {
     p.FFf[i] = (float)(pre * ax[a]); p.FFf[n + i] = (float)(pre * ay[a]); p.FFf[2 * n + i] = (float)(pre * az[a]);
   }
 }
-template <int A, bool PK>
+template <int A, int PK>
 __global__ void __launch_bounds__(FORCE_BLOCK) k_farforce_mixed(View p) {
   farforce_mixed_body<A, PK>(p, blockIdx.x);
 }
-template <int A, bool PK>
+template <int A, int PK>
 __global__ void __launch_bounds__(FORCE_BLOCK) kp_farforce_mixed(Pack pk) {
   RB_PACK_PROLOGUE(pk);
   (void)nb;
@@ -638,14 +665,16 @@ void launch_rho(const View &v, cudaStream_t st) {
     const int var = v.rho_var;
     const int threads = RHO_VARIANT_G[var] * (RHO_BLOCK / RHO_VARIANT_NP[var]);
     switch (var) {
-      case 1: k_rho_mixed<1, 1, 2, true><<<g, threads, 0, st>>>(v); break;
-      case 2: k_rho_mixed<2, 2, 2, true><<<g, threads, 0, st>>>(v); break;
-      case 3: k_rho_mixed<2, 4, 1, true><<<g, threads, 0, st>>>(v); break;
-      case 4: k_rho_mixed<1, 2, 2, false><<<g, threads, 0, st>>>(v); break;
-      case 5: k_rho_mixed<1, 1, 2, false><<<g, threads, 0, st>>>(v); break;
-      case 6: k_rho_mixed<2, 2, 2, false><<<g, threads, 0, st>>>(v); break;
-      case 7: k_rho_mixed<2, 4, 1, false><<<g, threads, 0, st>>>(v); break;
-      default: k_rho_mixed<1, 2, 2, true><<<g, threads, 0, st>>>(v); break;
+      case 1: k_rho_mixed<1, 1, 2, 1><<<g, threads, 0, st>>>(v); break;
+      case 2: k_rho_mixed<2, 2, 2, 1><<<g, threads, 0, st>>>(v); break;
+      case 3: k_rho_mixed<2, 4, 1, 1><<<g, threads, 0, st>>>(v); break;
+      case 4: k_rho_mixed<1, 2, 2, 0><<<g, threads, 0, st>>>(v); break;
+      case 5: k_rho_mixed<1, 1, 2, 0><<<g, threads, 0, st>>>(v); break;
+      case 6: k_rho_mixed<2, 2, 2, 0><<<g, threads, 0, st>>>(v); break;
+      case 7: k_rho_mixed<2, 4, 1, 0><<<g, threads, 0, st>>>(v); break;
+      case 8: k_rho_mixed<1, 2, 2, 2><<<g, threads, 0, st>>>(v); break;
+      case 9: k_rho_mixed<1, 1, 2, 2><<<g, threads, 0, st>>>(v); break;
+      default: k_rho_mixed<1, 2, 2, 1><<<g, threads, 0, st>>>(v); break;
     }
   } else {
     k_rho_fp64<<<dim3(v.ntile, (v.P + RHO_KTILE - 1) / RHO_KTILE), RHO_BLOCK, 0, st>>>(v);
@@ -678,15 +707,16 @@ int far_atoms_per_block(const View &v) {
 void launch_farforce(const View &v, cudaStream_t st) {
   if (v.prec == RBSOG_MIXED) {
     const int g = (int)((v.n + far_atoms_per_block(v) - 1) / far_atoms_per_block(v));
-    if (v.far_packed) {
-      if (v.far_A == 1) k_farforce_mixed<1, true><<<g, FORCE_BLOCK, 0, st>>>(v);
-      else if (v.far_A == 2) k_farforce_mixed<2, true><<<g, FORCE_BLOCK, 0, st>>>(v);
-      else k_farforce_mixed<4, true><<<g, FORCE_BLOCK, 0, st>>>(v);
-    } else {
-      if (v.far_A == 1) k_farforce_mixed<1, false><<<g, FORCE_BLOCK, 0, st>>>(v);
-      else if (v.far_A == 2) k_farforce_mixed<2, false><<<g, FORCE_BLOCK, 0, st>>>(v);
-      else k_farforce_mixed<4, false><<<g, FORCE_BLOCK, 0, st>>>(v);
-    }
+#define RB_FAR(AA)                                                                   \
+  do {                                                                               \
+    if (v.far_packed == 2) k_farforce_mixed<AA, 2><<<g, FORCE_BLOCK, 0, st>>>(v);      \
+    else if (v.far_packed == 1) k_farforce_mixed<AA, 1><<<g, FORCE_BLOCK, 0, st>>>(v); \
+    else k_farforce_mixed<AA, 0><<<g, FORCE_BLOCK, 0, st>>>(v);                        \
+  } while (0)
+    if (v.far_A == 1) RB_FAR(1);
+    else if (v.far_A == 2) RB_FAR(2);
+    else RB_FAR(4);
+#undef RB_FAR
   } else {
     const int g = (int)((v.n + FORCE_BLOCK - 1) / FORCE_BLOCK);
     k_farforce_fp64<<<g, FORCE_BLOCK, 0, st>>>(v);
@@ -727,14 +757,16 @@ void pack_rho(const PackPlan &q, cudaStream_t st) {
   const int g = q.total[PK_RHO], threads = RHO_VARIANT_G[q.rho_var] * (RHO_BLOCK / RHO_VARIANT_NP[q.rho_var]);
   const Pack k = q.pack(PK_RHO);
   switch (q.rho_var) {
-    case 1: kp_rho_mixed<1, 1, 2, true><<<g, threads, 0, st>>>(k); break;
-    case 2: kp_rho_mixed<2, 2, 2, true><<<g, threads, 0, st>>>(k); break;
-    case 3: kp_rho_mixed<2, 4, 1, true><<<g, threads, 0, st>>>(k); break;
-    case 4: kp_rho_mixed<1, 2, 2, false><<<g, threads, 0, st>>>(k); break;
-    case 5: kp_rho_mixed<1, 1, 2, false><<<g, threads, 0, st>>>(k); break;
-    case 6: kp_rho_mixed<2, 2, 2, false><<<g, threads, 0, st>>>(k); break;
-    case 7: kp_rho_mixed<2, 4, 1, false><<<g, threads, 0, st>>>(k); break;
-    default: kp_rho_mixed<1, 2, 2, true><<<g, threads, 0, st>>>(k); break;
+    case 1: kp_rho_mixed<1, 1, 2, 1><<<g, threads, 0, st>>>(k); break;
+    case 2: kp_rho_mixed<2, 2, 2, 1><<<g, threads, 0, st>>>(k); break;
+    case 3: kp_rho_mixed<2, 4, 1, 1><<<g, threads, 0, st>>>(k); break;
+    case 4: kp_rho_mixed<1, 2, 2, 0><<<g, threads, 0, st>>>(k); break;
+    case 5: kp_rho_mixed<1, 1, 2, 0><<<g, threads, 0, st>>>(k); break;
+    case 6: kp_rho_mixed<2, 2, 2, 0><<<g, threads, 0, st>>>(k); break;
+    case 7: kp_rho_mixed<2, 4, 1, 0><<<g, threads, 0, st>>>(k); break;
+    case 8: kp_rho_mixed<1, 2, 2, 2><<<g, threads, 0, st>>>(k); break;
+    case 9: kp_rho_mixed<1, 1, 2, 2><<<g, threads, 0, st>>>(k); break;
+    default: kp_rho_mixed<1, 2, 2, 1><<<g, threads, 0, st>>>(k); break;
   }
 }
 void pack_rhosum(const PackPlan &q, cudaStream_t st) {
@@ -746,15 +778,16 @@ void pack_corr(const PackPlan &q, cudaStream_t st) {
 void pack_farforce(const PackPlan &q, cudaStream_t st) {
   const int g = q.total[PK_FAR];
   const Pack k = q.pack(PK_FAR);
-  if (q.far_packed) {
-    if (q.far_A == 1) kp_farforce_mixed<1, true><<<g, FORCE_BLOCK, 0, st>>>(k);
-    else if (q.far_A == 2) kp_farforce_mixed<2, true><<<g, FORCE_BLOCK, 0, st>>>(k);
-    else kp_farforce_mixed<4, true><<<g, FORCE_BLOCK, 0, st>>>(k);
-  } else {
-    if (q.far_A == 1) kp_farforce_mixed<1, false><<<g, FORCE_BLOCK, 0, st>>>(k);
-    else if (q.far_A == 2) kp_farforce_mixed<2, false><<<g, FORCE_BLOCK, 0, st>>>(k);
-    else kp_farforce_mixed<4, false><<<g, FORCE_BLOCK, 0, st>>>(k);
-  }
+#define RB_FARP(AA)                                                                   \
+  do {                                                                                \
+    if (q.far_packed == 2) kp_farforce_mixed<AA, 2><<<g, FORCE_BLOCK, 0, st>>>(k);      \
+    else if (q.far_packed == 1) kp_farforce_mixed<AA, 1><<<g, FORCE_BLOCK, 0, st>>>(k); \
+    else kp_farforce_mixed<AA, 0><<<g, FORCE_BLOCK, 0, st>>>(k);                        \
+  } while (0)
+  if (q.far_A == 1) RB_FARP(1);
+  else if (q.far_A == 2) RB_FARP(2);
+  else RB_FARP(4);
+#undef RB_FARP
 }
 void pack_finish(const PackPlan &q, cudaStream_t st) {
   kp_finish<<<q.total[PK_PREP], 3 * PREP_BLOCK, 0, st>>>(q.pack(PK_PREP));

@@ -892,41 +892,32 @@ __device__ __forceinline__ void add_pair_sh(const View &p, const float4 *spf4, c
 // benchmark: one pass with every lane busy).
 constexpr int KB = 5;
 
-template <typename R, bool ENERGY, bool WIDE, bool CAPPED>
-__device__ __forceinline__ void near_kept_body(const View &p, int step_off, int bid, int nbk) {
-  constexpr bool MIX = sizeof(R) == 4;
+// The shell batch of every slot with kept lists (Sec. 2.2, F*_shell): Floyd's
+// P_R of |B| from the slot's Philox words (the same draws and resolution as
+// floyd()), the drawn members' slots written to bsel[slot][r] in draw order.
+// The batch depends on the step, the caller id and the lists, not on the
+// positions, so it is drawn in a kernel of its own ahead of the pair sums.
+// Same block layout as the pair kernel: a warp per run of APW slots, TPA
+// threads per atom (the Philox words in parallel, the resolution by the
+// first); each thread then gathers its SB_LOADS drawn entries with all loads
+// in flight before any store (the list is read-only here).
+constexpr int SB_LOADS = 8;
+__device__ __forceinline__ void sample_batch_body(const View &p, int step_off, int bid) {
   __shared__ unsigned short stsel[APB][RBSOG_MAX_PR + 2];
   __shared__ uint32_t bmask[APB][RBSOG_MAX_KEPT / 32 + 1];
-  __shared__ float4 spf4[MIX ? 3 * RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
-  const PairD *spd = p.pd;
-  const float4 *sg4 = p.gtab;
-  const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int a = warp * APW + lane / TPA, g = lane % TPA;
-  if (MIX) {
-    const float4 *src = reinterpret_cast<const float4 *>(p.pf);
-    for (int e = tid; e < 3 * p.ns * p.ns; e += NEAR_BLOCK) spf4[e] = __ldg(src + e);
-  }
-  __syncthreads();                               // the pair table
   const long long s = *p.step + step_off;
   const int nslot = p.cell_start[p.ncell];
-  // one warp per run of APW slots; a grid smaller than nblk_near (a capped
-  // number of resident blocks) takes the runs in a grid-stride loop
-  for (int wc = bid * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += nbk * NEAR_WARPS) {
-  const int slot = wc * APW + lane / TPA;
-  const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
-  const bool active = ui.w != SU_PAD;
-  const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
-  const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
-  double part[NEAR_NPART] = {};
-  Acc<R> fa, fb;
-  // ---- Floyd's P_R of |B|: Philox words in parallel, resolved in order -----
-  const int nB = nab.y, PR = p.P_R;
+  const int slot = (bid * NEAR_WARPS + warp) * APW + lane / TPA;
+  const uint32_t w = slot < nslot ? p.su[slot].w : SU_PAD;
+  const bool active = w != SU_PAD;
+  const int nB = active ? p.nAB[slot].y : 0, PR = p.P_R;
   const bool sampled = active && !p.whole_shell && nB > PR;
   if (sampled) {
-    for (int w = g; w < ((nB + 31) >> 5); w += TPA) bmask[a][w] = 0u;
-    const uint32_t id = ui.w & SU_ID_MASK;
-    for (int d = g; 2 * d < PR; d += TPA) {     // Philox word d serves samples 2d, 2d + 1
+    for (int q = g; q < ((nB + 31) >> 5); q += TPA) bmask[a][q] = 0u;
+    const uint32_t id = w & SU_ID_MASK;
+    for (int d = g; 2 * d < PR; d += TPA) {     // Philox word d serves draws 2d, 2d + 1
       const uint4 w4 = draw(p.seed, s, id, 0u, (uint32_t)d);
       const unsigned long long U0 = ((unsigned long long)w4.y << 32) | w4.x;
       const unsigned long long U1 = ((unsigned long long)w4.w << 32) | w4.z;
@@ -947,16 +938,73 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
     }
   }
   __syncwarp();
+  if (sampled) {
+    const int *lb = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
+    int *out = p.bsel + (int64_t)slot * PR;
+    for (int k0 = g; k0 < PR; k0 += TPA * SB_LOADS) {
+      int e[SB_LOADS];
+#pragma unroll
+      for (int i = 0; i < SB_LOADS; i++) {
+        const int k = k0 + TPA * i;
+        e[i] = k < PR ? __ldg(lb + stsel[a][k]) : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < SB_LOADS; i++)
+        if (k0 + TPA * i < PR) out[k0 + TPA * i] = e[i];
+    }
+  }
+}
+__global__ void __launch_bounds__(NEAR_BLOCK) k_sample_batch(View p, int step_off) {
+  sample_batch_body(p, step_off, blockIdx.x);
+}
+__global__ void __launch_bounds__(NEAR_BLOCK) kp_sample_batch(Pack pk, int step_off) {
+  RB_PACK_PROLOGUE_REF(pk);
+  (void)nb;
+  sample_batch_body(sv, step_off, bid);
+}
+void launch_sample_batch(const View &v, cudaStream_t st, int step_off) {
+  k_sample_batch<<<v.nblk_near, NEAR_BLOCK, 0, st>>>(v, step_off);
+}
+
+template <typename R, bool ENERGY, bool WIDE, bool CAPPED>
+__device__ __forceinline__ void near_kept_body(const View &p, int step_off, int bid, int nbk) {
+  constexpr bool MIX = sizeof(R) == 4;
+  __shared__ float4 spf4[MIX ? 3 * RBSOG_MAX_SPECIES * RBSOG_MAX_SPECIES : 1];
+  const PairD *spd = p.pd;
+  const float4 *sg4 = p.gtab;
+  const double *swa = p.sog_wa, *sw = p.sog_w, *sh2 = p.sog_h;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane % TPA;
+  (void)step_off;                                // the batch of this step is drawn by k_sample_batch
+  if (MIX) {
+    const float4 *src = reinterpret_cast<const float4 *>(p.pf);
+    for (int e = tid; e < 3 * p.ns * p.ns; e += NEAR_BLOCK) spf4[e] = __ldg(src + e);
+  }
+  __syncthreads();                               // the pair table
+  const int nslot = p.cell_start[p.ncell];
+  // one warp per run of APW slots; a grid smaller than nblk_near (a capped
+  // number of resident blocks) takes the runs in a grid-stride loop
+  for (int wc = bid * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += nbk * NEAR_WARPS) {
+  const int slot = wc * APW + lane / TPA;
+  const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const bool active = ui.w != SU_PAD;
+  const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
+  const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
+  double part[NEAR_NPART] = {};
+  Acc<R> fa, fb;
+  // ---- the batch (drawn by k_sample_batch) or all of B ----------------------
+  const int nB = nab.y, PR = p.P_R;
+  const bool sampled = active && !p.whole_shell && nB > PR;
   // ---- the batch's list entries, loaded before A's pairs so that their
   // latency overlaps that work -----------------------------------------------
   const R wgt = sampled ? (R)nB / (R)PR : (R)1;
-  const int *lb = p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
+  const int *lb = sampled ? p.bsel + (int64_t)max(slot, 0) * PR : p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
   const int nb = sampled ? PR : nB;
   int jb[KB];
 #pragma unroll
   for (int i = 0; i < KB; i++) {
     const int k = g + TPA * i;
-    jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+    jb[i] = k < nb ? lb[k] : -1;
   }
   // ---- A, exactly, dealt round-robin over the atom's threads; the
   // indicator r < r_shell is 1 for every member of A when r_core + skin lies
@@ -994,7 +1042,7 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
 #pragma unroll
     for (int i = 0; i < KB; i++) {
       const int k = b_from + g + TPA * i;
-      jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+      jb[i] = k < nb ? lb[k] : -1;
     }
   }
   for (int e0 = a_from; e0 < nab.x; e0 += 4 * TPA) {
@@ -1027,13 +1075,12 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
 #pragma unroll
     for (int i = 0; i < KB; i++) {
       const int k = k0 + TPA * KB + g + TPA * i;
-      jb[i] = k < nb ? lb[sampled ? (int)stsel[a][k] : k] : -1;
+      jb[i] = k < nb ? lb[k] : -1;
     }
   }
   combine_atom<R, ENERGY>(p, fa, fb, wgt, active, g, ui, part);
   warp_partials<MIX, ENERGY ? NEAR_NPART : 4>(p, part, wc, lane);
   if (!CAPPED) break;                            // a warp per run: one pass
-  __syncwarp();                                  // stsel / bmask of this warp are reused
   }
 }
 
@@ -1184,6 +1231,9 @@ void pack_near(const PackPlan &q, cudaStream_t st, int step_off) {
 void pack_build_lists(const PackPlan &q, cudaStream_t st) {
   if (q.total[PK_NEAR_W0]) kp_near<false, true><<<q.total[PK_NEAR_W0], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W0), 0);
   if (q.total[PK_NEAR_W1]) kp_near<true, true><<<q.total[PK_NEAR_W1], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR_W1), 0);
+}
+void pack_sample_batch(const PackPlan &q, cudaStream_t st, int step_off) {
+  kp_sample_batch<<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);
 }
 void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off) {
   if (q.near_wide) kp_near_kept<true><<<q.total[PK_NEAR], NEAR_BLOCK, 0, st>>>(q.pack(PK_NEAR), step_off);

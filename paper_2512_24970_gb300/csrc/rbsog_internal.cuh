@@ -105,6 +105,7 @@ struct alignas(16) View {
   double half_skin2;      // (skin / 2)^2, shaded down: the displacement limit
   int *lA, *lB;           // [nslot][RBSOG_MAX_CORE], [nslot][RBSOG_MAX_KEPT] member slots
   int2 *nAB;              // [nslot] (|A|, |B|) of each slot
+  int *bsel;              // [nslot][P_R] this step's shell batch: the drawn members' slots, in draw order
   double *xb;             // [3][n] positions at the last build
   int nc[3], ncell, small;
   int wrap;               // near field reduces differences to the minimum image (short box)
@@ -161,7 +162,7 @@ struct alignas(16) View {
   KPair *kpair;           // [Pmax / 2 + 1] mixed far-force records, one per pair of modes
   int far_A, far_S;       // mixed far force: atoms per thread, k segments per block
   int rho_var;            // mixed structure factor: launch shape (rbsog_schedule::rho_variant)
-  int far_packed;         // mixed far force: two modes per FP32x2 instruction (else scalar FP32)
+  int far_packed;         // mixed far force: 0 scalar FP32, 1 packed phase factors, 2 packed accumulation too
   int near_bps;           // kept near field: resident blocks per SM (0: one block per 4 runs of slots)
   int near_wide;          // kept near field: a thread's first members of A and of the batch gathered at once
   int rho_reduce;         // tile sums: 0 auto, 1 a block per mode, 2 a warp per mode
@@ -383,6 +384,14 @@ __device__ __forceinline__ float sin_poly(float phi, float z) {
   const float ps = __fmaf_rn(__fmaf_rn(__fmaf_rn(SC_S9, z, SC_S7), z, SC_S5), z, SC_S3);
   return __fmaf_rn(ps * z, phi, phi);
 }
+// cos(phi) of sincos_turn's minimax polynomial, two lanes, z = phi^2
+__device__ __forceinline__ unsigned long long cos_poly2(unsigned long long z) {
+  const unsigned long long pc =
+      fma2(fma2(fma2(fma2(pk2(SC_C10, SC_C10), z, pk2(SC_C8, SC_C8)), z, pk2(SC_C6, SC_C6)), z,
+                pk2(SC_C4, SC_C4)),
+           z, pk2(SC_C2, SC_C2));
+  return fma2(pc, z, pk2(1.0f, 1.0f));
+}
 // cos(phi) of sincos_turn's minimax polynomial, one lane
 __device__ __forceinline__ float cos_poly(float z) {
   const float pc =
@@ -473,6 +482,7 @@ void launch_ksample(const View &v, cudaStream_t st, int step_off);
 void launch_bin(const View &v, cudaStream_t st);
 void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
 void launch_build_lists(const View &v, cudaStream_t st);
+void launch_sample_batch(const View &v, cudaStream_t st, int step_off);
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy);
 void launch_kept_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
                        int cap_a, int cap_b, int *A, int *nA, int *B, int *nB, int *batch, int *nbatch,
@@ -523,6 +533,7 @@ void pack_prepare(const PackPlan &q, cudaStream_t st, int mode, int step_off);
 void pack_bin(const PackPlan &q, cudaStream_t st);
 void pack_near(const PackPlan &q, cudaStream_t st, int step_off);
 void pack_build_lists(const PackPlan &q, cudaStream_t st);
+void pack_sample_batch(const PackPlan &q, cudaStream_t st, int step_off);
 void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off);
 void pack_corr(const PackPlan &q, cudaStream_t st);
 void pack_rho(const PackPlan &q, cudaStream_t st);

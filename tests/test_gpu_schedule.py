@@ -29,7 +29,8 @@ def rms_rel(a, b):
 SCHEDULES = [(0, 2, 2, 4, 1, 0, 0, 0, 0), (1, 1, 1, 1, 1, 0, 0, 0, 0), (1, 4, 4, 2, 0, 0, 0, 0, 0), (2, 2, 2, 8, 1, 0, 0, 0, 0),
              (3, 1, 1, 4, 0, 0, 0, 0, 0), (3, 3, 4, 8, 1, 0, 0, 0, 0), (2, 4, 1, 2, 1, 0, 0, 0, 0), (5, 3, 2, 4, 0, 0, 0, 0, 0),
              (7, 1, 4, 1, 0, 0, 0, 0, 0), (6, 2, 2, 2, 1, 0, 0, 0, 0), (0, 2, 2, 4, 1, 0, 64, 0, 0),
-             (1, 2, 2, 4, 1, 0, 1000, 0, 0), (0, 2, 2, 4, 1, 0, 0, 0, 1), (1, 4, 2, 4, 1, 0, 0, 0, 2)]
+             (1, 2, 2, 4, 1, 0, 1000, 0, 0), (0, 2, 2, 4, 1, 0, 0, 0, 1), (1, 4, 2, 4, 1, 0, 0, 0, 2),
+             (8, 2, 2, 4, 2, 0, 0, 0, 0), (9, 3, 1, 8, 2, 0, 0, 0, 0), (9, 1, 4, 2, 2, 0, 0, 0, 0)]
 
 
 @pytest.mark.parametrize("P_F", [500, 1301])       # one column of modes; three, the last ragged, odd P
@@ -90,8 +91,8 @@ def test_schedule_rejects(rb):
     w = W.rock_salt((5, 5, 5), seed=1)
     ctx = rb.Context(0)
     ctx.set_system(w.pos, w.species, w.charge, w.mass, w.bmh, w.box, rb.MethodParams())
-    for bad in [(8, 2, 2, 4, 1, 0, 0, 0, 0), (-1, 2, 2, 4, 1, 0, 0, 0), (0, 0, 2, 4, 1, 0, 0, 0, 0), (0, 9, 2, 4, 1, 0, 0, 0, 0),
-                (0, 2, 3, 4, 1, 0, 0, 0, 0), (0, 2, 2, 3, 1, 0, 0, 0, 0), (0, 2, 2, 16, 1, 0, 0, 0, 0), (0, 2, 2, 4, 2, 0, 0, 0, 0),
+    for bad in [(10, 2, 2, 4, 1, 0, 0, 0, 0), (0, 2, 2, 4, 3, 0, 0, 0, 0), (-1, 2, 2, 4, 1, 0, 0, 0), (0, 0, 2, 4, 1, 0, 0, 0, 0), (0, 9, 2, 4, 1, 0, 0, 0, 0),
+                (0, 2, 3, 4, 1, 0, 0, 0, 0), (0, 2, 2, 3, 1, 0, 0, 0, 0), (0, 2, 2, 16, 1, 0, 0, 0, 0),
                 (0, 2, 2, 4, 1, -1, 0, 0, 0), (0, 2, 2, 4, 1, 17, 0, 0, 0), (0, 2, 2, 4, 1, 0, 31, 0, 0),
                 (0, 2, 2, 4, 1, 0, 65537, 0, 0), (0, 2, 2, 4, 1, 0, 0, 2, 0), (0, 2, 2, 4, 1, 0, 0, 0, 3), (0, 2, 2, 4, 1, 0, 0, 0, -1)]:
         with pytest.raises(rb.RbsogError) as e:
@@ -108,5 +109,5 @@ def test_tune_schedule(rb):
     best, table = autotune.tune_schedule(w, prm, warmup=3, steps=10)
     assert best in [q for q, _ in table]
     assert all(t > 0 for _, t in table)
-    assert len(table) == 8 * 4 + 3 * 4 * 2 - 1 + 2 * 6 - 1 + 2
+    assert len(table) == 10 * 4 + 3 * 4 * 3 - 1 + 2 * 6 - 1 + 2
     assert min(t for _, t in table) == dict(table)[best]

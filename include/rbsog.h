@@ -353,6 +353,18 @@ int rbsog_debug_get_kept_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel,
                                int32_t cap_b, int32_t *A, int32_t *nA, int32_t *B, int32_t *nB,
                                int32_t *batch, int32_t *nbatch, double *weight);
 
+/* Kept lists: the shell batch the last force evaluation's pair sums read
+ * (drawn by the batch kernel from B, Sec. 2.2 F*_shell), batch [nsel][P_R]
+ * caller ids in draw order; rows of atoms that took all of B stay -1.
+ * Compare with rbsog_debug_get_kept_lists at the same step.  Host pointers. */
+int rbsog_debug_get_kept_batch_used(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t *batch);
+
+/* Kept lists store B also as 16-bit slot offsets (modulo the slot count),
+ * which the batch kernel reads when every offset of the last build fits.
+ * force_wide != 0 makes it read the 32-bit rows always (same batch);
+ * *fits (may be NULL) = 1 when the last build's offsets all fit 16 bits. */
+int rbsog_debug_kept_b16(rbsog_ctx *ctx, int force_wide, int32_t *fits);
+
 /* k-batch of the last force evaluation: m [P][3] int32, c [P] FP64 with
  * c_p = S/(P_F |k_p|^2) (or the weights set below).  Host pointers. */
 int rbsog_debug_get_kbatch(rbsog_ctx *ctx, int32_t *m, double *c);

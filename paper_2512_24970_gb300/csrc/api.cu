@@ -635,7 +635,8 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.nh, rb::NH_STATE)) || (rc = dalloc(ctx, &v.ke_part, (size_t)v.nh_nblk)) ||
       (rc = dalloc(ctx, &v.kin_part, 6 * (size_t)v.nh_nblk)) || (rc = dalloc(ctx, &v.kin, 6)) ||
       (kept && ((rc = dalloc(ctx, &v.lA, NS * RBSOG_MAX_CORE)) || (rc = dalloc(ctx, &v.lB, NS * RBSOG_MAX_KEPT)) ||
-                (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.bsel, NS * (size_t)P.P_R)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
+                (rc = dalloc(ctx, &v.nAB, NS)) || (rc = dalloc(ctx, &v.bsel, NS * (size_t)P.P_R)) ||
+                (rc = dalloc(ctx, &v.lB16, NS * RBSOG_MAX_KEPT)) || (rc = dalloc(ctx, &v.b16_over, 1)) || (rc = dalloc(ctx, &v.xb, 3 * N))))) {
     free_system(ctx);
     return rc;
   }
@@ -703,6 +704,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
   CK(cudaMemsetAsync(v.red, 0, sizeof(double) * 24, ctx->st));
   CK(cudaMemsetAsync(v.cell_count, 0, sizeof(int) * ((size_t)v.ncell + (size_t)v.nc[1] * v.nc[2]), ctx->st));
   CK(cudaMemsetAsync(v.corr_ticket, 0, sizeof(unsigned), ctx->st));
+  if (v.b16_over) CK(cudaMemsetAsync(v.b16_over, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(v.lflag, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(v.nh, 0, sizeof(double) * rb::NH_STATE, ctx->st));   // the chain at rest
   CK(cudaMemsetAsync(v.nbuild, 0, sizeof(unsigned long long), ctx->st));
@@ -1070,6 +1072,52 @@ int rbsog_debug_get_kept_lists(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel,
   CK(cudaStreamSynchronize(ctx->st));
   cudaFree(dsel); cudaFree(dA); cudaFree(dnA); cudaFree(dB); cudaFree(dnB);
   if (batch) { cudaFree(dbatch); cudaFree(dnb); cudaFree(dw); }
+  return leave(ctx);
+}
+
+int rbsog_debug_get_kept_batch_used(rbsog_ctx *ctx, const int64_t *sel, int64_t nsel, int32_t *batch) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "per-step lists in use (list_every = 0)");
+  if (!ctx->lists_valid) return fail(ctx, RBSOG_E_INVAL, "no force evaluation with kept lists yet");
+  if (!sel || nsel <= 0 || !batch) return fail(ctx, RBSOG_E_INVAL, "bad batch arguments");
+  for (int64_t q = 0; q < nsel; q++)
+    if (sel[q] < 0 || sel[q] >= ctx->n) return fail(ctx, RBSOG_E_INVAL, "selected atom out of range");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  const View &v = ctx->v;
+  const size_t k = (size_t)nsel;
+  long long *dsel;
+  int *db;
+  CK(cudaMalloc(&dsel, sizeof(long long) * k));
+  CK(cudaMalloc(&db, sizeof(int) * k * v.P_R));
+  CK(cudaMemsetAsync(db, 0xFF, sizeof(int) * k * v.P_R, ctx->st));
+  std::vector<long long> hs(sel, sel + k);
+  CK(cudaMemcpyAsync(dsel, hs.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, ctx->st));
+  rb::launch_kept_batch_used(v, ctx->st, dsel, (int)nsel, db);
+  if ((rc = check_launch(ctx))) return rc;
+  CK(cudaMemcpyAsync(batch, db, sizeof(int) * k * v.P_R, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  cudaFree(dsel); cudaFree(db);
+  return leave(ctx);
+}
+
+int rbsog_debug_kept_b16(rbsog_ctx *ctx, int force_wide, int32_t *fits) {
+  if (!ctx) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (!ctx->v.kept) return fail(ctx, RBSOG_E_INVAL, "per-step lists in use (list_every = 0)");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  if (ctx->v.kept_wide != (force_wide != 0)) {
+    ctx->v.kept_wide = force_wide != 0;
+    ctx->graph_ok = false;                      // the step graph holds the view by value
+  }
+  if (fits) {
+    int h = 1;
+    CK(cudaMemcpyAsync(&h, ctx->v.b16_over, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *fits = h == 0;
+  }
   return leave(ctx);
 }
 

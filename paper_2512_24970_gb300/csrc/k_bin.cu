@@ -217,6 +217,7 @@ __device__ __forceinline__ void rowscan_body(const View &p) {
   __shared__ int wsum[32];
   if (skip_binning(p)) return;
   const int nt = blockDim.x, t = threadIdx.x;
+  if (t == 0 && p.b16_over) *p.b16_over = 0;     // a kept-list build follows: its own 16-bit check
   const int nrow = p.nc[1] * p.nc[2];
   const int per = (nrow + nt - 1) / nt;
   const int rb = min(t * per, nrow), re = min(rb + per, nrow);

@@ -639,6 +639,9 @@ __device__ __forceinline__ void near_body(const View &p, int step_off, int bid, 
         }
         int *dA = p.lA + (int64_t)slot * RBSOG_MAX_CORE;
         int *dB = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
+        unsigned short *dB16 = p.lB16 + (int64_t)slot * RBSOG_MAX_KEPT;
+        const int M = p.cell_start[p.ncell];
+        bool fits = true;
         for (int r = g; r < nr; r += TPA) {
           const int ng = rgo[warp][r + 1] - rgo[warp][r];
           const int4 sg = rseg[warp][r];
@@ -656,7 +659,11 @@ __device__ __forceinline__ void near_body(const View &p, int step_off, int bid, 
             while (sm) {
               const int b = __ffs(sm) - 1;
               sm &= sm - 1u;
-              dB[accB++] = row_slot(sg, 16 * w + 4 * (b >> 3) + (b & 3));
+              const int j = row_slot(sg, 16 * w + 4 * (b >> 3) + (b & 3));
+              unsigned short e;
+              fits &= kept_b16_encode(j, slot, M, e);
+              dB16[accB] = e;
+              dB[accB++] = j;
             }
           }
           for (int q = r + 1; q < min(r + TPA, nr); q++) {
@@ -664,6 +671,7 @@ __device__ __forceinline__ void near_body(const View &p, int step_off, int bid, 
             accA += ccnt[a][q];
           }
         }
+        if (!fits) atomicOr(p.b16_over, 1);
       }
       if (active && g == 0) p.nAB[slot] = ok ? make_int2(na, nb) : make_int2(0, 0);
       return;
@@ -914,6 +922,7 @@ __device__ __forceinline__ void sample_batch_body(const View &p, int step_off, i
   const bool active = w != SU_PAD;
   const int nB = active ? p.nAB[slot].y : 0, PR = p.P_R;
   const bool sampled = active && !p.whole_shell && nB > PR;
+  const bool b16 = !p.kept_wide && *p.b16_over == 0;   // every offset of the last build fits 16 bits
   if (sampled) {
     for (int q = g; q < ((nB + 31) >> 5); q += TPA) bmask[a][q] = 0u;
     const uint32_t id = w & SU_ID_MASK;
@@ -939,18 +948,33 @@ __device__ __forceinline__ void sample_batch_body(const View &p, int step_off, i
   }
   __syncwarp();
   if (sampled) {
-    const int *lb = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
     int *out = p.bsel + (int64_t)slot * PR;
-    for (int k0 = g; k0 < PR; k0 += TPA * SB_LOADS) {
-      int e[SB_LOADS];
+    if (b16) {                                   // half the bytes of B's row per draw
+      const unsigned short *lb = p.lB16 + (int64_t)slot * RBSOG_MAX_KEPT;
+      for (int k0 = g; k0 < PR; k0 += TPA * SB_LOADS) {
+        unsigned short e[SB_LOADS];
 #pragma unroll
-      for (int i = 0; i < SB_LOADS; i++) {
-        const int k = k0 + TPA * i;
-        e[i] = k < PR ? __ldg(lb + stsel[a][k]) : 0;
+        for (int i = 0; i < SB_LOADS; i++) {
+          const int k = k0 + TPA * i;
+          e[i] = k < PR ? __ldg(lb + stsel[a][k]) : (unsigned short)0;
+        }
+#pragma unroll
+        for (int i = 0; i < SB_LOADS; i++)
+          if (k0 + TPA * i < PR) out[k0 + TPA * i] = kept_b16_decode(e[i], slot, nslot);
       }
+    } else {
+      const int *lb = p.lB + (int64_t)slot * RBSOG_MAX_KEPT;
+      for (int k0 = g; k0 < PR; k0 += TPA * SB_LOADS) {
+        int e[SB_LOADS];
 #pragma unroll
-      for (int i = 0; i < SB_LOADS; i++)
-        if (k0 + TPA * i < PR) out[k0 + TPA * i] = e[i];
+        for (int i = 0; i < SB_LOADS; i++) {
+          const int k = k0 + TPA * i;
+          e[i] = k < PR ? __ldg(lb + stsel[a][k]) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < SB_LOADS; i++)
+          if (k0 + TPA * i < PR) out[k0 + TPA * i] = e[i];
+      }
     }
   }
 }
@@ -1140,6 +1164,21 @@ __global__ void k_kept_lists(View p, int step_off, const long long *sel, int nse
     nbatch[q] = m;
     weight[q] = take_all ? 1.0 : (double)nab.y / (double)p.P_R;
   }
+}
+
+// Parity hook: the batch the last evaluation's pair sums read (bsel) of
+// selected atoms, as caller ids; -1 rows for atoms that took all of B.
+__global__ void k_kept_batch_used(View p, const long long *sel, int nsel, int *batch) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsel) return;
+  const int slot = p.slot_of[sel[q]];
+  const int nB = p.nAB[slot].y, PR = p.P_R;
+  if (p.whole_shell || nB <= PR) return;
+  for (int r = 0; r < PR; r++) batch[(long long)q * PR + r] = p.perm[p.bsel[(int64_t)slot * PR + r]];
+}
+void launch_kept_batch_used(const View &v, cudaStream_t st, const long long *sel, int nsel, int *batch) {
+  const int b = 64, g = (nsel + b - 1) / b;
+  k_kept_batch_used<<<g, b, 0, st>>>(v, sel, nsel, batch);
 }
 
 void launch_kept_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,

@@ -106,6 +106,9 @@ struct alignas(16) View {
   int *lA, *lB;           // [nslot][RBSOG_MAX_CORE], [nslot][RBSOG_MAX_KEPT] member slots
   int2 *nAB;              // [nslot] (|A|, |B|) of each slot
   int *bsel;              // [nslot][P_R] this step's shell batch: the drawn members' slots, in draw order
+  unsigned short *lB16;   // [nslot][RBSOG_MAX_KEPT] B again, as 16-bit slot offsets (see kept_b16_encode)
+  int *b16_over;          // [1] set by a build when some offset of B does not fit 16 bits (then lB is read)
+  int kept_wide;          // read the 32-bit rows lB whatever the build found (parity hook)
   double *xb;             // [3][n] positions at the last build
   int nc[3], ncell, small;
   int wrap;               // near field reduces differences to the minimum image (short box)
@@ -309,6 +312,25 @@ __device__ __forceinline__ float pred_r2(float dx, float dy, float dz, const flo
   return r2;
 }
 
+// 16-bit form of a kept-list member: the slot offset j - i reduced modulo the
+// slot count M into [-M/2, M/2).  Slots run cell by cell with z slowest, so
+// the members of a list (within r_shell + skin, across periodic faces too)
+// lie within a few layers of cells of the atom's own slot in this cyclic
+// order.  Returns false when the offset needs more than 16 bits.
+__device__ __forceinline__ bool kept_b16_encode(int j, int i, int M, unsigned short &e) {
+  int d = j - i;
+  if (2 * d >= M) d -= M;
+  else if (2 * d < -M) d += M;
+  e = (unsigned short)d;
+  return d >= -32768 && d <= 32767;
+}
+__device__ __forceinline__ int kept_b16_decode(unsigned short e, int i, int M) {
+  int j = i + (int)(short)e;
+  if (j < 0) j += M;
+  else if (j >= M) j -= M;
+  return j;
+}
+
 // Packed FP32x2 arithmetic (two IEEE binary32 operations per instruction,
 // round to nearest, no contraction): same results as the scalar forms.
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
@@ -484,6 +506,7 @@ void launch_near(const View &v, cudaStream_t st, int step_off, bool energy);
 void launch_build_lists(const View &v, cudaStream_t st);
 void launch_sample_batch(const View &v, cudaStream_t st, int step_off);
 void launch_near_kept(const View &v, cudaStream_t st, int step_off, bool energy);
+void launch_kept_batch_used(const View &v, cudaStream_t st, const long long *sel, int nsel, int *batch);
 void launch_kept_lists(const View &v, cudaStream_t st, int step_off, const long long *sel, int nsel,
                        int cap_a, int cap_b, int *A, int *nA, int *B, int *nB, int *batch, int *nbatch,
                        double *weight);

@@ -39,7 +39,7 @@ EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor",
-    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_move_atoms", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_move_atoms", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kept_batch_used", "rbsog_debug_kept_b16", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -161,6 +161,8 @@ def load():
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
     L.rbsog_debug_get_kept_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
+    L.rbsog_debug_get_kept_batch_used.argtypes = [P, P, I64, P]
+    L.rbsog_debug_kept_b16.argtypes = [P, I32, P]
     L.rbsog_debug_get_kbatch.argtypes = [P, P, P]
     L.rbsog_debug_set_kbatch.argtypes = [P, I32, P, P]
     L.rbsog_debug_get_parts.argtypes = [P, P, P, P, P]
@@ -450,6 +452,20 @@ class Context:
         if batch:
             out.update(batch=bt, nbatch=nb, weight=wt)
         return out
+
+    def debug_kept_batch_used(self, sel):
+        """The shell batch the last evaluation's pair sums read (caller ids, draw order; -1 rows: all of B)."""
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        bt = np.full((sel.size, self.params.P_R), -1, dtype=np.int32)
+        self._ck(self._L.rbsog_debug_get_kept_batch_used(self.h, _np_ptr(sel), sel.size, _np_ptr(bt)))
+        return bt
+
+    def debug_kept_b16(self, force_wide=False):
+        """Read B's 32-bit rows always (force_wide) or the 16-bit ones where they fit; returns
+        whether the last build's offsets all fit 16 bits."""
+        f = np.zeros(1, dtype=np.int32)
+        self._ck(self._L.rbsog_debug_kept_b16(self.h, 1 if force_wide else 0, _np_ptr(f)))
+        return bool(f[0])
 
     def debug_kbatch(self, P=None):
         P = self.params.P_F if P is None else P

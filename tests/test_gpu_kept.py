@@ -62,6 +62,37 @@ def test_kept_lists_and_batches_bitexact(rb, orc, case):
     o = S.lists_skin(sel, cap_a=64, cap_b=512)
     for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    check_batch_used(ctx, sel, o, 20)
+
+
+def check_batch_used(ctx, sel, o, P_R):
+    """The batch the pair sums read (drawn by the batch kernel, from the 16-bit
+    or the 32-bit rows of B, kept in draw order) holds the oracle's batch (in
+    list order); -1 where all of B is taken."""
+    used = ctx.debug_kept_batch_used(sel)
+    drawn = o["nB"] > P_R
+    np.testing.assert_array_equal(np.sort(used[drawn], axis=1), np.sort(o["batch"][drawn], axis=1))
+    assert (used[~drawn] == -1).all()
+
+
+def test_kept_b16_and_wide_rows_agree(rb, orc):
+    """B read as 16-bit slot offsets (every offset of the build fits) or as
+    the 32-bit rows: the same batches and forces bit for bit, in both
+    precisions, through builds."""
+    w = W.rock_salt((9, 8, 7), seed=23, composition="LiCl-NaCl")
+    for prec in (rb.MIXED, rb.FP64):
+        out = []
+        for wide in (False, True):
+            ctx, S = setup_kept(rb, orc, w, list_every=-1, skin=1.0, precision=prec)
+            assert ctx.debug_kept_b16(force_wide=wide)
+            ctx.set_velocities(W.maxwell_boltzmann(w, 1200.0))
+            ctx.step(6)
+            F = ctx.compute_forces()
+            sel = np.arange(0, w.n, 7)
+            out.append((F, ctx.get_state()[0], ctx.debug_kept_batch_used(sel)))
+            assert ctx.debug_kept_b16(force_wide=wide)      # this small box: every offset fits
+        for a, b in zip(out[0], out[1]):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_kept_skin_zero_is_per_step_path(rb, orc):
@@ -135,11 +166,12 @@ def test_kept_skin_exceeded_is_reported(rb, orc):
     assert e.value.code == -3
 
 
-@pytest.mark.parametrize("key", ["nacl_64k", "liclnacl_216k"])
+@pytest.mark.parametrize("key", ["nacl_64k", "liclnacl_216k", "nacl_1m"])
 def test_kept_full_size_sampled(rb, orc, key):
     """Full-size workloads with kept lists (skin 1 A, rebuilt every 10 steps):
     lists and batches of sampled atoms bit-exact at the build and five steps
-    later; mixed near field of the sample within 1e-5 of the oracle's."""
+    later, and the batches the pair sums read; mixed near field of the sample
+    within 1e-5 of the oracle's.  At N = 64,000 B's 16-bit rows are in use."""
     w, cfg = W.make(key)
     ctx, S = setup_kept(rb, orc, w, list_every=10, P_R=cfg.P_R, P_F=cfg.P_F, precision=rb.MIXED, seed=cfg.seed,
                         step=3)
@@ -150,6 +182,9 @@ def test_kept_full_size_sampled(rb, orc, key):
     o = S.lists_skin(sel, cap_a=64, cap_b=512)
     for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    check_batch_used(ctx, sel, o, cfg.P_R)
+    if key == "nacl_64k":
+        assert ctx.debug_kept_b16()
     ctx.step(5)
     pos, _, step = ctx.get_state()
     assert step == 8
@@ -159,6 +194,7 @@ def test_kept_full_size_sampled(rb, orc, key):
     o = S.lists_skin(sel, cap_a=64, cap_b=512)
     for k in ("nA", "nB", "A", "B", "nbatch", "batch", "weight"):
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    check_batch_used(ctx, sel, o, cfg.P_R)     # the step's evaluation drew for step 8
     assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL
 
 

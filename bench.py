@@ -137,17 +137,17 @@ def dist_env():
 
 
 # kernels of one MD step: main branch k_prepare, k_rowscan, k_cellstart, k_scatter, k_rank,
-# k_near, k_corr (F^corr), k_finish; side branch k_ksample, k_rho, k_reduce (rho), k_farforce
-# (the histogram clear is a memset node)
-KERNELS_PER_STEP = 12
+# k_near, k_finish (F^corr from the near field's fixed-point totals); side branch k_ksample,
+# k_rho, k_reduce (rho), k_farforce (the histogram clear is a memset node)
+KERNELS_PER_STEP = 11
 # kept lists: the near field is the batch draw (k_sample_batch) and the pair
 # sums (k_near_kept); a build step adds the list build to the per-step graph;
 # a step that reuses the lists has no binning (4 kernels) and no build
-KERNELS_BUILD_STEP = 14
-KERNELS_KEEP_STEP = 9
+KERNELS_BUILD_STEP = 13
+KERNELS_KEEP_STEP = 8
 # automatic kept lists: every step's graph holds the binning and build
 # kernels (they return at once unless the step rebuilds)
-KERNELS_AUTO_STEP = 14
+KERNELS_AUTO_STEP = 13
 KERNEL_LABEL = {"near": "k_near", "rho": "k_rho", "farforce": "k_farforce"}
 
 

@@ -619,7 +619,7 @@ int rbsog_set_system(rbsog_ctx *ctx, int64_t n, const double *pos, const int32_t
       (rc = dalloc(ctx, &v.row_chunk, (size_t)v.nc[1] * v.nc[2] + 1)) ||
       (rc = dalloc(ctx, &v.chunk_info, (size_t)v.nblk_near * rb::NEAR_WARPS)) || (rc = dalloc(ctx, &v.sx, NS)) ||
       (rc = dalloc(ctx, &v.sy, NS)) || (rc = dalloc(ctx, &v.sz, NS)) || (rc = dalloc(ctx, &v.su, NS)) || (rc = dalloc(ctx, &v.near_part, (size_t)rb::NEAR_NPART * v.nblk_near * rb::NEAR_WARPS)) ||
-      (rc = dalloc(ctx, &v.corr_part, (size_t)rb::NEAR_NPART * 64)) || (rc = dalloc(ctx, &v.corr_ticket, 1)) ||
+      (rc = dalloc(ctx, &v.corr_part, (size_t)rb::NEAR_NPART * 64)) || (rc = dalloc(ctx, &v.corr_ticket, 1)) || (rc = dalloc(ctx, &v.corr_acc, 16 * (size_t)rb::CORR_COPIES)) ||
       (rc = dalloc(ctx, &v.red, 24)) || (rc = dalloc(ctx, &v.err, 1)) || (rc = dalloc(ctx, &v.step, 1)) ||
       (rc = dalloc(ctx, &pf, (size_t)n_species * n_species)) || (rc = dalloc(ctx, &pd, (size_t)n_species * n_species)) ||
       (rc = dalloc(ctx, &wa, (size_t)v.G)) || (rc = dalloc(ctx, &w, (size_t)v.G)) || (rc = dalloc(ctx, &h2, (size_t)v.G)) ||

@@ -320,7 +320,6 @@ int ensure_packed(rbsog_ensemble *e) {
     } else {
       rb::pack_near(q, st, 1);
     }
-    rb::pack_corr(q, st);
     cudaStreamWaitEvent(st, b.join, 0);
     rb::pack_finish(q, st);
     cudaEventRecord(b.done, st);

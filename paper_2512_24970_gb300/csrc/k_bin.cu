@@ -117,6 +117,11 @@ __device__ __forceinline__ void prepare_body(const View &p, int step_off, int bi
   // Nose-Hoover: the opening half step of the chain, every block alike
   const double s_open = (MODE == 1 && p.integ == RBSOG_NOSE_HOOVER) ? nh_open(p) : 1.0;
   const bool act = i < n;
+  // the fixed-point F_N totals of this evaluation start at zero (the near
+  // field adds to them after this kernel; k_finish of the last evaluation
+  // has read them)
+  if (bid == 0 && threadIdx.x < 3 * CORR_COPIES && p.npart == 4)
+    p.corr_acc[16 * (threadIdx.x / 3) + threadIdx.x % 3] = 0ull;
   const bool keep_check = p.kept && (p.auto_lists || !p.build);   // displacement since the last build
   if (act) {
     const int sp = p.spc[i];

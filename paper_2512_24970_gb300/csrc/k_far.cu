@@ -282,11 +282,6 @@ __device__ __forceinline__ void corr_body(const View &p, int blk) {
 }
 template <int NV>
 __global__ void __launch_bounds__(256) k_corr(View p) { corr_body<NV>(p, blockIdx.x); }
-__global__ void __launch_bounds__(256) kp_corr(Pack pk) {
-  RB_PACK_PROLOGUE_REF(pk);
-  (void)nb;
-  corr_body<4>(sv, bid);
-}
 
 // The per-k outputs of the tile sums (sr0, si0) = rho(k_p): rho, the force
 // record (FP64: c Im rho, c Re rho; mixed: the KPair half of mode k), c |rho|^2
@@ -606,10 +601,27 @@ template <typename R, int MODE>
 __device__ __forceinline__ void finish_body(const View &p, int bid) {
   constexpr bool MIX = sizeof(R) == 4;
   __shared__ double sv3[3][PREP_BLOCK];
+  __shared__ double fcorr[3];
   const int c = threadIdx.x / PREP_BLOCK, li = threadIdx.x % PREP_BLOCK;
   const int64_t i = (int64_t)bid * PREP_BLOCK + li;
   const int64_t n = p.n;
   const bool first = bid == 0 && threadIdx.x == 0;
+  // F^corr = (1/N) sum F_N: from the fixed-point totals in force-only
+  // evaluations (block 0 also files it where k_corr would), else from k_corr
+  if (threadIdx.x < 3) {
+    const int t = threadIdx.x;
+    double fc;
+    if (p.npart == 4) {
+      unsigned long long sum = 0ull;             // integer: any order gives the same total
+      for (int k = 0; k < CORR_COPIES; k++) sum += p.corr_acc[16 * k + t];
+      fc = (double)(long long)sum * (1.0 / CORR_FIX) / (double)n;
+      if (bid == 0) p.red[t] = fc;
+    } else {
+      fc = p.red[t];
+    }
+    fcorr[t] = fc;
+  }
+  __syncthreads();
   // the step counter advances here, after both branches joined: every kernel
   // of the step that reads it (k-batch, noise, shell batch) has finished
   if (MODE != 0 && first) *p.step += 1;
@@ -618,7 +630,7 @@ __device__ __forceinline__ void finish_body(const View &p, int bid) {
   if (act) {
     const double fn = MIX ? (double)p.FNf[c * n + i] : p.FNd[c * n + i];
     const double ff = MIX ? (double)p.FFf[c * n + i] : p.FFd[c * n + i];
-    const double F = fn - p.red[c] + ff;
+    const double F = fn - fcorr[c] + ff;
     if (MIX) p.Ff[c * n + i] = (float)F;
     else p.Fd[c * n + i] = F;
     if (MODE != 0) {
@@ -694,10 +706,11 @@ void launch_rhosum(const View &v, cudaStream_t st, bool energy) {
   if (energy) k_energy<<<1, 32, 0, st>>>(v);
 }
 
+// Energy evaluations only: force-only evaluations take F^corr from the
+// fixed-point totals in k_finish.
 void launch_corr(const View &v, cudaStream_t st, int step_off) {
   (void)step_off;
   if (v.npart == NEAR_NPART) k_corr<NEAR_NPART><<<CORR_BLOCKS, 256, 0, st>>>(v);
-  else k_corr<4><<<CORR_BLOCKS, 256, 0, st>>>(v);
 }
 
 int far_atoms_per_block(const View &v) {
@@ -744,7 +757,6 @@ int pack_blocks(const View &v, int kind) {
     case PK_NEAR: return v.nblk_near;
     case PK_NEAR_W0: return v.wrap ? 0 : v.nblk_near;
     case PK_NEAR_W1: return v.wrap ? v.nblk_near : 0;
-    case PK_CORR: return CORR_BLOCKS;
     case PK_RHO: return v.ntile * ((v.P + RHO_KTILE - 1) / RHO_KTILE);
     case PK_REDUCE: return (std::max(1, v.P) + 7) / 8;
     case PK_FAR: return (int)((v.n + far_atoms_per_block(v) - 1) / far_atoms_per_block(v));
@@ -771,9 +783,6 @@ void pack_rho(const PackPlan &q, cudaStream_t st) {
 }
 void pack_rhosum(const PackPlan &q, cudaStream_t st) {
   kp_reduce<<<q.total[PK_REDUCE], 256, 0, st>>>(q.pack(PK_REDUCE));
-}
-void pack_corr(const PackPlan &q, cudaStream_t st) {
-  kp_corr<<<q.total[PK_CORR], 256, 0, st>>>(q.pack(PK_CORR));
 }
 void pack_farforce(const PackPlan &q, cudaStream_t st) {
   const int g = q.total[PK_FAR];

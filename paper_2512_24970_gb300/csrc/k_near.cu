@@ -292,9 +292,29 @@ __device__ __forceinline__ void pred_r2_x4_packed(const float *sx, const float *
 }
 
 // One partial per warp of sum F_N and of the pair energy (FP32 sums of the
-// warp's eight atoms in mixed precision, FP64 otherwise).
+// warp's eight atoms in mixed precision, FP64 otherwise).  Force-only
+// evaluations (NP = 4) add the F_N sum to the fixed-point totals instead
+// (CORR_FIX); energy evaluations write every partial for k_corr.
 template <bool MIX, int NP>
 __device__ __forceinline__ void warp_partials(const View &p, double part[NEAR_NPART], int wchunk, int lane) {
+  if constexpr (NP == 4) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      if (MIX) {
+        float f = (float)part[c];
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+        part[c] = (double)f;
+      } else {
+        for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_down_sync(0xffffffffu, part[c], o);
+      }
+    }
+    if (lane == 0) {
+      unsigned long long *acc = p.corr_acc + 16 * (wchunk % CORR_COPIES);
+#pragma unroll
+      for (int c = 0; c < 3; c++) atomicAdd(acc + c, (unsigned long long)__double2ll_rn(part[c] * CORR_FIX));
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < NP; c++) {
     if (MIX) {

@@ -21,6 +21,16 @@ constexpr int PREP_BLOCK = 128;    // threads per block of k_prepare and k_finis
 constexpr int NEAR_BLOCK = 128;    // threads per block of the near-field kernel
 constexpr int NEAR_CHUNK = 8;      // atoms per warp of the near-field kernel (4 threads each)
 constexpr int NEAR_WARPS = 4;      // warps per near-field block
+// Force-only evaluations sum F_N over all atoms (for F^corr) as 64-bit
+// integers in units of 2^-40: integer addition does not depend on the order
+// in which the warps add, so one atomic add per warp keeps the result
+// reproducible bit for bit without a reduction pass.  Each warp's FP64
+// partial is rounded once (2^-41 at most); the total must stay below 2^23
+// in magnitude (it is a sum of random-batch noise, of order sqrt(N) |F|).
+constexpr double CORR_FIX = 1099511627776.0;          // 2^40
+// Warp w adds to copy w % CORR_COPIES (its own cache line), so that no
+// single address takes every warp's atomic; k_finish adds the copies.
+constexpr int CORR_COPIES = 32;
 constexpr int NEAR_NPART = 10;     // per-warp partials: sum F_N (3), U_N, pair virial (6)
 constexpr int RHO_BLOCK = 256;     // threads per block of the FP64 structure-factor kernel
 constexpr int RHO_KPT = 2;         // k-vectors per thread in the structure-factor kernels
@@ -151,6 +161,8 @@ struct alignas(16) View {
   uint4 *su;              // [nslot] (u_x, u_y, u_z, caller id | species << SU_SP_SHIFT)
   int nslot;              // n + 3 * ncell
   double *near_part;      // [nblk_near * NEAR_WARPS][npart]: sum F_N (x,y,z), pair energy, pair virial (6)
+  unsigned long long *corr_acc;  // [CORR_COPIES][16] force-only evaluations: sum F_N (x, y, z) in units
+                                 // of 2^-40 (two's complement), one 128-byte line per copy
   int npart;              // partials per warp: 4, or NEAR_NPART in energy evaluations
   int want_vir;           // energy evaluation: also the far-field virial terms
   double *vf;             // [Pmax] c_p (Fhat'/Fhat)(k_p^2) |rho_p|^2 (energy evaluations)
@@ -534,7 +546,6 @@ enum PackKind {
   PK_NEAR,      // near-field warps over runs of slots (kept lists)
   PK_NEAR_W0,   // the list walk of replicas without minimum-image wrapping (others: no blocks)
   PK_NEAR_W1,   // ... with it
-  PK_CORR,      // F^corr reduction
   PK_RHO,       // structure-factor tiles x columns of modes
   PK_REDUCE,    // one block per mode
   PK_FAR,       // far-force blocks
@@ -558,7 +569,6 @@ void pack_near(const PackPlan &q, cudaStream_t st, int step_off);
 void pack_build_lists(const PackPlan &q, cudaStream_t st);
 void pack_sample_batch(const PackPlan &q, cudaStream_t st, int step_off);
 void pack_near_kept(const PackPlan &q, cudaStream_t st, int step_off);
-void pack_corr(const PackPlan &q, cudaStream_t st);
 void pack_rho(const PackPlan &q, cudaStream_t st);
 void pack_rhosum(const PackPlan &q, cudaStream_t st);
 void pack_farforce(const PackPlan &q, cudaStream_t st);

@@ -92,11 +92,12 @@ __global__ void __launch_bounds__(RHO_BLOCK) k_rho_fp64(View p) {
 // same operations per lane in scalar FP32 instructions (bit for bit the same
 // results; it leaves the FMA pipe's two halves to be filled independently).
 constexpr int RHO_MCHUNK = 256;                  // atoms staged in shared memory per group and round
-// FP32 partial sums run over at most RHO_FLUSH atoms before they are added in
-// FP64: on lattice-like configurations the sums over one sublattice are
-// coherent (of order the number of atoms) while rho is small, so the FP32
-// rounding of a partial sum grows with its length; 64 atoms keep it near
-// 64 * 2^-24 of the largest partial
+// FP32 partial sums run over at most RHO_FLUSH atoms before they are added
+// exactly (TwoSum into an FP32 pair): on lattice-like configurations the sums
+// over one sublattice are coherent (of order the number of atoms) while rho
+// is small, so the FP32 rounding of a partial sum grows with its length; 64
+// atoms keep it near 64 * 2^-24 of the largest partial.  (FP64 adds of the
+// partials cost the FP64 pipe, which is narrow on this part.)
 constexpr int RHO_FLUSH = 64;
 constexpr int RHO_WARP_TILES = 160;  // tiles up to which the tile sums take a warp per mode
 constexpr int RHO_KTILE = RHO_BLOCK * RHO_KPT;    // modes per block row (512)
@@ -116,9 +117,12 @@ __device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
   int4 m[2 * NP];
 #pragma unroll
   for (int t = 0; t < 2 * NP; t++) m[t] = kb + t < p.P ? p.km[kb + t] : make_int4(0, 0, 0, 0);
-  double re[2 * NP], im[2 * NP];
+  // the flushed partials' sums as unevaluated FP32 pairs hi + lo per mode
+  // (Knuth's TwoSum: hi + lo is the exact sum of the flushed partials up to
+  // the rounding of lo), two modes per packed register
+  unsigned long long shr[NP], slr[NP], shi[NP], sli[NP];
 #pragma unroll
-  for (int t = 0; t < 2 * NP; t++) re[t] = im[t] = 0.0;
+  for (int q = 0; q < NP; q++) shr[q] = slr[q] = shi[q] = sli[q] = 0ull;
   const int nch = (sub + RHO_MCHUNK - 1) / RHO_MCHUNK;   // the same for every group
   for (int c = 0; c < nch; c++) {
     const int64_t base = g0 + (int64_t)c * RHO_MCHUNK;
@@ -177,13 +181,23 @@ __device__ __forceinline__ void rho_mixed_body(const View &p, int bid) {
     }
 #pragma unroll
     for (int j = 0; j < NP; j++) {
-      float x0, x1, y0, y1;
-      up2(fr[j], x0, x1);
-      up2(fi[j], y0, y1);
-      re[2 * j] += (double)x0; re[2 * j + 1] += (double)x1;
-      im[2 * j] += (double)y0; im[2 * j + 1] += (double)y1;
+      two_sum2(shr[j], slr[j], fr[j]);
+      two_sum2(shi[j], sli[j], fi[j]);
     }
     }
+  }
+  double re[2 * NP], im[2 * NP];
+#pragma unroll
+  for (int j = 0; j < NP; j++) {
+    float h0, h1, l0, l1;
+    up2(shr[j], h0, h1);
+    up2(slr[j], l0, l1);
+    re[2 * j] = (double)h0 + (double)l0;
+    re[2 * j + 1] = (double)h1 + (double)l1;
+    up2(shi[j], h0, h1);
+    up2(sli[j], l0, l1);
+    im[2 * j] = (double)h0 + (double)l0;
+    im[2 * j + 1] = (double)h1 + (double)l1;
   }
   if (G > 1) {
     if (grp > 0)

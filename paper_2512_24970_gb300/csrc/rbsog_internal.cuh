@@ -370,6 +370,19 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return r;
 }
 
+// (hi, lo) += x lane by lane, hi + lo kept as an unevaluated sum: Knuth's
+// TwoSum gives the rounding error of hi + x exactly, which goes into lo.
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  return fma2(b, pk2(-1.0f, -1.0f), a);         // a - b, one rounding
+}
+__device__ __forceinline__ void two_sum2(unsigned long long &hi, unsigned long long &lo, unsigned long long x) {
+  const unsigned long long s = add2(hi, x);
+  const unsigned long long bp = sub2(s, hi);
+  const unsigned long long e = add2(sub2(hi, sub2(s, bp)), sub2(x, bp));
+  hi = s;
+  lo = add2(lo, e);
+}
+
 // sincos_turn of two phases at once: the FP32 steps in packed pairs, the
 // half-turn bookkeeping per lane; lane by lane the same results.
 __device__ __forceinline__ void sincos_turn2(uint32_t th0, uint32_t th1, unsigned long long &s2,

@@ -326,6 +326,8 @@ def test_bench_launch_configuration(rb, orc):
     g, o = ctx.debug_kept_lists(sel), S.lists_skin(sel, cap_a=64, cap_b=512)
     for k in keys:
         np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    check_batch_used(ctx, sel, o, cfg.P_R)           # read from B's 16-bit rows
+    assert ctx.debug_kept_b16()
     assert rms_rel(parts["near"][sel], S.near(sel)) < MIXED_TOL
 
 

@@ -208,20 +208,22 @@ def measured_peaks(rbsog, local):
 
 
 def profiled_traffic(stage, kept=False):
-    """DRAM bytes per launch of the stage's kernel from the committed ncu summary,
-    only while the kernel source is the one that was profiled (else None)."""
+    """DRAM bytes per launch of the stage's kernels (with kept lists the near
+    field is the batch draw and the pair sums) from the committed ncu summary,
+    only while the kernels' source is the one that was profiled (else None)."""
     import hashlib
     src = {"near": "k_near.cu", "rho": "k_far.cu", "farforce": "k_far.cu"}.get(stage)
-    name = "k_near_kept" if (stage == "near" and kept) else KERNEL_LABEL.get(stage)
+    names = ["k_sample_batch", "k_near_kept"] if (stage == "near" and kept) else [KERNEL_LABEL.get(stage)]
     summ = os.path.join(ROOT, "profiles", "traffic_nacl64k.txt")
     if src is None or not os.path.exists(summ):
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_24970_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+    found = {}
     for line in open(summ):
         f = line.split()
-        if len(f) >= 3 and f[0] == name and f[1] == h:
-            return float(f[2])
-    return None
+        if len(f) >= 3 and f[0] in names and f[1] == h:
+            found[f[0]] = float(f[2])
+    return sum(found.values()) if len(found) == len(names) else None
 
 
 def force_error(rbsog, w, prm, dev):
@@ -445,7 +447,8 @@ def run_ours(args):
     issue_peak = peak_ops["fp32"]
     label = dict(KERNEL_LABEL)
     if list_every != 0:
-        label["near"] = "k_near_kept (+ list builds by k_near, charged per build made in the timed steps)"
+        label["near"] = ("k_sample_batch + k_near_kept (+ list builds by k_near, charged per build made in the "
+                         "timed steps)")
     # every hot kernel against the FMA-pipe peak, from its own live events (the
     # near field on the main stream, k_rho and k_farforce on the side stream,
     # running concurrently, so a live duration includes time spent sharing

@@ -49,6 +49,7 @@ struct rbsog_ctx {
   bool own_stream = false;
   bool profiling = false;
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
+  cudaStream_t st2_hi = nullptr;                // the same at the device's greatest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
   int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
@@ -132,10 +133,12 @@ int run_force(rbsog_ctx *ctx, const View &v0, int mode, int step_off, bool energ
   View v = v0;                     // energy evaluations also carry the virial partials
   v.npart = energy ? rb::NEAR_NPART : 4;
   v.want_vir = energy ? 1 : 0;
-  // both branches at the same priority: measured on one box with kept lists,
-  // the far-field branch first was 0.7 % slower per step, the near-field
-  // branch first 10 % slower
-  cudaStream_t st = ctx->st, st2 = ctx->st2;
+  // the longer branch first (priorities are kept as node priorities in the
+  // graph).  FP64: the far field (its FP64 sines); measured on one box with
+  // kept lists, both branches at the same priority were 17 % slower per step.
+  // Mixed: the two branches are about as long; the far field first was 0.7 %
+  // slower than the same priority, the near field first 10 %.
+  cudaStream_t st = ctx->st, st2 = v.prec == RBSOG_FP64 ? ctx->st2_hi : ctx->st2;
   const bool pr = ctx->profiling;
   // inside stream capture the stage events must become event-record nodes
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -401,6 +404,9 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
   for (int k = 0; k < 12 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->prof[k]);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
+  int prio_least = 0, prio_greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->st2_hi, cudaStreamNonBlocking, prio_greatest);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork0, cudaEventDisableTiming);
@@ -417,6 +423,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   cudaSetDevice(ctx->dev);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   if (ctx->st2) cudaStreamSynchronize(ctx->st2);
+  if (ctx->st2_hi) cudaStreamSynchronize(ctx->st2_hi);
   free_system(ctx);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -426,6 +433,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_fork0) cudaEventDestroy(ctx->ev_fork0);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
+  if (ctx->st2_hi) cudaStreamDestroy(ctx->st2_hi);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
 }

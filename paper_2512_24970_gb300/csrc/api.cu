@@ -38,6 +38,8 @@ struct rbsog_ctx {
   cudaGraphExec_t gexec = nullptr;       // step graph (with kept lists: the build variant)
   cudaGraphExec_t gexec_keep = nullptr;  // kept lists: the variant that reuses them
   cudaGraph_t gstep = nullptr;           // the captured step graph behind gexec (ensemble child graphs)
+  cudaGraphExec_t geval[2] = {};         // force-only evaluation graphs, by the view's build flag
+  bool eval_ok[2] = {false, false};
   uint64_t graph_gen = 0;                // bumped at every capture
   bool graph_ok = false;
   bool lists_valid = false;              // kept lists built since the last set_system / set_state
@@ -80,7 +82,19 @@ int dalloc(rbsog_ctx *ctx, T **p, size_t count) {
   return RBSOG_OK;
 }
 
+// Every captured graph holds the context's view by value: any change of the
+// view (or of what run_force launches) drops them.
+void invalidate_graphs(rbsog_ctx *ctx) {
+  ctx->graph_ok = false;
+  ctx->eval_ok[0] = ctx->eval_ok[1] = false;
+}
+
 void free_system(rbsog_ctx *ctx) {
+  for (int k = 0; k < 2; k++) {
+    if (ctx->geval[k]) cudaGraphExecDestroy(ctx->geval[k]);
+    ctx->geval[k] = nullptr;
+    ctx->eval_ok[k] = false;
+  }
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->gexec_keep) cudaGraphExecDestroy(ctx->gexec_keep);
   if (ctx->gstep) cudaGraphDestroy(ctx->gstep);
@@ -88,7 +102,7 @@ void free_system(rbsog_ctx *ctx) {
   ctx->graph_gen++;
   ctx->gexec = nullptr;
   ctx->gexec_keep = nullptr;
-  ctx->graph_ok = false;
+  invalidate_graphs(ctx);
   ctx->lists_valid = false;
   ctx->origin_pending = false;
   ctx->x_origin = ctx->x_save = nullptr;
@@ -247,8 +261,10 @@ int import_aos(rbsog_ctx *ctx, const double *src, double *dst, int kind) {
   return check_launch(ctx);
 }
 
-// Copy an SoA FP64/FP32 array to the caller as [n][3] FP64.
-int export_aos(rbsog_ctx *ctx, const double *srcd, const float *srcf, double *dst, int kind) {
+// Copy an SoA FP64/FP32 array to the caller as [n][3] FP64.  A host copy is
+// complete on return unless sync is false (the caller then synchronizes the
+// stream before it returns, e.g. through read_err).
+int export_aos(rbsog_ctx *ctx, const double *srcd, const float *srcf, double *dst, int kind, bool sync = true) {
   const int64_t n = ctx->n;
   double *out = (kind == RBSOG_PTR_HOST) ? ctx->stage : dst;
   if (srcd) rb::launch_soa_to_aos_d(srcd, out, n, ctx->st);
@@ -257,7 +273,7 @@ int export_aos(rbsog_ctx *ctx, const double *srcd, const float *srcf, double *ds
   if (rc) return rc;
   if (kind == RBSOG_PTR_HOST) {
     CK(cudaMemcpyAsync(dst, ctx->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
+    if (sync) CK(cudaStreamSynchronize(ctx->st));
   }
   return RBSOG_OK;
 }
@@ -738,7 +754,7 @@ int rbsog_set_core_radii(rbsog_ctx *ctx, const double *r_core_pair) {
       }
     v.core_pair = 1;
   }
-  ctx->graph_ok = false;
+  invalidate_graphs(ctx);
   ctx->forces_valid = false;
   ctx->lists_valid = false;
   return RBSOG_OK;
@@ -765,12 +781,35 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
   if ((rc = enter(ctx))) return rc;
   View vv;
   if ((rc = eval_view(ctx, vv))) return rc;
-  if ((rc = run_force(ctx, vv, 0, 0, ev))) return rc;
+  if (ev) {
+    if ((rc = run_force(ctx, vv, 0, 0, true))) return rc;
+  } else {
+    // force-only evaluations replay a captured graph (one launch instead of a
+    // dozen kernel launches from the host)
+    const int key = vv.build ? 1 : 0;
+    if (!ctx->eval_ok[key]) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+      rc = run_force(ctx, vv, 0, 0, false);
+      cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      if (ctx->geval[key]) cudaGraphExecDestroy(ctx->geval[key]);
+      ctx->geval[key] = nullptr;
+      e = cudaGraphInstantiate(&ctx->geval[key], g, cudaGraphInstantiateFlagUseNodePriority);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      ctx->eval_ok[key] = true;
+    }
+    CK(cudaGraphLaunch(ctx->geval[key], ctx->st));
+  }
   ctx->forces_valid = true;
   ctx->lists_valid = true;
   if (forces) {
-    if (ctx->v.prec == RBSOG_FP64) rc = export_aos(ctx, ctx->v.Fd, nullptr, forces, ptr_kind);
-    else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind);
+    // host forces: the copy completes with read_err's synchronization below
+    const bool sync = !(ptr_kind == RBSOG_PTR_HOST && !ev);
+    if (ctx->v.prec == RBSOG_FP64) rc = export_aos(ctx, ctx->v.Fd, nullptr, forces, ptr_kind, sync);
+    else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind, sync);
     if (rc) return rc;
   }
   if (ev) {
@@ -1113,7 +1152,7 @@ int rbsog_debug_kept_b16(rbsog_ctx *ctx, int force_wide, int32_t *fits) {
   if ((rc = enter(ctx))) return rc;
   if (ctx->v.kept_wide != (force_wide != 0)) {
     ctx->v.kept_wide = force_wide != 0;
-    ctx->graph_ok = false;                      // the step graph holds the view by value
+    invalidate_graphs(ctx);                      // the step graph holds the view by value
   }
   if (fits) {
     int h = 1;
@@ -1173,7 +1212,7 @@ int rbsog_debug_set_kbatch(rbsog_ctx *ctx, int32_t P, const int32_t *m, const do
     ctx->Pmax = 0;
     if ((rc = ensure_kcap(ctx, v.P_F))) return rc;
   }
-  ctx->graph_ok = false;
+  invalidate_graphs(ctx);
   ctx->forces_valid = false;
   return leave(ctx);
 }
@@ -1202,7 +1241,7 @@ int rbsog_debug_set_whole_shell(rbsog_ctx *ctx, int flag) {
   if (!ctx) return RBSOG_E_INVAL;
   if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
   ctx->v.whole_shell = flag ? 1 : 0;
-  ctx->graph_ok = false;
+  invalidate_graphs(ctx);
   ctx->forces_valid = false;
   return RBSOG_OK;
 }
@@ -1278,7 +1317,7 @@ int rbsog_set_schedule(rbsog_ctx *ctx, const rbsog_schedule *sched) {
   set_rho_tiling(ctx, v.P);
   ctx->Pmax = 0;                               // tile partials for the new tiling
   if ((rc = ensure_kcap(ctx, std::max(v.P, v.P_F)))) return rc;
-  ctx->graph_ok = false;
+  invalidate_graphs(ctx);
   return leave(ctx);
 }
 
@@ -1292,7 +1331,7 @@ int rbsog_set_profiling(rbsog_ctx *ctx, int on) {
   if (!ctx) return RBSOG_E_INVAL;
   if (ctx->profiling != (on != 0)) {
     ctx->profiling = on != 0;
-    ctx->graph_ok = false;
+    invalidate_graphs(ctx);
   }
   return RBSOG_OK;
 }

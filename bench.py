@@ -8,7 +8,9 @@ One JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle on a
 bounded sample of the same workload instead (the reference arm).
 
 Timing: W warm-up steps, then K steps, each preceded by an L2 flush (a
-512 MiB memset, outside the timed interval) and timed with CUDA events on the
+512 MiB memset, then a read of 256 MiB so that the memset's dirty lines are
+written back before the step rather than inside it; both outside the timed
+interval) and timed with CUDA events on the
 stream the library runs on; per-stage times come from the event nodes the
 library records inside its step graph.  Multi-GPU (torchrun): every rank runs
 an independent replica (weak scaling, no collective on the data path); the
@@ -31,6 +33,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20
+L2_CLEAN_BYTES = 256 << 20
+L2_DESC = "flushed before every step (512 MiB memset, then a 256 MiB read that leaves L2 clean)"
+
+
+class L2Flush:
+    """Evicts the step's data from L2 (126 MB on GB300) before a timed step:
+    writes a buffer larger than L2, then reads another one larger than L2, so
+    that the lines the write left dirty are written back here and not by the
+    first kernels of the step."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        self.r = torch.zeros(L2_CLEAN_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        self.w.zero_()
+        self.r.sum()
 SFU_LANES_PER_SM = 16      # MUFU lanes per SM per clock (sin, cos, ex2, rsq ...)
 ISSUE_PER_SM = 4           # warp instructions per SM per clock (4 schedulers)
 
@@ -345,14 +364,14 @@ def run_ours(args):
                              integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
                              T=cfg.T, dt=0.001, gamma=1.0, list_every=list_every, skin=skin)
     stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(torch, dev)
     K, Wm = args.steps, args.warmup
     # the skin of automatically rebuilt kept lists: timed candidates (outside
     # the timed region), unless given
     tuning = None
     if list_every < 0 and args.skin is None and not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream, flush=flush.zero_)
+        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream, flush=flush)
         prm = dataclasses.replace(prm, skin=skin)
         tuning = {"chosen_skin": skin, "candidates": [{"skin": a, "ms_per_step": b, "list_builds": c}
                                                       for a, b, c in table],
@@ -364,7 +383,7 @@ def run_ours(args):
         sched = tuple(int(x) for x in args.schedule.split(","))
     elif prec == rbsog.MIXED and not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream, flush=flush.zero_)
+        sched, table = autotune.tune_schedule(w, prm, device=local, stream=stream, flush=flush)
         sched_tuning = {"chosen": dict(zip(("rho_variant", "rho_blocks_per_sm", "far_atoms_per_thread",
                                              "far_segments", "far_packed", "near_blocks_per_sm", "rho_tile_atoms", "near_wide",
                                              "rho_reduce"), sched)),
@@ -384,7 +403,7 @@ def run_ours(args):
             c.set_schedule(*sched)
         with torch.cuda.stream(stream):
             for _ in range(Wm):
-                flush.zero_()
+                flush()
                 c.step(1)
             torch.cuda.synchronize()
             if ws > 1:
@@ -395,7 +414,7 @@ def run_ours(args):
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
             torch.cuda.synchronize()
             for k in range(K):
-                flush.zero_()
+                flush()
                 ev[k][0].record(stream)
                 c.step(1)
                 ev[k][1].record(stream)
@@ -410,7 +429,7 @@ def run_ours(args):
             mk = np.zeros(rbsog.NMARK)
             c.set_profiling(True)
             for k in range(ks):
-                flush.zero_()
+                flush()
                 c.step(1)
                 st += c.stage_times()          # waits for this step's last event
                 mk += c.stage_marks()
@@ -593,7 +612,7 @@ def run_ours(args):
             "ms_per_step": t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
             "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
-                       "r_shell": 12.0, "precision": args.precision, "l2": "flushed before every step (512 MiB memset)",
+                       "r_shell": 12.0, "precision": args.precision, "l2": L2_DESC,
                        "lists": ("per step" if not list_every else
                                  ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in the "
                                   "%d timed steps)" % (prm.skin, builds_timed, K)) if list_every < 0 else
@@ -642,16 +661,16 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
         c = ens.add_workload(w, prm)
         c.set_velocities(w.vel)
         natoms += w.n
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(torch, dev)
     def timed(step_fn):
         with torch.cuda.stream(stream):
             for _ in range(Wm):
-                flush.zero_()
+                flush()
                 step_fn()
             torch.cuda.synchronize()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
             for k in range(K):
-                flush.zero_()
+                flush()
                 ev[k][0].record(stream)
                 step_fn()
                 ev[k][1].record(stream)
@@ -666,7 +685,7 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
         tuning = {"chosen": list(q), "how": "given (--schedule)"}
     elif not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        best, table = autotune.tune_ensemble_schedule(ens, stream=stream, flush=flush.zero_)
+        best, table = autotune.tune_ensemble_schedule(ens, stream=stream, flush=flush)
         tuning = {"chosen": {"schedule": list(best[0]), "groups": best[1]},
                   "candidates": [{"schedule": list(q), "groups": g, "ms_per_step": t} for (q, g), t in table],
                   "how": "20 ensemble steps per candidate after 3 warm-up, each after an L2 flush and timed alone, "
@@ -679,7 +698,7 @@ def ensemble_measure(args, K, Wm, with_sequential=True):
                        "T 1100-1300 K, P_F = 500, P_R = 20", "atoms": natoms,
            "lists": ("per step" if not list_every else
                      "kept, rebuilt when an atom has moved by skin/2; skin min(1 A, L/2 - r_shell)"),
-           "launch": ens.launch_kind(), "l2": "flushed before every step (512 MiB memset)",
+           "launch": ens.launch_kind(), "l2": L2_DESC,
            "schedule_tuning": tuning}
     # the same ensemble with every replica in one packed group, and as child
     # graphs (each replica's own step graph), beside the tuned plan

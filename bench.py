@@ -362,7 +362,7 @@ def run_ours(args):
     skin = (cfg.skin if args.skin is None else args.skin) if list_every != 0 else 0.0
     prm = rbsog.MethodParams(P_R=P_R, P_F=P_F, seed=replica_seed(cfg.seed, rank), precision=prec,
                              integrator=rbsog.LANGEVIN_BAOAB if cfg.integrator == "langevin" else rbsog.NVE_VV,
-                             T=cfg.T, dt=0.001, gamma=1.0, list_every=list_every, skin=skin)
+                             T=cfg.T, dt=0.001, gamma=cfg.gamma, list_every=list_every, skin=skin)
     stream = torch.cuda.Stream(device=dev)
     flush = L2Flush(torch, dev)
     K, Wm = args.steps, args.warmup
@@ -371,12 +371,17 @@ def run_ours(args):
     tuning = None
     if list_every < 0 and args.skin is None and not args.no_autotune:
         from paper_2512_24970_gb300 import autotune
-        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream, flush=flush)
+        # 500 steps per candidate at N = 64,000, fewer for larger systems (at
+        # least 100): at P_F = 1000 the N = 216,000 and 1,024,000 workloads
+        # heat up, or blow up, within a few hundred Langevin steps at 1/ps
+        skin_steps = max(100, int(500 * 64000 / w.n))
+        skin, table, rejected = autotune.tune_skin(w, prm, device=local, stream=stream, flush=flush,
+                                                   steps=skin_steps)
         prm = dataclasses.replace(prm, skin=skin)
         tuning = {"chosen_skin": skin, "candidates": [{"skin": a, "ms_per_step": b, "list_builds": c}
                                                       for a, b, c in table],
                   "rejected": [{"skin": a, "why": r} for a, r in rejected],
-                  "how": "500 steps per candidate after 20 warm-up, each after an L2 flush and timed alone with CUDA events (autotune.tune_skin)"}
+                  "how": "%d steps per candidate after 20 warm-up, each after an L2 flush and timed alone with CUDA events (autotune.tune_skin)" % skin_steps}
 
     sched, sched_tuning = None, None
     if args.schedule:
@@ -388,8 +393,9 @@ def run_ours(args):
                                              "far_segments", "far_packed", "near_blocks_per_sm", "rho_tile_atoms", "near_wide",
                                              "rho_reduce"), sched)),
                         "candidates": [{"schedule": list(q), "ms_per_step": t} for q, t in table],
-                        "how": "100 MD steps per candidate after 10 warm-up, each after an L2 flush and timed alone "
-                               "with CUDA events, coordinate search (autotune.tune_schedule)"}
+                        "how": "100 MD steps per candidate after 10 warm-up, every candidate from the same initial "
+                               "state, each step after an L2 flush and timed alone with CUDA events, coordinate "
+                               "search (autotune.tune_schedule)"}
 
     def timed_run(params, clocks=None, k_stage=None):
         """Wm untimed steps, then K steps timed with CUDA events on the
@@ -612,7 +618,7 @@ def run_ours(args):
             "ms_per_step": t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == rbsog.MIXED else "f64", "data": "synthetic",
             "config": {"workload": cfg.description, "N": w.n, "P_F": P_F, "P_R": P_R, "r_core": 6.0,
-                       "r_shell": 12.0, "precision": args.precision, "l2": L2_DESC,
+                       "r_shell": 12.0, "precision": args.precision, "langevin_gamma_per_ps": cfg.gamma, "l2": L2_DESC,
                        "lists": ("per step" if not list_every else
                                  ("kept: skin %.2f A, rebuilt when an atom has moved by skin/2 (%d builds in the "
                                   "%d timed steps)" % (prm.skin, builds_timed, K)) if list_every < 0 else

@@ -117,6 +117,16 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     ctx = rbsog.Context(device, st.cuda_stream)
     ctx.set_workload(w, params)
+    # every candidate starts from the same state: along one long trajectory
+    # later candidates would run a different (e.g. warmer) system, with more
+    # list rebuilds
+    x0, v0, s0 = ctx.get_state()
+
+    def run_candidate(q):
+        ctx.set_schedule(*q)
+        ctx.set_state(x0, v0, s0)
+        return timed_steps(ctx, st, warmup, steps, flush)
+
     table = []
     best = ctx.schedule()
     try:
@@ -124,8 +134,7 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
         for rv in RHO_VARIANTS:
             for bps in RHO_BLOCKS_PER_SM:
                 q = (rv, bps) + tuple(best[2:])
-                ctx.set_schedule(*q)
-                t = timed_steps(ctx, st, warmup, steps, flush)
+                t = run_candidate(q)
                 table.append((q, t))
                 if best_t is None or t < best_t:
                     best, best_t = q, t
@@ -136,8 +145,7 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
                     q = (timed[0], timed[1], A, S, pk) + tuple(timed[5:])
                     if q == timed:
                         continue
-                    ctx.set_schedule(*q)
-                    t = timed_steps(ctx, st, warmup, steps, flush)
+                    t = run_candidate(q)
                     table.append((q, t))
                     if t < best_t:
                         best, best_t = q, t
@@ -148,8 +156,7 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
                     q = tuple(timed[:5]) + (nb, timed[6], wide) + tuple(timed[8:])
                     if q == timed:
                         continue
-                    ctx.set_schedule(*q)
-                    t = timed_steps(ctx, st, warmup, steps, flush)
+                    t = run_candidate(q)
                     table.append((q, t))
                     if t < best_t:
                         best, best_t = q, t
@@ -158,8 +165,7 @@ def tune_schedule(w, params: "rbsog.MethodParams", device: int = 0, stream=None,
             q = tuple(timed[:8]) + (red,)
             if q == timed:
                 continue
-            ctx.set_schedule(*q)
-            t = timed_steps(ctx, st, warmup, steps, flush)
+            t = run_candidate(q)
             table.append((q, t))
             if t < best_t:
                 best, best_t = q, t

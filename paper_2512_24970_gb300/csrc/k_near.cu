@@ -809,8 +809,10 @@ __device__ __forceinline__ void near_body(const View &p, int step_off, int bid, 
           for (int i = 0; i < 4; i++)
             if (js[i] >= 0) add_pair<R, ENERGY>(p, spf, spd, sg4, swa, sw, sh2, spi, ui, uj[i], fs);
         }
-      } else if (take_all) {
-        // whole shell, weight 1: every shell member of the thread's rows
+      } else if (take_all && !over) {
+        // whole shell, weight 1: every shell member of the thread's rows (a
+        // chunk rejected for overlong rows has no shell bits: its rows may
+        // reach past gres; the overflow is reported through p.err)
         for (int r = g; r < nr; r += TPA) {
           const int ng = rgo[warp][r + 1] - rgo[warp][r];
           const int4 sg = rseg[warp][r];

@@ -156,6 +156,7 @@ class Config:
     integrator: str        # "nve" | "langevin"
     list_every: int = -1   # kept random batch lists, rebuilt when an atom has moved by skin/2 ...
     skin: float = 1.0      # ... with this skin [A]
+    gamma: float = 1.0     # Langevin friction [1/ps]
 
 
 CONFIGS = {

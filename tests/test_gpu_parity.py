@@ -96,6 +96,27 @@ def test_fp64_forces_and_energy(rb, orc, case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
+def test_fp64_force_only_fcorr(rb, orc, case):
+    """Force-only evaluations (every MD step) take F^corr from the near
+    field's 64-bit integer totals in units of 2^-40, energy evaluations from
+    k_corr's FP64 sum of the warp partials: both against the oracle, and
+    against each other to the fixed point's rounding (at most one 2^-41 per
+    warp partial, divided by N)."""
+    w = CASES[case]()
+    ctx, S = setup_pair(rb, orc, w, P_F=300, step=2)
+    F = ctx.compute_forces()
+    fc = ctx.debug_parts()["Fcorr"]
+    Fe, _ = ctx.compute_forces(energy=True)
+    fce = ctx.debug_parts()["Fcorr"]
+    o = S.forces()
+    assert rms_rel(F, o["F"]) < FP64_TOL
+    np.testing.assert_allclose(fc, o["Fcorr"], rtol=1e-9, atol=1e-12)
+    # at most N/4 warp partials (runs of 8 padded slots), one rounding of 2^-41 each
+    assert np.abs(fc - fce).max() < (w.n / 4) * 2.0 ** -41 / w.n + 1e-14
+    assert rms_rel(F, Fe) < 1e-13
+
+
+@pytest.mark.parametrize("case", list(CASES))
 def test_mixed_forces(rb, orc, case):
     w = CASES[case]()
     ctx, S = setup_pair(rb, orc, w, P_F=300, precision=rb.MIXED, step=4)

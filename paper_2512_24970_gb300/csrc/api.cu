@@ -53,6 +53,7 @@ struct rbsog_ctx {
   cudaStream_t st2 = nullptr;                   // side stream of the structure-factor branch
   cudaStream_t st2_hi = nullptr;                // the same at the device's greatest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr;
+  cudaEvent_t ev_copy = nullptr;                // rbsog_move_atoms: the host data has been read
   cudaEvent_t prof[12] = {};  // stage boundaries, see rbsog_get_stage_times
   int rho_bps = 2;            // mixed structure factor: resident blocks per SM the tiling aims at
   rbsog_schedule sched{0, 2, 2, 4, 1, 0, 0, 0, 0};  // far-field launch shapes (rbsog_set_schedule)
@@ -426,6 +427,7 @@ int rbsog_create(rbsog_ctx **out, int cuda_device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     rbsog_destroy(ctx);
     return RBSOG_E_CUDA;
@@ -448,6 +450,7 @@ void rbsog_destroy(rbsog_ctx *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_fork0) cudaEventDestroy(ctx->ev_fork0);
+  if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st2_hi) cudaStreamDestroy(ctx->st2_hi);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
@@ -896,10 +899,21 @@ int rbsog_move_atoms(rbsog_ctx *ctx, const double *pos, int64_t step, int ptr_ki
   if (step < 0) return fail(ctx, RBSOG_E_INVAL, "negative step");
   int rc;
   if ((rc = enter(ctx))) return rc;
-  if ((rc = import_aos(ctx, pos, ctx->v.x, ptr_kind))) return rc;
   long long s = step;
-  CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
-  if (ptr_kind == RBSOG_PTR_HOST) CK(cudaStreamSynchronize(ctx->st));   // s and the staging buffer
+  if (ptr_kind == RBSOG_PTR_HOST) {
+    // the caller's positions and s are read by the copies; the return waits
+    // for those only, the layout conversion runs on while the caller goes on
+    CK(cudaMemcpyAsync(ctx->stage, pos, sizeof(double) * 3 * (size_t)ctx->n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaEventRecord(ctx->ev_copy, ctx->st));
+    rb::launch_aos_to_soa(ctx->stage, ctx->v.x, ctx->n, ctx->st);
+    if ((rc = check_launch(ctx))) return rc;
+    CK(cudaEventSynchronize(ctx->ev_copy));
+  } else {
+    if ((rc = import_aos(ctx, pos, ctx->v.x, ptr_kind))) return rc;
+    CK(cudaMemcpyAsync(ctx->v.step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));          // s is on this stack
+  }
   ctx->forces_valid = false;                   // the kept lists stay; the next evaluation checks them
   ctx->host_step = step;
   return leave(ctx);

@@ -430,3 +430,37 @@ def test_move_atoms_keeps_lists(rb, orc, precision):
     assert ctx.list_builds() == b0 + 1
     S.pos, S.step, S.build_pos = big, 6, big.copy()
     assert rms_rel(Fg, S.forces()["F"]) < tol
+
+
+def test_pinned_host_buffers(rb, orc):
+    """Positions handed over and forces read back through page-locked host
+    buffers (asynchronous copies; rbsog_move_atoms returns once its copies
+    have read the caller's data) give the same forces, bit for bit, as
+    pageable buffers, and the positions buffer may be overwritten as soon as
+    rbsog_move_atoms returns."""
+    torch = pytest.importorskip("torch")
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    out = []
+    for pinned in (False, True):
+        ctx, S = setup_kept(rb, orc, w, skin=1.0, list_every=-1, P_F=100, precision=rb.MIXED)
+        ctx.compute_forces()
+        rng = np.random.default_rng(2)
+        if pinned:
+            pos = torch.empty(w.pos.shape, dtype=torch.float64, pin_memory=True).numpy()
+            frc = torch.empty(w.pos.shape, dtype=torch.float64, pin_memory=True).numpy()
+        else:
+            pos = np.empty_like(w.pos)
+            frc = np.empty_like(w.pos)
+        res = []
+        for k in range(3):
+            pos[:] = w.pos + rng.uniform(-0.2, 0.2, w.pos.shape)
+            before = pos.copy()
+            ctx.move_atoms(pos, 5 + k)
+            pos[:] = np.nan                                   # reused at once: the call has read it
+            ctx.compute_forces(frc)
+            res.append(frc.copy())
+            np.testing.assert_array_equal(ctx.get_state()[0], before)
+        out.append(res)
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)

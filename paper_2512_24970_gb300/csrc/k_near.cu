@@ -1032,17 +1032,31 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   // number of resident blocks) takes the runs in a grid-stride loop
   for (int wc = bid * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += nbk * NEAR_WARPS) {
   const int slot = wc * APW + lane / TPA;
-  const uint4 ui = slot < nslot ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const bool inrange = slot < nslot;
+  const int PR = p.P_R;
+  // the slot record, the counts, the batch row and the first round of A's
+  // row are all issued at once: the rows' addresses depend on the slot only
+  // (rows of the last build, valid memory for every slot), the counts mask
+  // them below
+  const uint4 ui = inrange ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const int2 nab0 = inrange ? p.nAB[slot] : make_int2(0, 0);
+  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
+  int jbs[KB], ja0[4];
+#pragma unroll
+  for (int i = 0; i < KB; i++) {
+    const int k = g + TPA * i;
+    jbs[i] = (inrange && k < PR) ? __ldg(p.bsel + (int64_t)max(slot, 0) * PR + k) : -1;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) ja0[i] = inrange ? __ldg(la + g + TPA * i) : -1;
   const bool active = ui.w != SU_PAD;
-  const int2 nab = active ? p.nAB[slot] : make_int2(0, 0);
+  const int2 nab = active ? nab0 : make_int2(0, 0);
   const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
   double part[NEAR_NPART] = {};
   Acc<R> fa, fb;
   // ---- the batch (drawn by k_sample_batch) or all of B ----------------------
-  const int nB = nab.y, PR = p.P_R;
+  const int nB = nab.y;
   const bool sampled = active && !p.whole_shell && nB > PR;
-  // ---- the batch's list entries, loaded before A's pairs so that their
-  // latency overlaps that work -----------------------------------------------
   const R wgt = sampled ? (R)nB / (R)PR : (R)1;
   const int *lb = sampled ? p.bsel + (int64_t)max(slot, 0) * PR : p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
   const int nb = sampled ? PR : nB;
@@ -1050,12 +1064,11 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
 #pragma unroll
   for (int i = 0; i < KB; i++) {
     const int k = g + TPA * i;
-    jb[i] = k < nb ? lb[k] : -1;
+    jb[i] = sampled ? jbs[i] : (k < nb ? lb[k] : -1);
   }
   // ---- A, exactly, dealt round-robin over the atom's threads; the
   // indicator r < r_shell is 1 for every member of A when r_core + skin lies
   // well inside r_shell (no atom moves by more than skin/2 between builds) -----
-  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
   const bool acheck = !p.a_inside;
   int a_from = g, b_from = 0;                    // where the loops below start
   if (WIDE) {
@@ -1094,7 +1107,10 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   for (int e0 = a_from; e0 < nab.x; e0 += 4 * TPA) {
     int js[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++) js[i] = (e0 + TPA * i < nab.x) ? la[e0 + TPA * i] : -1;
+    for (int i = 0; i < 4; i++) {
+      const int e = e0 + TPA * i;
+      js[i] = e < nab.x ? ((!WIDE && e0 == g) ? ja0[i] : la[e]) : -1;   // the first round was issued above
+    }
     uint4 uj[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) uj[i] = p.su[max(js[i], 0)];
@@ -1130,8 +1146,10 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   }
 }
 
+// FP32 pair math: registers bounded for 7 resident blocks per SM (64 in the
+// default form, no spills); FP64: 4 (its pair terms need more registers)
 template <typename R, bool ENERGY, bool WIDE, bool CAPPED>
-__global__ void __launch_bounds__(NEAR_BLOCK, 4) k_near_kept(View p, int step_off) {
+__global__ void __launch_bounds__(NEAR_BLOCK, sizeof(R) == 4 ? 7 : 4) k_near_kept(View p, int step_off) {
   near_kept_body<R, ENERGY, WIDE, CAPPED>(p, step_off, blockIdx.x, gridDim.x);
 }
 template <bool WIDE>

@@ -940,9 +940,15 @@ __device__ __forceinline__ void sample_batch_body(const View &p, int step_off, i
   const long long s = *p.step + step_off;
   const int nslot = p.cell_start[p.ncell];
   const int slot = (bid * NEAR_WARPS + warp) * APW + lane / TPA;
-  const uint32_t w = slot < nslot ? p.su[slot].w : SU_PAD;
+  // the slot record and the counts are read for any slot within the slot
+  // buffers' capacity, together with the slot count that masks them (three
+  // loads in flight instead of one after another)
+  const bool cap = slot < p.nslot;
+  const uint32_t w0 = cap ? p.su[slot].w : SU_PAD;
+  const int nB0 = cap ? p.nAB[slot].y : 0;
+  const uint32_t w = slot < nslot ? w0 : SU_PAD;
   const bool active = w != SU_PAD;
-  const int nB = active ? p.nAB[slot].y : 0, PR = p.P_R;
+  const int nB = active ? nB0 : 0, PR = p.P_R;
   const bool sampled = active && !p.whole_shell && nB > PR;
   const bool b16 = !p.kept_wide && *p.b16_over == 0;   // every offset of the last build fits 16 bits
   if (sampled) {
@@ -1026,29 +1032,35 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
     const float4 *src = reinterpret_cast<const float4 *>(p.pf);
     for (int e = tid; e < 3 * p.ns * p.ns; e += NEAR_BLOCK) spf4[e] = __ldg(src + e);
   }
-  __syncthreads();                               // the pair table
   const int nslot = p.cell_start[p.ncell];
+  const int PR = p.P_R;
+  bool first = true;
   // one warp per run of APW slots; a grid smaller than nblk_near (a capped
-  // number of resident blocks) takes the runs in a grid-stride loop
+  // number of resident blocks) takes the runs in a grid-stride loop (every
+  // warp of a block makes the same number of passes, at least one)
   for (int wc = bid * NEAR_WARPS + warp; wc < p.nblk_near * NEAR_WARPS; wc += nbk * NEAR_WARPS) {
   const int slot = wc * APW + lane / TPA;
   const bool inrange = slot < nslot;
-  const int PR = p.P_R;
   // the slot record, the counts, the batch row and the first round of A's
-  // row are all issued at once: the rows' addresses depend on the slot only
-  // (rows of the last build, valid memory for every slot), the counts mask
-  // them below
-  const uint4 ui = inrange ? p.su[slot] : make_uint4(0u, 0u, 0u, SU_PAD);
-  const int2 nab0 = inrange ? p.nAB[slot] : make_int2(0, 0);
-  const int *la = p.lA + (int64_t)max(slot, 0) * RBSOG_MAX_CORE;
+  // row are all issued at once, for any slot within the slot buffers'
+  // capacity (rows of the last build, valid memory): the slot count and
+  // the counts mask them below
+  const bool cap = slot < p.nslot;
+  const int cs = cap ? slot : 0;
+  const uint4 ui0 = cap ? p.su[cs] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const int2 nab0 = cap ? p.nAB[cs] : make_int2(0, 0);
+  const int *la = p.lA + (int64_t)cs * RBSOG_MAX_CORE;
   int jbs[KB], ja0[4];
 #pragma unroll
   for (int i = 0; i < KB; i++) {
     const int k = g + TPA * i;
-    jbs[i] = (inrange && k < PR) ? __ldg(p.bsel + (int64_t)max(slot, 0) * PR + k) : -1;
+    jbs[i] = (cap && k < PR) ? __ldg(p.bsel + (int64_t)cs * PR + k) : -1;
   }
 #pragma unroll
-  for (int i = 0; i < 4; i++) ja0[i] = inrange ? __ldg(la + g + TPA * i) : -1;
+  for (int i = 0; i < 4; i++) ja0[i] = cap ? __ldg(la + g + TPA * i) : -1;
+  if (MIX && first) __syncthreads();             // the pair table (these loads in flight meanwhile)
+  first = false;
+  const uint4 ui = inrange ? ui0 : make_uint4(0u, 0u, 0u, SU_PAD);
   const bool active = ui.w != SU_PAD;
   const int2 nab = active ? nab0 : make_int2(0, 0);
   const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;
@@ -1058,7 +1070,7 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   const int nB = nab.y;
   const bool sampled = active && !p.whole_shell && nB > PR;
   const R wgt = sampled ? (R)nB / (R)PR : (R)1;
-  const int *lb = sampled ? p.bsel + (int64_t)max(slot, 0) * PR : p.lB + (int64_t)max(slot, 0) * RBSOG_MAX_KEPT;
+  const int *lb = sampled ? p.bsel + (int64_t)cs * PR : p.lB + (int64_t)cs * RBSOG_MAX_KEPT;
   const int nb = sampled ? PR : nB;
   int jb[KB];
 #pragma unroll

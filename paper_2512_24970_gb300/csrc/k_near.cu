@@ -1028,11 +1028,11 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane % TPA;
   (void)step_off;                                // the batch of this step is drawn by k_sample_batch
+  const int nslot = p.cell_start[p.ncell];       // in flight while the pair table is staged
   if (MIX) {
     const float4 *src = reinterpret_cast<const float4 *>(p.pf);
     for (int e = tid; e < 3 * p.ns * p.ns; e += NEAR_BLOCK) spf4[e] = __ldg(src + e);
   }
-  const int nslot = p.cell_start[p.ncell];
   const int PR = p.P_R;
   bool first = true;
   // one warp per run of APW slots; a grid smaller than nblk_near (a capped
@@ -1042,25 +1042,23 @@ __device__ __forceinline__ void near_kept_body(const View &p, int step_off, int 
   const int slot = wc * APW + lane / TPA;
   const bool inrange = slot < nslot;
   // the slot record, the counts, the batch row and the first round of A's
-  // row are all issued at once, for any slot within the slot buffers'
-  // capacity (rows of the last build, valid memory): the slot count and
-  // the counts mask them below
-  const bool cap = slot < p.nslot;
-  const int cs = cap ? slot : 0;
-  const uint4 ui0 = cap ? p.su[cs] : make_uint4(0u, 0u, 0u, SU_PAD);
-  const int2 nab0 = cap ? p.nAB[cs] : make_int2(0, 0);
+  // row are all issued at once (the rows' addresses depend on the slot only:
+  // rows of the last build, valid memory for every slot); the counts mask
+  // them below
+  const int cs = inrange ? slot : 0;
+  const uint4 ui = inrange ? p.su[cs] : make_uint4(0u, 0u, 0u, SU_PAD);
+  const int2 nab0 = inrange ? p.nAB[cs] : make_int2(0, 0);
   const int *la = p.lA + (int64_t)cs * RBSOG_MAX_CORE;
   int jbs[KB], ja0[4];
 #pragma unroll
   for (int i = 0; i < KB; i++) {
     const int k = g + TPA * i;
-    jbs[i] = (cap && k < PR) ? __ldg(p.bsel + (int64_t)cs * PR + k) : -1;
+    jbs[i] = (inrange && k < PR) ? __ldg(p.bsel + (int64_t)cs * PR + k) : -1;
   }
 #pragma unroll
-  for (int i = 0; i < 4; i++) ja0[i] = cap ? __ldg(la + g + TPA * i) : -1;
+  for (int i = 0; i < 4; i++) ja0[i] = inrange ? __ldg(la + g + TPA * i) : -1;
   if (MIX && first) __syncthreads();             // the pair table (these loads in flight meanwhile)
   first = false;
-  const uint4 ui = inrange ? ui0 : make_uint4(0u, 0u, 0u, SU_PAD);
   const bool active = ui.w != SU_PAD;
   const int2 nab = active ? nab0 : make_int2(0, 0);
   const int spi = active ? (int)(ui.w >> SU_SP_SHIFT) : 0;

@@ -565,23 +565,22 @@ def run_ours(args):
                 ctx.get_state(pos=traj[k])
             ctx.set_state(p0, v0s, s0)
             for k in range(3):
-                ctx.move_atoms(traj[k], s0 + 1 + k)
-                ctx.compute_forces(frc_h)
+                ctx.forces_at(traj[k], s0 + 1 + k, frc_h)
             ctx.set_state(p0, v0s, s0)
             ctx.compute_forces(frc_h)
             b0 = ctx.list_builds()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(Ke):
-                ctx.move_atoms(traj[k], s0 + 1 + k)     # H2D positions (pinned)
-                ctx.compute_forces(frc_h)               # force evaluation, D2H forces (pinned)
+                # H2D positions (pinned), force evaluation, D2H forces (pinned)
+                ctx.forces_at(traj[k], s0 + 1 + k, frc_h)
             torch.cuda.synchronize()
             te = time.perf_counter() - t0
             nb = ctx.list_builds() - b0
         e2e = {"value": w.n * Ke / te, "unit": "atom-steps/s", "h2d_bytes_per_step": 24 * w.n,
                "d2h_bytes_per_step": 24 * w.n,
-               "what": "rbsog_move_atoms(host positions of %d recorded steps of this run) + "
-                       "rbsog_compute_forces(host forces) per step%s" %
+               "what": "rbsog_forces_at(host positions of %d recorded steps of this run, host forces) "
+                       "per step, i.e. rbsog_move_atoms + rbsog_compute_forces in one call%s" %
                        (Ke, "; kept lists rebuilt by the device check: %d builds" % nb if list_every != 0 else "")}
     # ---- mixed vs FP64 force error on identical state and samples ---------------
     ferr = None

@@ -228,6 +228,24 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *pos, const double *vel, int64_
  * RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL, RBSOG_E_CUDA. */
 int rbsog_move_atoms(rbsog_ctx *ctx, const double *pos, int64_t step, int ptr_kind);
 
+/* Forces at given positions in one call: rbsog_move_atoms(pos, step) followed
+ * by the force-only rbsog_compute_forces(forces), with the same results bit
+ * for bit (Eqs. (Fshort), (long-rangeforce) and F^corr of Sec. 2.2, drawn
+ * with RNG step index step).  For a caller that integrates on its side (an
+ * external MD engine) and hands over positions and reads forces every step:
+ * the positions' copy, the layout conversions, the evaluation graph and the
+ * forces' copy are enqueued together and the host waits once.
+ *   pos    [n][3] FP64 [A], caller order (read)
+ *   forces [n][3] FP64 [eV/A] (written)
+ * ptr_kind: host (both pointers host memory; synchronous: both buffers may be
+ * reused on return) or device (both device memory of the context's device;
+ * asynchronous on the caller's stream, pos read and forces written in stream
+ * order).  Errors: RBSOG_E_NO_SYSTEM, RBSOG_E_INVAL (null pointer, step < 0,
+ * unknown ptr_kind), RBSOG_E_SKIN and RBSOG_E_CAP_OVERFLOW (host pointers; with
+ * device pointers they are reported by the next synchronizing call, e.g.
+ * rbsog_sync), RBSOG_E_CUDA. */
+int rbsog_forces_at(rbsog_ctx *ctx, const double *pos, int64_t step, double *forces, int ptr_kind);
+
 /* Kept lists (list_every != 0): the positions [n][3] FP64 [A] of the last
  * build of the lists the next evaluation uses, caller order.  Errors:
  * RBSOG_E_INVAL without kept lists or before the first evaluation. */

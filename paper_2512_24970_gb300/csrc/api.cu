@@ -775,6 +775,29 @@ int rbsog_set_velocities(rbsog_ctx *ctx, const double *vel, int ptr_kind) {
   return leave(ctx);
 }
 
+// A force-only evaluation: replays a captured graph (one launch instead of a
+// dozen kernel launches from the host), captured on first use.
+static int eval_forces_graph(rbsog_ctx *ctx, const View &vv) {
+  int rc;
+  const int key = vv.build ? 1 : 0;
+  if (!ctx->eval_ok[key]) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    rc = run_force(ctx, vv, 0, 0, false);
+    cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (ctx->geval[key]) cudaGraphExecDestroy(ctx->geval[key]);
+    ctx->geval[key] = nullptr;
+    e = cudaGraphInstantiate(&ctx->geval[key], g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->eval_ok[key] = true;
+  }
+  CK(cudaGraphLaunch(ctx->geval[key], ctx->st));
+  return RBSOG_OK;
+}
+
 int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double *virial,
                          int ptr_kind) {
   if (!ctx) return RBSOG_E_INVAL;
@@ -787,24 +810,7 @@ int rbsog_compute_forces(rbsog_ctx *ctx, double *forces, double *energy, double 
   if (ev) {
     if ((rc = run_force(ctx, vv, 0, 0, true))) return rc;
   } else {
-    // force-only evaluations replay a captured graph (one launch instead of a
-    // dozen kernel launches from the host)
-    const int key = vv.build ? 1 : 0;
-    if (!ctx->eval_ok[key]) {
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-      rc = run_force(ctx, vv, 0, 0, false);
-      cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
-      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      if (ctx->geval[key]) cudaGraphExecDestroy(ctx->geval[key]);
-      ctx->geval[key] = nullptr;
-      e = cudaGraphInstantiate(&ctx->geval[key], g, cudaGraphInstantiateFlagUseNodePriority);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(ctx, RBSOG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-      ctx->eval_ok[key] = true;
-    }
-    CK(cudaGraphLaunch(ctx->geval[key], ctx->st));
+    if ((rc = eval_forces_graph(ctx, vv))) return rc;
   }
   ctx->forces_valid = true;
   ctx->lists_valid = true;
@@ -916,6 +922,36 @@ int rbsog_move_atoms(rbsog_ctx *ctx, const double *pos, int64_t step, int ptr_ki
   }
   ctx->forces_valid = false;                   // the kept lists stay; the next evaluation checks them
   ctx->host_step = step;
+  return leave(ctx);
+}
+
+int rbsog_forces_at(rbsog_ctx *ctx, const double *pos, int64_t step, double *forces, int ptr_kind) {
+  if (!ctx || !pos || !forces) return RBSOG_E_INVAL;
+  if (!ctx->has_system) return fail(ctx, RBSOG_E_NO_SYSTEM, "no system");
+  if (step < 0) return fail(ctx, RBSOG_E_INVAL, "negative step");
+  if (ptr_kind != RBSOG_PTR_HOST && ptr_kind != RBSOG_PTR_DEVICE) return fail(ctx, RBSOG_E_INVAL, "bad ptr_kind");
+  int rc;
+  if ((rc = enter(ctx))) return rc;
+  // the positions (through the staging buffer for host memory) and the step
+  // counter, as rbsog_move_atoms; nothing waits here: for host buffers the
+  // single synchronization at the end covers both copies
+  const bool host = ptr_kind == RBSOG_PTR_HOST;
+  if (host)
+    CK(cudaMemcpyAsync(ctx->stage, pos, sizeof(double) * 3 * (size_t)ctx->n, cudaMemcpyHostToDevice, ctx->st));
+  rb::launch_aos_to_soa_step(host ? ctx->stage : pos, ctx->v.x, ctx->n, ctx->v.step, (long long)step, ctx->st);
+  if ((rc = check_launch(ctx))) return rc;
+  ctx->forces_valid = false;
+  ctx->host_step = step;
+  // the force-only evaluation of rbsog_compute_forces
+  View vv;
+  if ((rc = eval_view(ctx, vv))) return rc;
+  if ((rc = eval_forces_graph(ctx, vv))) return rc;
+  ctx->forces_valid = true;
+  ctx->lists_valid = true;
+  if (ctx->v.prec == RBSOG_FP64) rc = export_aos(ctx, ctx->v.Fd, nullptr, forces, ptr_kind, false);
+  else rc = export_aos(ctx, nullptr, ctx->v.Ff, forces, ptr_kind, false);
+  if (rc) return rc;
+  if (host && (rc = read_err(ctx))) return rc;   // synchronizes the stream
   return leave(ctx);
 }
 

@@ -412,6 +412,18 @@ __global__ void k_soa_to_aos(const T *soa, double *aos, int64_t n) {
 void launch_aos_to_soa(const double *aos, double *soa, int64_t n, cudaStream_t st) {
   k_aos_to_soa<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(aos, soa, n);
 }
+// The same conversion of new positions, which also sets the step counter
+// (a kernel argument instead of a copy from host memory).
+__global__ void k_aos_to_soa_step(const double *aos, double *soa, int64_t n, long long *step, long long s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *step = s;
+  if (i >= n) return;
+  for (int a = 0; a < 3; a++) soa[a * n + i] = aos[3 * i + a];
+}
+void launch_aos_to_soa_step(const double *aos, double *soa, int64_t n, long long *step, long long s,
+                            cudaStream_t st) {
+  k_aos_to_soa_step<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(aos, soa, n, step, s);
+}
 void launch_soa_to_aos_d(const double *soa, double *aos, int64_t n, cudaStream_t st) {
   k_soa_to_aos<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(soa, aos, n);
 }

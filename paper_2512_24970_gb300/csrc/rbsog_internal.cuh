@@ -596,6 +596,8 @@ constexpr int SF_STATIC_MAX_DEVICES = 64;
 cudaError_t sf_static_scratch(int dev, void **out);
 void launch_sf_static(const View &v, int P, const int *m, double *rho, void *scratch, cudaStream_t st);
 void launch_aos_to_soa(const double *aos, double *soa, int64_t n, cudaStream_t st);
+void launch_aos_to_soa_step(const double *aos, double *soa, int64_t n, long long *step, long long s,
+                            cudaStream_t st);
 void launch_soa_to_aos_d(const double *soa, double *aos, int64_t n, cudaStream_t st);
 void launch_soa_to_aos_f(const float *soa, double *aos, int64_t n, cudaStream_t st);
 

@@ -39,7 +39,7 @@ EXPORTS = [
     "rbsog_create", "rbsog_destroy", "rbsog_set_system", "rbsog_set_velocities",
     "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_set_state", "rbsog_sync",
     "rbsog_get_sog", "rbsog_set_core_radii", "rbsog_get_list_builds", "rbsog_get_thermostat", "rbsog_set_thermostat", "rbsog_get_kinetic_tensor",
-    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_move_atoms", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kept_batch_used", "rbsog_debug_kept_b16", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
+    "rbsog_get_list_origin", "rbsog_set_list_origin", "rbsog_move_atoms", "rbsog_forces_at", "rbsog_debug_get_lists", "rbsog_debug_get_kept_lists", "rbsog_debug_get_kept_batch_used", "rbsog_debug_kept_b16", "rbsog_debug_get_kbatch", "rbsog_debug_set_kbatch",
     "rbsog_debug_get_parts", "rbsog_debug_set_whole_shell", "rbsog_debug_sincos", "rbsog_set_profiling",
     "rbsog_get_stage_times", "rbsog_get_stage_marks", "rbsog_last_error", "rbsog_structure_factor_static",
     "rbsog_ensemble_create", "rbsog_ensemble_destroy", "rbsog_ensemble_add", "rbsog_ensemble_replica",
@@ -157,6 +157,7 @@ def load():
     L.rbsog_get_kinetic_tensor.argtypes = [P, P, I]
     L.rbsog_get_list_origin.argtypes = [P, P, I]
     L.rbsog_move_atoms.argtypes = [P, P, I64, I]
+    L.rbsog_forces_at.argtypes = [P, P, I64, P, I]
     L.rbsog_set_list_origin.argtypes = [P, P, I]
     L.rbsog_set_thermostat.argtypes = [P, P, P]
     L.rbsog_debug_get_lists.argtypes = [P, P, I64, I32, I32, P, P, P, P, P, P, P]
@@ -338,6 +339,27 @@ class Context:
             pos = np.ascontiguousarray(pos, dtype=np.float64)
         pp, kind = _ptr_kind(pos)
         self._ck(self._L.rbsog_move_atoms(self.h, pp, int(step), kind))
+
+    def forces_at(self, pos, step, forces=None):
+        """move_atoms(pos, step) and the force-only compute_forces in one call
+        (one synchronization for host arrays): forces [n, 3] FP64 at the
+        positions pos [n, 3].  pos and forces both numpy (host) or both CUDA
+        tensors of this context's device (asynchronous on its stream)."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
+        out = np.zeros((self.n, 3)) if forces is None else forces
+        for a in (pos, out):
+            n3 = a.size if isinstance(a, np.ndarray) else a.numel()
+            f64 = a.dtype == np.float64 if isinstance(a, np.ndarray) else str(a.dtype) == "torch.float64"
+            contig = a.flags["C_CONTIGUOUS"] if isinstance(a, np.ndarray) else a.is_contiguous()
+            if n3 != 3 * self.n or not f64 or not contig:
+                raise ValueError("pos and forces must be contiguous float64 arrays of shape [n, 3]")
+        pp, kind = _ptr_kind(pos)
+        fp, fkind = _ptr_kind(out)
+        if fkind != kind:
+            raise ValueError("pos and forces must both be host arrays or both device tensors")
+        self._ck(self._L.rbsog_forces_at(self.h, pp, int(step), fp, kind))
+        return out
 
     def list_origin(self):
         """Kept lists: the positions [n, 3] of their last build (with get_state, what a restore needs)."""

@@ -464,3 +464,56 @@ def test_pinned_host_buffers(rb, orc):
         ctx.close()
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_forces_at_matches_move_and_compute(rb, orc, precision):
+    """rbsog_forces_at (positions in, forces out, one call) gives the forces of
+    rbsog_move_atoms followed by rbsog_compute_forces bit for bit, with
+    pageable and page-locked host arrays and with device tensors, through a
+    move below skin/2 (the last build's lists kept), one past it (rebuilt on
+    the device) and one more; the first equals the oracle's kept-list forces."""
+    torch = pytest.importorskip("torch")
+    w = W.rock_salt((6, 6, 6), seed=4, composition="LiCl")
+    prec = rb.FP64 if precision == "fp64" else rb.MIXED
+    tol = 1e-12 if precision == "fp64" else MIXED_TOL
+    rng = np.random.default_rng(3)
+    small = w.pos + rng.uniform(-0.2, 0.2, w.pos.shape)      # every atom within 0.35 A < skin/2
+    big = small.copy()
+    big[0] += 0.8                                             # one atom past skin/2
+    moves = [(small, 5), (big, 6), (big + rng.uniform(-0.1, 0.1, w.pos.shape), 7)]
+    ctx, S = setup_kept(rb, orc, w, skin=1.0, list_every=-1, P_F=100, precision=prec)
+    ctx.compute_forces()
+    b0 = ctx.list_builds()
+    ref = []
+    for pos, s in moves:
+        ctx.move_atoms(pos, s)
+        ref.append(ctx.compute_forces().copy())
+    builds = ctx.list_builds() - b0
+    ctx.close()
+    assert builds == 1
+    for form in ("pageable", "pinned", "device"):
+        ctx, _ = setup_kept(rb, orc, w, skin=1.0, list_every=-1, P_F=100, precision=prec)
+        ctx.compute_forces()
+        b0 = ctx.list_builds()
+        for (pos, s), F0 in zip(moves, ref):
+            if form == "pageable":
+                F = ctx.forces_at(pos, s)
+            elif form == "pinned":
+                ph = torch.empty(pos.shape, dtype=torch.float64, pin_memory=True).numpy()
+                fh = torch.empty(pos.shape, dtype=torch.float64, pin_memory=True).numpy()
+                ph[:] = pos
+                F = ctx.forces_at(ph, s, fh).copy()
+            else:
+                pd = torch.tensor(pos, dtype=torch.float64, device="cuda:0")
+                fd = torch.empty(pos.shape, dtype=torch.float64, device="cuda:0")
+                ctx.forces_at(pd, s, fd)
+                ctx.sync()
+                F = fd.cpu().numpy()
+            np.testing.assert_array_equal(F, F0)
+        assert ctx.list_builds() - b0 == builds
+        with pytest.raises(ValueError):
+            ctx.forces_at(moves[0][0], 5, torch.empty(w.pos.shape, dtype=torch.float64, device="cuda:0"))
+        ctx.close()
+    S.pos, S.step, S.build_pos = small, 5, w.pos.copy()
+    assert rms_rel(ref[0], S.forces()["F"]) < tol

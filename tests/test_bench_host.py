@@ -1,6 +1,6 @@
 """Host logic of the benchmark's measurement, on the CPU: the clock record
-taken during the timed region, the algorithmic work model and the lookup of
-profiled DRAM bytes by source hash (no GPU)."""
+taken during the timed region, the algorithmic work model, the lookup of
+profiled DRAM bytes by source hash and the reference arm's line (no GPU)."""
 import hashlib
 import os
 import shutil
@@ -98,3 +98,32 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench.profiled_traffic("near", kept=True) is None
     assert bench.profiled_traffic("rho") is None
     assert bench.profiled_traffic("unknown") is None
+
+
+def test_reference_arm_line(monkeypatch, capsys, orc):
+    """The reference arm times the oracle on the host cores and prints one
+    line with the same metric as the GPU arm, its own cpu_baseline and an
+    end-to-end figure without copies (a short sample per step here)."""
+    import argparse
+    import json
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda w, cfg, P_F, P_R, budget_s=15.0: real(w, cfg, P_F, P_R, budget_s=0.2))
+    monkeypatch.delenv("RANK", raising=False)
+    args = argparse.Namespace(config="nacl_1k", P_F=None, P_R=None, steps=2, warmup=1, gpus=1)
+    bench.run_reference(args)
+    out = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "atom-steps/s" and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["value"] > 0
+    assert line["ms_per_step"] == pytest.approx(1000.0 * 1000 / line["value"])
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    # other ranks of a multi-process launch print nothing
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
